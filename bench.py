@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Loop-chain benchmark on one GB300: effective GB/s of the CloverLeaf-2D-shaped
+chain (3840^2 FP64, 25 dats, 83 loops and two reductions per step), tiled
+(skewed, one persistent kernel per step) against the untiled
+one-kernel-per-loop form on the same GPU.
+
+A step is one pass of the whole chain (83 loops queued through the C ABI,
+flushed by reading the step's two reductions).  Effective GB/s counts bytes
+the paper's way (Sec. 6.A): every dat argument of a loop costs 8 B per
+point of its range, RW twice, stencil re-use ignored.  The dats (3.0 GB)
+are larger than the 126 MB L2, so no flush is needed between steps.
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Prints one JSON line.  --impl reference times the CPU oracle (untiled,
+program order, FP64) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_DEFAULT = 3840
+WORKLOAD = "cloverleaf2d-shaped chain: 3840^2 FP64, halo 2, 25 dats U(0.5,1.5), 83 loops + 1 sum + 1 min reduction per step"
+PROFILE = os.path.join(ROOT, "profiles", "k_skewed_cloverleaf2d_3840.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_1704_00693_gb300", "csrc", "chain_kernels.cu")
+# FP64: 2 DFMA per clock per SM on GB300 (measured 1.97 at 1995 MHz), fma = 2 flops
+FP64_DFMA_PER_CLK_SM = 2
+NUM_SMS = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N_DEFAULT)
+    p.add_argument("--mode", default="skewed", choices=["skewed", "untiled", "auto"])
+    p.add_argument("--tile", default="", help="x,y tile (0 = automatic)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-untiled", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+def workload_numbers(chain):
+    from synth.program import body_flops, loop_points, untiled_bytes
+    U = untiled_bytes(chain)
+    flops = sum(body_flops(lp, chain) * loop_points(lp) for lp in chain.loops)
+    return U, flops
+
+
+def profile_traffic():
+    """dram bytes per launch of k_skewed from the committed ncu summary, if it
+    was taken on the current kernel source."""
+    try:
+        txt = open(PROFILE).read()
+    except OSError:
+        return None
+    src_hash = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256_16") != src_hash:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full_size"])
+    except (KeyError, ValueError):
+        return None
+
+
+def time_mode(chain, mode, tile, steps, warmup, stream, torch):
+    from paper_1704_00693_gb300.chain import ChainRunner
+    r = ChainRunner(chain, mode=mode, tile=tile, stream=stream.cuda_stream, timing=True)
+    try:
+        for _ in range(warmup):
+            r.step()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        kms, launches, kl = 0.0, 0, 0
+        stats = None
+        e0.record(stream)
+        for _ in range(steps):
+            r.step()
+            stats = r.stats()
+            kms += stats["kernel_ms"]
+            kl += stats["kernel_launches"]
+            launches += stats["launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    finally:
+        r.close()
+    return ms, kms, kl, launches, stats
+
+
+def time_e2e(chain, mode, tile, steps, stream, torch):
+    """Per step: upload every dat from pinned host memory, run the step, fetch
+    every dat back; copies inside the timed region."""
+    import numpy as np
+    from paper_1704_00693_gb300 import ops_dat_fetch, ops_dat_upload
+    from paper_1704_00693_gb300.chain import ChainRunner
+    r = ChainRunner(chain, mode=mode, tile=tile, stream=stream.cuda_stream, upload=False)
+    try:
+        host_in, host_out = [], []
+        for d in chain.dats:
+            t = torch.empty(d.init.shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = d.init
+            host_in.append(t)
+            host_out.append(torch.empty(d.init.shape, dtype=torch.float64, pin_memory=True))
+        bi = sum(t.numel() * 8 for t in host_in)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            for h, t in zip(r.dats, host_in):
+                ops_dat_upload(r.ctx, h, t.numpy())
+            r.step()
+            for h, t in zip(r.dats, host_out):
+                ops_dat_fetch(r.ctx, h, t.numpy())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) * 1e3
+        ms = max(e0.elapsed_time(e1), wall)
+    finally:
+        r.close()
+    return ms, bi
+
+
+def cpu_baseline(n_full, seconds=12.0):
+    """The oracle (untiled, program order, FP64, all host cores) on a bounded
+    sample: one step of the same chain on a grid with 1/4 of the points."""
+    import oracle
+    from synth import workloads as W
+    n = n_full // 2
+    chain = W.cloverleaf2d(n=n, steps=1)
+    U, _ = workload_numbers(chain)
+    oracle.build()
+    dats = [d.init.copy() for d in chain.dats]
+    t0 = time.perf_counter()
+    nsteps = 0
+    while True:
+        oracle.run_loops(chain, dats, chain.loops, [oracle.red_identity(op) for op in chain.reductions])
+        nsteps += 1
+        if time.perf_counter() - t0 > seconds or nsteps >= 3:
+            break
+    t = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": U * nsteps / t / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{nsteps} step(s) of the same chain at {n}^2 (1/4 of the points), untiled FP64 oracle",
+            "seconds": t}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from synth import workloads as W
+    n = args.n // 2
+    chain = W.cloverleaf2d(n=n, steps=1)
+    U, _ = workload_numbers(chain)
+    oracle.build()
+    dats = [d.init.copy() for d in chain.dats]
+    ident = [oracle.red_identity(op) for op in chain.reductions]
+    for _ in range(args.warmup):
+        oracle.run_loops(chain, dats, chain.loops, ident)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run_loops(chain, dats, chain.loops, ident)
+    t = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = U * args.steps / t / 1e9
+    line = {"metric": "loop-chain effective GB/s", "value": v, "unit": "GB/s", "impl": "reference",
+            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"each step: the chain at {n}^2 (1/4 of the points)"},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step the same chain at {n}^2"},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank, world, local = dist_env()
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (sm_103a)")
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1704_00693_gb300 import _build
+    _build.build()
+    from synth import workloads as W
+
+    chain = W.cloverleaf2d(n=args.n, steps=1)
+    U, flops = workload_numbers(chain)
+    tile = None
+    if args.tile:
+        tile = [int(x) for x in args.tile.split(",")] + [0]
+    stream = torch.cuda.Stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    barrier()
+    with ClockSampler(local) as clk:
+        ms, kms, kl, launches, st = time_mode(chain, args.mode, tile, args.steps, args.warmup, stream, torch)
+    barrier()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = U * args.steps * world / (ms * 1e-3) / 1e9
+
+    untiled = None
+    if not args.no_untiled and args.mode != "untiled":
+        ums, ukms, ukl, _, _ = time_mode(chain, "untiled", None, args.steps, args.warmup, stream, torch)
+        untiled = {"value": U * args.steps / (ums * 1e-3) / 1e9, "ms_per_step": ums / args.steps,
+                   "kernel_ms_per_step": ukms / args.steps, "kernel_launches_per_step": ukl / args.steps}
+
+    e2e = None
+    if not args.no_e2e:
+        esteps = max(1, min(3, args.steps))
+        ems, bi = time_e2e(chain, args.mode, tile, esteps, stream, torch)
+        e2e = {"value": U * esteps / (ems * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": bi,
+               "d2h_bytes_per_step": bi, "ms_per_step": ems / esteps}
+
+    # roofline of the dominant kernel (one persistent launch per step in tiled mode)
+    kernel_ms_per_launch = kms / max(1, kl)
+    launches_per_step = kl / max(1, args.steps)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = NUM_SMS * FP64_DFMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12
+    flops_per_launch = flops / launches_per_step
+    achieved = flops_per_launch / (kernel_ms_per_launch * 1e-3) / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = profile_traffic() if args.mode == "skewed" and args.n == N_DEFAULT else None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                "frac": achieved / peak_tflops, "traffic": traffic,
+                "kernel": "k_skewed" if args.mode != "untiled" else "k_untiled",
+                "peak_source": f"FP64: {NUM_SMS} SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 flop x {sm_max:.0f} MHz "
+                               "(unit count from a GB300 probe; MEASURED_PEAKS.json has no FP64 figure)",
+                "kernel_ms_per_launch": kernel_ms_per_launch,
+                "algorithmic_flops_per_launch": flops_per_launch,
+                "algorithmic_bytes_per_launch": U / launches_per_step,
+                "effective_hbm_frac": (U / launches_per_step) / (kernel_ms_per_launch * 1e-3) / 1e9 / hbm_peak,
+                "hbm_peak_gbs": hbm_peak}
+    if traffic is not None:
+        roofline["dram_gbs"] = traffic / (kernel_ms_per_launch * 1e-3) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(args.n)
+
+    line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "mode": args.mode, "tile": st["tile"] if st else None,
+                       "tiles": st["tiles"] if st else None, "l2": "inputs larger than L2 (25 dats, 3.0 GB)",
+                       "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "untiled_bytes_per_step": U, "flops_per_step": flops},
+            "speedup_vs_untiled": (untiled["ms_per_step"] / (ms / args.steps)) if untiled else None,
+            "untiled": untiled, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk.summary(),
+            "plan": {"phases": st["phases"], "barriers": st["barriers"], "skew": st["skew"],
+                     "plan_cache_hits": st["plan_cache_hits"]} if st else None}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

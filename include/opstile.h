@@ -1,0 +1,228 @@
+/*
+ * opstile: run-time loop-chain tiling of OPS-style stencil loops on one
+ * GB300 (sm_103a).  C ABI.
+ *
+ * The method is the paper's (Reguly, Mudalige, Giles, "Loop Tiling in
+ * Large-Scale Stencil Codes at Run-time with OPS"):
+ *   - Sec. 3: blocks, datasets (dats) with halos, stencils, and parallel
+ *     loops whose result must not depend on the order of their points;
+ *   - Sec. 4.A: ops_par_loop only queues the loop; the queue is executed when
+ *     the host needs data back (a reduction result, a fetch) or calls
+ *     ops_execute;
+ *   - Sec. 4.B, Algorithm 1: at flush time a dependency analysis walks the
+ *     queued loops backwards and gives every tile of every loop its own
+ *     (skewed) range; Algorithm 2 then runs tile by tile, loop by loop;
+ *   - Sec. 4.D: overlapped tiles that recompute what crosses a tile
+ *     boundary, so tiles become independent;
+ *   - Sec. 4.C: tile-size selection from the bytes per grid point and the
+ *     last-level cache size.
+ * Loop bodies are not function pointers: they are short programs in a fixed
+ * register IR (weighted stencil sums, polynomials, min/max/select,
+ * reductions) that the library's CUDA kernels interpret.
+ *
+ * Conventions for every function below:
+ *   - returns OPS_OK (0) or a negative OPS_ERR_* code; on error
+ *     ops_last_error(ctx) describes it (string owned by ctx, valid until the
+ *     next call on ctx);
+ *   - handles are small non-negative ints inside one context;
+ *   - pointers named host_* are host memory, dev_* device memory; the
+ *     library copies what it needs before returning unless stated;
+ *   - a context is not thread-safe: use one per host thread;
+ *   - no call aborts the process; a CUDA failure is returned as
+ *     OPS_ERR_CUDA with the CUDA error string.
+ */
+#ifndef OPSTILE_H
+#define OPSTILE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define OPS_OK 0
+#define OPS_ERR_INVALID_ARG -1   /* bad argument, handle or IR */
+#define OPS_ERR_BOUNDS -2        /* a loop would access outside [-d_m, size + d_p) */
+#define OPS_ERR_DEVICE_BOUNDS -3 /* a kernel in checked mode caught an out-of-range access */
+#define OPS_ERR_NOMEM -4         /* device allocation failed or over the HBM budget */
+#define OPS_ERR_TIMEOUT -5       /* a device-side wait ran past its limit */
+#define OPS_ERR_NOT_CONVERGED -6 /* a solve hit its iteration cap */
+#define OPS_ERR_CUDA -7          /* a CUDA call failed */
+#define OPS_ERR_STATE -8         /* call not allowed in the current state */
+#define OPS_ERR_NO_DEVICE -9     /* no usable sm_103a device */
+
+/* ---- execution modes of a flushed chain ---- */
+#define OPS_MODE_UNTILED 0    /* one kernel per loop over its full range (the comparator) */
+#define OPS_MODE_SKEWED 1     /* Algorithm 1 tiles, run by one persistent kernel (Algorithm 2) */
+#define OPS_MODE_OVERLAPPED 2 /* independent shared-memory tiles with halo recomputation (Sec. 4.D) */
+#define OPS_MODE_AUTO 3       /* library picks per segment */
+
+/* ---- argument kinds, access modes, reduction operators ---- */
+#define OPS_ARG_DAT 0    /* a dat accessed through a stencil */
+#define OPS_ARG_SCALAR 1 /* read the current value of a reduction handle */
+#define OPS_ARG_RED 2    /* contribute to a reduction handle */
+#define OPS_READ 0
+#define OPS_WRITE 1
+#define OPS_RW 2
+#define OPS_INC 3
+#define OPS_RED_SUM 0
+#define OPS_RED_MIN 1
+#define OPS_RED_MAX 2
+
+/* ---- loop-body IR opcodes: one instruction = 6 int32 (op, d, a, b, c, e) ----
+ * Eight FP64 registers r0..r7 per grid point start at +0.0; K is the loop's
+ * constant pool; v(a, p) is the dat of argument a at this point shifted by
+ * point p of that argument's stencil.  Arithmetic is IEEE FP64 with round to
+ * nearest; fma rounds once; nothing is reassociated or contracted. */
+#define OPS_IR_LD 1    /* r[d] = v(a, b); a SCALAR argument gives its value (b = 0) */
+#define OPS_IR_CST 2   /* r[d] = K[a] */
+#define OPS_IR_ADD 3   /* r[d] = r[a] + r[b] */
+#define OPS_IR_SUB 4   /* r[d] = r[a] - r[b] */
+#define OPS_IR_MUL 5   /* r[d] = r[a] * r[b] */
+#define OPS_IR_FMA 6   /* r[d] = fma(r[a], r[b], r[c]) */
+#define OPS_IR_DIV 7   /* r[d] = r[a] / r[b] */
+#define OPS_IR_MIN 8   /* r[d] = r[b] < r[a] ? r[b] : r[a] */
+#define OPS_IR_MAX 9   /* r[d] = r[b] > r[a] ? r[b] : r[a] */
+#define OPS_IR_SGT 10  /* r[d] = r[a] > r[b] ? r[c] : r[e] */
+#define OPS_IR_WSUM 11 /* r[d] = K[b] v(a,0); r[d] = fma(K[b+p], v(a,p), r[d]) for p = 1..np-1 */
+#define OPS_IR_WACC 12 /* r[d] = fma(K[b+p], v(a,p), r[d]) for p = 0..np-1 */
+#define OPS_IR_POLY 13 /* t = K[b+c]; t = fma(t, r[a], K[b+i]) for i = c-1..0; r[d] = t */
+#define OPS_IR_ST 14   /* arg d WRITE/RW: dat = r[a]; arg d INC: dat = dat + r[a] */
+#define OPS_IR_RED 15  /* reduction arg d takes the contribution r[a] */
+
+/* limits of one loop */
+#define OPS_MAX_ARGS 8
+#define OPS_MAX_STENCIL_POINTS 32
+#define OPS_MAX_INS 64
+#define OPS_MAX_CONSTS 128
+#define OPS_MAX_REDS_PER_LOOP 4
+
+typedef struct ops_ctx_s* ops_ctx;
+
+/* device = OPS_DEVICE_NONE makes a host-only context: declarations,
+ * validation and planning work, anything that would run loops returns
+ * OPS_ERR_NO_DEVICE.  No CUDA call is made. */
+#define OPS_DEVICE_NONE -1
+
+typedef struct {
+  int device;          /* CUDA device ordinal */
+  void* stream;        /* cudaStream_t all work is ordered on; NULL: the library creates one */
+  int mode;            /* OPS_MODE_* */
+  int tile[3];         /* skewed / overlapped tile size per dimension; 0 = automatic */
+  int segment;         /* at most this many loops per tiled segment; 0 = up to the flush */
+  int check;           /* 1: kernels bounds-check every access (OPS_ERR_DEVICE_BOUNDS) */
+  int64_t l2_bytes;    /* cache budget for automatic tile sizes (Sec. 4.C); 0 = 3/4 of L2 */
+  int64_t hbm_budget;  /* cap on bytes the library allocates; 0 = no cap */
+  int timeout_ms;      /* limit of every device-side wait (grid barriers); 0 = 2000 */
+  int blocks_per_sm;   /* persistent-kernel CTAs per SM; 0 = as many as fit */
+  int test_skip_barrier_block; /* test hook: this CTA never arrives at grid barriers; -1 = off */
+  int timing;          /* 1: record CUDA events around the chain kernels (kernel_ms in ops_flush_stats) */
+} ops_config;
+
+/* Fill *cfg with defaults (device 0, own stream, OPS_MODE_AUTO, automatic tiles). */
+void ops_config_default(ops_config* cfg);
+
+/* Create a context on cfg->device.  *out receives the context.  Fails with
+ * OPS_ERR_NO_DEVICE if the device is not compute capability 10.3. */
+int ops_init(ops_ctx* out, const ops_config* cfg);
+/* Flush nothing; free every library-owned buffer and the context. */
+int ops_finalize(ops_ctx ctx);
+const char* ops_last_error(ops_ctx ctx);
+/* Change mode / tile / segment for later flushes (tile may be NULL). */
+int ops_set_mode(ops_ctx ctx, int mode, const int* tile, int segment);
+
+/* ---- declarations (Sec. 3) ---- */
+/* A structured block of 1, 2 or 3 dimensions. */
+int ops_decl_block(ops_ctx ctx, int dims, const char* name, int* out);
+/* A FP64 dat of size[0..dims) interior points with halo depths d_m (below)
+ * and d_p (above) per dimension (unused dimensions: size 1, halos 0).
+ * dev_ptr0 == NULL: the library allocates a zeroed, padded array (x rows
+ * start 128-byte aligned) and owns it.  Otherwise dev_ptr0 is borrowed: it
+ * must point at grid point (0,0,0) of caller-owned device memory in which
+ * point (x,y,z) is dev_ptr0[x + pitch*y + plane*z] for every point of the
+ * allocation box; it must outlive the dat. */
+int ops_decl_dat(ops_ctx ctx, int block, const int size[3], const int d_m[3], const int d_p[3],
+                 double* dev_ptr0, int64_t pitch, int64_t plane, const char* name, int* out);
+/* A stencil of npts offsets (3 ints per point; unused dimensions 0). */
+int ops_decl_stencil(ops_ctx ctx, int dims, int npts, const int* offsets, const char* name, int* out);
+/* A reduction handle (OPS_RED_*), a device-resident FP64 value that starts at
+ * the operator's identity, accumulates the contributions of every loop that
+ * reduces into it, and is read (and reset) by ops_reduction_result. */
+int ops_decl_reduction(ops_ctx ctx, int op, int* out);
+
+/* ---- parallel loops (Sec. 3, Sec. 4.A) ---- */
+typedef struct {
+  int kind;    /* OPS_ARG_DAT / OPS_ARG_SCALAR / OPS_ARG_RED */
+  int handle;  /* dat or reduction handle */
+  int stencil; /* stencil handle (DAT); ignored otherwise */
+  int access;  /* OPS_READ / OPS_WRITE / OPS_RW / OPS_INC (DAT) */
+} ops_arg;
+
+/* Queue a loop over range[2*d .. 2*d+1) (half-open, per dimension) of
+ * `block`.  The body is `nins` instructions (code: 6 int32 each) with
+ * `nconsts` constants; both are copied.  Checked here: handles, IR
+ * well-formedness, a dat appears at most once, written args use a stencil
+ * whose only point is the origin, every access stays inside
+ * [-d_m, size + d_p) (else OPS_ERR_BOUNDS).  Nothing runs. */
+int ops_par_loop(ops_ctx ctx, int block, int dims, const int* range, int nargs, const ops_arg* args,
+                 int nins, const int32_t* code, int nconsts, const double* consts, const char* name);
+/* Run every queued loop (Sec. 4.A flush).  Returns after the work is
+ * queued on the stream; device errors surface at the next ops_sync. */
+int ops_execute(ops_ctx ctx);
+/* Drop every queued loop without running it. */
+int ops_queue_clear(ops_ctx ctx);
+/* Flush, wait, copy the reduction's value to *host_out and reset it. */
+int ops_reduction_result(ops_ctx ctx, int red, double* host_out);
+/* Flush, wait and check the device error word (OPS_ERR_TIMEOUT,
+ * OPS_ERR_DEVICE_BOUNDS). */
+int ops_sync(ops_ctx ctx);
+
+/* ---- data movement ---- */
+/* Flush, then copy the dat's whole allocation box (halos included) into the
+ * dense host array host_out of ex*ey*ez doubles, x fastest. */
+int ops_dat_fetch(ops_ctx ctx, int dat, double* host_out, int64_t nelems);
+/* Copy a dense host array of the allocation box into the dat (after the
+ * queued loops, in stream order). */
+int ops_dat_upload(ops_ctx ctx, int dat, const double* host_in, int64_t nelems);
+/* Current device address of grid point (0,0,0) and strides of a dat; ext
+ * receives the allocation extents (may be NULL). */
+int ops_dat_info(ops_ctx ctx, int dat, double** dev_ptr0, int64_t* pitch, int64_t* plane, int* ext);
+
+/* ---- statistics of the most recent flush ---- */
+typedef struct {
+  double plan_ms;        /* host time spent building plans (0 on a cache hit) */
+  int segments;          /* tiled segments executed */
+  int loops;             /* loops executed */
+  int tiles;             /* tiles in the last skewed / overlapped segment */
+  int phases;            /* non-empty (tile, loop) pieces executed */
+  int barriers;          /* grid barriers executed by persistent kernels */
+  int launches;          /* kernel launches issued by the flush */
+  int plan_cache_hits;   /* segments whose plan came from the cache */
+  int mode;              /* OPS_MODE_* of the last segment */
+  int tile[3];           /* tile size of the last tiled segment */
+  int64_t redundant_points; /* overlapped mode: extra points computed */
+  int64_t points;        /* loop points executed (excluding redundancy) */
+  int skew[3];           /* largest spread of the loops' tile ends over all but the last tile */
+  double kernel_ms;      /* timing=1: device time of the flush's chain kernels (persistent kernel,
+                            or the per-loop kernels), measured with CUDA events on the context's stream */
+  int kernel_launches;   /* chain kernels covered by kernel_ms */
+} ops_flush_stats;
+/* Statistics of the most recent flush; with timing=1 this waits for that
+ * flush's kernels to finish. */
+int ops_last_stats(ops_ctx ctx, ops_flush_stats* out);
+
+/* ---- plan inspection (host only; no device work) ----
+ * Build the skewed plan (Algorithm 1) for the currently queued loops with the
+ * given tile sizes, without executing them.  out_ranges receives, for every
+ * dimension d < dims, tile t and loop l, the pair (start, end) at
+ * out_ranges[2 * (offset_d + t * nloops + l)], offset_d = nloops * sum of
+ * ntiles of the dimensions before d; out_ntiles[d] receives the tile counts.
+ * cap is the number of ints out_ranges can hold. */
+int ops_plan_skewed(ops_ctx ctx, const int* tile, int* out_ntiles, int* out_ranges, int64_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OPSTILE_H */

@@ -1,0 +1,239 @@
+"""Python binding of libopstile (include/opstile.h): argument marshalling only.
+
+Every function keeps the C name and signature shape; handles are ints,
+host arrays are numpy arrays, device addresses are ints.  A non-zero status
+raises OpsError carrying the code and ops_last_error's message.  The CUDA
+library must have been built (`paper_1704_00693_gb300._build.build()`, or
+`__graft_entry__.build()`); importing this module without it fails loudly —
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _build
+
+OPS_OK = 0
+OPS_ERR_INVALID_ARG = -1
+OPS_ERR_BOUNDS = -2
+OPS_ERR_DEVICE_BOUNDS = -3
+OPS_ERR_NOMEM = -4
+OPS_ERR_TIMEOUT = -5
+OPS_ERR_NOT_CONVERGED = -6
+OPS_ERR_CUDA = -7
+OPS_ERR_STATE = -8
+OPS_ERR_NO_DEVICE = -9
+
+OPS_MODE_UNTILED, OPS_MODE_SKEWED, OPS_MODE_OVERLAPPED, OPS_MODE_AUTO = 0, 1, 2, 3
+OPS_ARG_DAT, OPS_ARG_SCALAR, OPS_ARG_RED = 0, 1, 2
+OPS_READ, OPS_WRITE, OPS_RW, OPS_INC = 0, 1, 2, 3
+OPS_RED_SUM, OPS_RED_MIN, OPS_RED_MAX = 0, 1, 2
+OPS_DEVICE_NONE = -1
+
+MODES = {"untiled": OPS_MODE_UNTILED, "skewed": OPS_MODE_SKEWED, "overlapped": OPS_MODE_OVERLAPPED,
+         "auto": OPS_MODE_AUTO}
+
+
+class OpsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"opstile error {code}: {msg}")
+        self.code = code
+
+
+class ops_config(C.Structure):
+    _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("mode", C.c_int), ("tile", C.c_int * 3),
+                ("segment", C.c_int), ("check", C.c_int), ("l2_bytes", C.c_int64), ("hbm_budget", C.c_int64),
+                ("timeout_ms", C.c_int), ("blocks_per_sm", C.c_int), ("test_skip_barrier_block", C.c_int),
+                ("timing", C.c_int)]
+
+
+class ops_arg(C.Structure):
+    _fields_ = [("kind", C.c_int), ("handle", C.c_int), ("stencil", C.c_int), ("access", C.c_int)]
+
+
+class ops_flush_stats(C.Structure):
+    _fields_ = [("plan_ms", C.c_double), ("segments", C.c_int), ("loops", C.c_int), ("tiles", C.c_int),
+                ("phases", C.c_int), ("barriers", C.c_int), ("launches", C.c_int), ("plan_cache_hits", C.c_int),
+                ("mode", C.c_int), ("tile", C.c_int * 3), ("redundant_points", C.c_int64), ("points", C.c_int64),
+                ("skew", C.c_int * 3), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int)]
+
+    def as_dict(self):
+        return {k: (list(getattr(self, k)) if k in ("tile", "skew") else getattr(self, k))
+                for k, _ in self._fields_}
+
+
+_lib = None
+EXPORTS = []  # filled from the header at import
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: Optional[str] = None):
+    """Load libopstile.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise ImportError(f"libopstile.so not built at {p}: run paper_1704_00693_gb300._build.build()")
+    L = C.CDLL(p)
+    L.ops_last_error.restype = C.c_char_p
+    L.ops_config_default.restype = None
+    _lib = L
+    return L
+
+
+def _check(ctx, rc: int):
+    if rc != OPS_OK:
+        msg = load().ops_last_error(ctx).decode(errors="replace") if ctx else ""
+        raise OpsError(rc, msg)
+
+
+def _i3(v) -> C.Array:
+    return (C.c_int * 3)(*[int(x) for x in v])
+
+
+# ---------------------------------------------------------------- lifecycle
+def ops_config_default() -> ops_config:
+    cfg = ops_config()
+    load().ops_config_default(C.byref(cfg))
+    return cfg
+
+
+def ops_init(cfg: Optional[ops_config] = None):
+    L = load()
+    if cfg is None:
+        cfg = ops_config_default()
+    ctx = C.c_void_p()
+    rc = L.ops_init(C.byref(ctx), C.byref(cfg))
+    if rc != OPS_OK:
+        raise OpsError(rc, "ops_init failed (no sm_103a device?)" if rc == OPS_ERR_NO_DEVICE else "ops_init failed")
+    return ctx
+
+
+def ops_finalize(ctx):
+    _check(None, load().ops_finalize(ctx))
+
+
+def ops_last_error(ctx) -> str:
+    return load().ops_last_error(ctx).decode(errors="replace")
+
+
+def ops_set_mode(ctx, mode: int, tile: Optional[Sequence[int]] = None, segment: int = 0):
+    t = _i3(tile) if tile is not None else None
+    _check(ctx, load().ops_set_mode(ctx, C.c_int(mode), t, C.c_int(segment)))
+
+
+# ------------------------------------------------------------- declarations
+def ops_decl_block(ctx, dims: int, name: str = "") -> int:
+    out = C.c_int()
+    _check(ctx, load().ops_decl_block(ctx, C.c_int(dims), name.encode(), C.byref(out)))
+    return out.value
+
+
+def ops_decl_dat(ctx, block: int, size, d_m, d_p, dev_ptr0: int = 0, pitch: int = 0, plane: int = 0,
+                 name: str = "") -> int:
+    out = C.c_int()
+    _check(ctx, load().ops_decl_dat(ctx, C.c_int(block), _i3(size), _i3(d_m), _i3(d_p), C.c_void_p(dev_ptr0 or None),
+                                    C.c_int64(pitch), C.c_int64(plane), name.encode(), C.byref(out)))
+    return out.value
+
+
+def ops_decl_stencil(ctx, dims: int, points, name: str = "") -> int:
+    pts = np.ascontiguousarray(np.asarray(points, dtype=np.int32).reshape(-1, 3))
+    out = C.c_int()
+    _check(ctx, load().ops_decl_stencil(ctx, C.c_int(dims), C.c_int(pts.shape[0]),
+                                        pts.ctypes.data_as(C.POINTER(C.c_int)), name.encode(), C.byref(out)))
+    return out.value
+
+
+def ops_decl_reduction(ctx, op: int) -> int:
+    out = C.c_int()
+    _check(ctx, load().ops_decl_reduction(ctx, C.c_int(op), C.byref(out)))
+    return out.value
+
+
+# -------------------------------------------------------------------- loops
+def ops_par_loop(ctx, block: int, dims: int, rng, args, code, consts, name: str = ""):
+    r = np.zeros(6, dtype=np.int32)
+    for d in range(dims):
+        r[2 * d], r[2 * d + 1] = rng[d]
+    a = (ops_arg * max(1, len(args)))(*[ops_arg(*x) for x in args])
+    code = np.ascontiguousarray(np.asarray(code, dtype=np.int32).reshape(-1, 6))
+    consts = np.ascontiguousarray(np.asarray(consts, dtype=np.float64).ravel())
+    _check(ctx, load().ops_par_loop(ctx, C.c_int(block), C.c_int(dims), r.ctypes.data_as(C.POINTER(C.c_int)),
+                                    C.c_int(len(args)), a, C.c_int(code.shape[0]),
+                                    code.ctypes.data_as(C.POINTER(C.c_int32)), C.c_int(consts.size),
+                                    consts.ctypes.data_as(C.POINTER(C.c_double)), name.encode()))
+
+
+def ops_execute(ctx):
+    _check(ctx, load().ops_execute(ctx))
+
+
+def ops_sync(ctx):
+    _check(ctx, load().ops_sync(ctx))
+
+
+def ops_queue_clear(ctx):
+    _check(ctx, load().ops_queue_clear(ctx))
+
+
+def ops_reduction_result(ctx, red: int) -> float:
+    v = C.c_double()
+    _check(ctx, load().ops_reduction_result(ctx, C.c_int(red), C.byref(v)))
+    return v.value
+
+
+# ------------------------------------------------------------ data movement
+def ops_dat_info(ctx, dat: int):
+    p = C.c_void_p()
+    pitch = C.c_int64()
+    plane = C.c_int64()
+    ext = (C.c_int * 3)()
+    _check(ctx, load().ops_dat_info(ctx, C.c_int(dat), C.byref(p), C.byref(pitch), C.byref(plane), ext))
+    return (p.value or 0), pitch.value, plane.value, tuple(ext)
+
+
+def ops_dat_fetch(ctx, dat: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+    _, _, _, ext = ops_dat_info(ctx, dat)
+    if out is None:
+        out = np.empty((ext[2], ext[1], ext[0]), dtype=np.float64)
+    assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == ext[0] * ext[1] * ext[2]
+    _check(ctx, load().ops_dat_fetch(ctx, C.c_int(dat), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                     C.c_int64(out.size)))
+    return out
+
+
+def ops_dat_upload(ctx, dat: int, host: np.ndarray):
+    h = np.ascontiguousarray(host, dtype=np.float64)
+    _check(ctx, load().ops_dat_upload(ctx, C.c_int(dat), h.ctypes.data_as(C.POINTER(C.c_double)),
+                                      C.c_int64(h.size)))
+
+
+def ops_last_stats(ctx) -> dict:
+    s = ops_flush_stats()
+    _check(ctx, load().ops_last_stats(ctx, C.byref(s)))
+    return s.as_dict()
+
+
+def ops_plan_skewed(ctx, tile, ndim: int, nloops: int):
+    """Algorithm 1 ranges for the queued loops: list over d of arrays
+    [ntiles_d, nloops, 2]."""
+    cap = 2 * nloops * sum(max(1, 4096) for _ in range(ndim)) * 64
+    buf = np.zeros(cap, dtype=np.int32)
+    nt = (C.c_int * 3)()
+    t = _i3(list(tile) + [1] * (3 - len(tile)))
+    _check(ctx, load().ops_plan_skewed(ctx, t, nt, buf.ctypes.data_as(C.POINTER(C.c_int)), C.c_int64(cap)))
+    out, pos = [], 0
+    for d in range(ndim):
+        n = nt[d] * nloops * 2
+        out.append(buf[pos:pos + n].reshape(nt[d], nloops, 2).copy())
+        pos += n
+    return out

@@ -1,0 +1,87 @@
+// Internal structures shared by the host runtime (runtime.cpp, plan.cpp) and
+// the device kernels (chain_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "opstile.h"
+
+namespace opstile {
+
+constexpr int kNReg = 8;
+constexpr int kThreads = 256;  // threads per CTA of every chain kernel
+
+// Device error word values (first writer wins).
+constexpr int kDevErrTimeout = 1;
+constexpr int kDevErrBounds = 2;
+
+// One argument of a loop, resolved to device addresses.
+struct DArg {
+  double* ptr0;       // grid point (0,0,0) of the dat
+  int64_t pitch;      // elements between consecutive y
+  int64_t plane;      // elements between consecutive z
+  int kind;           // OPS_ARG_*
+  int access;         // OPS_READ ...
+  int npts;           // stencil points (DAT)
+  int slot;           // SCALAR: scalar slot; RED: index among this loop's reductions
+  int alo[3], ahi[3]; // allocation box of the dat in grid coordinates [alo, ahi)
+  int slo[3], shi[3]; // stencil extent (most negative / most positive offset)
+  int32_t off[OPS_MAX_STENCIL_POINTS];  // linear element offsets of the stencil points
+};
+
+// One loop as the kernels see it (copied to shared memory per CTA).
+struct DLoop {
+  int nargs, nins, nreds;
+  int rng[6];                          // declared range x0 x1 y0 y1 z0 z1
+  int red_op[OPS_MAX_REDS_PER_LOOP];   // OPS_RED_* of each reduction
+  int part_row;                        // first partial row of this loop's reductions
+  int pad_;
+  int ins[OPS_MAX_INS][6];
+  double K[OPS_MAX_CONSTS];
+  DArg args[OPS_MAX_ARGS];
+};
+
+// A (tile, loop) piece of a skewed segment, in execution order.
+struct Phase {
+  int loop;      // index into the segment's DLoop table
+  int barrier;   // 1: grid barrier before this phase
+  int box[6];    // x0 x1 y0 y1 z0 z1 (non-empty)
+};
+
+// A reduction partial row: which scalar slot it folds into, with which operator.
+struct FoldRow {
+  int slot;
+  int op;
+};
+
+// Double-double accumulator for deterministic, compensated sums.
+struct DD {
+  double hi, lo;
+};
+
+struct LaunchEnv {
+  cudaStream_t stream;
+  int num_sms;
+  double* scal;         // reduction / scalar slots
+  DD* part;             // reduction partials: rows x part_stride
+  int part_stride;      // >= grid size of any chain kernel
+  const FoldRow* rows;  // per partial row: target slot and operator
+  int* err;             // device error word
+  unsigned* bar;        // grid barrier state (2 words)
+  int check;
+  long long timeout_ns;
+  int skip_block;       // test hook: CTA that never arrives at grid barriers (-1 = none)
+};
+
+// Launch helpers implemented in chain_kernels.cu.
+int untiled_grid(const LaunchEnv& env, const int* box);
+cudaError_t launch_untiled(const LaunchEnv& env, const DLoop* d_loop, const int* box, int grid);
+cudaError_t launch_part_init(const LaunchEnv& env, int row0, int nrows);
+cudaError_t launch_fold(const LaunchEnv& env, int row0, int nrows, int grid_used);
+int skewed_max_grid(int num_sms, int blocks_per_sm);
+cudaError_t launch_skewed(const LaunchEnv& env, const DLoop* d_loops, const Phase* d_phases, int nphases,
+                          int grid);
+cudaError_t launch_set_scalar(const LaunchEnv& env, int slot, double value);
+
+}  // namespace opstile

@@ -1,0 +1,253 @@
+// Run-time dependency analysis of a queued chain segment.
+//
+// build_skewed_ranges is Algorithm 1 of Sec. 4.B.  The union of the loops'
+// ranges is cut into tiles of `tile[d]` points per dimension; walking the
+// loops from last to first, every tile of every loop gets a range that starts
+// where the same loop's previous tile ended and ends far enough right to
+//   - produce what later loops of the same tile read (read-after-write),
+//   - not leave for the next tile a read or write of a value that a later
+//     loop of this tile overwrites (write-after-read / write-after-write),
+// or, with no dependency, at the tile boundary.  Readings of the printed
+// algorithm: ranges are half-open; a tile's start is the previous tile's
+// final end (prose step 3), so tiles are completed in increasing order per
+// (loop, dimension); the default end of 0-based tile t is
+// min(loop end, union start + (t+1) * tile); ends are clamped to at least the
+// start and the last tile ends at the loop's end; m / p are the most negative
+// / most positive stencil offsets, or 0; WAR/WAW looks at every dat argument
+// (a written one has a point stencil, m = 0: the WAW case); empty ranges do
+// not update the dependency records, which are never reset.  Dimensions are
+// independent; tiles run lexicographically with x fastest.
+#include "plan.h"
+
+#include <algorithm>
+#include <climits>
+
+namespace opstile {
+
+namespace {
+constexpr int kNone = INT_MIN / 4;  // "no dependency recorded" / minus infinity
+constexpr int kFar = INT_MAX / 4;
+}  // namespace
+
+void build_skewed_ranges(const std::vector<PLoop>& loops, int ndats, int ndim, const int tile[3], SkewedPlan& out) {
+  const int L = (int)loops.size();
+  out.ndim = ndim;
+  for (int d = 0; d < 3; ++d) {
+    out.tile[d] = 1;
+    out.ntiles[d] = 1;
+    out.ranges[d].clear();
+    out.skew[d] = 0;
+  }
+  for (int d = 0; d < ndim; ++d) {
+    int ustart = kFar, uend = -kFar;
+    for (const PLoop& lp : loops) {
+      ustart = std::min(ustart, lp.rng[2 * d]);
+      uend = std::max(uend, lp.rng[2 * d + 1]);
+    }
+    const int ts = std::max(1, tile[d]);
+    const int T = uend > ustart ? (uend - ustart - 1) / ts + 1 : 1;
+    out.tile[d] = ts;
+    out.ntiles[d] = T;
+    std::vector<int>& R = out.ranges[d];
+    R.assign((size_t)2 * T * L, 0);
+    // dependency records per (tile, dat): end of reads / writes by later loops
+    std::vector<int> rd_end((size_t)T * ndats, kNone), rd_start((size_t)T * ndats, kFar);
+    std::vector<int> wr_end((size_t)T * ndats, kNone), wr_start((size_t)T * ndats, kFar);
+    for (int l = L - 1; l >= 0; --l) {
+      const PLoop& lp = loops[l];
+      const int lo = lp.rng[2 * d], hi = lp.rng[2 * d + 1];
+      for (int t = 0; t < T; ++t) {
+        const int start = t == 0 ? lo : R[2 * ((t - 1) * L + l) + 1];
+        int end = kNone;
+        if (t == T - 1) {
+          end = hi;
+        } else {
+          for (const PArg& a : lp.args) {  // read-after-write
+            if (a.kind != OPS_ARG_DAT || !a.writes) continue;
+            const int re = rd_end[(size_t)t * ndats + a.dat];
+            if (re != kNone) end = std::min(hi, std::max(end, re));
+          }
+          for (const PArg& a : lp.args) {  // write-after-read / write-after-write
+            if (a.kind != OPS_ARG_DAT) continue;
+            const int we = wr_end[(size_t)t * ndats + a.dat];
+            if (we != kNone) end = std::min(hi, std::max(end, we - a.slo[d]));
+          }
+        }
+        if (end == kNone) end = std::min(hi, ustart + (t + 1) * ts);
+        if (end < start) end = start;
+        R[2 * (t * L + l)] = start;
+        R[2 * (t * L + l) + 1] = end;
+        if (end <= start) continue;
+        for (const PArg& a : lp.args) {
+          if (a.kind != OPS_ARG_DAT) continue;
+          const size_t k = (size_t)t * ndats + a.dat;
+          if (a.reads) {
+            rd_end[k] = std::max(rd_end[k], end + a.shi[d]);
+            rd_start[k] = std::min(rd_start[k], start + a.slo[d]);
+          }
+          if (a.writes) {
+            wr_end[k] = std::max(wr_end[k], end);
+            wr_start[k] = std::min(wr_start[k], start);
+          }
+        }
+      }
+    }
+    // skew: spread of the loops' tile ends, largest over all but the last tile
+    int sk = 0;
+    for (int t = 0; t + 1 < T; ++t) {
+      int mn = kFar, mx = -kFar;
+      for (int l = 0; l < L; ++l) {
+        const int s = R[2 * (t * L + l)], e = R[2 * (t * L + l) + 1];
+        if (e <= s) continue;
+        mn = std::min(mn, e);
+        mx = std::max(mx, e);
+      }
+      if (mx >= mn) sk = std::max(sk, mx - mn);
+    }
+    out.skew[d] = sk;
+  }
+}
+
+namespace {
+bool boxes_meet(const int* a, const int* b) {
+  for (int d = 0; d < 3; ++d)
+    if (a[2 * d] >= b[2 * d + 1] || b[2 * d] >= a[2 * d + 1]) return false;
+  return true;
+}
+void grow(const int* box, const PArg& a, int* out) {
+  for (int d = 0; d < 3; ++d) {
+    out[2 * d] = box[2 * d] + a.slo[d];
+    out[2 * d + 1] = box[2 * d + 1] + a.shi[d];
+  }
+}
+// Does phase q (loop lq over box bq) touch data that phase p (loop lp over
+// box bp) writes, or write data that p touches?
+bool conflict(const PLoop& lp, const int* bp, const PLoop& lq, const int* bq) {
+  int gp[6], gq[6];
+  for (const PArg& a : lp.args) {
+    if (a.kind != OPS_ARG_DAT) continue;
+    for (const PArg& b : lq.args) {
+      if (b.kind != OPS_ARG_DAT || b.dat != a.dat) continue;
+      if (!a.writes && !b.writes) continue;
+      // region of the dat touched by each phase (reads widened by the stencil)
+      if (a.reads) grow(bp, a, gp);
+      else for (int i = 0; i < 6; ++i) gp[i] = bp[i];
+      if (b.reads) grow(bq, b, gq);
+      else for (int i = 0; i < 6; ++i) gq[i] = bq[i];
+      if (boxes_meet(gp, gq)) return true;
+    }
+  }
+  return false;
+}
+}  // namespace
+
+void build_phases(const std::vector<PLoop>& loops, SkewedPlan& plan) {
+  const int L = (int)loops.size();
+  plan.phases.clear();
+  plan.nbarriers = 0;
+  plan.points = 0;
+  std::vector<int> epoch;  // phases since the last barrier
+  for (int tz = 0; tz < plan.ntiles[2]; ++tz)
+    for (int ty = 0; ty < plan.ntiles[1]; ++ty)
+      for (int tx = 0; tx < plan.ntiles[0]; ++tx)
+        for (int l = 0; l < L; ++l) {
+          Phase P;
+          P.loop = l;
+          P.barrier = 0;
+          const int t[3] = {tx, ty, tz};
+          bool empty = false;
+          for (int d = 0; d < 3; ++d) {
+            if (d < plan.ndim) {
+              const std::vector<int>& R = plan.ranges[d];
+              P.box[2 * d] = R[2 * (t[d] * L + l)];
+              P.box[2 * d + 1] = R[2 * (t[d] * L + l) + 1];
+            } else {
+              P.box[2 * d] = loops[l].rng[2 * d];
+              P.box[2 * d + 1] = loops[l].rng[2 * d + 1];
+            }
+            if (P.box[2 * d + 1] <= P.box[2 * d]) empty = true;
+          }
+          if (empty) continue;
+          bool need = false;
+          for (int e : epoch) {
+            const Phase& Q = plan.phases[e];
+            if (conflict(loops[Q.loop], Q.box, loops[l], P.box)) {
+              need = true;
+              break;
+            }
+          }
+          if (need) {
+            P.barrier = 1;
+            ++plan.nbarriers;
+            epoch.clear();
+          }
+          epoch.push_back((int)plan.phases.size());
+          int64_t n = 1;
+          for (int d = 0; d < 3; ++d) n *= (int64_t)(P.box[2 * d + 1] - P.box[2 * d]);
+          plan.points += n;
+          plan.phases.push_back(P);
+        }
+}
+
+// Overlapped tile (Sec. 4.D, read dependencies only): the last loops keep the
+// tile's owned box; an earlier loop that writes a dat read by later loops of
+// the tile widens its box to everything those reads touch (clipped to its own
+// range); what is read but not produced inside the tile is the live-in
+// footprint.
+void build_overlap_tile(const std::vector<PLoop>& loops, int ndats, int ndim, const int owned[6], OverlapTile& out) {
+  const int L = (int)loops.size();
+  for (int i = 0; i < 6; ++i) out.owned[i] = owned[i];
+  out.box.assign((size_t)6 * L, 0);
+  std::vector<int> rb((size_t)6 * ndats);
+  for (int k = 0; k < ndats; ++k)
+    for (int d = 0; d < 3; ++d) {
+      rb[6 * k + 2 * d] = kFar;
+      rb[6 * k + 2 * d + 1] = -kFar;
+    }
+  for (int l = L - 1; l >= 0; --l) {
+    const PLoop& lp = loops[l];
+    int box[6];
+    bool empty = false;
+    for (int d = 0; d < 3; ++d) {
+      const int lo = lp.rng[2 * d], hi = lp.rng[2 * d + 1];
+      int blo, bhi;
+      if (d < ndim) {
+        blo = std::max(lo, owned[2 * d]);
+        bhi = std::min(hi, owned[2 * d + 1]);
+        if (bhi <= blo) {
+          blo = kFar;
+          bhi = -kFar;
+        }
+        for (const PArg& a : lp.args) {
+          if (a.kind != OPS_ARG_DAT || !a.writes) continue;
+          const int rlo = rb[6 * a.dat + 2 * d], rhi = rb[6 * a.dat + 2 * d + 1];
+          if (rhi <= rlo) continue;
+          blo = std::min(blo, std::max(lo, rlo));
+          bhi = std::max(bhi, std::min(hi, rhi));
+        }
+      } else {
+        blo = lo;
+        bhi = hi;
+      }
+      box[2 * d] = blo;
+      box[2 * d + 1] = bhi;
+      if (bhi <= blo) empty = true;
+    }
+    int* ob = &out.box[(size_t)6 * l];
+    if (empty) {
+      for (int i = 0; i < 6; ++i) ob[i] = 0;
+      continue;
+    }
+    for (int i = 0; i < 6; ++i) ob[i] = box[i];
+    for (const PArg& a : lp.args) {
+      if (a.kind != OPS_ARG_DAT || !a.reads) continue;
+      for (int d = 0; d < 3; ++d) {
+        rb[6 * a.dat + 2 * d] = std::min(rb[6 * a.dat + 2 * d], box[2 * d] + a.slo[d]);
+        rb[6 * a.dat + 2 * d + 1] = std::max(rb[6 * a.dat + 2 * d + 1], box[2 * d + 1] + a.shi[d]);
+      }
+    }
+  }
+  out.foot = rb;
+}
+
+}  // namespace opstile

@@ -1,0 +1,941 @@
+// Host runtime of opstile: context, declarations, delayed-execution queue
+// (Sec. 4.A), flush into segments, plan cache (Sec. 4.B: plans are re-used
+// when the same loop sequence comes back), tile-size choice (Sec. 4.C) and
+// kernel launches.  Implements the C ABI of include/opstile.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "opstile.h"
+#include "plan.h"
+
+using namespace opstile;
+
+namespace {
+
+struct Block {
+  int dims;
+  std::string name;
+};
+
+struct Dat {
+  int block;
+  int size[3], dm[3], dp[3], ext[3];
+  double* alloc = nullptr;  // owned allocation (nullptr if borrowed)
+  double* ptr0 = nullptr;   // grid point (0,0,0)
+  int64_t pitch = 0, plane = 0;
+  size_t bytes = 0;
+  std::string name;
+};
+
+struct Stencil {
+  int dims;
+  std::vector<int> off;  // 3 per point
+  int lo[3], hi[3];
+  std::string name;
+};
+
+struct QLoop {
+  int block, dims;
+  int rng[6];
+  std::vector<ops_arg> args;
+  std::vector<int32_t> code;
+  std::vector<double> K;
+  std::string name;
+};
+
+struct CachedPlan {
+  std::vector<int> key;
+  SkewedPlan plan;
+  Phase* d_phases = nullptr;
+};
+
+}  // namespace
+
+struct ops_ctx_s {
+  ops_config cfg;
+  bool host_only = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  int64_t l2_size = 0;
+  std::vector<Block> blocks;
+  std::vector<Dat> dats;
+  std::vector<Stencil> stencils;
+  std::vector<int> red_ops;
+  std::vector<QLoop> queue;
+  // device state
+  double* d_scal = nullptr;
+  int scal_cap = 0;
+  DD* d_part = nullptr;
+  int part_rows_cap = 0;
+  int part_stride = 0;
+  FoldRow* d_rows = nullptr;
+  int rows_cap = 0;
+  int* d_err = nullptr;
+  unsigned* d_bar = nullptr;
+  DLoop* d_loops = nullptr;
+  int loops_cap = 0;
+  int skewed_grid = 0;
+  std::map<std::vector<int>, std::unique_ptr<CachedPlan>> plans;
+  int64_t allocated = 0;
+  std::string err;
+  ops_flush_stats stats;
+  // timing=1: event pairs around the chain kernels of the last flush
+  std::vector<cudaEvent_t> ev_pool;
+  int ev_used = 0;
+};
+
+namespace {
+
+int fail(ops_ctx c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(ops_ctx c, cudaError_t e, const char* what) {
+  return fail(c, OPS_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(c, expr)                              \
+  do {                                                 \
+    cudaError_t e_ = (expr);                           \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr); \
+  } while (0)
+
+int dev_alloc(ops_ctx c, void** p, size_t bytes) {
+  if (c->cfg.hbm_budget > 0 && c->allocated + (int64_t)bytes > c->cfg.hbm_budget)
+    return fail(c, OPS_ERR_NOMEM, "allocation of %zu bytes exceeds the HBM budget (%lld of %lld used)", bytes,
+                (long long)c->allocated, (long long)c->cfg.hbm_budget);
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, OPS_ERR_NOMEM, "cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+  }
+  c->allocated += (int64_t)bytes;
+  return OPS_OK;
+}
+
+void dev_free(ops_ctx c, void* p, size_t bytes) {
+  if (p) {
+    cudaFree(p);
+    c->allocated -= (int64_t)bytes;
+  }
+}
+
+// Grow a device array to hold at least n elements (contents discarded).
+template <class T>
+int ensure(ops_ctx c, T** p, int* cap, int n) {
+  if (n <= *cap) return OPS_OK;
+  int nc = std::max(n, *cap * 2);
+  nc = std::max(nc, 16);
+  if (*p) {
+    cudaStreamSynchronize(c->stream);
+    dev_free(c, *p, sizeof(T) * (size_t)*cap);
+    *p = nullptr;
+    *cap = 0;
+  }
+  int rc = dev_alloc(c, (void**)p, sizeof(T) * (size_t)nc);
+  if (rc) return rc;
+  *cap = nc;
+  return OPS_OK;
+}
+
+bool valid_reg(int r) { return r >= 0 && r < kNReg; }
+
+double red_identity(int op) {
+  return op == OPS_RED_SUM ? 0.0 : (op == OPS_RED_MIN ? __builtin_inf() : -__builtin_inf());
+}
+
+LaunchEnv make_env(ops_ctx c) {
+  LaunchEnv env;
+  env.stream = c->stream;
+  env.num_sms = c->num_sms;
+  env.scal = c->d_scal;
+  env.part = c->d_part;
+  env.part_stride = c->part_stride;
+  env.rows = c->d_rows;
+  env.err = c->d_err;
+  env.bar = c->d_bar;
+  env.check = c->cfg.check;
+  env.timeout_ns = (long long)(c->cfg.timeout_ms > 0 ? c->cfg.timeout_ms : 2000) * 1000000ll;
+  env.skip_block = c->cfg.test_skip_barrier_block;
+  return env;
+}
+
+// ---------------------------------------------------------------------------
+// validation of one queued loop
+// ---------------------------------------------------------------------------
+int validate_loop(ops_ctx c, const QLoop& q) {
+  const int nargs = (int)q.args.size();
+  const int nK = (int)q.K.size();
+  int nreds = 0;
+  std::vector<int> seen_dat, seen_red;
+  for (int i = 0; i < nargs; ++i) {
+    const ops_arg& a = q.args[i];
+    if (a.kind == OPS_ARG_DAT) {
+      if (a.handle < 0 || a.handle >= (int)c->dats.size())
+        return fail(c, OPS_ERR_INVALID_ARG, "loop '%s' arg %d: bad dat handle %d", q.name.c_str(), i, a.handle);
+      if (c->dats[a.handle].block != q.block)
+        return fail(c, OPS_ERR_INVALID_ARG, "loop '%s' arg %d: dat on another block", q.name.c_str(), i);
+      if (a.stencil < 0 || a.stencil >= (int)c->stencils.size())
+        return fail(c, OPS_ERR_INVALID_ARG, "loop '%s' arg %d: bad stencil %d", q.name.c_str(), i, a.stencil);
+      if (a.access < OPS_READ || a.access > OPS_INC)
+        return fail(c, OPS_ERR_INVALID_ARG, "loop '%s' arg %d: bad access mode", q.name.c_str(), i);
+      if (std::find(seen_dat.begin(), seen_dat.end(), a.handle) != seen_dat.end())
+        return fail(c, OPS_ERR_INVALID_ARG, "loop '%s': dat %d appears twice", q.name.c_str(), a.handle);
+      seen_dat.push_back(a.handle);
+      const Stencil& s = c->stencils[a.stencil];
+      const int npts = (int)s.off.size() / 3;
+      if (a.access != OPS_READ) {
+        if (npts != 1 || s.off[0] || s.off[1] || s.off[2])
+          return fail(c, OPS_ERR_INVALID_ARG, "loop '%s' arg %d: a written dat must use the point stencil {0}",
+                      q.name.c_str(), i);
+      }
+      const Dat& D = c->dats[a.handle];
+      for (int d = 0; d < q.dims; ++d) {
+        if (q.rng[2 * d + 1] <= q.rng[2 * d]) continue;
+        const int lo = q.rng[2 * d] + s.lo[d], hi = q.rng[2 * d + 1] - 1 + s.hi[d];
+        if (lo < -D.dm[d] || hi >= D.size[d] + D.dp[d])
+          return fail(c, OPS_ERR_BOUNDS,
+                      "loop '%s' arg %d (dat '%s'): access [%d, %d] in dim %d outside [%d, %d)", q.name.c_str(), i,
+                      D.name.c_str(), lo, hi, d, -D.dm[d], D.size[d] + D.dp[d]);
+      }
+    } else if (a.kind == OPS_ARG_SCALAR || a.kind == OPS_ARG_RED) {
+      if (a.handle < 0 || a.handle >= (int)c->red_ops.size())
+        return fail(c, OPS_ERR_INVALID_ARG, "loop '%s' arg %d: bad reduction handle %d", q.name.c_str(), i, a.handle);
+      if (a.kind == OPS_ARG_RED) {
+        if (std::find(seen_red.begin(), seen_red.end(), a.handle) != seen_red.end())
+          return fail(c, OPS_ERR_INVALID_ARG, "loop '%s': reduction %d appears twice", q.name.c_str(), a.handle);
+        seen_red.push_back(a.handle);
+        ++nreds;
+      }
+    } else {
+      return fail(c, OPS_ERR_INVALID_ARG, "loop '%s' arg %d: bad kind %d", q.name.c_str(), i, a.kind);
+    }
+  }
+  if (nreds > OPS_MAX_REDS_PER_LOOP)
+    return fail(c, OPS_ERR_INVALID_ARG, "loop '%s': more than %d reductions", q.name.c_str(), OPS_MAX_REDS_PER_LOOP);
+  const int nins = (int)q.code.size() / 6;
+  auto is_dat = [&](int a) { return a >= 0 && a < nargs && q.args[a].kind == OPS_ARG_DAT; };
+  for (int pc = 0; pc < nins; ++pc) {
+    const int32_t* I = &q.code[6 * pc];
+    const int op = I[0], d = I[1], a = I[2], b = I[3], cc = I[4], e = I[5];
+    bool ok = true;
+    switch (op) {
+      case OPS_IR_LD:
+        ok = valid_reg(d) && a >= 0 && a < nargs;
+        if (ok && q.args[a].kind == OPS_ARG_DAT) {
+          const int acc = q.args[a].access;
+          ok = (acc == OPS_READ || acc == OPS_RW) && b >= 0 && b < (int)c->stencils[q.args[a].stencil].off.size() / 3;
+        } else if (ok) {
+          ok = q.args[a].kind == OPS_ARG_SCALAR && b == 0;
+        }
+        break;
+      case OPS_IR_CST: ok = valid_reg(d) && a >= 0 && a < nK; break;
+      case OPS_IR_ADD: case OPS_IR_SUB: case OPS_IR_MUL: case OPS_IR_DIV: case OPS_IR_MIN: case OPS_IR_MAX:
+        ok = valid_reg(d) && valid_reg(a) && valid_reg(b);
+        break;
+      case OPS_IR_FMA: ok = valid_reg(d) && valid_reg(a) && valid_reg(b) && valid_reg(cc); break;
+      case OPS_IR_SGT: ok = valid_reg(d) && valid_reg(a) && valid_reg(b) && valid_reg(cc) && valid_reg(e); break;
+      case OPS_IR_WSUM: case OPS_IR_WACC:
+        ok = valid_reg(d) && is_dat(a) && (q.args[a].access == OPS_READ || q.args[a].access == OPS_RW) && b >= 0 &&
+             b + (int)c->stencils[q.args[a].stencil].off.size() / 3 <= nK;
+        break;
+      case OPS_IR_POLY: ok = valid_reg(d) && valid_reg(a) && b >= 0 && cc >= 0 && b + cc < nK; break;
+      case OPS_IR_ST: ok = is_dat(d) && q.args[d].access != OPS_READ && valid_reg(a); break;
+      case OPS_IR_RED: ok = d >= 0 && d < nargs && q.args[d].kind == OPS_ARG_RED && valid_reg(a); break;
+      default: ok = false;
+    }
+    if (!ok)
+      return fail(c, OPS_ERR_INVALID_ARG, "loop '%s': malformed IR instruction %d (op %d %d %d %d %d %d)",
+                  q.name.c_str(), pc, op, d, a, b, cc, e);
+  }
+  return OPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// flush
+// ---------------------------------------------------------------------------
+void fill_dloop(ops_ctx c, const QLoop& q, DLoop& L, int part_row, std::vector<FoldRow>& rows) {
+  std::memset(&L, 0, sizeof L);
+  L.nargs = (int)q.args.size();
+  L.nins = (int)q.code.size() / 6;
+  for (int i = 0; i < 6; ++i) L.rng[i] = q.rng[i];
+  for (int d = q.dims; d < 3; ++d) {
+    L.rng[2 * d] = 0;
+    L.rng[2 * d + 1] = 1;
+  }
+  std::memcpy(L.ins, q.code.data(), sizeof(int32_t) * q.code.size());
+  std::memcpy(L.K, q.K.data(), sizeof(double) * q.K.size());
+  L.part_row = part_row;
+  int k = 0;
+  for (int i = 0; i < L.nargs; ++i) {
+    const ops_arg& a = q.args[i];
+    DArg& A = L.args[i];
+    A.kind = a.kind;
+    A.access = a.access;
+    if (a.kind == OPS_ARG_DAT) {
+      const Dat& D = c->dats[a.handle];
+      const Stencil& s = c->stencils[a.stencil];
+      A.ptr0 = D.ptr0;
+      A.pitch = D.pitch;
+      A.plane = D.plane;
+      A.npts = (int)s.off.size() / 3;
+      for (int p = 0; p < A.npts; ++p)
+        A.off[p] = (int32_t)(s.off[3 * p] + s.off[3 * p + 1] * D.pitch + s.off[3 * p + 2] * D.plane);
+      for (int d = 0; d < 3; ++d) {
+        A.alo[d] = -D.dm[d];
+        A.ahi[d] = D.size[d] + D.dp[d];
+        A.slo[d] = s.lo[d];
+        A.shi[d] = s.hi[d];
+      }
+    } else if (a.kind == OPS_ARG_SCALAR) {
+      A.slot = a.handle;
+    } else {
+      A.slot = k;
+      L.red_op[k] = c->red_ops[a.handle];
+      rows.push_back(FoldRow{a.handle, c->red_ops[a.handle]});
+      ++k;
+    }
+  }
+  L.nreds = k;
+}
+
+PLoop plan_loop(ops_ctx c, const QLoop& q) {
+  PLoop p;
+  for (int i = 0; i < 6; ++i) p.rng[i] = q.rng[i];
+  for (int d = q.dims; d < 3; ++d) {
+    p.rng[2 * d] = 0;
+    p.rng[2 * d + 1] = 1;
+  }
+  for (const ops_arg& a : q.args) {
+    PArg pa;
+    pa.kind = a.kind;
+    pa.dat = a.kind == OPS_ARG_DAT ? a.handle : -1;
+    pa.reads = a.kind == OPS_ARG_DAT && (a.access == OPS_READ || a.access == OPS_RW || a.access == OPS_INC);
+    pa.writes = a.kind == OPS_ARG_DAT && a.access != OPS_READ;
+    for (int d = 0; d < 3; ++d) {
+      pa.slo[d] = a.kind == OPS_ARG_DAT ? c->stencils[a.stencil].lo[d] : 0;
+      pa.shi[d] = a.kind == OPS_ARG_DAT ? c->stencils[a.stencil].hi[d] : 0;
+    }
+    p.args.push_back(pa);
+  }
+  return p;
+}
+
+// Automatic tile size (Sec. 4.C, adapted): bytes per grid point = 8 x the
+// number of distinct dats of the segment; rows stay whole (x untiled, so
+// every access is a long coalesced row) and the outermost tiled dimension
+// gets as many points as fit the L2 budget.
+void auto_tile(ops_ctx c, const std::vector<PLoop>& pl, int ndim, int tile[3]) {
+  std::vector<char> used(c->dats.size(), 0);
+  int ndat = 0;
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  for (const PLoop& p : pl) {
+    for (const PArg& a : p.args)
+      if (a.kind == OPS_ARG_DAT && !used[a.dat]) {
+        used[a.dat] = 1;
+        ++ndat;
+      }
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], p.rng[2 * d]);
+      hi[d] = std::max(hi[d], p.rng[2 * d + 1]);
+    }
+  }
+  const int64_t budget = c->cfg.l2_bytes > 0 ? c->cfg.l2_bytes : (c->l2_size > 0 ? c->l2_size * 3 / 4 : 96ll << 20);
+  const int64_t bpp = 8ll * std::max(1, ndat);
+  int64_t pts = std::max<int64_t>(1, budget / bpp);
+  for (int d = 0; d < 3; ++d) tile[d] = std::max(1, hi[d] - lo[d]);
+  // shrink the outermost dimensions first until a tile fits the budget
+  for (int d = ndim - 1; d >= 0; --d) {
+    int64_t inner = 1;
+    for (int e = 0; e < d; ++e) inner *= tile[e];
+    if (inner * tile[d] <= pts) break;
+    if (d == 0) {
+      tile[0] = (int)std::max<int64_t>(1, pts);
+    } else {
+      tile[d] = (int)std::max<int64_t>(1, pts / inner);
+      if (inner <= pts) break;
+    }
+  }
+}
+
+// Record a timing event on the context's stream (timing=1 only).
+int record_event(ops_ctx c) {
+  if (!c->cfg.timing) return OPS_OK;
+  if (c->ev_used == (int)c->ev_pool.size()) {
+    cudaEvent_t e;
+    CUDA_TRY(c, cudaEventCreate(&e));
+    c->ev_pool.push_back(e);
+  }
+  CUDA_TRY(c, cudaEventRecord(c->ev_pool[c->ev_used++], c->stream));
+  return OPS_OK;
+}
+
+int run_segment(ops_ctx c, int first, int count, int dl_base, const std::vector<DLoop>& hl) {
+  const QLoop& q0 = c->queue[first];
+  const int ndim = q0.dims;
+  int mode = c->cfg.mode;
+  if (mode == OPS_MODE_AUTO) mode = count >= 2 ? OPS_MODE_SKEWED : OPS_MODE_UNTILED;
+  if (mode == OPS_MODE_OVERLAPPED) mode = OPS_MODE_SKEWED;  // overlapped executor: see ops_set_mode
+  LaunchEnv env = make_env(c);
+  c->stats.mode = mode;
+  ++c->stats.segments;
+  c->stats.loops += count;
+  if (mode == OPS_MODE_UNTILED || count == 1) {
+    for (int i = 0; i < count; ++i) {
+      const QLoop& q = c->queue[first + i];
+      int box[6];
+      for (int k = 0; k < 6; ++k) box[k] = q.rng[k];
+      for (int d = q.dims; d < 3; ++d) {
+        box[2 * d] = 0;
+        box[2 * d + 1] = 1;
+      }
+      bool empty = false;
+      int64_t n = 1;
+      for (int d = 0; d < 3; ++d) {
+        if (box[2 * d + 1] <= box[2 * d]) empty = true;
+        n *= (int64_t)(box[2 * d + 1] - box[2 * d]);
+      }
+      const DLoop& L = hl[dl_base + i];
+      if (empty) continue;
+      c->stats.points += n;
+      const int grid = untiled_grid(env, box);
+      int rc = record_event(c);
+      if (rc) return rc;
+      CUDA_TRY(c, launch_untiled(env, c->d_loops + dl_base + i, box, grid));
+      rc = record_event(c);
+      if (rc) return rc;
+      ++c->stats.launches;
+      ++c->stats.kernel_launches;
+      if (L.nreds) {
+        CUDA_TRY(c, launch_fold(env, L.part_row, L.nreds, grid));
+        ++c->stats.launches;
+      }
+    }
+    return OPS_OK;
+  }
+  // skewed: plan lookup by the loop sequence (ranges, dats, stencils, access)
+  std::vector<PLoop> pl;
+  pl.reserve(count);
+  for (int i = 0; i < count; ++i) pl.push_back(plan_loop(c, c->queue[first + i]));
+  int tile[3] = {c->cfg.tile[0], c->cfg.tile[1], c->cfg.tile[2]};
+  if (tile[0] <= 0 || (ndim > 1 && tile[1] <= 0) || (ndim > 2 && tile[2] <= 0)) {
+    int at[3];
+    auto_tile(c, pl, ndim, at);
+    for (int d = 0; d < 3; ++d)
+      if (tile[d] <= 0) tile[d] = at[d];
+  }
+  std::vector<int> key;
+  key.push_back(ndim);
+  for (int d = 0; d < 3; ++d) key.push_back(tile[d]);
+  for (int i = 0; i < count; ++i) {
+    const QLoop& q = c->queue[first + i];
+    for (int k = 0; k < 6; ++k) key.push_back(q.rng[k]);
+    key.push_back((int)q.args.size());
+    for (const ops_arg& a : q.args) {
+      key.push_back(a.kind);
+      key.push_back(a.handle);
+      key.push_back(a.kind == OPS_ARG_DAT ? a.stencil : -1);
+      key.push_back(a.access);
+    }
+  }
+  CachedPlan* cp = nullptr;
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    cp = it->second.get();
+    ++c->stats.plan_cache_hits;
+  } else {
+    auto t0 = std::chrono::steady_clock::now();
+    std::unique_ptr<CachedPlan> np(new CachedPlan);
+    np->key = key;
+    build_skewed_ranges(pl, (int)c->dats.size(), ndim, tile, np->plan);
+    build_phases(pl, np->plan);
+    auto t1 = std::chrono::steady_clock::now();
+    c->stats.plan_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+    if (!np->plan.phases.empty()) {
+      int rc = dev_alloc(c, (void**)&np->d_phases, sizeof(Phase) * np->plan.phases.size());
+      if (rc) return rc;
+      CUDA_TRY(c, cudaMemcpyAsync(np->d_phases, np->plan.phases.data(), sizeof(Phase) * np->plan.phases.size(),
+                                  cudaMemcpyHostToDevice, c->stream));
+      CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    cp = np.get();
+    c->plans[key] = std::move(np);
+  }
+  const SkewedPlan& P = cp->plan;
+  int ntiles = 1;
+  for (int d = 0; d < 3; ++d) {
+    ntiles *= P.ntiles[d];
+    c->stats.tile[d] = P.tile[d];
+    c->stats.skew[d] = P.skew[d];
+  }
+  c->stats.tiles = ntiles;
+  c->stats.phases += (int)P.phases.size();
+  c->stats.barriers += P.nbarriers;
+  c->stats.points += P.points;
+  if (P.phases.empty()) return OPS_OK;
+  int row0 = -1, nrows = 0;
+  for (int i = 0; i < count; ++i) {
+    const DLoop& L = hl[dl_base + i];
+    if (L.nreds) {
+      if (row0 < 0) row0 = L.part_row;
+      nrows = L.part_row + L.nreds - row0;
+    }
+  }
+  if (nrows) {
+    CUDA_TRY(c, launch_part_init(env, row0, nrows));
+    ++c->stats.launches;
+  }
+  int rc = record_event(c);
+  if (rc) return rc;
+  CUDA_TRY(c, launch_skewed(env, c->d_loops + dl_base, cp->d_phases, (int)P.phases.size(), c->skewed_grid));
+  rc = record_event(c);
+  if (rc) return rc;
+  ++c->stats.launches;
+  ++c->stats.kernel_launches;
+  if (nrows) {
+    CUDA_TRY(c, launch_fold(env, row0, nrows, c->skewed_grid));
+    ++c->stats.launches;
+  }
+  return OPS_OK;
+}
+
+int flush(ops_ctx c) {
+  if (c->queue.empty()) return OPS_OK;
+  std::memset(&c->stats, 0, sizeof c->stats);
+  c->ev_used = 0;
+  if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context cannot execute loops");
+  const int n = (int)c->queue.size();
+  std::vector<DLoop> hl(n);
+  std::vector<FoldRow> rows;
+  for (int i = 0; i < n; ++i) fill_dloop(c, c->queue[i], hl[i], (int)rows.size(), rows);
+  int rc = ensure(c, &c->d_loops, &c->loops_cap, n);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_loops, hl.data(), sizeof(DLoop) * n, cudaMemcpyHostToDevice, c->stream));
+  if (!rows.empty()) {
+    rc = ensure(c, &c->d_rows, &c->rows_cap, (int)rows.size());
+    if (rc) return rc;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_rows, rows.data(), sizeof(FoldRow) * rows.size(), cudaMemcpyHostToDevice,
+                                c->stream));
+    int cap = c->part_rows_cap;
+    if ((int)rows.size() > cap) {
+      int want = std::max((int)rows.size(), 8);
+      if (c->d_part) {
+        cudaStreamSynchronize(c->stream);
+        dev_free(c, c->d_part, sizeof(DD) * (size_t)c->part_rows_cap * c->part_stride);
+        c->d_part = nullptr;
+      }
+      rc = dev_alloc(c, (void**)&c->d_part, sizeof(DD) * (size_t)want * c->part_stride);
+      if (rc) return rc;
+      c->part_rows_cap = want;
+    }
+  }
+  // segments end where a loop reads (SCALAR) a reduction that an earlier loop
+  // of the same segment reduces into: that is a dependency on every point
+  int first = 0;
+  const int seglim = c->cfg.segment > 0 ? c->cfg.segment : (1 << 30);
+  std::vector<int> reduced;
+  for (int i = 0; i <= n; ++i) {
+    bool cut = i == n || i - first >= seglim;
+    if (!cut) {
+      for (const ops_arg& a : c->queue[i].args)
+        if (a.kind == OPS_ARG_SCALAR && std::find(reduced.begin(), reduced.end(), a.handle) != reduced.end())
+          cut = true;
+      if (!cut && c->queue[i].dims != c->queue[first].dims) cut = true;
+      if (!cut && c->queue[i].block != c->queue[first].block) cut = true;
+    }
+    if (cut && i > first) {
+      rc = run_segment(c, first, i - first, first, hl);
+      if (rc) {
+        c->queue.clear();
+        return rc;
+      }
+      first = i;
+      reduced.clear();
+    }
+    if (i < n)
+      for (const ops_arg& a : c->queue[i].args)
+        if (a.kind == OPS_ARG_RED) reduced.push_back(a.handle);
+  }
+  c->queue.clear();
+  return OPS_OK;
+}
+
+int check_device_error(ops_ctx c) {
+  int h = 0;
+  CUDA_TRY(c, cudaMemcpyAsync(&h, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (h) {
+    CUDA_TRY(c, cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    if (h == kDevErrTimeout)
+      return fail(c, OPS_ERR_TIMEOUT, "a device-side wait exceeded %d ms", c->cfg.timeout_ms > 0 ? c->cfg.timeout_ms : 2000);
+    return fail(c, OPS_ERR_DEVICE_BOUNDS, "a kernel caught an out-of-range access (checked mode)");
+  }
+  return OPS_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void ops_config_default(ops_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->device = 0;
+  cfg->mode = OPS_MODE_AUTO;
+  cfg->timeout_ms = 2000;
+  cfg->test_skip_barrier_block = -1;
+}
+
+int ops_init(ops_ctx* out, const ops_config* cfg) {
+  if (!out) return OPS_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::unique_ptr<ops_ctx_s> c(new ops_ctx_s);
+  if (cfg) c->cfg = *cfg;
+  else ops_config_default(&c->cfg);
+  std::memset(&c->stats, 0, sizeof c->stats);
+  if (c->cfg.device < 0) {  // host-only: declarations, validation and planning
+    c->host_only = true;
+    *out = c.release();
+    return OPS_OK;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || c->cfg.device >= ndev) {
+    cudaGetLastError();
+    return OPS_ERR_NO_DEVICE;
+  }
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, c->cfg.device) != cudaSuccess) return OPS_ERR_NO_DEVICE;
+  if (prop.major != 10 || prop.minor != 3) return OPS_ERR_NO_DEVICE;
+  if (cudaSetDevice(c->cfg.device) != cudaSuccess) return OPS_ERR_NO_DEVICE;
+  c->num_sms = prop.multiProcessorCount;
+  c->l2_size = prop.l2CacheSize;
+  ops_ctx cp = c.get();
+  if (c->cfg.stream) {
+    c->stream = (cudaStream_t)c->cfg.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return OPS_ERR_CUDA;
+    c->own_stream = true;
+  }
+  int rc = dev_alloc(cp, (void**)&c->d_err, sizeof(int));
+  if (!rc) rc = dev_alloc(cp, (void**)&c->d_bar, 4 * sizeof(unsigned));
+  if (rc) return rc;
+  cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+  cudaMemsetAsync(c->d_bar, 0, 4 * sizeof(unsigned), c->stream);
+  c->skewed_grid = skewed_max_grid(c->num_sms, c->cfg.blocks_per_sm);
+  c->part_stride = std::max(c->skewed_grid, c->num_sms * 8);
+  if (c->skewed_grid <= 0) return OPS_ERR_CUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return OPS_ERR_CUDA;
+  *out = c.release();
+  return OPS_OK;
+}
+
+int ops_finalize(ops_ctx c) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  if (!c->host_only) {
+    cudaStreamSynchronize(c->stream);
+    for (Dat& d : c->dats) dev_free(c, d.alloc, d.bytes);
+    for (auto& kv : c->plans)
+      if (kv.second->d_phases) dev_free(c, kv.second->d_phases, sizeof(Phase) * kv.second->plan.phases.size());
+    dev_free(c, c->d_scal, sizeof(double) * (size_t)c->scal_cap);
+    dev_free(c, c->d_part, sizeof(DD) * (size_t)c->part_rows_cap * c->part_stride);
+    dev_free(c, c->d_rows, sizeof(FoldRow) * (size_t)c->rows_cap);
+    dev_free(c, c->d_loops, sizeof(DLoop) * (size_t)c->loops_cap);
+    dev_free(c, c->d_err, sizeof(int));
+    dev_free(c, c->d_bar, 4 * sizeof(unsigned));
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+  }
+  delete c;
+  return OPS_OK;
+}
+
+const char* ops_last_error(ops_ctx c) { return c ? c->err.c_str() : "null context"; }
+
+int ops_set_mode(ops_ctx c, int mode, const int* tile, int segment) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  if (mode < OPS_MODE_UNTILED || mode > OPS_MODE_AUTO) return fail(c, OPS_ERR_INVALID_ARG, "bad mode %d", mode);
+  c->cfg.mode = mode;
+  if (tile)
+    for (int d = 0; d < 3; ++d) c->cfg.tile[d] = tile[d];
+  c->cfg.segment = segment;
+  return OPS_OK;
+}
+
+int ops_decl_block(ops_ctx c, int dims, const char* name, int* out) {
+  if (!c || !out) return OPS_ERR_INVALID_ARG;
+  if (dims < 1 || dims > 3) return fail(c, OPS_ERR_INVALID_ARG, "block dims must be 1..3 (got %d)", dims);
+  c->blocks.push_back(Block{dims, name ? name : ""});
+  *out = (int)c->blocks.size() - 1;
+  return OPS_OK;
+}
+
+int ops_decl_dat(ops_ctx c, int block, const int size[3], const int d_m[3], const int d_p[3], double* dev_ptr0,
+                 int64_t pitch, int64_t plane, const char* name, int* out) {
+  if (!c || !out || !size || !d_m || !d_p) return OPS_ERR_INVALID_ARG;
+  if (block < 0 || block >= (int)c->blocks.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad block %d", block);
+  const int dims = c->blocks[block].dims;
+  Dat D;
+  D.block = block;
+  D.name = name ? name : "";
+  for (int d = 0; d < 3; ++d) {
+    D.size[d] = d < dims ? size[d] : 1;
+    D.dm[d] = d < dims ? d_m[d] : 0;
+    D.dp[d] = d < dims ? d_p[d] : 0;
+    if (D.size[d] < 1 || D.dm[d] < 0 || D.dp[d] < 0)
+      return fail(c, OPS_ERR_INVALID_ARG, "dat '%s': bad size/halo in dim %d", D.name.c_str(), d);
+    D.ext[d] = D.size[d] + D.dm[d] + D.dp[d];
+  }
+  if (dev_ptr0) {
+    if (pitch < D.ext[0] || plane < pitch * (D.ext[1] > 1 ? 1 : 0))
+      return fail(c, OPS_ERR_INVALID_ARG, "dat '%s': pitch/plane too small", D.name.c_str());
+    D.ptr0 = dev_ptr0;
+    D.pitch = pitch;
+    D.plane = plane;
+  } else {
+    // point x = 0 starts a 128-byte line: pad the row front to round_up(d_m, 16)
+    const int64_t xo = (D.dm[0] + 15) / 16 * 16;
+    D.pitch = (xo + D.size[0] + D.dp[0] + 15) / 16 * 16;
+    D.plane = D.pitch * D.ext[1];
+    D.bytes = sizeof(double) * (size_t)(D.plane * D.ext[2]);
+    if (!c->host_only) {
+      int rc = dev_alloc(c, (void**)&D.alloc, D.bytes);
+      if (rc) return rc;
+      CUDA_TRY(c, cudaMemsetAsync(D.alloc, 0, D.bytes, c->stream));
+      D.ptr0 = D.alloc + xo + D.pitch * D.dm[1] + D.plane * D.dm[2];
+    }
+  }
+  c->dats.push_back(D);
+  *out = (int)c->dats.size() - 1;
+  return OPS_OK;
+}
+
+int ops_decl_stencil(ops_ctx c, int dims, int npts, const int* offsets, const char* name, int* out) {
+  if (!c || !out || !offsets) return OPS_ERR_INVALID_ARG;
+  if (dims < 1 || dims > 3 || npts < 1 || npts > OPS_MAX_STENCIL_POINTS)
+    return fail(c, OPS_ERR_INVALID_ARG, "stencil: dims 1..3 and 1..%d points", OPS_MAX_STENCIL_POINTS);
+  Stencil s;
+  s.dims = dims;
+  s.name = name ? name : "";
+  s.off.assign(offsets, offsets + 3 * npts);
+  for (int d = 0; d < 3; ++d) {
+    s.lo[d] = 0;
+    s.hi[d] = 0;
+  }
+  for (int p = 0; p < npts; ++p)
+    for (int d = 0; d < 3; ++d) {
+      if (d >= dims && s.off[3 * p + d] != 0)
+        return fail(c, OPS_ERR_INVALID_ARG, "stencil '%s': offset in unused dim %d", s.name.c_str(), d);
+      s.lo[d] = std::min(s.lo[d], s.off[3 * p + d]);
+      s.hi[d] = std::max(s.hi[d], s.off[3 * p + d]);
+    }
+  c->stencils.push_back(s);
+  *out = (int)c->stencils.size() - 1;
+  return OPS_OK;
+}
+
+int ops_decl_reduction(ops_ctx c, int op, int* out) {
+  if (!c || !out) return OPS_ERR_INVALID_ARG;
+  if (op < OPS_RED_SUM || op > OPS_RED_MAX) return fail(c, OPS_ERR_INVALID_ARG, "bad reduction op %d", op);
+  const int h = (int)c->red_ops.size();
+  if (!c->host_only) {
+    int rc = flush(c);  // the slot array may be reallocated
+    if (rc) return rc;
+    if (h >= c->scal_cap) {
+      const int nc = std::max(16, 2 * c->scal_cap);
+      double* nd = nullptr;
+      rc = dev_alloc(c, (void**)&nd, sizeof(double) * nc);
+      if (rc) return rc;
+      if (c->d_scal) {
+        CUDA_TRY(c, cudaMemcpyAsync(nd, c->d_scal, sizeof(double) * c->scal_cap, cudaMemcpyDeviceToDevice, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        dev_free(c, c->d_scal, sizeof(double) * c->scal_cap);
+      }
+      c->d_scal = nd;
+      c->scal_cap = nc;
+    }
+    LaunchEnv env = make_env(c);
+    CUDA_TRY(c, launch_set_scalar(env, h, red_identity(op)));
+  }
+  c->red_ops.push_back(op);
+  *out = h;
+  return OPS_OK;
+}
+
+int ops_par_loop(ops_ctx c, int block, int dims, const int* range, int nargs, const ops_arg* args, int nins,
+                 const int32_t* code, int nconsts, const double* consts, const char* name) {
+  if (!c || !range || (nargs > 0 && !args) || (nins > 0 && !code) || (nconsts > 0 && !consts))
+    return OPS_ERR_INVALID_ARG;
+  if (block < 0 || block >= (int)c->blocks.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad block %d", block);
+  if (dims != c->blocks[block].dims) return fail(c, OPS_ERR_INVALID_ARG, "loop dims %d != block dims", dims);
+  if (nargs < 0 || nargs > OPS_MAX_ARGS || nins < 0 || nins > OPS_MAX_INS || nconsts < 0 || nconsts > OPS_MAX_CONSTS)
+    return fail(c, OPS_ERR_INVALID_ARG, "loop '%s': limits are %d args, %d instructions, %d constants",
+                name ? name : "", OPS_MAX_ARGS, OPS_MAX_INS, OPS_MAX_CONSTS);
+  QLoop q;
+  q.block = block;
+  q.dims = dims;
+  q.name = name ? name : "";
+  for (int d = 0; d < 3; ++d) {
+    q.rng[2 * d] = d < dims ? range[2 * d] : 0;
+    q.rng[2 * d + 1] = d < dims ? range[2 * d + 1] : 1;
+    if (q.rng[2 * d + 1] < q.rng[2 * d])
+      return fail(c, OPS_ERR_INVALID_ARG, "loop '%s': range end < start in dim %d", q.name.c_str(), d);
+  }
+  q.args.assign(args, args + nargs);
+  q.code.assign(code, code + 6 * nins);
+  q.K.assign(consts, consts + nconsts);
+  int rc = validate_loop(c, q);
+  if (rc) return rc;
+  c->queue.push_back(std::move(q));
+  return OPS_OK;
+}
+
+int ops_execute(ops_ctx c) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  return flush(c);
+}
+
+int ops_queue_clear(ops_ctx c) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  c->queue.clear();
+  return OPS_OK;
+}
+
+int ops_sync(ops_ctx c) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  int rc = flush(c);
+  if (rc) return rc;
+  if (c->host_only) return OPS_OK;
+  return check_device_error(c);
+}
+
+int ops_reduction_result(ops_ctx c, int red, double* host_out) {
+  if (!c || !host_out) return OPS_ERR_INVALID_ARG;
+  if (red < 0 || red >= (int)c->red_ops.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad reduction %d", red);
+  int rc = flush(c);
+  if (rc) return rc;
+  if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
+  CUDA_TRY(c, cudaMemcpyAsync(host_out, c->d_scal + red, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  rc = check_device_error(c);  // synchronises the stream
+  if (rc) return rc;
+  LaunchEnv env = make_env(c);
+  CUDA_TRY(c, launch_set_scalar(env, red, red_identity(c->red_ops[red])));
+  ++c->stats.launches;
+  return OPS_OK;
+}
+
+int ops_dat_fetch(ops_ctx c, int dat, double* host_out, int64_t nelems) {
+  if (!c || !host_out) return OPS_ERR_INVALID_ARG;
+  if (dat < 0 || dat >= (int)c->dats.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad dat %d", dat);
+  const Dat& D = c->dats[dat];
+  if (nelems != (int64_t)D.ext[0] * D.ext[1] * D.ext[2])
+    return fail(c, OPS_ERR_INVALID_ARG, "dat '%s': fetch needs %lld elements", D.name.c_str(),
+                (long long)D.ext[0] * D.ext[1] * D.ext[2]);
+  int rc = flush(c);
+  if (rc) return rc;
+  if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
+  const double* base = D.ptr0 - D.dm[0] - D.pitch * D.dm[1] - D.plane * D.dm[2];
+  for (int z = 0; z < D.ext[2]; ++z)
+    CUDA_TRY(c, cudaMemcpy2DAsync(host_out + (size_t)z * D.ext[0] * D.ext[1], sizeof(double) * D.ext[0],
+                                  base + (size_t)z * D.plane, sizeof(double) * D.pitch, sizeof(double) * D.ext[0],
+                                  D.ext[1], cudaMemcpyDeviceToHost, c->stream));
+  return check_device_error(c);
+}
+
+int ops_dat_upload(ops_ctx c, int dat, const double* host_in, int64_t nelems) {
+  if (!c || !host_in) return OPS_ERR_INVALID_ARG;
+  if (dat < 0 || dat >= (int)c->dats.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad dat %d", dat);
+  const Dat& D = c->dats[dat];
+  if (nelems != (int64_t)D.ext[0] * D.ext[1] * D.ext[2])
+    return fail(c, OPS_ERR_INVALID_ARG, "dat '%s': upload needs %lld elements", D.name.c_str(),
+                (long long)D.ext[0] * D.ext[1] * D.ext[2]);
+  if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
+  int rc = flush(c);
+  if (rc) return rc;
+  double* base = D.ptr0 - D.dm[0] - D.pitch * D.dm[1] - D.plane * D.dm[2];
+  for (int z = 0; z < D.ext[2]; ++z)
+    CUDA_TRY(c, cudaMemcpy2DAsync(base + (size_t)z * D.plane, sizeof(double) * D.pitch,
+                                  host_in + (size_t)z * D.ext[0] * D.ext[1], sizeof(double) * D.ext[0],
+                                  sizeof(double) * D.ext[0], D.ext[1], cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return OPS_OK;
+}
+
+int ops_dat_info(ops_ctx c, int dat, double** dev_ptr0, int64_t* pitch, int64_t* plane, int* ext) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  if (dat < 0 || dat >= (int)c->dats.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad dat %d", dat);
+  const Dat& D = c->dats[dat];
+  if (dev_ptr0) *dev_ptr0 = D.ptr0;
+  if (pitch) *pitch = D.pitch;
+  if (plane) *plane = D.plane;
+  if (ext)
+    for (int d = 0; d < 3; ++d) ext[d] = D.ext[d];
+  return OPS_OK;
+}
+
+int ops_last_stats(ops_ctx c, ops_flush_stats* out) {
+  if (!c || !out) return OPS_ERR_INVALID_ARG;
+  if (c->cfg.timing && c->ev_used >= 2) {
+    double ms = 0.0;
+    for (int i = 0; i + 1 < c->ev_used; i += 2) {
+      CUDA_TRY(c, cudaEventSynchronize(c->ev_pool[i + 1]));
+      float t = 0.f;
+      CUDA_TRY(c, cudaEventElapsedTime(&t, c->ev_pool[i], c->ev_pool[i + 1]));
+      ms += t;
+    }
+    c->stats.kernel_ms = ms;
+  }
+  *out = c->stats;
+  return OPS_OK;
+}
+
+int ops_plan_skewed(ops_ctx c, const int* tile, int* out_ntiles, int* out_ranges, int64_t cap) {
+  if (!c || !tile || !out_ntiles || !out_ranges) return OPS_ERR_INVALID_ARG;
+  if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
+  const int ndim = c->queue[0].dims;
+  std::vector<PLoop> pl;
+  for (const QLoop& q : c->queue) {
+    if (q.dims != ndim) return fail(c, OPS_ERR_INVALID_ARG, "queued loops of different dimensionality");
+    pl.push_back(plan_loop(c, q));
+  }
+  int t[3] = {1, 1, 1};
+  for (int d = 0; d < ndim; ++d) {
+    if (tile[d] < 1) return fail(c, OPS_ERR_INVALID_ARG, "tile sizes must be >= 1");
+    t[d] = tile[d];
+  }
+  SkewedPlan P;
+  build_skewed_ranges(pl, (int)c->dats.size(), ndim, t, P);
+  int64_t need = 0;
+  for (int d = 0; d < ndim; ++d) need += (int64_t)P.ranges[d].size();
+  if (need > cap) return fail(c, OPS_ERR_INVALID_ARG, "out_ranges needs %lld ints", (long long)need);
+  int64_t pos = 0;
+  for (int d = 0; d < ndim; ++d) {
+    out_ntiles[d] = P.ntiles[d];
+    std::memcpy(out_ranges + pos, P.ranges[d].data(), sizeof(int) * P.ranges[d].size());
+    pos += (int64_t)P.ranges[d].size();
+  }
+  return OPS_OK;
+}
+
+}  // extern "C"

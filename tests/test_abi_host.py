@@ -1,0 +1,176 @@
+"""Host-side checks of the C ABI: no GPU needed (host-only contexts)."""
+import ctypes as C
+import os
+import random
+import re
+
+import numpy as np
+import pytest
+
+import paper_1704_00693_gb300 as ops
+from paper_1704_00693_gb300 import _build
+from oracle import plan as oplan
+from synth import workloads as W
+from synth.program import DAT, READ, WRITE, RW, INC, BodyBuilder
+
+from bruteforce import check_skewed, random_chain
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _build.build()
+    return ops.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "opstile.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(ops_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 19
+    for n in names:
+        assert hasattr(lib, n), f"{n} declared in include/opstile.h but not exported"
+
+
+def host_ctx():
+    cfg = ops.ops_config_default()
+    cfg.device = ops.OPS_DEVICE_NONE
+    return ops.ops_init(cfg)
+
+
+def declare(ctx, chain):
+    b = ops.ops_decl_block(ctx, chain.ndim)
+    dats = [ops.ops_decl_dat(ctx, b, chain.size, chain.d_m, chain.d_p) for _ in chain.dats]
+    st = [ops.ops_decl_stencil(ctx, chain.ndim, s) for s in chain.stencils]
+    reds = [ops.ops_decl_reduction(ctx, op) for op in chain.reductions]
+    return b, dats, st, reds
+
+
+def enqueue(ctx, chain, b, dats, st, reds, loops=None):
+    for lp in (chain.loops if loops is None else loops):
+        args = [(a.kind, dats[a.handle] if a.kind == DAT else reds[a.handle], st[a.stencil] if a.kind == DAT else -1,
+                 a.access) for a in lp.args]
+        code = lp.code if lp.code.size else np.array([[ops.OPS_ARG_DAT, 0, 0, 0, 0, 0]], np.int32)[:0]
+        ops.ops_par_loop(ctx, b, chain.ndim, lp.rng, args, code, lp.consts, lp.name)
+
+
+def test_host_context_rejects_execution(lib):
+    ctx = host_ctx()
+    c = W.small2d(n=16, reps=1)
+    b, dats, st, reds = declare(ctx, c)
+    enqueue(ctx, c, b, dats, st, reds)
+    with pytest.raises(ops.OpsError) as e:
+        ops.ops_execute(ctx)
+    assert e.value.code == ops.OPS_ERR_NO_DEVICE
+    ops.ops_queue_clear(ctx)
+    ops.ops_finalize(ctx)
+
+
+def test_validation_errors(lib):
+    ctx = host_ctx()
+    b = ops.ops_decl_block(ctx, 2)
+    d0 = ops.ops_decl_dat(ctx, b, (8, 8, 1), (1, 1, 0), (1, 1, 0))
+    d1 = ops.ops_decl_dat(ctx, b, (8, 8, 1), (1, 1, 0), (1, 1, 0))
+    p0 = ops.ops_decl_stencil(ctx, 2, [(0, 0, 0)])
+    s5 = ops.ops_decl_stencil(ctx, 2, W.S5)
+    far = ops.ops_decl_stencil(ctx, 2, [(2, 0, 0)])
+    code, K = BodyBuilder().wsum(0, 0, [0.2] * 5).st(1, 0).build()
+    rng = ((0, 8), (0, 8))
+    ops.ops_par_loop(ctx, b, 2, rng, [(0, d0, s5, READ), (0, d1, p0, WRITE)], code, K)  # fine
+    # reads outside the halo
+    with pytest.raises(ops.OpsError) as e:
+        c2, K2 = BodyBuilder().wsum(0, 0, [1.0]).st(1, 0).build()
+        ops.ops_par_loop(ctx, b, 2, rng, [(0, d0, far, READ), (0, d1, p0, WRITE)], c2, K2)
+    assert e.value.code == ops.OPS_ERR_BOUNDS
+    # a written dat with a non-point stencil
+    with pytest.raises(ops.OpsError) as e:
+        ops.ops_par_loop(ctx, b, 2, rng, [(0, d0, s5, READ), (0, d1, s5, WRITE)], code, K)
+    assert e.value.code == ops.OPS_ERR_INVALID_ARG
+    # the same dat twice
+    with pytest.raises(ops.OpsError):
+        ops.ops_par_loop(ctx, b, 2, rng, [(0, d0, s5, READ), (0, d0, p0, WRITE)], code, K)
+    # malformed IR: register out of range, constant pool too short, LD of a WRITE arg
+    bad = code.copy()
+    bad[0, 1] = 9
+    with pytest.raises(ops.OpsError):
+        ops.ops_par_loop(ctx, b, 2, rng, [(0, d0, s5, READ), (0, d1, p0, WRITE)], bad, K)
+    with pytest.raises(ops.OpsError):
+        ops.ops_par_loop(ctx, b, 2, rng, [(0, d0, s5, READ), (0, d1, p0, WRITE)], code, K[:3])
+    c3, K3 = BodyBuilder().ld(0, 1, 0).st(1, 0).build()
+    with pytest.raises(ops.OpsError):
+        ops.ops_par_loop(ctx, b, 2, rng, [(0, d0, s5, READ), (0, d1, p0, WRITE)], c3, K3)
+    # INC store is allowed, reading an INC arg is not
+    c4, K4 = BodyBuilder().wsum(0, 0, [0.2] * 5).st(1, 0).build()
+    ops.ops_par_loop(ctx, b, 2, rng, [(0, d0, s5, READ), (0, d1, p0, INC)], c4, K4)
+    ops.ops_queue_clear(ctx)
+    ops.ops_finalize(ctx)
+
+
+def _abi_plan(chain_like, loops, stencils, ndim, tile):
+    ctx = host_ctx()
+    b = ops.ops_decl_block(ctx, ndim)
+    ndats = 1 + max(a.handle for lp in loops for a in lp.args if a.kind == DAT)
+    nreds = 1 + max([a.handle for lp in loops for a in lp.args if a.kind != DAT] + [-1])
+    size = [1, 1, 1]
+    for d in range(ndim):
+        size[d] = max(lp.rng[d][1] for lp in loops) + 2
+    dats = [ops.ops_decl_dat(ctx, b, size, [4 if d < ndim else 0 for d in range(3)],
+                             [4 if d < ndim else 0 for d in range(3)]) for _ in range(ndats)]
+    st = [ops.ops_decl_stencil(ctx, ndim, s) for s in stencils]
+    reds = [ops.ops_decl_reduction(ctx, ops.OPS_RED_SUM) for _ in range(nreds)]
+    for lp in loops:
+        args = [(a.kind, dats[a.handle], st[a.stencil], a.access) if a.kind == DAT else
+                (a.kind, reds[a.handle], -1, a.access) for a in lp.args]
+        # a minimal valid body: store 0 into every written arg
+        bb = BodyBuilder()
+        for i, a in enumerate(lp.args):
+            if a.kind == DAT and a.access != READ:
+                bb.st(i, 0)
+        code, K = bb.build()
+        ops.ops_par_loop(ctx, b, ndim, lp.rng[:ndim], args, code, K, lp.name)
+    out = ops.ops_plan_skewed(ctx, tile, ndim, len(loops))
+    ops.ops_queue_clear(ctx)
+    ops.ops_finalize(ctx)
+    return out
+
+
+def test_worked_example_through_abi(lib):
+    c = W.worked_example_1d()
+    out = _abi_plan(c, c.loops, c.stencils, 1, [4])
+    assert out[0][:, 0].tolist() == [[0, 5], [5, 8]]
+    assert out[0][:, 1].tolist() == [[0, 4], [4, 8]]
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_library_plan_matches_oracle_plan(lib, ndim):
+    """The C++ planner and the oracle's restatement of Algorithm 1 must give
+    identical integer ranges; the brute-force check validates them."""
+    rnd = random.Random(3000 + ndim)
+    sizes = {1: (30,), 2: (12, 10), 3: (7, 6, 5)}[ndim]
+    for trial in range({1: 60, 2: 30, 3: 10}[ndim]):
+        n = [rnd.randint(max(2, s // 2), s) for s in sizes]
+        loops, st = random_chain(rnd, ndim, n, ndats=rnd.randint(3, 5), nloops=rnd.randint(2, 7))
+        ts = [rnd.randint(1, n[d] + 2) for d in range(ndim)]
+        got = _abi_plan(None, loops, st, ndim, ts)
+        nt, rg, _ = oplan.skewed_plan(loops, st, ndim, ts)
+        for d in range(ndim):
+            want = np.array([[list(rg[d][t][l]) for l in range(len(loops))] for t in range(nt[d])])
+            assert got[d].shape == want.shape
+            assert (got[d] == want).all(), f"dim {d}: library {got[d].tolist()} oracle {want.tolist()}"
+        if trial < 8:
+            check_skewed(loops, st, ndim, nt, rg)
+
+
+def test_cloverleaf_shaped_plan_matches_oracle(lib):
+    c = W.cloverleaf2d(n=200, steps=1)
+    for tile in ([200, 17], [64, 50], [210, 210]):
+        got = _abi_plan(c, c.loops, c.stencils, 2, tile)
+        nt, rg, _ = oplan.skewed_plan(c.loops, c.stencils, 2, tile)
+        for d in range(2):
+            want = np.array([[list(rg[d][t][l]) for l in range(len(c.loops))] for t in range(nt[d])])
+            assert (got[d] == want).all()

@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA library against the FP64 oracle, through the C ABI.
+
+Every execution mode must reproduce the untiled program-order result of the
+oracle bit for bit (explicitly rounded IEEE operations on both sides, no
+contraction); reductions, whose summation order differs, within 1e-12
+relative of the exactly rounded oracle value (min/max exactly).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1704_00693_gb300 as ops
+from paper_1704_00693_gb300.chain import ChainRunner
+from synth import workloads as W
+from synth.program import (Arg, BodyBuilder, Chain, DatSpec, Loop, DAT, REDARG, SCALAR, READ, WRITE, RW, INC,
+                           RSUM, RMIN, RMAX, FMA, ADD, MUL)
+from synth import rng as R
+
+pytestmark = pytest.mark.gpu
+
+RED_TOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1704_00693_gb300 import _build
+    _build.build()
+    oracle.build()
+
+
+def run_gpu(chain, mode, tile=None, steps=None, **kw):
+    r = ChainRunner(chain, mode=mode, tile=tile, **kw)
+    try:
+        hist = r.run(steps)
+        dats = r.fetch()
+        stats = r.stats()
+    finally:
+        r.close()
+    return dats, hist, stats
+
+
+def assert_same(chain, got, ref, hist=None, ref_hist=None, what=""):
+    for k, (a, b) in enumerate(zip(got, ref)):
+        if not np.array_equal(a, b):
+            diff = np.argwhere(a != b)
+            raise AssertionError(f"{what}: dat {chain.dats[k].name} differs at {len(diff)} points, first {diff[:3]}, "
+                                 f"max abs diff {np.nanmax(np.abs(a - b))}")
+    if hist is not None:
+        for s, (h1, h2) in enumerate(zip(hist, ref_hist)):
+            for i, (v1, v2) in enumerate(zip(h1, h2)):
+                op = chain.reductions[i]
+                if op == RSUM:
+                    assert abs(v1 - v2) <= RED_TOL * abs(v2), f"{what}: step {s} sum {v1} vs {v2}"
+                else:
+                    assert v1 == v2, f"{what}: step {s} min/max {v1} vs {v2}"
+
+
+def test_worked_example_1d():
+    c = W.worked_example_1d()
+    ref, _ = oracle.run_chain(c)
+    for mode, tile in [("untiled", None), ("skewed", (4,)), ("skewed", (1,)), ("skewed", (3,))]:
+        got, _, st = run_gpu(c, mode, tile)
+        assert_same(c, got, ref, what=f"{mode} {tile}")
+
+
+@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 0, 0)), ("skewed", (0, 40, 0)),
+                                       ("skewed", (100, 33, 0))])
+def test_small2d_chain_bit_exact(mode, tile):
+    """8 loops x 10 repetitions on 256^2 (radius-1 stencils, zero halo)."""
+    c = W.small2d(n=256, reps=10)
+    ref, _ = oracle.run_chain(c)
+    got, _, st = run_gpu(c, mode, tile)
+    assert_same(c, got, ref, what=f"{mode} {tile}")
+    if mode == "skewed":
+        assert st["mode"] == ops.OPS_MODE_SKEWED
+
+
+@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 32, 0)), ("skewed", (0, 17, 0)),
+                                       ("skewed", (37, 23, 0)), ("skewed", (0, 0, 0)), ("auto", None)])
+def test_cloverleaf_shaped_chain(mode, tile):
+    """83-loop CloverLeaf-shaped steps on a 100^2 grid (ragged tiles), with
+    node ranges, thin halo strips, RW updates and two reductions per step;
+    the min reduction feeds the next step's constants."""
+    c = W.cloverleaf2d(n=100, steps=3)
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist, st = run_gpu(c, mode, tile)
+    assert_same(c, got, ref, hist, ref_hist, what=f"{mode} {tile}")
+
+
+def test_jacobi_eigenmode_closed_form_on_gpu():
+    n, K, nu = 63, 30, 0.125
+    c = W.jacobi2d(n, K, nu=nu, p=2, q=1)
+    ref, _ = oracle.run_chain(c)
+    got, _, st = run_gpu(c, "skewed", (0, 16, 0))
+    assert_same(c, got, ref, what="jacobi")
+    import math
+    lam = -4 * math.sin(math.pi * 2 / (2 * (n + 1))) ** 2 - 4 * math.sin(math.pi * 1 / (2 * (n + 1))) ** 2
+    want = c.dats[0].init * (1 + nu * lam) ** K
+    assert np.abs(got[0] - want).max() <= 1e-13 * np.abs(want).max()
+    assert st["barriers"] > 0 and st["tiles"] == 4
+
+
+def test_constant_and_linear_fields():
+    c = W.small2d(n=48, reps=2, constant=0.75)
+    got, _, _ = run_gpu(c, "skewed", (0, 10, 0))
+    for d in got:
+        assert (d == 0.75).all()
+    a0, bx, by = 0.5, 0.25, -0.375
+    c = W.linear2d(40, a0, bx, by)
+    ref, _ = oracle.run_chain(c)
+    got, _, _ = run_gpu(c, "skewed", (0, 7, 0))
+    assert_same(c, got, ref, what="linear")
+
+
+def test_opensbli_shaped_3d():
+    c = W.opensbli3d(n=20, steps=1)
+    ref, _ = oracle.run_chain(c)
+    for mode, tile in [("untiled", None), ("skewed", (0, 0, 6)), ("skewed", (0, 7, 5))]:
+        got, _, st = run_gpu(c, mode, tile)
+        assert_same(c, got, ref, what=f"3d {mode} {tile}")
+
+
+def edge_chain(n=30):
+    """Edge cases: an empty range, a one-point range, INC and RW updates, a
+    1-wide strip, a loop reading a reduction through a SCALAR argument
+    (splits the segment), MIN/MAX/SUM reductions, DIV and SGT."""
+    size, d_m, d_p = (n, n, 1), (2, 2, 0), (2, 2, 0)
+    shp = (1, n + 4, n + 4)
+    dats = [DatSpec(f"e{k}", R.uniform(R.subseed(99, "edge", k), shp, 0.5, 1.5)) for k in range(4)]
+    st = [[(0, 0, 0)], W.S5, W.S4P, [(-2, 0, 0), (2, 0, 0), (0, -2, 0), (0, 2, 0)]]
+    loops = []
+    c, K = BodyBuilder().wsum(0, 0, [0.2] * 5).st(1, 0).build()
+    loops.append(Loop("empty", ((5, 5), (0, n)), [Arg(DAT, 0, 1, READ), Arg(DAT, 1, 0, WRITE)], c, K))
+    loops.append(Loop("onept", ((3, 4), (7, 8)), [Arg(DAT, 0, 1, READ), Arg(DAT, 1, 0, WRITE)], c, K))
+    c, K = BodyBuilder().wsum(0, 0, [0.1, 0.2, 0.3, 0.1]).st(1, 0).build()
+    loops.append(Loop("inc", ((0, n), (0, n)), [Arg(DAT, 0, 2, READ), Arg(DAT, 2, 0, INC)], c, K))
+    bb = BodyBuilder().ld(0, 1, 0).ld(1, 0, 0).emit(7, 2, 0, 1)  # DIV
+    bb.cst(3, 1.0).emit(10, 4, 2, 3, 0, 1).st(1, 4)  # SGT
+    c, K = bb.build()
+    loops.append(Loop("rw_div_sgt", ((-1, n + 1), (0, n)), [Arg(DAT, 0, 0, READ), Arg(DAT, 1, 0, RW)], c, K))
+    c, K = BodyBuilder().wsum(0, 0, [0.25, 0.25, 0.25, 0.25]).st(1, 0).build()
+    loops.append(Loop("strip", ((0, n), (0, 1)), [Arg(DAT, 1, 3, READ), Arg(DAT, 3, 0, WRITE)], c, K))
+    bb = BodyBuilder().wsum(0, 0, [0.3, -0.1, 0.2, 0.05, 0.15]).red(1, 0).red(2, 0).red(3, 0)
+    c, K = bb.build()
+    loops.append(Loop("reds", ((0, n), (0, n)), [Arg(DAT, 2, 1, READ), Arg(REDARG, 0), Arg(REDARG, 1),
+                                                 Arg(REDARG, 2)], c, K))
+    bb = BodyBuilder().ld(0, 1, 0).ld(1, 2, 0).ld(2, 0, 0).emit(FMA, 3, 0, 2, 1).st(3, 3)
+    c, K = bb.build()
+    # min and max are exact whatever the order, so the dats stay bit-exact
+    loops.append(Loop("use_scalar", ((0, n), (0, n)), [Arg(DAT, 0, 0, READ), Arg(SCALAR, 1), Arg(SCALAR, 2),
+                                                       Arg(DAT, 3, 0, WRITE)], c, K))
+    c, K = BodyBuilder().wsum(0, 0, [0.5] + [0.125] * 4).st(1, 0).build()
+    loops.append(Loop("after", ((0, n), (0, n)), [Arg(DAT, 3, 1, READ), Arg(DAT, 0, 0, WRITE)], c, K))
+    return Chain("edge", 2, size, d_m, d_p, dats, st, [RSUM, RMIN, RMAX], loops, steps=2)
+
+
+@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 7, 0)), ("skewed", (11, 5, 0))])
+def test_edge_cases(mode, tile):
+    c = edge_chain()
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist, st = run_gpu(c, mode, tile)
+    assert_same(c, got, ref, hist, ref_hist, what=f"edge {mode} {tile}")
+
+
+def test_checked_mode_same_result():
+    c = W.cloverleaf2d(n=64, steps=1)
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist, _ = run_gpu(c, "skewed", (0, 16, 0), check=True)
+    assert_same(c, got, ref, hist, ref_hist, what="checked")
+
+
+def test_barrier_timeout_reports_and_context_recovers():
+    """One CTA never arrives at grid barriers: every wait gives up after the
+    limit, the kernel returns, the host sees OPS_ERR_TIMEOUT; a new context
+    on the same device then runs normally."""
+    c = W.small2d(n=64, reps=1)
+    r = ChainRunner(c, mode="skewed", tile=(0, 8, 0), timeout_ms=200, skip_barrier_block=0)
+    try:
+        r.enqueue_step()
+        with pytest.raises(ops.OpsError) as e:
+            ops.ops_sync(r.ctx)
+        assert e.value.code == ops.OPS_ERR_TIMEOUT
+    finally:
+        r.close()
+    ref, _ = oracle.run_chain(c)
+    got, _, _ = run_gpu(c, "skewed", (0, 8, 0))
+    assert_same(c, got, ref, what="after timeout")
+
+
+def test_plan_cache_reuse_and_stats():
+    c = W.cloverleaf2d(n=80, steps=3)
+    r = ChainRunner(c, mode="skewed", tile=(0, 20, 0))
+    try:
+        r.step()
+        s1 = r.stats()
+        r.step()
+        s2 = r.stats()
+    finally:
+        r.close()
+    assert s1["plan_cache_hits"] == 0 and s1["plan_ms"] > 0
+    assert s2["plan_cache_hits"] >= 1 and s2["plan_ms"] == 0
+    assert s2["tiles"] == 5 and s2["loops"] == len(c.loops)
+
+
+def test_full_size_cloverleaf_one_step():
+    """The benchmark's workload (3840^2, 83 loops, automatic tiles, the
+    benchmark's launch configuration) for one step, every point checked."""
+    c = W.cloverleaf2d(n=3840, steps=1)
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist, st = run_gpu(c, "skewed")
+    assert_same(c, got, ref, hist, ref_hist, what="full size")
+    assert st["tiles"] > 1
