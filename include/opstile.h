@@ -222,6 +222,60 @@ int ops_last_stats(ops_ctx ctx, ops_flush_stats* out);
  * cap is the number of ints out_ranges can hold. */
 int ops_plan_skewed(ops_ctx ctx, const int* tile, int* out_ntiles, int* out_ranges, int64_t cap);
 
+/* ---- one loop without any device allocation ----
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate device memory.  cudaMalloc and cudaFree can synchronise the whole
+ * GPU, which stalls every other stream of a process that serves requests
+ * concurrently; and a program whose device memory belongs to another
+ * allocator (a framework's caching allocator, a pool reserved up front)
+ * must not grow its footprint behind that allocator's back.  Such callers
+ * run a loop here instead of through a context.
+ *
+ * ops_loop_noalloc runs one parallel loop (same IR, same access rules, same
+ * kernel and bit-identical results as a single queued loop run by
+ * ops_par_loop + ops_execute) over caller-owned dats, and returns its
+ * reductions.  Its only scratch (loop descriptor, reduction partials and
+ * slots) is a fixed array of OPS_NOALLOC_SCRATCH_BYTES inside the library's
+ * device image: every GPU that loads the library holds it until the process
+ * exits.  No call allocates: no cudaMalloc, cudaFree or allocating library
+ * routine.
+ *   - The first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress, with that device current) and caches it; make
+ *     that first call before any stream capture on the device.
+ *   - Every call on a device shares the one array and overwrites what the
+ *     previous call left there; two calls whose work overlaps on the GPU
+ *     (different streams, no ordering between them) race and give wrong
+ *     results.  Order them on one stream, or synchronise in between.
+ *   - Requests beyond the fixed capacity (more than OPS_MAX_ARGS arguments,
+ *     OPS_MAX_INS instructions, OPS_MAX_CONSTS constants,
+ *     OPS_MAX_STENCIL_POINTS points per stencil or OPS_MAX_REDS_PER_LOOP
+ *     reductions) return OPS_ERR_NOMEM and launch nothing.
+ * Arguments, all host memory except the addresses inside views:
+ *   dims, range: as ops_par_loop; args[i].handle is ignored;
+ *   views[i]: for DAT args, the dat (address of grid point (0,0,0), strides,
+ *     allocation box [lo, hi) in grid coordinates; every access must lie
+ *     inside it, else OPS_ERR_BOUNDS);
+ *   stencil_npts[i], stencil_offsets: for DAT args, the number of stencil
+ *     points and their offsets (3 ints each), concatenated in argument order;
+ *   scalar_values[i]: the value a SCALAR arg reads;
+ *   red_ops[i]: OPS_RED_* of a RED arg; host_red_out[i] receives its result;
+ *   stream: cudaStream_t the work is ordered on (NULL = legacy stream).
+ * With reductions the call waits for the loop; without, it returns once the
+ * work is queued.  Other errors: OPS_ERR_INVALID_ARG (malformed IR or
+ * arguments), OPS_ERR_CUDA. */
+#define OPS_NOALLOC_SCRATCH_BYTES (128 * 1024)
+typedef struct {
+  double* ptr0;   /* device address of grid point (0,0,0) */
+  int64_t pitch;  /* elements between consecutive y */
+  int64_t plane;  /* elements between consecutive z */
+  int lo[3];      /* allocation box, grid coordinates, inclusive */
+  int hi[3];      /* exclusive */
+} ops_dat_view;
+int ops_loop_noalloc(int dims, const int* range, int nargs, const ops_arg* args, const ops_dat_view* views,
+                     const int* stencil_npts, const int* stencil_offsets, int nins, const int32_t* code,
+                     int nconsts, const double* consts, const double* scalar_values, const int* red_ops,
+                     double* host_red_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -237,3 +237,43 @@ def ops_plan_skewed(ctx, tile, ndim: int, nloops: int):
         out.append(buf[pos:pos + n].reshape(nt[d], nloops, 2).copy())
         pos += n
     return out
+
+
+# ------------------------------------------------ one loop, no device allocation
+class ops_dat_view(C.Structure):
+    _fields_ = [("ptr0", C.c_void_p), ("pitch", C.c_int64), ("plane", C.c_int64), ("lo", C.c_int * 3),
+                ("hi", C.c_int * 3)]
+
+
+def ops_loop_noalloc(dims: int, rng, args, views, stencils, code, consts, scalar_values=None, red_ops=None,
+                     stream: int = 0):
+    """Run one loop over caller-owned dats without allocating device memory.
+
+    args: (kind, access) per argument; views: per argument an ops_dat_view
+    (or None for non-dat args); stencils: per argument a list of 3-int
+    offsets (None for non-dat args); scalar_values / red_ops: per argument
+    (ignored where not SCALAR / RED).  Returns the per-argument reduction
+    results (None where not RED)."""
+    n = len(args)
+    r = np.zeros(6, dtype=np.int32)
+    for d in range(dims):
+        r[2 * d], r[2 * d + 1] = rng[d]
+    a = (ops_arg * max(1, n))(*[ops_arg(k, 0, 0, acc) for k, acc in args])
+    v = (ops_dat_view * max(1, n))(*[x if x is not None else ops_dat_view() for x in views])
+    npts = np.array([len(s) if s is not None else 0 for s in stencils], dtype=np.int32)
+    offs = [p for s in stencils if s is not None for p in s]
+    offs = np.ascontiguousarray(np.asarray(offs if offs else [(0, 0, 0)], dtype=np.int32).reshape(-1, 3))
+    code = np.ascontiguousarray(np.asarray(code, dtype=np.int32).reshape(-1, 6))
+    consts = np.ascontiguousarray(np.asarray(consts, dtype=np.float64).ravel())
+    sv = np.ascontiguousarray(np.asarray(scalar_values if scalar_values is not None else [0.0] * n, dtype=np.float64))
+    ro = np.ascontiguousarray(np.asarray(red_ops if red_ops is not None else [0] * n, dtype=np.int32))
+    out = np.full(max(1, n), np.nan)
+    rc = load().ops_loop_noalloc(C.c_int(dims), r.ctypes.data_as(C.POINTER(C.c_int)), C.c_int(n), a, v,
+                                 npts.ctypes.data_as(C.POINTER(C.c_int)), offs.ctypes.data_as(C.POINTER(C.c_int)),
+                                 C.c_int(code.shape[0]), code.ctypes.data_as(C.POINTER(C.c_int32)),
+                                 C.c_int(consts.size), consts.ctypes.data_as(C.POINTER(C.c_double)),
+                                 sv.ctypes.data_as(C.POINTER(C.c_double)), ro.ctypes.data_as(C.POINTER(C.c_int)),
+                                 out.ctypes.data_as(C.POINTER(C.c_double)), C.c_void_p(stream or None))
+    if rc != OPS_OK:
+        raise OpsError(rc, "ops_loop_noalloc failed")
+    return [float(out[i]) if args[i][0] == OPS_ARG_RED else None for i in range(n)]

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libopstile.so")
 
-SOURCES = ["runtime.cpp", "plan.cpp", "chain_kernels.cu"]
+SOURCES = ["runtime.cpp", "plan.cpp", "chain_kernels.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
