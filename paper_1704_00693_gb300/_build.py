@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
-BUILD = os.path.join(HERE, "_build")
+BUILD = os.environ.get("OPSTILE_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libopstile.so")
 
 SOURCES = ["runtime.cpp", "plan.cpp", "chain_kernels.cu", "noalloc.cu"]
@@ -59,6 +59,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(obj_dir, exist_ok=True)
     common = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
               "-I", INCLUDE, "-I", CSRC] + ARCH
+    # optional tuning macros, e.g. OPSTILE_NVCC_DEFS="OPS_PTS=2 OPS_MIN_CTAS=2"
+    common += ["-D" + d for d in os.environ.get("OPSTILE_NVCC_DEFS", "").split()]
 
     def compile_one(src: str) -> str:
         obj = os.path.join(obj_dir, os.path.basename(src) + ".o")

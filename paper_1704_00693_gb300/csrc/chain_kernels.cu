@@ -6,15 +6,39 @@
 // built with -fmad=false, so a point's value is bit-identical whatever the
 // schedule: untiled, skewed (Sec. 4.B, Algorithm 2) or overlapped (Sec. 4.D).
 //
-// FP64 on GB300 issues about two DFMA per clock per SM, so the interpreter's
-// integer work (dispatch, addressing) hides behind the FP64 pipe for any body
-// with a few fma per point; light bodies (copies) are bound by HBM.
+// Interpreter layout.  A thread owns a group of kPts points (consecutive
+// rows of one x, or kPts flattened points of a thin box).  Each instruction
+// is decoded once, warp-uniformly, from the shared-memory copy of the loop
+// and applied to the whole group: decoding is amortised over kPts points
+// and every stencil load comes with kPts independent siblings.  The eight IR
+// registers of every point live in shared memory as R[reg][point][thread]
+// (consecutive threads hit consecutive words: no bank conflicts, no local
+// memory).  FP64 on GB300 issues about two DFMA per clock per SM, so a body
+// with a handful of fma per point is bound by the FP64 pipe once the
+// interpreter's own instructions stay well below ~60 per FP64 instruction.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include "internal.h"
 
 namespace opstile {
+
+#ifndef OPS_PTS
+#define OPS_PTS 4
+#endif
+#ifndef OPS_MIN_CTAS
+#define OPS_MIN_CTAS 2
+#endif
+constexpr int kPts = OPS_PTS;  // points per thread
+
+// Shared memory of the chain kernels (dynamic, 16-byte aligned).
+struct ChainSmem {
+  DLoop L;
+  DD sh[32];                                 // block reductions
+  DD sred[OPS_MAX_REDS_PER_LOOP * kThreads]; // per-thread reduction accumulators
+  double R[kNReg * kPts * kThreads];         // IR registers [reg][point][thread]
+};
+constexpr size_t kChainSmem = sizeof(ChainSmem);
 
 // ----------------------------------------------------------------------------
 // compensated accumulation (Knuth's two-sum; order fixed by the launch shape)
@@ -39,6 +63,11 @@ __device__ __forceinline__ DD red_combine(int op, DD a, DD b) {
   if (op == OPS_RED_MIN) return DD{(b.hi < a.hi) ? b.hi : a.hi, 0.0};
   return DD{(b.hi > a.hi) ? b.hi : a.hi, 0.0};
 }
+__device__ __forceinline__ DD red_add(int op, DD a, double x) {
+  if (op == OPS_RED_SUM) return dd_add(a, x);
+  if (op == OPS_RED_MIN) return DD{(x < a.hi) ? x : a.hi, 0.0};
+  return DD{(x > a.hi) ? x : a.hi, 0.0};
+}
 __device__ __forceinline__ DD shfl_down_dd(DD v, int o) {
   return DD{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
 }
@@ -58,9 +87,18 @@ __device__ DD block_combine(int op, DD v, DD* sh) {
   return v;
 }
 
+__device__ __forceinline__ void red_init(ChainSmem& S) {
+  for (int k = 0; k < S.L.nreds; ++k) S.sred[k * kThreads + threadIdx.x] = DD{red_identity(S.L.red_op[k]), 0.0};
+}
+
 // ----------------------------------------------------------------------------
-// one grid point of one loop body
+// a group of points
 // ----------------------------------------------------------------------------
+struct Group {
+  int x[kPts], y[kPts], z[kPts];
+  unsigned mask;  // bit p: point p exists
+};
+
 __device__ __forceinline__ bool point_ok(const DLoop& L, int x, int y, int z) {
   if (x < L.rng[0] || x >= L.rng[1] || y < L.rng[2] || y >= L.rng[3] || z < L.rng[4] || z >= L.rng[5])
     return false;
@@ -74,82 +112,181 @@ __device__ __forceinline__ bool point_ok(const DLoop& L, int x, int y, int z) {
   return true;
 }
 
-__device__ __forceinline__ void run_point(const DLoop& L, int x, int y, int z, const double* __restrict__ scal,
-                                          DD* acc) {
-  double r[kNReg];
+// Address of the group's point p in the dat of argument A.
+__device__ __forceinline__ const double* gptr(const DArg& A, const Group& g, int p) {
+  return A.ptr0 + ((int64_t)g.x[p] + (int64_t)g.y[p] * A.pitch + (int64_t)g.z[p] * A.plane);
+}
+
+__device__ __forceinline__ void run_group(ChainSmem& S, const Group& g, const double* __restrict__ scal) {
+  const DLoop& L = S.L;
+  double* Rt = S.R + threadIdx.x;  // register r, point p at Rt[(r * kPts + p) * kThreads]
+  constexpr int RS = kPts * kThreads;
+  const unsigned m = g.mask;
+  for (int r = 0; r < kNReg; ++r)
+    if ((L.zmask >> r) & 1) {
 #pragma unroll
-  for (int i = 0; i < kNReg; ++i) r[i] = 0.0;
+      for (int p = 0; p < kPts; ++p) Rt[r * RS + p * kThreads] = 0.0;
+    }
   const int nins = L.nins;
   for (int pc = 0; pc < nins; ++pc) {
-    const int* I = L.ins[pc];
-    const int op = I[0], d = I[1], a = I[2], b = I[3];
+    const int2 i01 = *reinterpret_cast<const int2*>(&L.ins[pc][0]);
+    const int2 i23 = *reinterpret_cast<const int2*>(&L.ins[pc][2]);
+    const int2 i45 = *reinterpret_cast<const int2*>(&L.ins[pc][4]);
+    const int op = i01.x;
+    double* Rd = Rt + i01.y * RS;
+    const double* Ra = Rt + i23.x * RS;
+    const double* Rb = Rt + i23.y * RS;
     switch (op) {
       case OPS_IR_LD: {
-        const DArg& A = L.args[a];
+        const DArg& A = L.args[i23.x];
         if (A.kind == OPS_ARG_SCALAR) {
-          r[d] = scal[A.slot];
+          const double v = scal[A.slot];
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = v;
         } else {
-          r[d] = A.ptr0[x + y * A.pitch + z * A.plane + A.off[b]];
+          const int32_t o = A.off[i23.y];
+          double v[kPts];
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) v[p] = ((m >> p) & 1u) ? gptr(A, g, p)[o] : 0.0;
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = v[p];
         }
         break;
       }
-      case OPS_IR_CST: r[d] = L.K[a]; break;
-      case OPS_IR_ADD: r[d] = __dadd_rn(r[a], r[b]); break;
-      case OPS_IR_SUB: r[d] = __dsub_rn(r[a], r[b]); break;
-      case OPS_IR_MUL: r[d] = __dmul_rn(r[a], r[b]); break;
-      case OPS_IR_FMA: r[d] = __fma_rn(r[a], r[b], r[I[4]]); break;
-      case OPS_IR_DIV: r[d] = __ddiv_rn(r[a], r[b]); break;
-      case OPS_IR_MIN: r[d] = (r[b] < r[a]) ? r[b] : r[a]; break;
-      case OPS_IR_MAX: r[d] = (r[b] > r[a]) ? r[b] : r[a]; break;
-      case OPS_IR_SGT: r[d] = (r[a] > r[b]) ? r[I[4]] : r[I[5]]; break;
+      case OPS_IR_CST: {
+        const double v = L.K[i23.x];
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = v;
+        break;
+      }
+      case OPS_IR_ADD:
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = __dadd_rn(Ra[p * kThreads], Rb[p * kThreads]);
+        break;
+      case OPS_IR_SUB:
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = __dsub_rn(Ra[p * kThreads], Rb[p * kThreads]);
+        break;
+      case OPS_IR_MUL:
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = __dmul_rn(Ra[p * kThreads], Rb[p * kThreads]);
+        break;
+      case OPS_IR_DIV:
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = __ddiv_rn(Ra[p * kThreads], Rb[p * kThreads]);
+        break;
+      case OPS_IR_MIN:
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) {
+          const double a = Ra[p * kThreads], b = Rb[p * kThreads];
+          Rd[p * kThreads] = (b < a) ? b : a;
+        }
+        break;
+      case OPS_IR_MAX:
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) {
+          const double a = Ra[p * kThreads], b = Rb[p * kThreads];
+          Rd[p * kThreads] = (b > a) ? b : a;
+        }
+        break;
+      case OPS_IR_FMA: {
+        const double* Rc = Rt + i45.x * RS;
+#pragma unroll
+        for (int p = 0; p < kPts; ++p)
+          Rd[p * kThreads] = __fma_rn(Ra[p * kThreads], Rb[p * kThreads], Rc[p * kThreads]);
+        break;
+      }
+      case OPS_IR_SGT: {
+        const double* Rc = Rt + i45.x * RS;
+        const double* Re = Rt + i45.y * RS;
+#pragma unroll
+        for (int p = 0; p < kPts; ++p)
+          Rd[p * kThreads] = (Ra[p * kThreads] > Rb[p * kThreads]) ? Rc[p * kThreads] : Re[p * kThreads];
+        break;
+      }
       case OPS_IR_WSUM:
       case OPS_IR_WACC: {
-        const DArg& A = L.args[a];
-        const double* p = A.ptr0 + (x + y * A.pitch + z * A.plane);
-        const double* Kb = L.K + b;
+        const DArg& A = L.args[i23.x];
+        const double* Kb = L.K + i23.y;
         const int n = A.npts;
-        double t = r[d];
+        const double* base[kPts];
+        double t[kPts];
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) base[p] = gptr(A, g, p);
         int q = 0;
         if (op == OPS_IR_WSUM) {
-          t = __dmul_rn(Kb[0], p[A.off[0]]);
+          const int32_t o = A.off[0];
+          const double k = Kb[0];
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) t[p] = __dmul_rn(k, ((m >> p) & 1u) ? base[p][o] : 0.0);
           q = 1;
+        } else {
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) t[p] = Rd[p * kThreads];
         }
-        for (; q + 4 <= n; q += 4) {
-          const double v0 = p[A.off[q]], v1 = p[A.off[q + 1]], v2 = p[A.off[q + 2]], v3 = p[A.off[q + 3]];
-          t = __fma_rn(Kb[q], v0, t);
-          t = __fma_rn(Kb[q + 1], v1, t);
-          t = __fma_rn(Kb[q + 2], v2, t);
-          t = __fma_rn(Kb[q + 3], v3, t);
+        for (; q + 2 <= n; q += 2) {
+          const int32_t o0 = A.off[q], o1 = A.off[q + 1];
+          const double k0 = Kb[q], k1 = Kb[q + 1];
+          double v0[kPts], v1[kPts];
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) {
+            const bool on = (m >> p) & 1u;
+            v0[p] = on ? base[p][o0] : 0.0;
+            v1[p] = on ? base[p][o1] : 0.0;
+          }
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) t[p] = __fma_rn(k1, v1[p], __fma_rn(k0, v0[p], t[p]));
         }
-        for (; q < n; ++q) t = __fma_rn(Kb[q], p[A.off[q]], t);
-        r[d] = t;
+        if (q < n) {
+          const int32_t o = A.off[q];
+          const double k = Kb[q];
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) t[p] = __fma_rn(k, ((m >> p) & 1u) ? base[p][o] : 0.0, t[p]);
+        }
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = t[p];
         break;
       }
       case OPS_IR_POLY: {
-        const int c = I[4];
-        double t = L.K[b + c];
-        for (int i = c - 1; i >= 0; --i) t = __fma_rn(t, r[a], L.K[b + i]);
-        r[d] = t;
+        const int c = i45.x;
+        const double* Kb = L.K + i23.y;
+        double x[kPts], t[kPts];
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) {
+          x[p] = Ra[p * kThreads];
+          t[p] = Kb[c];
+        }
+        for (int i = c - 1; i >= 0; --i) {
+          const double k = Kb[i];
+#pragma unroll
+          for (int p = 0; p < kPts; ++p) t[p] = __fma_rn(t[p], x[p], k);
+        }
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = t[p];
         break;
       }
       case OPS_IR_ST: {
-        const DArg& A = L.args[d];
-        double* q = A.ptr0 + (x + y * A.pitch + z * A.plane);
-        if (A.access == OPS_INC)
-          *q = __dadd_rn(*q, r[a]);
-        else
-          *q = r[a];
+        const DArg& A = L.args[i01.y];
+        const bool inc = A.access == OPS_INC;
+#pragma unroll
+        for (int p = 0; p < kPts; ++p) {
+          if ((m >> p) & 1u) {
+            double* q = const_cast<double*>(gptr(A, g, p));
+            const double v = Ra[p * kThreads];
+            *q = inc ? __dadd_rn(*q, v) : v;
+          }
+        }
         break;
       }
       case OPS_IR_RED: {
-        const int k = L.args[d].slot;
+        const int k = L.args[i01.y].slot;
         const int rop = L.red_op[k];
-        if (rop == OPS_RED_SUM)
-          acc[k] = dd_add(acc[k], r[a]);
-        else if (rop == OPS_RED_MIN)
-          acc[k].hi = (r[a] < acc[k].hi) ? r[a] : acc[k].hi;
-        else
-          acc[k].hi = (r[a] > acc[k].hi) ? r[a] : acc[k].hi;
+        DD* slot = S.sred + k * kThreads + threadIdx.x;
+        DD acc = *slot;
+#pragma unroll
+        for (int p = 0; p < kPts; ++p)
+          if ((m >> p) & 1u) acc = red_add(rop, acc, Ra[p * kThreads]);
+        *slot = acc;
         break;
       }
       default:
@@ -165,55 +302,119 @@ __device__ __forceinline__ void stage_loop(DLoop* dst, const DLoop* src) {
   constexpr int n = sizeof(DLoop) / sizeof(int4);
   for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = s[i];
 }
-static_assert(sizeof(DLoop) % sizeof(int4) == 0, "DLoop must be a multiple of 16 bytes");
 
-// Run this CTA's share of `box` for the staged loop L.  Rows of at least 128
-// points are split into 256-wide x chunks (coalesced); thinner boxes are
-// flattened.  `part` is this CTA's unit index and `nparts` the number of CTAs.
-__device__ __forceinline__ void run_box(const DLoop& L, const int* box, const double* __restrict__ scal, DD* acc,
-                                        int part, int nparts, int check, int* err) {
+// Drop points that fail the checked-mode test, flagging the error word.
+__device__ __forceinline__ void check_group(const DLoop& L, Group& g, int* err) {
+#pragma unroll
+  for (int p = 0; p < kPts; ++p)
+    if (((g.mask >> p) & 1u) && !point_ok(L, g.x[p], g.y[p], g.z[p])) {
+      g.mask &= ~(1u << p);
+      atomicCAS(err, 0, kDevErrBounds);
+    }
+}
+
+// Run this CTA's share of `box` for the staged loop.  Boxes with rows of at
+// least 128 points are cut into units of 256 consecutive x by kPts
+// consecutive rows (a thread takes one x and kPts rows: coalesced loads, and
+// the rows share stencil neighbours in L1); thinner boxes are flattened into
+// units of 256 * kPts points.  Units are enumerated as part, part + nparts,
+// ... with coordinates advanced incrementally (no division in the loop).
+__device__ __forceinline__ void run_box(ChainSmem& S, const int* box, const double* __restrict__ scal, int part,
+                                        int nparts, int check, int* err) {
   const int x0 = box[0], nx = box[1] - box[0];
   const int y0 = box[2], ny = box[3] - box[2];
   const int z0 = box[4], nz = box[5] - box[4];
   if (nx <= 0 || ny <= 0 || nz <= 0) return;
+  Group g;
   if (nx >= 128) {
     const int xch = (nx + kThreads - 1) / kThreads;
-    const long long units = (long long)xch * ny * nz;
-    for (long long u = part; u < units; u += nparts) {
-      const int xc = (int)(u % xch);
-      const long long row = u / xch;
-      const int y = y0 + (int)(row % ny);
-      const int z = z0 + (int)(row / ny);
+    const int nrg = (ny + kPts - 1) / kPts;  // row groups per plane
+    const int nunits = xch * nrg * nz;
+    int u = part;
+    int xc = u % xch, rg = (u / xch) % nrg, z = u / (xch * nrg);
+    const int dxc = nparts % xch, drg = (nparts / xch) % nrg, dz = nparts / (xch * nrg);
+    while (u < nunits) {
       const int x = x0 + xc * kThreads + (int)threadIdx.x;
-      if (x < x0 + nx) {
-        if (check && !point_ok(L, x, y, z)) {
-          atomicCAS(err, 0, kDevErrBounds);
-          continue;
-        }
-        run_point(L, x, y, z, scal, acc);
+      g.mask = 0;
+#pragma unroll
+      for (int p = 0; p < kPts; ++p) {
+        const int y = rg * kPts + p;
+        g.x[p] = x;
+        g.y[p] = y0 + y;
+        g.z[p] = z0 + z;
+        if (x < x0 + nx && y < ny) g.mask |= 1u << p;
+      }
+      if (check) check_group(S.L, g, err);
+      if (g.mask) run_group(S, g, scal);
+      u += nparts;
+      xc += dxc;
+      rg += drg;
+      z += dz;
+      if (xc >= xch) {
+        xc -= xch;
+        ++rg;
+      }
+      if (rg >= nrg) {
+        rg -= nrg;
+        ++z;
       }
     }
   } else {
-    const long long npts = (long long)nx * ny * nz;
-    for (long long p = (long long)part * kThreads + threadIdx.x; p < npts; p += (long long)nparts * kThreads) {
-      const int x = x0 + (int)(p % nx);
-      const long long row = p / nx;
-      const int y = y0 + (int)(row % ny);
-      const int z = z0 + (int)(row / ny);
-      if (check && !point_ok(L, x, y, z)) {
-        atomicCAS(err, 0, kDevErrBounds);
-        continue;
+    const int npts = nx * ny * nz;
+    const int step = nparts * kThreads * kPts;
+    // point p of the thread's group: linear index i + p * kThreads
+    int i = part * kThreads * kPts + (int)threadIdx.x;
+    int x = i % nx, row = i / nx;
+    int y = row % ny, zz = row / ny;
+    const int dx = step % nx, drow = step / nx;
+    const int dy = drow % ny, dzz = drow / ny;
+    const int px = kThreads % nx, prow = kThreads / nx;
+    const int py = prow % ny, pz = prow / ny;
+    while (i < npts) {
+      g.mask = 0;
+      int xp = x, yp = y, zp = zz;
+#pragma unroll
+      for (int p = 0; p < kPts; ++p) {
+        g.x[p] = x0 + xp;
+        g.y[p] = y0 + yp;
+        g.z[p] = z0 + zp;
+        if (i + p * kThreads < npts) g.mask |= 1u << p;
+        xp += px;
+        yp += py;
+        zp += pz;
+        if (xp >= nx) {
+          xp -= nx;
+          ++yp;
+        }
+        if (yp >= ny) {
+          yp -= ny;
+          ++zp;
+        }
       }
-      run_point(L, x, y, z, scal, acc);
+      if (check) check_group(S.L, g, err);
+      if (g.mask) run_group(S, g, scal);
+      i += step;
+      x += dx;
+      y += dy;
+      zz += dzz;
+      if (x >= nx) {
+        x -= nx;
+        ++y;
+      }
+      if (y >= ny) {
+        y -= ny;
+        ++zz;
+      }
     }
   }
 }
 
 // Fold this CTA's reduction accumulators into its partial column (assign or combine).
-__device__ __forceinline__ void flush_partials(const DLoop& L, DD* acc, DD* part, int stride, DD* sh, bool assign) {
+__device__ __forceinline__ void flush_partials(ChainSmem& S, DD* part, int stride, bool assign) {
+  const DLoop& L = S.L;
   for (int k = 0; k < L.nreds; ++k) {
     const int op = L.red_op[k];
-    DD v = block_combine(op, acc[k], sh);
+    DD v = block_combine(op, S.sred[k * kThreads + threadIdx.x], S.sh);
     if (threadIdx.x == 0) {
       DD* dst = part + (size_t)(L.part_row + k) * stride + blockIdx.x;
       *dst = assign ? v : red_combine(op, *dst, v);
@@ -225,31 +426,32 @@ __device__ __forceinline__ void flush_partials(const DLoop& L, DD* acc, DD* part
 // ----------------------------------------------------------------------------
 // untiled: one launch per loop over a box (the comparator form)
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) k_untiled(const DLoop* __restrict__ gL, int bx0, int bx1, int by0,
-                                                      int by1, int bz0, int bz1, const double* __restrict__ scal,
-                                                      DD* part, int stride, int check, int* err) {
-  __shared__ __align__(16) DLoop L;
-  __shared__ DD sh[32];
-  stage_loop(&L, gL);
+__global__ void __launch_bounds__(kThreads, OPS_MIN_CTAS) k_untiled(const DLoop* __restrict__ gL, int bx0, int bx1,
+                                                                    int by0, int by1, int bz0, int bz1,
+                                                                    const double* __restrict__ scal, DD* part,
+                                                                    int stride, int check, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ChainSmem& S = *reinterpret_cast<ChainSmem*>(smem_raw);
+  stage_loop(&S.L, gL);
   __syncthreads();
-  DD acc[OPS_MAX_REDS_PER_LOOP];
-  for (int k = 0; k < OPS_MAX_REDS_PER_LOOP; ++k) acc[k] = DD{red_identity(k < L.nreds ? L.red_op[k] : 0), 0.0};
+  red_init(S);
   const int box[6] = {bx0, bx1, by0, by1, bz0, bz1};
-  run_box(L, box, scal, acc, blockIdx.x, gridDim.x, check, err);
-  if (L.nreds) flush_partials(L, acc, part, stride, sh, true);
+  run_box(S, box, scal, blockIdx.x, gridDim.x, check, err);
+  if (S.L.nreds) flush_partials(S, part, stride, true);
 }
 
 int untiled_grid(const LaunchEnv& env, const int* box) {
   const long long nx = box[1] - box[0], ny = box[3] - box[2], nz = box[5] - box[4];
-  long long units = nx >= 128 ? ((nx + kThreads - 1) / kThreads) * ny * nz : (nx * ny * nz + kThreads - 1) / kThreads;
+  long long units = nx >= 128 ? ((nx + kThreads - 1) / kThreads) * ((ny + kPts - 1) / kPts) * nz
+                              : (nx * ny * nz + (long long)kThreads * kPts - 1) / ((long long)kThreads * kPts);
   long long cap = (long long)env.num_sms * 8;
   if (units < 1) units = 1;
   return (int)(units < cap ? units : cap);
 }
 
 cudaError_t launch_untiled(const LaunchEnv& env, const DLoop* d_loop, const int* box, int grid) {
-  k_untiled<<<grid, kThreads, 0, env.stream>>>(d_loop, box[0], box[1], box[2], box[3], box[4], box[5], env.scal,
-                                               env.part, env.part_stride, env.check, env.err);
+  k_untiled<<<grid, kThreads, kChainSmem, env.stream>>>(d_loop, box[0], box[1], box[2], box[3], box[4], box[5],
+                                                        env.scal, env.part, env.part_stride, env.check, env.err);
   return cudaGetLastError();
 }
 
@@ -317,8 +519,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Sense-by-generation grid barrier with a wall-clock limit.  On timeout the
-// error word is set and every CTA leaves the kernel at its next barrier.
+// Grid barrier by arrival counter and generation, with a wall-clock limit.
+// On timeout the error word is set and every CTA leaves the kernel at its
+// next barrier.
 __device__ bool grid_barrier(unsigned* bar, int* err, long long timeout_ns, bool skip) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -353,15 +556,15 @@ __device__ bool grid_barrier(unsigned* bar, int* err, long long timeout_ns, bool
   return *(volatile int*)err == 0;
 }
 
-__global__ void __launch_bounds__(kThreads) k_skewed(const DLoop* __restrict__ loops, const Phase* __restrict__ phases,
-                                                     int nphases, const double* __restrict__ scal, DD* part,
-                                                     int stride, int check, int* err, unsigned* bar,
-                                                     long long timeout_ns, int skip_block) {
-  __shared__ __align__(16) DLoop L;
-  __shared__ DD sh[32];
+__global__ void __launch_bounds__(kThreads, OPS_MIN_CTAS) k_skewed(const DLoop* __restrict__ loops,
+                                                                   const Phase* __restrict__ phases, int nphases,
+                                                                   const double* __restrict__ scal, DD* part,
+                                                                   int stride, int check, int* err, unsigned* bar,
+                                                                   long long timeout_ns, int skip_block) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ChainSmem& S = *reinterpret_cast<ChainSmem*>(smem_raw);
   const bool skip = (int)blockIdx.x == skip_block;
   int cur = -1;
-  DD acc[OPS_MAX_REDS_PER_LOOP];
   for (int ph = 0; ph < nphases; ++ph) {
     const Phase P = phases[ph];
     if (P.barrier && ph > 0) {
@@ -369,19 +572,25 @@ __global__ void __launch_bounds__(kThreads) k_skewed(const DLoop* __restrict__ l
     }
     if (P.loop != cur) {
       __syncthreads();
-      stage_loop(&L, loops + P.loop);
+      stage_loop(&S.L, loops + P.loop);
       __syncthreads();
       cur = P.loop;
     }
-    for (int k = 0; k < OPS_MAX_REDS_PER_LOOP; ++k) acc[k] = DD{red_identity(k < L.nreds ? L.red_op[k] : 0), 0.0};
-    run_box(L, P.box, scal, acc, blockIdx.x, gridDim.x, check, err);
-    if (L.nreds) flush_partials(L, acc, part, stride, sh, false);
+    red_init(S);
+    run_box(S, P.box, scal, blockIdx.x, gridDim.x, check, err);
+    if (S.L.nreds) flush_partials(S, part, stride, false);
   }
+}
+
+cudaError_t chain_kernels_setup() {
+  cudaError_t e = cudaFuncSetAttribute(k_untiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_skewed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kChainSmem);
 }
 
 int skewed_max_grid(int num_sms, int blocks_per_sm) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_skewed, kThreads, 0) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_skewed, kThreads, kChainSmem) != cudaSuccess) return 0;
   if (blocks_per_sm > 0 && blocks_per_sm < per_sm) per_sm = blocks_per_sm;
   return per_sm * num_sms;
 }
@@ -401,7 +610,8 @@ cudaError_t launch_skewed(const LaunchEnv& env, const DLoop* d_loops, const Phas
   long long a9 = env.timeout_ns;
   int a10 = env.skip_block;
   void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10};
-  return cudaLaunchCooperativeKernel((const void*)k_skewed, dim3(grid), dim3(kThreads), args, 0, env.stream);
+  return cudaLaunchCooperativeKernel((const void*)k_skewed, dim3(grid), dim3(kThreads), args, kChainSmem,
+                                     env.stream);
 }
 
 }  // namespace opstile

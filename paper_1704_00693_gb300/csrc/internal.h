@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "opstile.h"
@@ -11,6 +12,9 @@ namespace opstile {
 
 constexpr int kNReg = 8;
 constexpr int kThreads = 256;  // threads per CTA of every chain kernel
+// Kernels index the points of one loop with 32-bit ints (plus a grid-stride
+// margin), so a loop covers fewer than 2^31 - 2^24 points.
+constexpr int kMaxLoopPoints = (1 << 30) + ((1 << 30) - (1 << 24));
 
 // Device error word values (first writer wins).
 constexpr int kDevErrTimeout = 1;
@@ -36,11 +40,40 @@ struct DLoop {
   int rng[6];                          // declared range x0 x1 y0 y1 z0 z1
   int red_op[OPS_MAX_REDS_PER_LOOP];   // OPS_RED_* of each reduction
   int part_row;                        // first partial row of this loop's reductions
-  int pad_;
+  int zmask;                           // registers read before written (start at +0.0)
+  int pad_;                            // header = 16 ints: ins rows start 8-byte aligned
   int ins[OPS_MAX_INS][6];
   double K[OPS_MAX_CONSTS];
   DArg args[OPS_MAX_ARGS];
 };
+
+// Host side: registers of a filled DLoop that an instruction reads before any
+// instruction writes them; only those are zeroed per point.
+inline void finish_dloop(DLoop& L) {
+  int written = 0, zmask = 0;
+  auto rd = [&](int r) {
+    if (!((written >> r) & 1)) zmask |= 1 << r;
+  };
+  for (int pc = 0; pc < L.nins; ++pc) {
+    const int* I = L.ins[pc];
+    const int op = I[0], d = I[1], a = I[2], b = I[3], c = I[4], e = I[5];
+    switch (op) {
+      case OPS_IR_ADD: case OPS_IR_SUB: case OPS_IR_MUL: case OPS_IR_DIV: case OPS_IR_MIN: case OPS_IR_MAX:
+        rd(a); rd(b); break;
+      case OPS_IR_FMA: rd(a); rd(b); rd(c); break;
+      case OPS_IR_SGT: rd(a); rd(b); rd(c); rd(e); break;
+      case OPS_IR_WACC: rd(d); break;
+      case OPS_IR_POLY: rd(a); break;
+      case OPS_IR_ST: case OPS_IR_RED: rd(a); break;
+      default: break;
+    }
+    if (op != OPS_IR_ST && op != OPS_IR_RED) written |= 1 << d;
+  }
+  L.zmask = zmask;
+}
+
+static_assert(offsetof(DLoop, ins) % 16 == 0, "instruction rows are read as int2");
+static_assert(sizeof(DLoop) % 16 == 0, "DLoop is staged with 16-byte copies");
 
 // A (tile, loop) piece of a skewed segment, in execution order.
 struct Phase {
@@ -75,6 +108,8 @@ struct LaunchEnv {
 };
 
 // Launch helpers implemented in chain_kernels.cu.
+// chain_kernels_setup: once per device (opts the kernels into their shared memory).
+cudaError_t chain_kernels_setup();
 int untiled_grid(const LaunchEnv& env, const int* box);
 cudaError_t launch_untiled(const LaunchEnv& env, const DLoop* d_loop, const int* box, int grid);
 cudaError_t launch_part_init(const LaunchEnv& env, int row0, int nrows);

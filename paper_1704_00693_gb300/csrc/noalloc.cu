@@ -57,6 +57,8 @@ cudaError_t scratch_for_current_device(unsigned char** out, int* num_sms) {
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
+    e = chain_kernels_setup();
+    if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = (unsigned char*)p;
     g_num_sms[dev] = sms;
   }
@@ -91,6 +93,8 @@ extern "C" int ops_loop_noalloc(int dims, const int* range, int nargs, const ops
     L.rng[2 * d + 1] = d < dims ? range[2 * d + 1] : 1;
     if (L.rng[2 * d + 1] < L.rng[2 * d]) return OPS_ERR_INVALID_ARG;
   }
+  if ((int64_t)(L.rng[1] - L.rng[0]) * (L.rng[3] - L.rng[2]) * (L.rng[5] - L.rng[4]) > (int64_t)kMaxLoopPoints)
+    return OPS_ERR_INVALID_ARG;
   double scal[64] = {0.0};
   FoldRow rows[8] = {};
   int nreds = 0, off_pos = 0;
@@ -185,6 +189,7 @@ extern "C" int ops_loop_noalloc(int dims, const int* range, int nargs, const ops
     }
     if (!ok) return OPS_ERR_INVALID_ARG;
   }
+  finish_dloop(L);
   // ---- scratch and launch shape ----
   unsigned char* S = nullptr;
   int sms = 0;

@@ -232,6 +232,11 @@ int validate_loop(ops_ctx c, const QLoop& q) {
   }
   if (nreds > OPS_MAX_REDS_PER_LOOP)
     return fail(c, OPS_ERR_INVALID_ARG, "loop '%s': more than %d reductions", q.name.c_str(), OPS_MAX_REDS_PER_LOOP);
+  int64_t npts = 1;
+  for (int d = 0; d < 3; ++d) npts *= (int64_t)(q.rng[2 * d + 1] - q.rng[2 * d]);
+  if (npts > (int64_t)kMaxLoopPoints)
+    return fail(c, OPS_ERR_INVALID_ARG, "loop '%s': %lld points, at most %d per loop", q.name.c_str(),
+                (long long)npts, kMaxLoopPoints);
   const int nins = (int)q.code.size() / 6;
   auto is_dat = [&](int a) { return a >= 0 && a < nargs && q.args[a].kind == OPS_ARG_DAT; };
   for (int pc = 0; pc < nins; ++pc) {
@@ -316,6 +321,7 @@ void fill_dloop(ops_ctx c, const QLoop& q, DLoop& L, int part_row, std::vector<F
     }
   }
   L.nreds = k;
+  finish_dloop(L);
 }
 
 PLoop plan_loop(ops_ctx c, const QLoop& q) {
@@ -643,6 +649,7 @@ int ops_init(ops_ctx* out, const ops_config* cfg) {
   if (rc) return rc;
   cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
   cudaMemsetAsync(c->d_bar, 0, 4 * sizeof(unsigned), c->stream);
+  if (chain_kernels_setup() != cudaSuccess) return OPS_ERR_CUDA;
   c->skewed_grid = skewed_max_grid(c->num_sms, c->cfg.blocks_per_sm);
   c->part_stride = std::max(c->skewed_grid, c->num_sms * 8);
   if (c->skewed_grid <= 0) return OPS_ERR_CUDA;
