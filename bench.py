@@ -32,7 +32,7 @@ if ROOT not in sys.path:
 
 N_DEFAULT = 3840
 WORKLOAD = "cloverleaf2d-shaped chain: 3840^2 FP64, halo 2, 25 dats U(0.5,1.5), 83 loops + 1 sum + 1 min reduction per step"
-PROFILE = os.path.join(ROOT, "profiles", "k_skewed_cloverleaf2d_3840.md")
+PROFILE = os.path.join(ROOT, "profiles", "chain_cloverleaf2d_3840.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_1704_00693_gb300", "csrc", "chain_kernels.cu")
 # FP64: 2 DFMA per clock per SM on GB300 (measured 1.97 at 1995 MHz), fma = 2 flops
 FP64_DFMA_PER_CLK_SM = 2
@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--mode", default="skewed", choices=["skewed", "untiled", "auto"])
+    p.add_argument("--mode", default="auto", choices=["skewed", "untiled", "auto"])
     p.add_argument("--tile", default="", help="x,y tile (0 = automatic)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -120,9 +120,10 @@ def workload_numbers(chain):
     return U, flops
 
 
-def profile_traffic():
-    """dram bytes per launch of k_skewed from the committed ncu summary, if it
-    was taken on the current kernel source."""
+def profile_traffic(schedule, tile):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source with the same
+    schedule (mode and tile)."""
     try:
         txt = open(PROFILE).read()
     except OSError:
@@ -134,6 +135,9 @@ def profile_traffic():
             k, v = line.strip()[2:].split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_sha256_16") != src_hash:
+        return None
+    want = schedule if tile is None else f"{schedule} {tile[0]}x{tile[1]}"
+    if vals.get("schedule") != want:
         return None
     try:
         return float(vals["dram_bytes_per_launch_full_size"])
@@ -147,6 +151,11 @@ def time_mode(chain, mode, tile, steps, warmup, stream, torch):
     try:
         for _ in range(warmup):
             r.step()
+        # in auto mode, keep warming up until the autotuner has timed every candidate
+        extra = 0
+        while mode == "auto" and r.stats()["tuning"] and extra < 24:
+            r.step()
+            extra += 1
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -303,10 +312,13 @@ def main():
         untiled = {"value": U * args.steps / (ums * 1e-3) / 1e9, "ms_per_step": ums / args.steps,
                    "kernel_ms_per_step": ukms / args.steps, "kernel_launches_per_step": ukl / args.steps}
 
+    # the schedule the timed steps ran (the autotuner's pick in auto mode)
+    chosen_mode = {0: "untiled", 1: "skewed", 2: "overlapped"}.get(st["mode"], "skewed") if st else args.mode
+    chosen_tile = list(st["tile"]) if st and chosen_mode != "untiled" else None
     e2e = None
     if not args.no_e2e:
         esteps = max(1, min(3, args.steps))
-        ems, bi = time_e2e(chain, args.mode, tile, esteps, stream, torch)
+        ems, bi = time_e2e(chain, chosen_mode, chosen_tile, esteps, stream, torch)
         e2e = {"value": U * esteps / (ems * 1e-3) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": bi,
                "d2h_bytes_per_step": bi, "ms_per_step": ems / esteps}
 
@@ -323,10 +335,10 @@ def main():
     flops_per_launch = flops / launches_per_step
     achieved = flops_per_launch / (kernel_ms_per_launch * 1e-3) / 1e12
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    traffic = profile_traffic() if args.mode == "skewed" and args.n == N_DEFAULT else None
+    traffic = profile_traffic(chosen_mode, chosen_tile) if args.n == N_DEFAULT else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": "k_skewed" if args.mode != "untiled" else "k_untiled",
+                "kernel": "k_skewed" if chosen_mode == "skewed" else "k_untiled",
                 "peak_source": f"FP64: {NUM_SMS} SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 flop x {sm_max:.0f} MHz "
                                "(unit count from a GB300 probe; MEASURED_PEAKS.json has no FP64 figure)",
                 "kernel_ms_per_launch": kernel_ms_per_launch,
@@ -344,7 +356,8 @@ def main():
     line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "mode": args.mode, "tile": st["tile"] if st else None,
+            "config": {"workload": WORKLOAD, "mode": args.mode, "schedule": chosen_mode,
+                       "tile": st["tile"] if st else None,
                        "tiles": st["tiles"] if st else None, "l2": "inputs larger than L2 (25 dats, 3.0 GB)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "untiled_bytes_per_step": U, "flops_per_step": flops},

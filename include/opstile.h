@@ -208,6 +208,7 @@ typedef struct {
   double kernel_ms;      /* timing=1: device time of the flush's chain kernels (persistent kernel,
                             or the per-loop kernels), measured with CUDA events on the context's stream */
   int kernel_launches;   /* chain kernels covered by kernel_ms */
+  int tuning;            /* OPS_MODE_AUTO: 1 while the autotuner is still timing candidates */
 } ops_flush_stats;
 /* Statistics of the most recent flush; with timing=1 this waits for that
  * flush's kernels to finish. */

@@ -59,7 +59,8 @@ class ops_flush_stats(C.Structure):
     _fields_ = [("plan_ms", C.c_double), ("segments", C.c_int), ("loops", C.c_int), ("tiles", C.c_int),
                 ("phases", C.c_int), ("barriers", C.c_int), ("launches", C.c_int), ("plan_cache_hits", C.c_int),
                 ("mode", C.c_int), ("tile", C.c_int * 3), ("redundant_points", C.c_int64), ("points", C.c_int64),
-                ("skew", C.c_int * 3), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int)]
+                ("skew", C.c_int * 3), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int),
+                ("tuning", C.c_int)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k in ("tile", "skew") else getattr(self, k))

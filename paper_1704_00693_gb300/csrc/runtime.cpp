@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -59,6 +60,15 @@ struct CachedPlan {
   Phase* d_phases = nullptr;
 };
 
+// Autotuning state of one segment signature.
+struct TuneRec {
+  std::vector<std::array<int, 4>> cand;  // (mode, tile x, tile y, tile z)
+  std::vector<double> ms;                // device time of each candidate (-1: not yet run)
+  int pending = -1;                      // candidate whose events are outstanding
+  int best = -1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
 }  // namespace
 
 struct ops_ctx_s {
@@ -87,6 +97,7 @@ struct ops_ctx_s {
   int loops_cap = 0;
   int skewed_grid = 0;
   std::map<std::vector<int>, std::unique_ptr<CachedPlan>> plans;
+  std::map<std::vector<int>, TuneRec> tune;
   int64_t allocated = 0;
   std::string err;
   ops_flush_stats stats;
@@ -395,12 +406,11 @@ int record_event(ops_ctx c) {
   return OPS_OK;
 }
 
-int run_segment(ops_ctx c, int first, int count, int dl_base, const std::vector<DLoop>& hl) {
+// Execute a segment in a given mode; tile_in entries <= 0 are chosen automatically.
+int run_segment_mode(ops_ctx c, int first, int count, int dl_base, const std::vector<DLoop>& hl, int mode,
+                     const int* tile_in) {
   const QLoop& q0 = c->queue[first];
   const int ndim = q0.dims;
-  int mode = c->cfg.mode;
-  if (mode == OPS_MODE_AUTO) mode = count >= 2 ? OPS_MODE_SKEWED : OPS_MODE_UNTILED;
-  if (mode == OPS_MODE_OVERLAPPED) mode = OPS_MODE_SKEWED;  // overlapped executor: see ops_set_mode
   LaunchEnv env = make_env(c);
   c->stats.mode = mode;
   ++c->stats.segments;
@@ -442,7 +452,7 @@ int run_segment(ops_ctx c, int first, int count, int dl_base, const std::vector<
   std::vector<PLoop> pl;
   pl.reserve(count);
   for (int i = 0; i < count; ++i) pl.push_back(plan_loop(c, c->queue[first + i]));
-  int tile[3] = {c->cfg.tile[0], c->cfg.tile[1], c->cfg.tile[2]};
+  int tile[3] = {tile_in[0], tile_in[1], tile_in[2]};
   if (tile[0] <= 0 || (ndim > 1 && tile[1] <= 0) || (ndim > 2 && tile[2] <= 0)) {
     int at[3];
     auto_tile(c, pl, ndim, at);
@@ -522,6 +532,102 @@ int run_segment(ops_ctx c, int first, int count, int dl_base, const std::vector<
     ++c->stats.launches;
   }
   return OPS_OK;
+}
+
+// Signature of a segment: its loops' ranges and arguments (what a plan depends on).
+std::vector<int> segment_signature(ops_ctx c, int first, int count) {
+  std::vector<int> sig;
+  sig.push_back(c->queue[first].dims);
+  for (int i = 0; i < count; ++i) {
+    const QLoop& q = c->queue[first + i];
+    for (int k = 0; k < 6; ++k) sig.push_back(q.rng[k]);
+    sig.push_back((int)q.args.size());
+    for (const ops_arg& a : q.args) {
+      sig.push_back(a.kind);
+      sig.push_back(a.handle);
+      sig.push_back(a.kind == OPS_ARG_DAT ? a.stencil : -1);
+      sig.push_back(a.access);
+    }
+  }
+  return sig;
+}
+
+// Autotuner (the paper picks tile sizes by a cache heuristic, Sec. 4.C; here
+// the heuristic only seeds the search): every schedule of a segment gives
+// bit-identical dats, so successive flushes of the same segment each run one
+// candidate -- untiled, or skewed with the cache-fitting outer tile size h0
+// and 2, 4, 8, 16 times it -- timed with CUDA events; afterwards the fastest
+// candidate is used for that segment.
+int run_segment_auto(ops_ctx c, int first, int count, int dl_base, const std::vector<DLoop>& hl) {
+  const int ndim = c->queue[first].dims;
+  TuneRec& T = c->tune[segment_signature(c, first, count)];
+  if (T.cand.empty()) {
+    std::vector<PLoop> pl;
+    for (int i = 0; i < count; ++i) pl.push_back(plan_loop(c, c->queue[first + i]));
+    int at[3];
+    auto_tile(c, pl, ndim, at);
+    int ext[3] = {1, 1, 1};
+    for (int d = 0; d < 3; ++d) {
+      int lo = 1 << 30, hi = -(1 << 30);
+      for (const PLoop& p : pl) {
+        lo = std::min(lo, p.rng[2 * d]);
+        hi = std::max(hi, p.rng[2 * d + 1]);
+      }
+      ext[d] = std::max(1, hi - lo);
+    }
+    int od = 0;  // outermost dimension the seed tile cuts
+    for (int d = ndim - 1; d >= 0; --d)
+      if (at[d] < ext[d]) {
+        od = d;
+        break;
+      }
+    T.cand.push_back({OPS_MODE_UNTILED, 0, 0, 0});
+    for (int f = 1; f <= 16; f *= 2) {
+      std::array<int, 4> cd = {OPS_MODE_SKEWED, at[0], at[1], at[2]};
+      cd[1 + od] = (int)std::min<int64_t>((int64_t)at[od] * f, ext[od]);
+      T.cand.push_back(cd);
+      if (cd[1 + od] >= ext[od]) break;
+    }
+    T.ms.assign(T.cand.size(), -1.0);
+    CUDA_TRY(c, cudaEventCreate(&T.e0));
+    CUDA_TRY(c, cudaEventCreate(&T.e1));
+  }
+  if (T.pending >= 0) {
+    float t = 0.f;
+    CUDA_TRY(c, cudaEventSynchronize(T.e1));
+    CUDA_TRY(c, cudaEventElapsedTime(&t, T.e0, T.e1));
+    T.ms[T.pending] = t;
+    T.pending = -1;
+  }
+  int pick = T.best;
+  if (pick < 0) {
+    for (size_t i = 0; i < T.cand.size() && pick < 0; ++i)
+      if (T.ms[i] < 0) pick = (int)i;
+    if (pick < 0) {
+      pick = 0;
+      for (size_t i = 1; i < T.cand.size(); ++i)
+        if (T.ms[i] < T.ms[pick]) pick = (int)i;
+      T.best = pick;
+    }
+  }
+  const bool tuning = T.best < 0;
+  c->stats.tuning |= tuning ? 1 : 0;
+  if (tuning) CUDA_TRY(c, cudaEventRecord(T.e0, c->stream));
+  const std::array<int, 4>& cd = T.cand[pick];
+  int rc = run_segment_mode(c, first, count, dl_base, hl, cd[0], &cd[1]);
+  if (rc) return rc;
+  if (tuning) {
+    CUDA_TRY(c, cudaEventRecord(T.e1, c->stream));
+    T.pending = pick;
+  }
+  return OPS_OK;
+}
+
+int run_segment(ops_ctx c, int first, int count, int dl_base, const std::vector<DLoop>& hl) {
+  int mode = c->cfg.mode;
+  if (mode == OPS_MODE_AUTO && count >= 2) return run_segment_auto(c, first, count, dl_base, hl);
+  if (mode == OPS_MODE_AUTO) mode = OPS_MODE_UNTILED;
+  return run_segment_mode(c, first, count, dl_base, hl, mode, c->cfg.tile);
 }
 
 int flush(ops_ctx c) {
@@ -672,6 +778,10 @@ int ops_finalize(ops_ctx c) {
     dev_free(c, c->d_err, sizeof(int));
     dev_free(c, c->d_bar, 4 * sizeof(unsigned));
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (auto& kv : c->tune) {
+      if (kv.second.e0) cudaEventDestroy(kv.second.e0);
+      if (kv.second.e1) cudaEventDestroy(kv.second.e1);
+    }
     if (c->own_stream) cudaStreamDestroy(c->stream);
   }
   delete c;

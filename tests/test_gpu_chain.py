@@ -202,6 +202,26 @@ def test_plan_cache_reuse_and_stats():
     assert s2["tiles"] == 5 and s2["loops"] == len(c.loops)
 
 
+def test_autotuner_settles_and_stays_exact():
+    """AUTO mode times one candidate schedule per step (untiled, then skewed
+    tiles of growing height), then keeps the fastest; every step's dats stay
+    bit-identical to the oracle whichever candidate ran."""
+    c = W.cloverleaf2d(n=120, steps=10)
+    ref, ref_hist = oracle.run_chain(c)
+    r = ChainRunner(c, mode="auto")
+    try:
+        tuning = []
+        for _ in range(c.steps):
+            r.step()
+            tuning.append(r.stats()["tuning"])
+        got = r.fetch()
+        hist = r.history
+    finally:
+        r.close()
+    assert tuning[0] == 1 and tuning[-1] == 0
+    assert_same(c, got, ref, hist, ref_hist, what="auto")
+
+
 def test_full_size_cloverleaf_one_step():
     """The benchmark's workload (3840^2, 83 loops, automatic tiles, the
     benchmark's launch configuration) for one step, every point checked."""
