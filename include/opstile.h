@@ -223,6 +223,51 @@ int ops_last_stats(ops_ctx ctx, ops_flush_stats* out);
  * cap is the number of ints out_ranges can hold. */
 int ops_plan_skewed(ops_ctx ctx, const int* tile, int* out_ntiles, int* out_ranges, int64_t cap);
 
+/* ---- heat-conduction solves (TeaLeaf-shaped, Sec. 5 and Sec. 6.C) ----
+ * Solve A x = b on an n x n cell grid for the implicit heat-conduction
+ * operator (A u)_c = u_c + sum over the four faces f of c of
+ * k_f (u_c - u_nb), k_f the harmonic mean 2 ka kb / (ka + kb) of the two
+ * cells' conductivities; a boundary face takes the cell's own conductivity
+ * and u = 0 outside the grid.  Arrays are n*n doubles, x fastest.
+ * precision OPS_PREC_FP64: textbook CG in FP64 from x = 0 until
+ *   |r|_2 <= tol |b|_2 for the recursively updated residual.
+ * precision OPS_PREC_MIXED: iterative refinement; r = b - A x, its norm and
+ *   x += |r| d in FP64; each correction d solves A d = r / |r| by CG with FP32
+ *   vectors and operator, FP64-accumulated dot products and FP64 scalars, to
+ *   relative residual inner_tol; stops when the true FP64 residual
+ *   |b - A x| <= tol |b|.
+ * Several grids of different sizes can be solved in one batch: they advance
+ * together, one CG iteration per group of five kernel launches, and each
+ * result is independent of the others in the batch. */
+#define OPS_PREC_FP64 0
+#define OPS_PREC_MIXED 1
+typedef struct {
+  double tol;        /* relative residual target */
+  double inner_tol;  /* MIXED: relative residual of each inner FP32 solve (0: 1e-4) */
+  int precision;     /* OPS_PREC_* */
+  int maxit;         /* cap on CG iterations (inner iterations for MIXED) */
+  int maxouter;      /* MIXED: cap on refinement corrections (0: 100) */
+} ops_cg_params;
+typedef struct {
+  int iterations;    /* CG iterations (inner iterations in total for MIXED) */
+  int outer;         /* refinement corrections applied (MIXED) */
+  int converged;     /* 1 if the tolerance was reached */
+  double relres;     /* final relative residual (FP64: recursive; MIXED: true FP64 residual) */
+} ops_cg_stats;
+/* Solve one system; host_x receives n*n doubles.  Returns OPS_OK, or
+ * OPS_ERR_NOT_CONVERGED (x and stats still filled) if maxit was reached. */
+int ops_cg_solve(ops_ctx ctx, int n, const double* host_kappa, const double* host_rhs, const ops_cg_params* params,
+                 double* host_x, ops_cg_stats* stats);
+/* w = A u for the operator above, once, through the solver's own device
+ * code (precision OPS_PREC_MIXED: u rounded to float, the FP32 operator, w
+ * widened back).  host arrays of n*n doubles. */
+int ops_heat_apply(ops_ctx ctx, int n, const double* host_kappa, const double* host_u, int precision,
+                   double* host_w);
+/* Solve count systems of sizes n[i] together (same parameters). */
+int ops_cg_solve_batch(ops_ctx ctx, int count, const int* n, const double* const* host_kappa,
+                       const double* const* host_rhs, const ops_cg_params* params, double* const* host_x,
+                       ops_cg_stats* stats);
+
 /* ---- one loop without any device allocation ----
  * The paper has no counterpart: this is a service for callers that must not
  * allocate device memory.  cudaMalloc and cudaFree can synchronise the whole

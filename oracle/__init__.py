@@ -192,6 +192,20 @@ def matvec(kappa: np.ndarray, u: np.ndarray) -> np.ndarray:
     return w
 
 
+def matvec32(kappa: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """The FP32 operator: FP64 faces rounded to float, u rounded to float,
+    the same term order with single-rounding float fma; result widened."""
+    n = kappa.shape[0]
+    kx, ky, dg = faces(kappa)
+    kxf = np.ascontiguousarray(kx, dtype=np.float32)
+    kyf = np.ascontiguousarray(ky, dtype=np.float32)
+    dgf = np.ascontiguousarray(dg, dtype=np.float32)
+    uf = np.ascontiguousarray(u, dtype=np.float32)
+    w = np.zeros((n, n), dtype=np.float32)
+    lib().ora_matvec32(C.c_int(n), _fp(kxf), _fp(kyf), _fp(dgf), _fp(uf), _fp(w))
+    return w.astype(np.float64)
+
+
 def cg64(kappa: np.ndarray, b: np.ndarray, tol: float, maxit: int = 100000):
     n = kappa.shape[0]
     x = np.zeros((n, n))

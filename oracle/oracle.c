@@ -423,7 +423,7 @@ void ora_matvec(int n, const double* kx, const double* ky, const double* diag, c
 }
 
 /* FP32 operator: coefficients rounded to float, same term order with fmaf */
-static void matvec32(int n, const float* kx, const float* ky, const float* diag, const float* u, float* w) {
+void ora_matvec32(int n, const float* kx, const float* ky, const float* diag, const float* u, float* w) {
 #pragma omp parallel for schedule(static)
   for (int j = 0; j < n; ++j)
     for (int i = 0; i < n; ++i) {
@@ -534,7 +534,7 @@ int ora_cg_refine(int n, const double* kappa, const double* b, double tol, doubl
     double rho0 = rho;
     int it = 0;
     while (total < maxit) {
-      matvec32(n, kxf, kyf, dgf, pf, wf);
+      ora_matvec32(n, kxf, kyf, dgf, pf, wf);
       double pw = xdot32(pf, wf, N);
       double alpha = rho / pw;
       float af = (float)alpha;

@@ -278,3 +278,61 @@ def ops_loop_noalloc(dims: int, rng, args, views, stencils, code, consts, scalar
     if rc != OPS_OK:
         raise OpsError(rc, "ops_loop_noalloc failed")
     return [float(out[i]) if args[i][0] == OPS_ARG_RED else None for i in range(n)]
+
+
+# ------------------------------------------------------ heat-conduction solves
+OPS_PREC_FP64, OPS_PREC_MIXED = 0, 1
+
+
+class ops_cg_params(C.Structure):
+    _fields_ = [("tol", C.c_double), ("inner_tol", C.c_double), ("precision", C.c_int), ("maxit", C.c_int),
+                ("maxouter", C.c_int)]
+
+
+class ops_cg_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("converged", C.c_int), ("relres", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def _cg_params(tol, precision, maxit, inner_tol, maxouter):
+    return ops_cg_params(float(tol), float(inner_tol), int(precision), int(maxit), int(maxouter))
+
+
+def ops_heat_apply(ctx, kappa: np.ndarray, u: np.ndarray, precision: int = OPS_PREC_FP64) -> np.ndarray:
+    n = kappa.shape[0]
+    k = np.ascontiguousarray(kappa, dtype=np.float64)
+    uu = np.ascontiguousarray(u, dtype=np.float64)
+    w = np.empty((n, n))
+    P = C.POINTER(C.c_double)
+    _check(ctx, load().ops_heat_apply(ctx, C.c_int(n), k.ctypes.data_as(P), uu.ctypes.data_as(P),
+                                      C.c_int(precision), w.ctypes.data_as(P)))
+    return w
+
+
+def ops_cg_solve_batch(ctx, kappas, rhss, tol: float, precision: int, maxit: int = 100000, inner_tol: float = 0.0,
+                       maxouter: int = 0):
+    """Solve len(kappas) systems together; returns (list of x, list of stats
+    dicts).  A solve that hits maxit is reported by stats['converged'] == 0."""
+    cnt = len(kappas)
+    ks = [np.ascontiguousarray(k, dtype=np.float64) for k in kappas]
+    bs = [np.ascontiguousarray(b, dtype=np.float64) for b in rhss]
+    xs = [np.empty_like(k) for k in ks]
+    ns = (C.c_int * cnt)(*[k.shape[0] for k in ks])
+    P = C.POINTER(C.c_double)
+    kp = (P * cnt)(*[k.ctypes.data_as(P) for k in ks])
+    bp = (P * cnt)(*[b.ctypes.data_as(P) for b in bs])
+    xp = (P * cnt)(*[x.ctypes.data_as(P) for x in xs])
+    st = (ops_cg_stats * cnt)()
+    prm = _cg_params(tol, precision, maxit, inner_tol, maxouter)
+    rc = load().ops_cg_solve_batch(ctx, C.c_int(cnt), ns, kp, bp, C.byref(prm), xp, st)
+    if rc not in (OPS_OK, OPS_ERR_NOT_CONVERGED):
+        _check(ctx, rc)
+    return xs, [s.as_dict() for s in st]
+
+
+def ops_cg_solve(ctx, kappa, rhs, tol: float, precision: int, maxit: int = 100000, inner_tol: float = 0.0,
+                 maxouter: int = 0):
+    xs, st = ops_cg_solve_batch(ctx, [kappa], [rhs], tol, precision, maxit, inner_tol, maxouter)
+    return xs[0], st[0]

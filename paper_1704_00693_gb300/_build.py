@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.environ.get("OPSTILE_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libopstile.so")
 
-SOURCES = ["runtime.cpp", "plan.cpp", "chain_kernels.cu", "noalloc.cu"]
+SOURCES = ["runtime.cpp", "plan.cpp", "chain_kernels.cu", "cg.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -57,7 +57,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     nvcc = _nvcc()
     obj_dir = os.path.join(BUILD, "obj")
     os.makedirs(obj_dir, exist_ok=True)
-    common = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2,-ffp-contract=off",
+    common = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "--extended-lambda", "-Xcompiler",
+              "-fPIC,-O2,-ffp-contract=off",
               "-I", INCLUDE, "-I", CSRC] + ARCH
     # optional tuning macros, e.g. OPSTILE_NVCC_DEFS="OPS_PTS=2 OPS_MIN_CTAS=2"
     common += ["-D" + d for d in os.environ.get("OPSTILE_NVCC_DEFS", "").split()]

@@ -1,0 +1,776 @@
+// Batched CG for the 5-point heat-conduction operator (TeaLeaf-shaped solves,
+// Sec. 5 and Sec. 6.C), GB300 design:
+//   - the operator is (A u)_c = d_c u_c - sum_f k_f u_nb over the four faces,
+//     k_f the harmonic mean of the two cells' conductivity (a boundary face
+//     takes the cell's own), d_c = 1 + sum_f k_f, neighbours outside are 0;
+//   - mixed precision: the bandwidth-bound sweeps (matvec, axpy) run in FP32
+//     with FP32 copies of the face coefficients; dot products accumulate the
+//     exact FP64 products of FP32 values in double-double; the residual
+//     r = b - A x, its norm and the correction x += |r| d are FP64
+//     (iterative refinement);
+//   - every problem is a state machine advanced by one CG iteration per
+//     "tick" of five kernels (sweep, scalars, sweep, scalars, sweep), so many
+//     grids of different sizes share every launch; a problem's reductions use
+//     only its own work units in a fixed order, so its result does not depend
+//     on what else is in the batch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "cg.h"
+
+namespace opstile {
+
+constexpr int kCgThreads = 256;
+constexpr int kCgUnitPts = 2048;
+
+// ---------------------------------------------------------------------------
+// double-double accumulation (two-sum), as in the chain kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ DD cg_dd_add(DD a, double x) {
+  const double s = __dadd_rn(a.hi, x);
+  const double bp = __dsub_rn(s, a.hi);
+  const double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bp)), __dsub_rn(x, bp));
+  return DD{s, __dadd_rn(a.lo, e)};
+}
+__device__ __forceinline__ DD cg_dd_merge(DD a, DD b) {
+  DD t = cg_dd_add(a, b.hi);
+  t.lo = __dadd_rn(t.lo, b.lo);
+  return t;
+}
+__device__ __forceinline__ DD cg_shfl(DD v, int o) {
+  return DD{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+// block sum in a fixed tree, valid in thread 0
+__device__ DD cg_block_sum(DD v, DD* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = cg_dd_merge(v, cg_shfl(v, o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : DD{0.0, 0.0};
+    for (int o = 16; o > 0; o >>= 1) v = cg_dd_merge(v, cg_shfl(v, o));
+  }
+  __syncthreads();
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// the operator at one cell, in the fixed term order
+// ---------------------------------------------------------------------------
+template <class T>
+struct OpView {
+  const T *kx, *ky, *dg;
+  int n;
+};
+__device__ __forceinline__ double av64(const OpView<double>& A, const double* u, int j, int i) {
+  const int n = A.n;
+  const int64_t c = (int64_t)j * n + i;
+  const double uW = i > 0 ? u[c - 1] : 0.0;
+  const double uE = i < n - 1 ? u[c + 1] : 0.0;
+  const double uS = j > 0 ? u[c - n] : 0.0;
+  const double uN = j < n - 1 ? u[c + n] : 0.0;
+  const int64_t fx = (int64_t)j * (n + 1) + i, fy = (int64_t)j * n + i;
+  double t = __dmul_rn(A.dg[c], u[c]);
+  t = __fma_rn(-A.kx[fx], uW, t);
+  t = __fma_rn(-A.kx[fx + 1], uE, t);
+  t = __fma_rn(-A.ky[fy], uS, t);
+  t = __fma_rn(-A.ky[fy + n], uN, t);
+  return t;
+}
+__device__ __forceinline__ float av32(const OpView<float>& A, const float* u, int j, int i) {
+  const int n = A.n;
+  const int64_t c = (int64_t)j * n + i;
+  const float uW = i > 0 ? u[c - 1] : 0.0f;
+  const float uE = i < n - 1 ? u[c + 1] : 0.0f;
+  const float uS = j > 0 ? u[c - n] : 0.0f;
+  const float uN = j < n - 1 ? u[c + n] : 0.0f;
+  const int64_t fx = (int64_t)j * (n + 1) + i, fy = (int64_t)j * n + i;
+  float t = __fmul_rn(A.dg[c], u[c]);
+  t = __fmaf_rn(-A.kx[fx], uW, t);
+  t = __fmaf_rn(-A.kx[fx + 1], uE, t);
+  t = __fmaf_rn(-A.ky[fy], uS, t);
+  t = __fmaf_rn(-A.ky[fy + n], uN, t);
+  return t;
+}
+
+// Visit the points of a unit: rows [j0, j0+nr) x columns [c0, c0+w); narrow
+// units put several rows side by side in the block (division once per unit).
+template <class F>
+__device__ __forceinline__ void for_unit(const CgUnit& U, F f) {
+  if (U.w >= kCgThreads) {
+    for (int r = 0; r < U.nr; ++r)
+      for (int c = threadIdx.x; c < U.w; c += kCgThreads) f(U.j0 + r, U.c0 + c);
+  } else {
+    const int rpp = kCgThreads / U.w;
+    const int tr = threadIdx.x / U.w, tc = threadIdx.x - tr * U.w;
+    if (tr < rpp)
+      for (int r = tr; r < U.nr; r += rpp) f(U.j0 + r, U.c0 + tc);
+  }
+}
+
+__device__ __forceinline__ double hmean(double a, double b) {
+  return __ddiv_rn(__dmul_rn(__dmul_rn(2.0, a), b), __dadd_rn(a, b));
+}
+
+// ---------------------------------------------------------------------------
+// set-up: face coefficients from the conductivity (held in P.r on entry)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCgThreads) k_cg_setup(CgProb* probs, const CgUnit* units, int u0, int u1) {
+  for (int u = u0 + blockIdx.x; u < u1; u += gridDim.x) {
+    const CgUnit U = units[u];
+    CgProb& P = probs[U.prob];
+    const int n = P.n;
+    const double* kap = P.r;
+    for_unit(U, [&](int j, int i) {
+      const int64_t c = (int64_t)j * n + i;
+      const double kc = kap[c];
+      const double kw = i > 0 ? hmean(kap[c - 1], kc) : kc;
+      const double ks = j > 0 ? hmean(kap[c - n], kc) : kc;
+      const int64_t fx = (int64_t)j * (n + 1) + i, fy = (int64_t)j * n + i;
+      P.kx[fx] = kw;
+      P.ky[fy] = ks;
+      P.kx32[fx] = (float)kw;
+      P.ky32[fy] = (float)ks;
+      if (i == n - 1) {
+        P.kx[fx + 1] = kc;
+        P.kx32[fx + 1] = (float)kc;
+      }
+      if (j == n - 1) {
+        P.ky[fy + n] = kc;
+        P.ky32[fy + n] = (float)kc;
+      }
+    });
+  }
+}
+// diagonal once every face is known
+__global__ void __launch_bounds__(kCgThreads) k_cg_setup2(CgProb* probs, const CgUnit* units, int u0, int u1) {
+  for (int u = u0 + blockIdx.x; u < u1; u += gridDim.x) {
+    const CgUnit U = units[u];
+    CgProb& P = probs[U.prob];
+    const int n = P.n;
+    for_unit(U, [&](int j, int i) {
+      const int64_t c = (int64_t)j * n + i;
+      const int64_t fx = (int64_t)j * (n + 1) + i, fy = (int64_t)j * n + i;
+      double d = __dadd_rn(1.0, P.kx[fx]);
+      d = __dadd_rn(d, P.kx[fx + 1]);
+      d = __dadd_rn(d, P.ky[fy]);
+      d = __dadd_rn(d, P.ky[fy + n]);
+      P.dg[c] = d;
+      P.dg32[c] = (float)d;
+      P.x[c] = 0.0;
+    });
+  }
+}
+
+// ---------------------------------------------------------------------------
+// tick kernels
+// ---------------------------------------------------------------------------
+// A: residual (OUTER/FINISH), w = A p (INNER, CG64); partial dots per unit
+__global__ void __launch_bounds__(kCgThreads) k_cg_a(CgProb* probs, const CgUnit* units, int nunits, DD* part) {
+  __shared__ DD sh[32];
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const CgUnit U = units[u];
+    const CgProb& P = probs[U.prob];
+    const int st = P.state, n = P.n;
+    DD acc{0.0, 0.0};
+    if (st == CG_OUTER || st == CG_FINISH) {
+      const OpView<double> A{P.kx, P.ky, P.dg, n};
+      const double* x = P.x;
+      const double* b = P.b;
+      double* r = P.r;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        const double rc = __dsub_rn(b[c], av64(A, x, j, i));
+        r[c] = rc;
+        acc = cg_dd_add(acc, __dmul_rn(rc, rc));
+      });
+    } else if (st == CG_INNER) {
+      const OpView<float> A{P.kx32, P.ky32, P.dg32, n};
+      const float* p = P.p32;
+      float* w = P.w32;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        const float wc = av32(A, p, j, i);
+        w[c] = wc;
+        acc = cg_dd_add(acc, __dmul_rn((double)p[c], (double)wc));
+      });
+    } else if (st == CG64) {
+      const OpView<double> A{P.kx, P.ky, P.dg, n};
+      const double* p = P.p64;
+      double* w = P.w64;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        const double wc = av64(A, p, j, i);
+        w[c] = wc;
+        acc = cg_dd_add(acc, __dmul_rn(p[c], wc));
+      });
+    }
+    acc = cg_block_sum(acc, sh);
+    if (threadIdx.x == 0) part[u] = acc;
+  }
+}
+
+// B: INIT (scaled residual into the FP32 inner vectors), INNER / CG64 updates
+__global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit* units, int nunits, DD* part) {
+  __shared__ DD sh[32];
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const CgUnit U = units[u];
+    const CgProb& P = probs[U.prob];
+    const int st = P.state, n = P.n;
+    DD acc{0.0, 0.0};
+    if (st == CG_INIT) {
+      const double inv = __ddiv_rn(1.0, P.nr);
+      const double* r = P.r;
+      float *r32 = P.r32, *p32 = P.p32, *d32 = P.d32;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        const float rs = (float)__dmul_rn(r[c], inv);
+        r32[c] = rs;
+        p32[c] = rs;
+        d32[c] = 0.0f;
+        acc = cg_dd_add(acc, __dmul_rn((double)rs, (double)rs));
+      });
+    } else if (st == CG_INNER) {
+      const float af = (float)P.alpha;
+      const float *p32 = P.p32, *w32 = P.w32;
+      float *r32 = P.r32, *d32 = P.d32;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        d32[c] = __fmaf_rn(af, p32[c], d32[c]);
+        const float r = __fmaf_rn(-af, w32[c], r32[c]);
+        r32[c] = r;
+        acc = cg_dd_add(acc, __dmul_rn((double)r, (double)r));
+      });
+    } else if (st == CG64_INIT) {
+      const double* b = P.b;
+      double *x = P.x, *r = P.r, *p = P.p64;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        const double bc = b[c];
+        x[c] = 0.0;
+        r[c] = bc;
+        p[c] = bc;
+        acc = cg_dd_add(acc, __dmul_rn(bc, bc));
+      });
+    } else if (st == CG64) {
+      const double a = P.alpha;
+      const double *p = P.p64, *w = P.w64;
+      double *x = P.x, *r = P.r;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        x[c] = __fma_rn(a, p[c], x[c]);
+        const double rc = __fma_rn(-a, w[c], r[c]);
+        r[c] = rc;
+        acc = cg_dd_add(acc, __dmul_rn(rc, rc));
+      });
+    }
+    acc = cg_block_sum(acc, sh);
+    if (threadIdx.x == 0) part[u] = acc;
+  }
+}
+
+// C: search-direction update (INNER, CG64) or the refinement correction (FINISH)
+__global__ void __launch_bounds__(kCgThreads) k_cg_c(CgProb* probs, const CgUnit* units, int nunits) {
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const CgUnit U = units[u];
+    const CgProb& P = probs[U.prob];
+    const int st = P.state, n = P.n;
+    if (st == CG_INNER) {
+      const float bf = (float)P.beta;
+      const float* r32 = P.r32;
+      float* p32 = P.p32;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        p32[c] = __fmaf_rn(bf, p32[c], r32[c]);
+      });
+    } else if (st == CG_FINISH) {
+      const double nr = P.nr;
+      const float* d32 = P.d32;
+      double* x = P.x;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        x[c] = __fma_rn(nr, (double)d32[c], x[c]);
+      });
+    } else if (st == CG64) {
+      const double bt = P.beta;
+      const double* r = P.r;
+      double* p = P.p64;
+      for_unit(U, [&](int j, int i) {
+        const int64_t c = (int64_t)j * n + i;
+        p[c] = __fma_rn(bt, p[c], r[c]);
+      });
+    }
+  }
+}
+
+// One operator application for one slot: FP64 reads u from x and writes
+// A u to r; FP32 reads p32 and writes w32.
+__global__ void __launch_bounds__(kCgThreads) k_cg_apply(const CgProb* probs, const CgUnit* units, int u0, int u1,
+                                                         int prec) {
+  for (int u = u0 + blockIdx.x; u < u1; u += gridDim.x) {
+    const CgUnit U = units[u];
+    const CgProb& P = probs[U.prob];
+    const int n = P.n;
+    if (prec == 0) {
+      const OpView<double> A{P.kx, P.ky, P.dg, n};
+      const double* x = P.x;
+      double* r = P.r;
+      for_unit(U, [&](int j, int i) { r[(int64_t)j * n + i] = av64(A, x, j, i); });
+    } else {
+      const OpView<float> A{P.kx32, P.ky32, P.dg32, n};
+      const float* p = P.p32;
+      float* w = P.w32;
+      for_unit(U, [&](int j, int i) { w[(int64_t)j * n + i] = av32(A, p, j, i); });
+    }
+  }
+}
+
+// Sum of a problem's unit partials in a fixed order (one warp per problem).
+__device__ __forceinline__ double warp_partial_sum(const DD* part, int u0, int u1) {
+  const int lane = threadIdx.x & 31;
+  DD v{0.0, 0.0};
+  for (int u = u0 + lane; u < u1; u += 32) v = cg_dd_merge(v, part[u]);
+  for (int o = 16; o > 0; o >>= 1) v = cg_dd_merge(v, cg_shfl(v, o));
+  return __dadd_rn(v.hi, v.lo);
+}
+
+// Scalars after kernel A.
+__global__ void k_cg_s1(CgProb* probs, const int2* ranges, int nslots, const DD* part) {
+  const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= nslots) return;
+  CgProb& P = probs[p];
+  const int st = P.state;
+  if (st != CG_OUTER && st != CG_FINISH && st != CG_INNER && st != CG64) return;
+  const double s = warp_partial_sum(part, ranges[p].x, ranges[p].y);
+  if ((threadIdx.x & 31) != 0) return;
+  if (st == CG_OUTER || st == CG_FINISH) {
+    if (st == CG_FINISH) ++P.outer;
+    const double nr = sqrt(s);
+    if (P.outer == 0) P.nb = nr;
+    const double rel = P.nb > 0.0 ? nr / P.nb : 0.0;
+    P.rel = rel;
+    if (rel <= P.tol) {
+      P.conv = 1;
+      P.state = CG_DONE;
+    } else if (P.outer >= P.maxouter || P.it >= P.maxit) {
+      P.state = CG_DONE;
+    } else {
+      P.nr = nr;
+      P.state = CG_INIT;
+    }
+  } else {
+    P.alpha = P.rho / s;
+  }
+}
+
+// Scalars after kernel B.
+__global__ void k_cg_s2(CgProb* probs, const int2* ranges, int nslots, const DD* part) {
+  const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= nslots) return;
+  CgProb& P = probs[p];
+  const int st = P.state;
+  if (st != CG_INIT && st != CG_INNER && st != CG64_INIT && st != CG64) return;
+  const double s = warp_partial_sum(part, ranges[p].x, ranges[p].y);
+  if ((threadIdx.x & 31) != 0) return;
+  if (st == CG_INIT) {
+    P.rho = s;
+    P.rho0 = s;
+    P.state = s > 0.0 ? CG_INNER : CG_FINISH;
+  } else if (st == CG_INNER) {
+    ++P.it;
+    if (sqrt(s) <= P.inner_tol * sqrt(P.rho0) || P.it >= P.maxit) {
+      P.state = CG_FINISH;
+    } else {
+      P.beta = s / P.rho;
+      P.rho = s;
+    }
+  } else if (st == CG64_INIT) {
+    P.rho = s;
+    P.nb = sqrt(s);
+    P.rel = 1.0;
+    if (s == 0.0) {
+      P.rel = 0.0;
+      P.conv = 1;
+      P.state = CG_DONE;
+    } else {
+      P.state = CG64;
+    }
+  } else {
+    ++P.it;
+    P.beta = s / P.rho;
+    P.rho = s;
+    P.rel = sqrt(s) / P.nb;
+    if (sqrt(s) <= P.tol * P.nb) {
+      P.conv = 1;
+      P.state = CG_DONE;
+    } else if (P.it >= P.maxit) {
+      P.state = CG_DONE;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+}  // namespace
+
+int64_t cg_problem_bytes(int n) {
+  const size_t N = (size_t)n * n, F = (size_t)n * (n + 1);
+  return (int64_t)(5 * al256(8 * N) + 2 * al256(8 * F) + al256(8 * N) + 2 * al256(4 * F) + 5 * al256(4 * N));
+}
+
+CgBatch::CgBatch(cudaStream_t stream, int num_sms) : stream_(stream), num_sms_(num_sms) {}
+
+CgBatch::~CgBatch() {
+  cudaStreamSynchronize(stream_);
+  cudaFree(dprob_);
+  cudaFree(dunits_);
+  cudaFree(dranges_);
+  cudaFree(dpart_);
+}
+
+static void units_for(int slot, int n, std::vector<CgUnit>& out) {
+  if (n >= kCgThreads) {
+    for (int j = 0; j < n; ++j)
+      for (int c0 = 0; c0 < n; c0 += kCgUnitPts) out.push_back(CgUnit{slot, j, 1, c0, std::min(kCgUnitPts, n - c0)});
+  } else {
+    const int nr = std::max(1, kCgUnitPts / n);
+    for (int j = 0; j < n; j += nr) out.push_back(CgUnit{slot, j, std::min(nr, n - j), 0, n});
+  }
+}
+
+int CgBatch::add(int n, const double* kappa, const double* rhs, double tol, int prec, double inner_tol, int maxit,
+                 int maxouter, void* slab) {
+  int slot = -1;
+  for (size_t i = 0; i < live_.size(); ++i)
+    if (!live_[i]) {
+      slot = (int)i;
+      break;
+    }
+  if (slot < 0) {
+    slot = (int)live_.size();
+    live_.push_back(0);
+    reported_.push_back(0);
+    hprob_.push_back(CgProb());
+  }
+  const size_t N = (size_t)n * n, F = (size_t)n * (n + 1);
+  CgProb P;
+  std::memset(&P, 0, sizeof P);
+  P.n = n;
+  P.prec = prec;
+  P.state = prec == 0 ? CG64_INIT : CG_OUTER;
+  P.maxit = maxit;
+  P.maxouter = maxouter;
+  P.tol = tol;
+  P.inner_tol = inner_tol;
+  char* s = (char*)slab;
+  auto take = [&](size_t bytes) {
+    char* p = s;
+    s += al256(bytes);
+    return p;
+  };
+  P.b = (double*)take(8 * N);
+  P.x = (double*)take(8 * N);
+  P.r = (double*)take(8 * N);
+  P.p64 = (double*)take(8 * N);
+  P.w64 = (double*)take(8 * N);
+  P.kx = (double*)take(8 * F);
+  P.ky = (double*)take(8 * F);
+  P.dg = (double*)take(8 * N);
+  P.kx32 = (float*)take(4 * F);
+  P.ky32 = (float*)take(4 * F);
+  P.dg32 = (float*)take(4 * N);
+  P.r32 = (float*)take(4 * N);
+  P.p32 = (float*)take(4 * N);
+  P.w32 = (float*)take(4 * N);
+  P.d32 = (float*)take(4 * N);
+  hprob_[slot] = P;
+  live_[slot] = 1;
+  reported_[slot] = 0;
+  if ((int)hstate_.size() > slot) hstate_[slot] = -1;  // upload and set up at the next rebuild
+  ++nlive_;
+  units_dirty_ = true;
+  // conductivity goes to P.r for the set-up kernels, the right-hand side to P.b
+  cudaMemcpyAsync(P.r, kappa, 8 * N, cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(P.b, rhs, 8 * N, cudaMemcpyHostToDevice, stream_);
+  return slot;
+}
+
+void CgBatch::remove(int slot) {
+  if (slot < 0 || slot >= (int)live_.size() || !live_[slot]) return;
+  live_[slot] = 0;
+  hprob_[slot].state = CG_FREE;
+  --nlive_;
+  units_dirty_ = true;
+}
+
+cudaError_t CgBatch::rebuild_units() {
+  // the device array of problems must hold every slot; slots keep their
+  // device state across rebuilds (only new problems are uploaded)
+  const int nslots = (int)hprob_.size();
+  if (nslots > dprob_cap_) {
+    CgProb* nd = nullptr;
+    const int cap = std::max(nslots, 2 * dprob_cap_);
+    cudaError_t e = cudaMalloc(&nd, sizeof(CgProb) * cap);
+    if (e != cudaSuccess) return e;
+    if (dprob_) {
+      cudaMemcpyAsync(nd, dprob_, sizeof(CgProb) * dprob_cap_, cudaMemcpyDeviceToDevice, stream_);
+      cudaStreamSynchronize(stream_);
+      cudaFree(dprob_);
+    }
+    dprob_ = nd;
+    dprob_cap_ = cap;
+  }
+  std::vector<CgUnit> units;
+  std::vector<int2> ranges(nslots);
+  std::vector<int> fresh;
+  for (int s = 0; s < nslots; ++s) {
+    const int u0 = (int)units.size();
+    if (live_[s]) units_for(s, hprob_[s].n, units);
+    ranges[s] = make_int2(u0, (int)units.size());
+  }
+  nunits_ = (int)units.size();
+  const int need_units = std::max(1, nunits_);
+  if (need_units > dunits_cap_) {
+    cudaStreamSynchronize(stream_);
+    cudaFree(dunits_);
+    dunits_cap_ = std::max(need_units, 2 * dunits_cap_);
+    cudaError_t e = cudaMalloc(&dunits_, sizeof(CgUnit) * dunits_cap_);
+    if (e != cudaSuccess) return e;
+  }
+  if (nslots > dranges_cap_) {
+    cudaStreamSynchronize(stream_);
+    cudaFree(dranges_);
+    dranges_cap_ = std::max(nslots, 2 * dranges_cap_);
+    cudaError_t e = cudaMalloc(&dranges_, sizeof(int2) * dranges_cap_);
+    if (e != cudaSuccess) return e;
+  }
+  if (need_units > dpart_cap_) {
+    cudaStreamSynchronize(stream_);
+    cudaFree(dpart_);
+    dpart_cap_ = std::max(need_units, 2 * dpart_cap_);
+    cudaError_t e = cudaMalloc(&dpart_, sizeof(DD) * dpart_cap_);
+    if (e != cudaSuccess) return e;
+  }
+  if (nunits_)
+    cudaMemcpyAsync(dunits_, units.data(), sizeof(CgUnit) * nunits_, cudaMemcpyHostToDevice, stream_);
+  cudaMemcpyAsync(dranges_, ranges.data(), sizeof(int2) * nslots, cudaMemcpyHostToDevice, stream_);
+  // upload the problems added since the last rebuild and run their set-up
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < nslots; ++s) {
+    const bool is_new = live_[s] && ((int)hstate_.size() <= s || hstate_[s] == -1);
+    if ((int)hstate_.size() <= s) hstate_.push_back(-1);
+    if (!live_[s]) {
+      hstate_[s] = -1;
+      // a freed slot must read as free on the device
+      CgProb P;
+      std::memset(&P, 0, sizeof P);
+      P.state = CG_FREE;
+      cudaMemcpyAsync(dprob_ + s, &P, sizeof P, cudaMemcpyHostToDevice, stream_);
+      continue;
+    }
+    if (is_new) {
+      cudaMemcpyAsync(dprob_ + s, &hprob_[s], sizeof(CgProb), cudaMemcpyHostToDevice, stream_);
+      const int u0 = ranges[s].x, u1 = ranges[s].y;
+      const int g = std::max(1, std::min(u1 - u0, num_sms_ * 4));
+      k_cg_setup<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, u0, u1);
+      k_cg_setup2<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, u0, u1);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      hstate_[s] = hprob_[s].state;
+    }
+  }
+  units_dirty_ = false;
+  return cudaSuccess;
+}
+
+cudaError_t CgBatch::run(int ticks) {
+  if (units_dirty_) {
+    cudaError_t e = rebuild_units();
+    if (e != cudaSuccess) return e;
+  }
+  if (nunits_ == 0) return cudaSuccess;
+  const int nslots = (int)hprob_.size();
+  const int2* ranges = dranges_;
+  const int g = std::max(1, std::min(nunits_, num_sms_ * 8));
+  const int gs = (nslots + 7) / 8;
+  for (int t = 0; t < ticks; ++t) {
+    k_cg_a<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_, dpart_);
+    k_cg_s1<<<gs, 256, 0, stream_>>>(dprob_, ranges, nslots, dpart_);
+    k_cg_b<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_, dpart_);
+    k_cg_s2<<<gs, 256, 0, stream_>>>(dprob_, ranges, nslots, dpart_);
+    k_cg_c<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t CgBatch::poll(std::vector<int>& done) {
+  done.clear();
+  const int nslots = (int)hprob_.size();
+  if (!nslots || !dprob_) return cudaSuccess;
+  std::vector<CgProb> tmp(nslots);
+  cudaError_t e = cudaMemcpyAsync(tmp.data(), dprob_, sizeof(CgProb) * nslots, cudaMemcpyDeviceToHost, stream_);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(stream_);
+  if (e != cudaSuccess) return e;
+  for (int s = 0; s < nslots; ++s)
+    if (live_[s] && !reported_[s] && tmp[s].state == CG_DONE) {
+      reported_[s] = 1;
+      done.push_back(s);
+    }
+  return cudaSuccess;
+}
+
+cudaError_t CgBatch::apply(int slot, int prec, const double* host_u, double* host_w) {
+  if (units_dirty_) {
+    cudaError_t e = rebuild_units();
+    if (e != cudaSuccess) return e;
+  }
+  const CgProb& H = hprob_[slot];
+  const size_t N = (size_t)H.n * H.n;
+  std::vector<int2> ranges(hprob_.size());
+  cudaError_t e = cudaMemcpyAsync(ranges.data(), dranges_, sizeof(int2) * ranges.size(), cudaMemcpyDeviceToHost,
+                                  stream_);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+  if (e != cudaSuccess) return e;
+  std::vector<float> f;
+  if (prec == 0) {
+    e = cudaMemcpyAsync(H.x, host_u, 8 * N, cudaMemcpyHostToDevice, stream_);
+  } else {
+    f.resize(N);
+    for (size_t i = 0; i < N; ++i) f[i] = (float)host_u[i];
+    e = cudaMemcpyAsync(H.p32, f.data(), 4 * N, cudaMemcpyHostToDevice, stream_);
+  }
+  if (e != cudaSuccess) return e;
+  const int u0 = ranges[slot].x, u1 = ranges[slot].y;
+  k_cg_apply<<<std::max(1, std::min(u1 - u0, num_sms_ * 4)), kCgThreads, 0, stream_>>>(dprob_, dunits_, u0, u1, prec);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (prec == 0) {
+    e = cudaMemcpyAsync(host_w, H.r, 8 * N, cudaMemcpyDeviceToHost, stream_);
+  } else {
+    e = cudaMemcpyAsync(f.data(), H.w32, 4 * N, cudaMemcpyDeviceToHost, stream_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream_);
+    for (size_t i = 0; i < N && e == cudaSuccess; ++i) host_w[i] = (double)f[i];
+  }
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(stream_);
+}
+
+cudaError_t CgBatch::fetch(int slot, double* host_x, CgProb* info) {
+  const CgProb& H = hprob_[slot];
+  const size_t N = (size_t)H.n * H.n;
+  cudaError_t e = cudaSuccess;
+  if (host_x) e = cudaMemcpyAsync(host_x, H.x, 8 * N, cudaMemcpyDeviceToHost, stream_);
+  if (e != cudaSuccess) return e;
+  if (info) e = cudaMemcpyAsync(info, dprob_ + slot, sizeof(CgProb), cudaMemcpyDeviceToHost, stream_);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(stream_);
+}
+
+}  // namespace opstile
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+using namespace opstile;
+
+extern "C" int ops_cg_solve_batch(ops_ctx ctx, int count, const int* n, const double* const* host_kappa,
+                                  const double* const* host_rhs, const ops_cg_params* params,
+                                  double* const* host_x, ops_cg_stats* stats) {
+  if (!ctx || count < 1 || !n || !host_kappa || !host_rhs || !params || !host_x) return OPS_ERR_INVALID_ARG;
+  if (ctx_host_only(ctx)) return ctx_fail(ctx, OPS_ERR_NO_DEVICE, "host-only context");
+  const ops_cg_params& P = *params;
+  if (!(P.tol > 0.0) || (P.precision != OPS_PREC_FP64 && P.precision != OPS_PREC_MIXED) || P.maxit < 1)
+    return ctx_fail(ctx, OPS_ERR_INVALID_ARG, "cg: tol > 0, precision FP64/MIXED and maxit >= 1 required");
+  for (int i = 0; i < count; ++i)
+    if (n[i] < 1 || n[i] > 46000 || !host_kappa[i] || !host_rhs[i] || !host_x[i])
+      return ctx_fail(ctx, OPS_ERR_INVALID_ARG, "cg: grid side must be 1..46000 with all arrays given");
+  const double inner_tol = P.inner_tol > 0.0 ? P.inner_tol : 1e-4;
+  const int maxouter = P.maxouter > 0 ? P.maxouter : 100;
+  std::vector<void*> slabs(count, nullptr);
+  std::vector<int> slots(count, -1);
+  int rc = OPS_OK;
+  {
+    CgBatch B(ctx_stream(ctx), ctx_num_sms(ctx));
+    for (int i = 0; i < count && rc == OPS_OK; ++i) {
+      rc = ctx_alloc(ctx, &slabs[i], (size_t)cg_problem_bytes(n[i]));
+      if (rc == OPS_OK)
+        slots[i] = B.add(n[i], host_kappa[i], host_rhs[i], P.tol, P.precision, inner_tol, P.maxit, maxouter,
+                         slabs[i]);
+    }
+    int remaining = count;
+    std::vector<int> done;
+    // every live problem reaches CG_DONE within maxit iterations plus one
+    // refinement step per correction; the loop bound only guards the host
+    const long long max_ticks = 2ll * P.maxit + 4ll * maxouter + 64;
+    long long ticks = 0;
+    while (rc == OPS_OK && remaining > 0) {
+      if (ticks > max_ticks) {
+        rc = ctx_fail(ctx, OPS_ERR_NOT_CONVERGED, "cg: tick limit reached");
+        break;
+      }
+      const int chunk = 8;
+      cudaError_t e = B.run(chunk);
+      ticks += chunk;
+      if (e == cudaSuccess) e = B.poll(done);
+      if (e != cudaSuccess) {
+        rc = ctx_fail(ctx, OPS_ERR_CUDA, cudaGetErrorString(e));
+        break;
+      }
+      remaining -= (int)done.size();
+    }
+    bool all_conv = true;
+    for (int i = 0; i < count && rc == OPS_OK; ++i) {
+      CgProb info;
+      cudaError_t e = B.fetch(slots[i], host_x[i], &info);
+      if (e != cudaSuccess) {
+        rc = ctx_fail(ctx, OPS_ERR_CUDA, cudaGetErrorString(e));
+        break;
+      }
+      if (stats) {
+        stats[i].iterations = info.it;
+        stats[i].outer = info.outer;
+        stats[i].converged = info.conv;
+        stats[i].relres = info.rel;
+      }
+      all_conv = all_conv && info.conv;
+    }
+    if (rc == OPS_OK && !all_conv) rc = ctx_fail(ctx, OPS_ERR_NOT_CONVERGED, "cg: iteration cap reached");
+  }
+  for (int i = 0; i < count; ++i)
+    if (slabs[i]) ctx_free(ctx, slabs[i], (size_t)cg_problem_bytes(n[i]));
+  return rc;
+}
+
+extern "C" int ops_cg_solve(ops_ctx ctx, int n, const double* host_kappa, const double* host_rhs,
+                            const ops_cg_params* params, double* host_x, ops_cg_stats* stats) {
+  return ops_cg_solve_batch(ctx, 1, &n, &host_kappa, &host_rhs, params, &host_x, stats);
+}
+
+extern "C" int ops_heat_apply(ops_ctx ctx, int n, const double* host_kappa, const double* host_u, int precision,
+                              double* host_w) {
+  if (!ctx || n < 1 || n > 46000 || !host_kappa || !host_u || !host_w) return OPS_ERR_INVALID_ARG;
+  if (ctx_host_only(ctx)) return ctx_fail(ctx, OPS_ERR_NO_DEVICE, "host-only context");
+  if (precision != OPS_PREC_FP64 && precision != OPS_PREC_MIXED)
+    return ctx_fail(ctx, OPS_ERR_INVALID_ARG, "precision must be OPS_PREC_FP64 or OPS_PREC_MIXED");
+  void* slab = nullptr;
+  const size_t bytes = (size_t)cg_problem_bytes(n);
+  int rc = ctx_alloc(ctx, &slab, bytes);
+  if (rc) return rc;
+  {
+    CgBatch B(ctx_stream(ctx), ctx_num_sms(ctx));
+    std::vector<double> zero((size_t)n * n, 0.0);
+    const int slot = B.add(n, host_kappa, zero.data(), 1.0, OPS_PREC_FP64, 1e-4, 1, 1, slab);
+    cudaError_t e = B.apply(slot, precision == OPS_PREC_FP64 ? 0 : 1, host_u, host_w);
+    if (e != cudaSuccess) rc = ctx_fail(ctx, OPS_ERR_CUDA, cudaGetErrorString(e));
+  }
+  ctx_free(ctx, slab, bytes);
+  return rc;
+}

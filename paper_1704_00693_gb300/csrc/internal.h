@@ -107,6 +107,14 @@ struct LaunchEnv {
   int skip_block;       // test hook: CTA that never arrives at grid barriers (-1 = none)
 };
 
+// Context services for the other translation units (runtime.cpp).
+cudaStream_t ctx_stream(ops_ctx c);
+int ctx_num_sms(ops_ctx c);
+bool ctx_host_only(ops_ctx c);
+int ctx_alloc(ops_ctx c, void** p, size_t bytes);  // OPS_OK or OPS_ERR_NOMEM (budget-checked)
+void ctx_free(ops_ctx c, void* p, size_t bytes);
+int ctx_fail(ops_ctx c, int code, const char* msg);
+
 // Launch helpers implemented in chain_kernels.cu.
 // chain_kernels_setup: once per device (opts the kernels into their shared memory).
 cudaError_t chain_kernels_setup();

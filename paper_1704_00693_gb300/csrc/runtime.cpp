@@ -707,6 +707,18 @@ int check_device_error(ops_ctx c) {
 }  // namespace
 
 // ===========================================================================
+// context services for cg.cu and serve.cpp
+// ===========================================================================
+namespace opstile {
+cudaStream_t ctx_stream(ops_ctx c) { return c->stream; }
+int ctx_num_sms(ops_ctx c) { return c->num_sms; }
+bool ctx_host_only(ops_ctx c) { return c->host_only; }
+int ctx_alloc(ops_ctx c, void** p, size_t bytes) { return dev_alloc(c, p, bytes); }
+void ctx_free(ops_ctx c, void* p, size_t bytes) { dev_free(c, p, bytes); }
+int ctx_fail(ops_ctx c, int code, const char* msg) { return fail(c, code, "%s", msg); }
+}  // namespace opstile
+
+// ===========================================================================
 // C ABI
 // ===========================================================================
 extern "C" {
