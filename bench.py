@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-untiled", action="store_true")
+    p.add_argument("--no-serve", action="store_true", help="skip the served-solves measurement")
+    p.add_argument("--no-cg", action="store_true", help="skip the 4000^2 CG measurement")
+    p.add_argument("--serve-requests", type=int, default=512)
     return p.parse_args()
 
 
@@ -211,6 +214,116 @@ def time_e2e(chain, mode, tile, steps, stream, torch):
     return ms, bi
 
 
+def mem_available_bytes():
+    try:
+        for line in open("/proc/meminfo"):
+            if line.startswith("MemAvailable:"):
+                return int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def bench_serving(nreq=512, seq_sample=32, tol=1e-8, budget=48 << 30):
+    """Served mixed-size diffusion solves (FP32 sweeps + FP64 refinement,
+    continuous batching) against sequential untiled FP64 CG solves on the
+    same GPU.  Requests: n uniform over multiples of 64 in [64, 2048],
+    conductivity log-uniform in [0.1, 10], RHS U(0,1), tolerance 1e-8."""
+    import numpy as np
+    import paper_1704_00693_gb300 as ops
+    from synth import workloads as W
+    reqs = W.serving_stream(nreq)
+    need = sum(16 * n * n for _, n, _ in reqs) * 1.2
+    reuse = need > 0.5 * mem_available_bytes()
+    cache = {}
+
+    def problem(i):
+        _, n, s = reqs[i]
+        if reuse:  # not enough host memory for every grid: one grid per size
+            if n not in cache:
+                cache[n] = W.cg_problem(n, 1e-1, 1e1, seed=s)
+            return cache[n]
+        return W.cg_problem(n, 1e-1, 1e1, seed=s)
+
+    probs = [problem(i) for i in range(nreq)]
+    # sequential untiled FP64 baseline on a bounded sample (same request order)
+    ctx = ops.ops_init()
+    try:
+        ops.ops_cg_solve(ctx, *probs[0], tol, ops.OPS_PREC_FP64)  # warm-up
+        t0 = time.perf_counter()
+        for i in range(seq_sample):
+            ops.ops_cg_solve(ctx, *probs[i], tol, ops.OPS_PREC_FP64)
+        t_seq = time.perf_counter() - t0
+    finally:
+        ops.ops_finalize(ctx)
+    seq_rate = seq_sample / t_seq
+    # scale the sample's rate to the whole stream by the cells it holds
+    cells_all = sum(n * n for _, n, _ in reqs)
+    cells_sample = sum(reqs[i][1] ** 2 for i in range(seq_sample))
+    seq_rate_all = seq_rate * (cells_sample / seq_sample) / (cells_all / nreq)
+
+    def serve(arrivals):
+        srv = ops.ops_serve_open(tol, ops.OPS_PREC_MIXED, hbm_budget=budget)
+        try:
+            ids = []
+            t0 = time.perf_counter()
+            for i in range(nreq):
+                wait = arrivals[i] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+                ids.append(ops.ops_serve_submit(srv, *probs[i]))
+            res = [ops.ops_serve_poll(srv, rid, reqs[i][1]) for i, rid in enumerate(ids)]
+            makespan = time.perf_counter() - t0
+        finally:
+            ops.ops_serve_close(srv)
+        lat = np.array([st["latency_ms"] for _, st in res])
+        conv = sum(st["converged"] for _, st in res)
+        return {"solves_per_s": nreq / makespan, "makespan_s": makespan, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "converged": conv}, res
+
+    sat, res = serve([0.0] * nreq)
+    # check a few results against the oracle's FP64 residual
+    import oracle
+    worst = max(oracle.relres(*probs[i], res[i][0]) for i in range(0, nreq, max(1, nreq // 8)))
+    rate = 1.5 * seq_rate_all
+    poisson = [t / rate for t, _, _ in reqs]
+    load, _ = serve(poisson)
+    return {"requests": nreq, "sizes": "n uniform over multiples of 64 in [64, 2048]",
+            "tol": tol, "precision": "fp32 sweeps + fp64 refinement", "distinct_grids": not reuse,
+            "saturation": sat, "offered_1.5x_seq": dict(load, offered_rate=rate),
+            "sequential_fp64": {"solves_per_s": seq_rate_all, "sample": seq_sample,
+                                "sample_solves_per_s": seq_rate},
+            "speedup_vs_sequential_fp64": sat["solves_per_s"] / seq_rate_all,
+            "worst_sampled_oracle_relres": worst}
+
+
+def bench_cg(n=4000, tol=1e-10):
+    """TeaLeaf-shaped solve: conductivity log-uniform in [1e-2, 1e2], RHS
+    U(0,1); FP64 CG against FP32 sweeps with FP64 residual and refinement."""
+    import paper_1704_00693_gb300 as ops
+    from synth import workloads as W
+    kappa, b = W.cg_problem(n, 1e-2, 1e2)
+    ctx = ops.ops_init()
+    out = {"n": n, "tol": tol}
+    try:
+        runs = [("fp64", ops.OPS_PREC_FP64, 0.0), ("mixed_inner1e-4", ops.OPS_PREC_MIXED, 1e-4),
+                ("mixed_inner1e-5", ops.OPS_PREC_MIXED, 1e-5), ("mixed_inner1e-6", ops.OPS_PREC_MIXED, 1e-6)]
+        for name, prec, itol in runs:
+            ops.ops_cg_solve(ctx, kappa[:512, :512].copy(), b[:512, :512].copy(), tol, prec, inner_tol=itol)
+            t0 = time.perf_counter()
+            x, st = ops.ops_cg_solve(ctx, kappa, b, tol, prec, inner_tol=itol)
+            dt = time.perf_counter() - t0
+            out[name] = {"seconds": dt, "iterations": st["iterations"], "outer": st["outer"],
+                         "converged": st["converged"], "relres": st["relres"],
+                         "ms_per_iteration": dt * 1e3 / max(1, st["iterations"])}
+    finally:
+        ops.ops_finalize(ctx)
+    best = min((k for k in out if k.startswith("mixed")), key=lambda k: out[k]["seconds"])
+    out["best_mixed"] = best
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out[best]["seconds"]
+    return out
+
+
 def cpu_baseline(n_full, seconds=12.0):
     """The oracle (untiled, program order, FP64, all host cores) on a bounded
     sample: one step of the same chain on a grid with 1/4 of the points."""
@@ -352,6 +465,8 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.n)
+    cg = bench_cg() if rank == 0 and not args.no_cg else None
+    serving = bench_serving(args.serve_requests) if rank == 0 and not args.no_serve else None
 
     line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -364,6 +479,7 @@ def main():
             "speedup_vs_untiled": (untiled["ms_per_step"] / (ms / args.steps)) if untiled else None,
             "untiled": untiled, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
+            "cg_4000": cg, "serving": serving,
             "plan": {"phases": st["phases"], "barriers": st["barriers"], "skew": st["skew"],
                      "plan_cache_hits": st["plan_cache_hits"]} if st else None}
     if rank == 0:

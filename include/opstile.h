@@ -268,6 +268,42 @@ int ops_cg_solve_batch(ops_ctx ctx, int count, const int* n, const double* const
                        const double* const* host_rhs, const ops_cg_params* params, double* const* host_x,
                        ops_cg_stats* stats);
 
+/* ---- serving: continuous batching of heat-conduction solves ----
+ * A server owns a context on cfg->device and one device pool of
+ * cfg->hbm_budget bytes.  Submitted requests queue in FIFO order; a worker
+ * thread admits the oldest ones whenever the running batch has fewer than
+ * max_batch solves and the pool has room for the request's arrays (about
+ * 92 bytes per cell), advances every admitted solve ticks_per_poll CG
+ * iterations at a time in one batch, and retires finished ones, so requests
+ * arriving while others run join the batch as memory frees up.  Each
+ * request's result is the same alone and in any mix (see ops_cg_solve_batch).
+ * The serving loop itself makes no device allocation. */
+typedef struct ops_server_s* ops_server;
+typedef struct {
+  int device;
+  int64_t hbm_budget;    /* bytes of the request pool */
+  int max_batch;         /* solves advanced together (0: 1024) */
+  int ticks_per_poll;    /* CG iterations between completion checks (0: 4) */
+  ops_cg_params params;  /* tolerance, precision, caps for every request */
+} ops_serve_config;
+typedef struct {
+  int iterations, outer, converged;
+  double relres;
+  double queue_ms;       /* submit -> admitted */
+  double service_ms;     /* admitted -> result ready */
+  double latency_ms;     /* submit -> result ready */
+  double submit_ms, done_ms;  /* host steady-clock stamps (ms) */
+} ops_solve_stats;
+int ops_serve_open(ops_server* out, const ops_serve_config* cfg);
+/* Queue a solve (arrays of n*n doubles are copied); *id identifies it.
+ * OPS_ERR_NOMEM if it could never fit the pool. */
+int ops_serve_submit(ops_server srv, int n, const double* host_kappa, const double* host_rhs, uint64_t* id);
+/* OPS_OK and x (n*n doubles) + stats once the solve is done (the request is
+ * then forgotten); OPS_ERR_STATE while pending (wait = 0); wait = 1 blocks. */
+int ops_serve_poll(ops_server srv, uint64_t id, int wait, double* host_x, ops_solve_stats* stats);
+/* Finish running solves, drop queued ones, free the pool and the context. */
+int ops_serve_close(ops_server srv);
+
 /* ---- one loop without any device allocation ----
  * The paper has no counterpart: this is a service for callers that must not
  * allocate device memory.  cudaMalloc and cudaFree can synchronise the whole

@@ -336,3 +336,60 @@ def ops_cg_solve(ctx, kappa, rhs, tol: float, precision: int, maxit: int = 10000
                  maxouter: int = 0):
     xs, st = ops_cg_solve_batch(ctx, [kappa], [rhs], tol, precision, maxit, inner_tol, maxouter)
     return xs[0], st[0]
+
+
+# ------------------------------------------------------------------ serving
+class ops_serve_config(C.Structure):
+    _fields_ = [("device", C.c_int), ("hbm_budget", C.c_int64), ("max_batch", C.c_int), ("ticks_per_poll", C.c_int),
+                ("params", ops_cg_params)]
+
+
+class ops_solve_stats(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("outer", C.c_int), ("converged", C.c_int), ("relres", C.c_double),
+                ("queue_ms", C.c_double), ("service_ms", C.c_double), ("latency_ms", C.c_double),
+                ("submit_ms", C.c_double), ("done_ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def ops_serve_open(tol: float, precision: int, hbm_budget: int, device: int = 0, max_batch: int = 0,
+                   ticks_per_poll: int = 0, maxit: int = 100000, inner_tol: float = 0.0, maxouter: int = 0):
+    cfg = ops_serve_config(device, int(hbm_budget), int(max_batch), int(ticks_per_poll),
+                           _cg_params(tol, precision, maxit, inner_tol, maxouter))
+    srv = C.c_void_p()
+    rc = load().ops_serve_open(C.byref(srv), C.byref(cfg))
+    if rc != OPS_OK:
+        raise OpsError(rc, "ops_serve_open failed")
+    return srv
+
+
+def ops_serve_submit(srv, kappa: np.ndarray, rhs: np.ndarray) -> int:
+    n = kappa.shape[0]
+    k = np.ascontiguousarray(kappa, dtype=np.float64)
+    b = np.ascontiguousarray(rhs, dtype=np.float64)
+    rid = C.c_uint64()
+    P = C.POINTER(C.c_double)
+    rc = load().ops_serve_submit(srv, C.c_int(n), k.ctypes.data_as(P), b.ctypes.data_as(P), C.byref(rid))
+    if rc != OPS_OK:
+        raise OpsError(rc, "ops_serve_submit failed")
+    return rid.value
+
+
+def ops_serve_poll(srv, rid: int, n: int, wait: bool = True):
+    """(x, stats) once done; None while pending (wait=False)."""
+    x = np.empty((n, n))
+    st = ops_solve_stats()
+    rc = load().ops_serve_poll(srv, C.c_uint64(rid), C.c_int(1 if wait else 0),
+                               x.ctypes.data_as(C.POINTER(C.c_double)), C.byref(st))
+    if rc == OPS_ERR_STATE:
+        return None
+    if rc != OPS_OK:
+        raise OpsError(rc, "ops_serve_poll failed")
+    return x, st.as_dict()
+
+
+def ops_serve_close(srv):
+    rc = load().ops_serve_close(srv)
+    if rc != OPS_OK:
+        raise OpsError(rc, "ops_serve_close failed")

@@ -5,7 +5,10 @@
 //     takes the cell's own), d_c = 1 + sum_f k_f, neighbours outside are 0;
 //   - mixed precision: the bandwidth-bound sweeps (matvec, axpy) run in FP32
 //     with FP32 copies of the face coefficients; dot products accumulate the
-//     exact FP64 products of FP32 values in double-double; the residual
+//     (exact) FP64 products of FP32 values with one FP64 fma per term per
+//     thread, then fixed-order FP64 trees over threads, units and problems
+//     (compensated two-sums per term, or long dependent chains of them, would
+//     make the solver FP64-latency-bound on GB300); the residual
 //     r = b - A x, its norm and the correction x += |r| d are FP64
 //     (iterative refinement);
 //   - every problem is a state machine advanced by one CG iteration per
@@ -24,40 +27,26 @@
 namespace opstile {
 
 constexpr int kCgThreads = 256;
-constexpr int kCgUnitPts = 2048;
+constexpr int kCgUnitPts = 8192;  // points per work unit (whole rows where they fit)
 
 // ---------------------------------------------------------------------------
-// double-double accumulation (two-sum), as in the chain kernels
+// reductions
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ DD cg_dd_add(DD a, double x) {
-  const double s = __dadd_rn(a.hi, x);
-  const double bp = __dsub_rn(s, a.hi);
-  const double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bp)), __dsub_rn(x, bp));
-  return DD{s, __dadd_rn(a.lo, e)};
-}
-__device__ __forceinline__ DD cg_dd_merge(DD a, DD b) {
-  DD t = cg_dd_add(a, b.hi);
-  t.lo = __dadd_rn(t.lo, b.lo);
-  return t;
-}
-__device__ __forceinline__ DD cg_shfl(DD v, int o) {
-  return DD{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
-}
-// block sum in a fixed tree, valid in thread 0
-__device__ DD cg_block_sum(DD v, DD* sh) {
-  for (int o = 16; o > 0; o >>= 1) v = cg_dd_merge(v, cg_shfl(v, o));
+// block sum of doubles in a fixed tree (plain FP64: short dependent chains,
+// which matter on GB300's slow FP64 pipe), valid in thread 0
+__device__ double cg_block_sum_d(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   __syncthreads();
   if (lane == 0) sh[w] = v;
   __syncthreads();
   if (w == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : DD{0.0, 0.0};
-    for (int o = 16; o > 0; o >>= 1) v = cg_dd_merge(v, cg_shfl(v, o));
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
   }
   __syncthreads();
   return v;
 }
-
 // ---------------------------------------------------------------------------
 // the operator at one cell, in the fixed term order
 // ---------------------------------------------------------------------------
@@ -171,12 +160,12 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_setup2(CgProb* probs, const C
 // ---------------------------------------------------------------------------
 // A: residual (OUTER/FINISH), w = A p (INNER, CG64); partial dots per unit
 __global__ void __launch_bounds__(kCgThreads) k_cg_a(CgProb* probs, const CgUnit* units, int nunits, DD* part) {
-  __shared__ DD sh[32];
+  __shared__ double sh[32];
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const CgUnit U = units[u];
     const CgProb& P = probs[U.prob];
     const int st = P.state, n = P.n;
-    DD acc{0.0, 0.0};
+    double acc = 0.0;  // per-thread FP64 fma accumulation, then a fixed FP64 tree
     if (st == CG_OUTER || st == CG_FINISH) {
       const OpView<double> A{P.kx, P.ky, P.dg, n};
       const double* x = P.x;
@@ -186,7 +175,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_a(CgProb* probs, const CgUnit
         const int64_t c = (int64_t)j * n + i;
         const double rc = __dsub_rn(b[c], av64(A, x, j, i));
         r[c] = rc;
-        acc = cg_dd_add(acc, __dmul_rn(rc, rc));
+        acc = __fma_rn(rc, rc, acc);
       });
     } else if (st == CG_INNER) {
       const OpView<float> A{P.kx32, P.ky32, P.dg32, n};
@@ -196,7 +185,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_a(CgProb* probs, const CgUnit
         const int64_t c = (int64_t)j * n + i;
         const float wc = av32(A, p, j, i);
         w[c] = wc;
-        acc = cg_dd_add(acc, __dmul_rn((double)p[c], (double)wc));
+        acc = __fma_rn((double)p[c], (double)wc, acc);
       });
     } else if (st == CG64) {
       const OpView<double> A{P.kx, P.ky, P.dg, n};
@@ -206,22 +195,22 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_a(CgProb* probs, const CgUnit
         const int64_t c = (int64_t)j * n + i;
         const double wc = av64(A, p, j, i);
         w[c] = wc;
-        acc = cg_dd_add(acc, __dmul_rn(p[c], wc));
+        acc = __fma_rn(p[c], wc, acc);
       });
     }
-    acc = cg_block_sum(acc, sh);
-    if (threadIdx.x == 0) part[u] = acc;
+    const double tot = cg_block_sum_d(acc, sh);
+    if (threadIdx.x == 0) part[u] = DD{tot, 0.0};
   }
 }
 
 // B: INIT (scaled residual into the FP32 inner vectors), INNER / CG64 updates
 __global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit* units, int nunits, DD* part) {
-  __shared__ DD sh[32];
+  __shared__ double sh[32];
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const CgUnit U = units[u];
     const CgProb& P = probs[U.prob];
     const int st = P.state, n = P.n;
-    DD acc{0.0, 0.0};
+    double acc = 0.0;  // per-thread FP64 fma accumulation, then a fixed FP64 tree
     if (st == CG_INIT) {
       const double inv = __ddiv_rn(1.0, P.nr);
       const double* r = P.r;
@@ -232,7 +221,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit
         r32[c] = rs;
         p32[c] = rs;
         d32[c] = 0.0f;
-        acc = cg_dd_add(acc, __dmul_rn((double)rs, (double)rs));
+        acc = __fma_rn((double)rs, (double)rs, acc);
       });
     } else if (st == CG_INNER) {
       const float af = (float)P.alpha;
@@ -243,7 +232,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit
         d32[c] = __fmaf_rn(af, p32[c], d32[c]);
         const float r = __fmaf_rn(-af, w32[c], r32[c]);
         r32[c] = r;
-        acc = cg_dd_add(acc, __dmul_rn((double)r, (double)r));
+        acc = __fma_rn((double)r, (double)r, acc);
       });
     } else if (st == CG64_INIT) {
       const double* b = P.b;
@@ -254,7 +243,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit
         x[c] = 0.0;
         r[c] = bc;
         p[c] = bc;
-        acc = cg_dd_add(acc, __dmul_rn(bc, bc));
+        acc = __fma_rn(bc, bc, acc);
       });
     } else if (st == CG64) {
       const double a = P.alpha;
@@ -265,11 +254,11 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit
         x[c] = __fma_rn(a, p[c], x[c]);
         const double rc = __fma_rn(-a, w[c], r[c]);
         r[c] = rc;
-        acc = cg_dd_add(acc, __dmul_rn(rc, rc));
+        acc = __fma_rn(rc, rc, acc);
       });
     }
-    acc = cg_block_sum(acc, sh);
-    if (threadIdx.x == 0) part[u] = acc;
+    const double tot = cg_block_sum_d(acc, sh);
+    if (threadIdx.x == 0) part[u] = DD{tot, 0.0};
   }
 }
 
@@ -329,24 +318,24 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_apply(const CgProb* probs, co
   }
 }
 
-// Sum of a problem's unit partials in a fixed order (one warp per problem).
-__device__ __forceinline__ double warp_partial_sum(const DD* part, int u0, int u1) {
-  const int lane = threadIdx.x & 31;
-  DD v{0.0, 0.0};
-  for (int u = u0 + lane; u < u1; u += 32) v = cg_dd_merge(v, part[u]);
-  for (int o = 16; o > 0; o >>= 1) v = cg_dd_merge(v, cg_shfl(v, o));
-  return __dadd_rn(v.hi, v.lo);
+// Sum of a problem's unit partials in a fixed order (one block per problem,
+// thread-strided then a fixed tree); valid in thread 0.
+__device__ __forceinline__ double block_partial_sum(const DD* part, int u0, int u1, double* sh) {
+  double v = 0.0;
+  for (int u = u0 + (int)threadIdx.x; u < u1; u += blockDim.x) v = __dadd_rn(v, __dadd_rn(part[u].hi, part[u].lo));
+  return cg_block_sum_d(v, sh);
 }
 
 // Scalars after kernel A.
 __global__ void k_cg_s1(CgProb* probs, const int2* ranges, int nslots, const DD* part) {
-  const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  __shared__ double sh[32];
+  const int p = blockIdx.x;
   if (p >= nslots) return;
   CgProb& P = probs[p];
-  const int st = P.state;
+  const int st = P.state;  // uniform over the block
   if (st != CG_OUTER && st != CG_FINISH && st != CG_INNER && st != CG64) return;
-  const double s = warp_partial_sum(part, ranges[p].x, ranges[p].y);
-  if ((threadIdx.x & 31) != 0) return;
+  const double s = block_partial_sum(part, ranges[p].x, ranges[p].y, sh);
+  if (threadIdx.x != 0) return;
   if (st == CG_OUTER || st == CG_FINISH) {
     if (st == CG_FINISH) ++P.outer;
     const double nr = sqrt(s);
@@ -369,13 +358,14 @@ __global__ void k_cg_s1(CgProb* probs, const int2* ranges, int nslots, const DD*
 
 // Scalars after kernel B.
 __global__ void k_cg_s2(CgProb* probs, const int2* ranges, int nslots, const DD* part) {
-  const int p = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  __shared__ double sh[32];
+  const int p = blockIdx.x;
   if (p >= nslots) return;
   CgProb& P = probs[p];
-  const int st = P.state;
+  const int st = P.state;  // uniform over the block
   if (st != CG_INIT && st != CG_INNER && st != CG64_INIT && st != CG64) return;
-  const double s = warp_partial_sum(part, ranges[p].x, ranges[p].y);
-  if ((threadIdx.x & 31) != 0) return;
+  const double s = block_partial_sum(part, ranges[p].x, ranges[p].y, sh);
+  if (threadIdx.x != 0) return;
   if (st == CG_INIT) {
     P.rho = s;
     P.rho0 = s;
@@ -429,14 +419,17 @@ CgBatch::CgBatch(cudaStream_t stream, int num_sms) : stream_(stream), num_sms_(n
 
 CgBatch::~CgBatch() {
   cudaStreamSynchronize(stream_);
+  if (gexec_) cudaGraphExecDestroy(gexec_);
   cudaFree(dprob_);
   cudaFree(dunits_);
   cudaFree(dranges_);
   cudaFree(dpart_);
 }
 
+// Units of whole rows holding about kCgUnitPts cells (rows wider than that
+// are cut into column chunks); they depend only on n, never on the batch.
 static void units_for(int slot, int n, std::vector<CgUnit>& out) {
-  if (n >= kCgThreads) {
+  if (n > kCgUnitPts) {
     for (int j = 0; j < n; ++j)
       for (int c0 = 0; c0 < n; c0 += kCgUnitPts) out.push_back(CgUnit{slot, j, 1, c0, std::min(kCgUnitPts, n - c0)});
   } else {
@@ -587,6 +580,10 @@ cudaError_t CgBatch::rebuild_units() {
     }
   }
   units_dirty_ = false;
+  if (gexec_) {  // the captured ticks refer to the old unit table
+    cudaGraphExecDestroy(gexec_);
+    gexec_ = nullptr;
+  }
   return cudaSuccess;
 }
 
@@ -599,15 +596,29 @@ cudaError_t CgBatch::run(int ticks) {
   const int nslots = (int)hprob_.size();
   const int2* ranges = dranges_;
   const int g = std::max(1, std::min(nunits_, num_sms_ * 8));
-  const int gs = (nslots + 7) / 8;
-  for (int t = 0; t < ticks; ++t) {
-    k_cg_a<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_, dpart_);
-    k_cg_s1<<<gs, 256, 0, stream_>>>(dprob_, ranges, nslots, dpart_);
-    k_cg_b<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_, dpart_);
-    k_cg_s2<<<gs, 256, 0, stream_>>>(dprob_, ranges, nslots, dpart_);
-    k_cg_c<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_);
+  const int gs = nslots;  // scalar kernels: one block per problem slot
+  // the tick sequence is captured once per batch composition and replayed
+  if (!gexec_ || gticks_ != ticks) {
+    if (gexec_) cudaGraphExecDestroy(gexec_);
+    gexec_ = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (int t = 0; t < ticks; ++t) {
+      k_cg_a<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_, dpart_);
+      k_cg_s1<<<gs, 256, 0, stream_>>>(dprob_, ranges, nslots, dpart_);
+      k_cg_b<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_, dpart_);
+      k_cg_s2<<<gs, 256, 0, stream_>>>(dprob_, ranges, nslots, dpart_);
+      k_cg_c<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(stream_, &graph);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&gexec_, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    gticks_ = ticks;
   }
-  return cudaGetLastError();
+  return cudaGraphLaunch(gexec_, stream_);
 }
 
 cudaError_t CgBatch::poll(std::vector<int>& done) {

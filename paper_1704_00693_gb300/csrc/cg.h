@@ -83,6 +83,8 @@ class CgBatch {
   int dpart_cap_ = 0;
   bool units_dirty_ = true;
   std::vector<int> hstate_;
+  cudaGraphExec_t gexec_ = nullptr;  // captured tick sequence for the current units
+  int gticks_ = 0;
 };
 
 }  // namespace opstile

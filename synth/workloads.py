@@ -435,8 +435,12 @@ def cg_problem(n: int, klo: float, khi: float, seed: int = None):
     """Cell conductivity log-uniform in [klo, khi] and a U(0,1) right-hand side
     on an n x n grid (row-major, x fastest)."""
     seed = R.subseed(R.BASE_SEED, "cg", n) if seed is None else seed
-    kappa = R.log_uniform(R.subseed(seed, "kappa"), (n, n), klo, khi)
-    rhs = R.uniform(R.subseed(seed, "rhs"), (n, n))
+    # numpy's PCG64 (same stream on every platform) is used here for speed:
+    # the serving workload draws hundreds of grids of up to 2048^2 cells
+    g = np.random.Generator(np.random.PCG64(seed & ((1 << 63) - 1)))
+    u = g.random((n, n))
+    kappa = np.exp(np.log(klo) + (np.log(khi) - np.log(klo)) * u)
+    rhs = g.random((n, n))
     return kappa, rhs
 
 
