@@ -57,6 +57,11 @@ extern "C" {
 #define OPS_MODE_UNTILED 0    /* one kernel per loop over its full range (the comparator) */
 #define OPS_MODE_SKEWED 1     /* Algorithm 1 tiles, run by one persistent kernel (Algorithm 2) */
 #define OPS_MODE_OVERLAPPED 2 /* independent shared-memory tiles with halo recomputation (Sec. 4.D) */
+/* OPS_MODE_OVERLAPPED applies to a segment whose dats are all library-owned
+ * with one common size and halo, and whose tile footprints fit one CTA's
+ * shared memory after the tile is shrunk; other segments run skewed.  It
+ * writes every written dat into a second buffer of the same shape, which then
+ * becomes the dat's storage: ops_dat_info returns the new address. */
 #define OPS_MODE_AUTO 3       /* library picks per segment */
 
 /* ---- argument kinds, access modes, reduction operators ---- */
@@ -222,6 +227,14 @@ int ops_last_stats(ops_ctx ctx, ops_flush_stats* out);
  * ntiles of the dimensions before d; out_ntiles[d] receives the tile counts.
  * cap is the number of ints out_ranges can hold. */
 int ops_plan_skewed(ops_ctx ctx, const int* tile, int* out_ntiles, int* out_ranges, int64_t cap);
+/* Build the overlapped-tile geometry (Sec. 4.D) of one tile for the currently
+ * queued loops, without executing them.  owned = x0 x1 y0 y1 z0 z1 of the
+ * tile (half-open).  out_boxes receives 6 ints per queued loop: the box that
+ * loop computes inside the tile (all zero when empty); out_foot receives 6
+ * ints per declared dat: the box of its values the tile's loops read (lo >
+ * hi in every dimension when no loop reads it).  Dimensions >= the loops'
+ * dimensionality hold the loops' (0, 1). */
+int ops_plan_overlapped(ops_ctx ctx, const int owned[6], int* out_boxes, int* out_foot);
 
 /* ---- heat-conduction solves (TeaLeaf-shaped, Sec. 5 and Sec. 6.C) ----
  * Solve A x = b on an n x n cell grid for the implicit heat-conduction

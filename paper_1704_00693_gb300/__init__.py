@@ -240,6 +240,20 @@ def ops_plan_skewed(ctx, tile, ndim: int, nloops: int):
     return out
 
 
+def ops_plan_overlapped(ctx, owned, nloops: int, ndats: int):
+    """Overlapped-tile geometry of one tile for the queued loops: (boxes
+    [nloops, 3, 2], footprints [ndats, 3, 2]); owned = per-dimension (lo, hi)."""
+    o = np.zeros(6, dtype=np.int32)
+    for d in range(3):
+        o[2 * d], o[2 * d + 1] = owned[d] if d < len(owned) else (0, 1)
+    boxes = np.zeros(6 * max(1, nloops), dtype=np.int32)
+    foot = np.zeros(6 * max(1, ndats), dtype=np.int32)
+    ip = C.POINTER(C.c_int)
+    _check(ctx, load().ops_plan_overlapped(ctx, o.ctypes.data_as(ip), boxes.ctypes.data_as(ip),
+                                           foot.ctypes.data_as(ip)))
+    return boxes[:6 * nloops].reshape(nloops, 3, 2).copy(), foot[:6 * ndats].reshape(ndats, 3, 2).copy()
+
+
 # ------------------------------------------------ one loop, no device allocation
 class ops_dat_view(C.Structure):
     _fields_ = [("ptr0", C.c_void_p), ("pitch", C.c_int64), ("plane", C.c_int64), ("lo", C.c_int * 3),

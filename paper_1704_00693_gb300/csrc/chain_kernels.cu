@@ -31,13 +31,19 @@ namespace opstile {
 #endif
 constexpr int kPts = OPS_PTS;  // points per thread
 
-// Shared memory of the chain kernels (dynamic, 16-byte aligned).
-struct ChainSmem {
+// Shared memory of the chain kernels (dynamic, 16-byte aligned), for P
+// points per thread.
+template <int P>
+struct ChainSmemT {
   DLoop L;
   DD sh[32];                                 // block reductions
   DD sred[OPS_MAX_REDS_PER_LOOP * kThreads]; // per-thread reduction accumulators
-  double R[kNReg * kPts * kThreads];         // IR registers [reg][point][thread]
+  int own[6];                                // overlapped tiles: only points in this box reduce
+  int own_check;
+  int pad_;
+  double R[kNReg * P * kThreads];            // IR registers [reg][point][thread]
 };
+using ChainSmem = ChainSmemT<kPts>;
 constexpr size_t kChainSmem = sizeof(ChainSmem);
 
 // ----------------------------------------------------------------------------
@@ -87,15 +93,17 @@ __device__ DD block_combine(int op, DD v, DD* sh) {
   return v;
 }
 
-__device__ __forceinline__ void red_init(ChainSmem& S) {
+template <int P>
+__device__ __forceinline__ void red_init(ChainSmemT<P>& S) {
   for (int k = 0; k < S.L.nreds; ++k) S.sred[k * kThreads + threadIdx.x] = DD{red_identity(S.L.red_op[k]), 0.0};
 }
 
 // ----------------------------------------------------------------------------
 // a group of points
 // ----------------------------------------------------------------------------
-struct Group {
-  int x[kPts], y[kPts], z[kPts];
+template <int P>
+struct GroupT {
+  int x[P], y[P], z[P];
   unsigned mask;  // bit p: point p exists
 };
 
@@ -113,19 +121,21 @@ __device__ __forceinline__ bool point_ok(const DLoop& L, int x, int y, int z) {
 }
 
 // Address of the group's point p in the dat of argument A.
-__device__ __forceinline__ const double* gptr(const DArg& A, const Group& g, int p) {
+template <int P>
+__device__ __forceinline__ const double* gptr(const DArg& A, const GroupT<P>& g, int p) {
   return A.ptr0 + ((int64_t)g.x[p] + (int64_t)g.y[p] * A.pitch + (int64_t)g.z[p] * A.plane);
 }
 
-__device__ __forceinline__ void run_group(ChainSmem& S, const Group& g, const double* __restrict__ scal) {
+template <int P>
+__device__ __forceinline__ void run_group(ChainSmemT<P>& S, const GroupT<P>& g, const double* __restrict__ scal) {
   const DLoop& L = S.L;
-  double* Rt = S.R + threadIdx.x;  // register r, point p at Rt[(r * kPts + p) * kThreads]
-  constexpr int RS = kPts * kThreads;
+  double* Rt = S.R + threadIdx.x;  // register r, point p at Rt[(r * P + p) * kThreads]
+  constexpr int RS = P * kThreads;
   const unsigned m = g.mask;
   for (int r = 0; r < kNReg; ++r)
     if ((L.zmask >> r) & 1) {
 #pragma unroll
-      for (int p = 0; p < kPts; ++p) Rt[r * RS + p * kThreads] = 0.0;
+      for (int p = 0; p < P; ++p) Rt[r * RS + p * kThreads] = 0.0;
     }
   const int nins = L.nins;
   for (int pc = 0; pc < nins; ++pc) {
@@ -142,49 +152,49 @@ __device__ __forceinline__ void run_group(ChainSmem& S, const Group& g, const do
         if (A.kind == OPS_ARG_SCALAR) {
           const double v = scal[A.slot];
 #pragma unroll
-          for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = v;
+          for (int p = 0; p < P; ++p) Rd[p * kThreads] = v;
         } else {
           const int32_t o = A.off[i23.y];
-          double v[kPts];
+          double v[P];
 #pragma unroll
-          for (int p = 0; p < kPts; ++p) v[p] = ((m >> p) & 1u) ? gptr(A, g, p)[o] : 0.0;
+          for (int p = 0; p < P; ++p) v[p] = ((m >> p) & 1u) ? gptr(A, g, p)[o] : 0.0;
 #pragma unroll
-          for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = v[p];
+          for (int p = 0; p < P; ++p) Rd[p * kThreads] = v[p];
         }
         break;
       }
       case OPS_IR_CST: {
         const double v = L.K[i23.x];
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = v;
+        for (int p = 0; p < P; ++p) Rd[p * kThreads] = v;
         break;
       }
       case OPS_IR_ADD:
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = __dadd_rn(Ra[p * kThreads], Rb[p * kThreads]);
+        for (int p = 0; p < P; ++p) Rd[p * kThreads] = __dadd_rn(Ra[p * kThreads], Rb[p * kThreads]);
         break;
       case OPS_IR_SUB:
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = __dsub_rn(Ra[p * kThreads], Rb[p * kThreads]);
+        for (int p = 0; p < P; ++p) Rd[p * kThreads] = __dsub_rn(Ra[p * kThreads], Rb[p * kThreads]);
         break;
       case OPS_IR_MUL:
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = __dmul_rn(Ra[p * kThreads], Rb[p * kThreads]);
+        for (int p = 0; p < P; ++p) Rd[p * kThreads] = __dmul_rn(Ra[p * kThreads], Rb[p * kThreads]);
         break;
       case OPS_IR_DIV:
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = __ddiv_rn(Ra[p * kThreads], Rb[p * kThreads]);
+        for (int p = 0; p < P; ++p) Rd[p * kThreads] = __ddiv_rn(Ra[p * kThreads], Rb[p * kThreads]);
         break;
       case OPS_IR_MIN:
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) {
+        for (int p = 0; p < P; ++p) {
           const double a = Ra[p * kThreads], b = Rb[p * kThreads];
           Rd[p * kThreads] = (b < a) ? b : a;
         }
         break;
       case OPS_IR_MAX:
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) {
+        for (int p = 0; p < P; ++p) {
           const double a = Ra[p * kThreads], b = Rb[p * kThreads];
           Rd[p * kThreads] = (b > a) ? b : a;
         }
@@ -192,7 +202,7 @@ __device__ __forceinline__ void run_group(ChainSmem& S, const Group& g, const do
       case OPS_IR_FMA: {
         const double* Rc = Rt + i45.x * RS;
 #pragma unroll
-        for (int p = 0; p < kPts; ++p)
+        for (int p = 0; p < P; ++p)
           Rd[p * kThreads] = __fma_rn(Ra[p * kThreads], Rb[p * kThreads], Rc[p * kThreads]);
         break;
       }
@@ -200,7 +210,7 @@ __device__ __forceinline__ void run_group(ChainSmem& S, const Group& g, const do
         const double* Rc = Rt + i45.x * RS;
         const double* Re = Rt + i45.y * RS;
 #pragma unroll
-        for (int p = 0; p < kPts; ++p)
+        for (int p = 0; p < P; ++p)
           Rd[p * kThreads] = (Ra[p * kThreads] > Rb[p * kThreads]) ? Rc[p * kThreads] : Re[p * kThreads];
         break;
       }
@@ -209,67 +219,67 @@ __device__ __forceinline__ void run_group(ChainSmem& S, const Group& g, const do
         const DArg& A = L.args[i23.x];
         const double* Kb = L.K + i23.y;
         const int n = A.npts;
-        const double* base[kPts];
-        double t[kPts];
+        const double* base[P];
+        double t[P];
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) base[p] = gptr(A, g, p);
+        for (int p = 0; p < P; ++p) base[p] = gptr(A, g, p);
         int q = 0;
         if (op == OPS_IR_WSUM) {
           const int32_t o = A.off[0];
           const double k = Kb[0];
 #pragma unroll
-          for (int p = 0; p < kPts; ++p) t[p] = __dmul_rn(k, ((m >> p) & 1u) ? base[p][o] : 0.0);
+          for (int p = 0; p < P; ++p) t[p] = __dmul_rn(k, ((m >> p) & 1u) ? base[p][o] : 0.0);
           q = 1;
         } else {
 #pragma unroll
-          for (int p = 0; p < kPts; ++p) t[p] = Rd[p * kThreads];
+          for (int p = 0; p < P; ++p) t[p] = Rd[p * kThreads];
         }
         for (; q + 2 <= n; q += 2) {
           const int32_t o0 = A.off[q], o1 = A.off[q + 1];
           const double k0 = Kb[q], k1 = Kb[q + 1];
-          double v0[kPts], v1[kPts];
+          double v0[P], v1[P];
 #pragma unroll
-          for (int p = 0; p < kPts; ++p) {
+          for (int p = 0; p < P; ++p) {
             const bool on = (m >> p) & 1u;
             v0[p] = on ? base[p][o0] : 0.0;
             v1[p] = on ? base[p][o1] : 0.0;
           }
 #pragma unroll
-          for (int p = 0; p < kPts; ++p) t[p] = __fma_rn(k1, v1[p], __fma_rn(k0, v0[p], t[p]));
+          for (int p = 0; p < P; ++p) t[p] = __fma_rn(k1, v1[p], __fma_rn(k0, v0[p], t[p]));
         }
         if (q < n) {
           const int32_t o = A.off[q];
           const double k = Kb[q];
 #pragma unroll
-          for (int p = 0; p < kPts; ++p) t[p] = __fma_rn(k, ((m >> p) & 1u) ? base[p][o] : 0.0, t[p]);
+          for (int p = 0; p < P; ++p) t[p] = __fma_rn(k, ((m >> p) & 1u) ? base[p][o] : 0.0, t[p]);
         }
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = t[p];
+        for (int p = 0; p < P; ++p) Rd[p * kThreads] = t[p];
         break;
       }
       case OPS_IR_POLY: {
         const int c = i45.x;
         const double* Kb = L.K + i23.y;
-        double x[kPts], t[kPts];
+        double x[P], t[P];
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) {
+        for (int p = 0; p < P; ++p) {
           x[p] = Ra[p * kThreads];
           t[p] = Kb[c];
         }
         for (int i = c - 1; i >= 0; --i) {
           const double k = Kb[i];
 #pragma unroll
-          for (int p = 0; p < kPts; ++p) t[p] = __fma_rn(t[p], x[p], k);
+          for (int p = 0; p < P; ++p) t[p] = __fma_rn(t[p], x[p], k);
         }
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) Rd[p * kThreads] = t[p];
+        for (int p = 0; p < P; ++p) Rd[p * kThreads] = t[p];
         break;
       }
       case OPS_IR_ST: {
         const DArg& A = L.args[i01.y];
         const bool inc = A.access == OPS_INC;
 #pragma unroll
-        for (int p = 0; p < kPts; ++p) {
+        for (int p = 0; p < P; ++p) {
           if ((m >> p) & 1u) {
             double* q = const_cast<double*>(gptr(A, g, p));
             const double v = Ra[p * kThreads];
@@ -284,8 +294,13 @@ __device__ __forceinline__ void run_group(ChainSmem& S, const Group& g, const do
         DD* slot = S.sred + k * kThreads + threadIdx.x;
         DD acc = *slot;
 #pragma unroll
-        for (int p = 0; p < kPts; ++p)
-          if ((m >> p) & 1u) acc = red_add(rop, acc, Ra[p * kThreads]);
+        for (int p = 0; p < P; ++p) {
+          if (!((m >> p) & 1u)) continue;
+          if (S.own_check && (g.x[p] < S.own[0] || g.x[p] >= S.own[1] || g.y[p] < S.own[2] || g.y[p] >= S.own[3] ||
+                              g.z[p] < S.own[4] || g.z[p] >= S.own[5]))
+            continue;  // redundant point of an overlapped tile
+          acc = red_add(rop, acc, Ra[p * kThreads]);
+        }
         *slot = acc;
         break;
       }
@@ -304,9 +319,10 @@ __device__ __forceinline__ void stage_loop(DLoop* dst, const DLoop* src) {
 }
 
 // Drop points that fail the checked-mode test, flagging the error word.
-__device__ __forceinline__ void check_group(const DLoop& L, Group& g, int* err) {
+template <int P>
+__device__ __forceinline__ void check_group(const DLoop& L, GroupT<P>& g, int* err) {
 #pragma unroll
-  for (int p = 0; p < kPts; ++p)
+  for (int p = 0; p < P; ++p)
     if (((g.mask >> p) & 1u) && !point_ok(L, g.x[p], g.y[p], g.z[p])) {
       g.mask &= ~(1u << p);
       atomicCAS(err, 0, kDevErrBounds);
@@ -319,16 +335,17 @@ __device__ __forceinline__ void check_group(const DLoop& L, Group& g, int* err) 
 // the rows share stencil neighbours in L1); thinner boxes are flattened into
 // units of 256 * kPts points.  Units are enumerated as part, part + nparts,
 // ... with coordinates advanced incrementally (no division in the loop).
-__device__ __forceinline__ void run_box(ChainSmem& S, const int* box, const double* __restrict__ scal, int part,
+template <int P>
+__device__ __forceinline__ void run_box(ChainSmemT<P>& S, const int* box, const double* __restrict__ scal, int part,
                                         int nparts, int check, int* err) {
   const int x0 = box[0], nx = box[1] - box[0];
   const int y0 = box[2], ny = box[3] - box[2];
   const int z0 = box[4], nz = box[5] - box[4];
   if (nx <= 0 || ny <= 0 || nz <= 0) return;
-  Group g;
+  GroupT<P> g;
   if (nx >= 128) {
     const int xch = (nx + kThreads - 1) / kThreads;
-    const int nrg = (ny + kPts - 1) / kPts;  // row groups per plane
+    const int nrg = (ny + P - 1) / P;  // row groups per plane
     const int nunits = xch * nrg * nz;
     int u = part;
     int xc = u % xch, rg = (u / xch) % nrg, z = u / (xch * nrg);
@@ -337,8 +354,8 @@ __device__ __forceinline__ void run_box(ChainSmem& S, const int* box, const doub
       const int x = x0 + xc * kThreads + (int)threadIdx.x;
       g.mask = 0;
 #pragma unroll
-      for (int p = 0; p < kPts; ++p) {
-        const int y = rg * kPts + p;
+      for (int p = 0; p < P; ++p) {
+        const int y = rg * P + p;
         g.x[p] = x;
         g.y[p] = y0 + y;
         g.z[p] = z0 + z;
@@ -361,9 +378,9 @@ __device__ __forceinline__ void run_box(ChainSmem& S, const int* box, const doub
     }
   } else {
     const int npts = nx * ny * nz;
-    const int step = nparts * kThreads * kPts;
+    const int step = nparts * kThreads * P;
     // point p of the thread's group: linear index i + p * kThreads
-    int i = part * kThreads * kPts + (int)threadIdx.x;
+    int i = part * kThreads * P + (int)threadIdx.x;
     int x = i % nx, row = i / nx;
     int y = row % ny, zz = row / ny;
     const int dx = step % nx, drow = step / nx;
@@ -374,7 +391,7 @@ __device__ __forceinline__ void run_box(ChainSmem& S, const int* box, const doub
       g.mask = 0;
       int xp = x, yp = y, zp = zz;
 #pragma unroll
-      for (int p = 0; p < kPts; ++p) {
+      for (int p = 0; p < P; ++p) {
         g.x[p] = x0 + xp;
         g.y[p] = y0 + yp;
         g.z[p] = z0 + zp;
@@ -410,7 +427,8 @@ __device__ __forceinline__ void run_box(ChainSmem& S, const int* box, const doub
 }
 
 // Fold this CTA's reduction accumulators into its partial column (assign or combine).
-__device__ __forceinline__ void flush_partials(ChainSmem& S, DD* part, int stride, bool assign) {
+template <int P>
+__device__ __forceinline__ void flush_partials(ChainSmemT<P>& S, DD* part, int stride, bool assign) {
   const DLoop& L = S.L;
   for (int k = 0; k < L.nreds; ++k) {
     const int op = L.red_op[k];
@@ -433,6 +451,7 @@ __global__ void __launch_bounds__(kThreads, OPS_MIN_CTAS) k_untiled(const DLoop*
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ChainSmem& S = *reinterpret_cast<ChainSmem*>(smem_raw);
   stage_loop(&S.L, gL);
+  if (threadIdx.x == 0) S.own_check = 0;
   __syncthreads();
   red_init(S);
   const int box[6] = {bx0, bx1, by0, by1, bz0, bz1};
@@ -564,6 +583,7 @@ __global__ void __launch_bounds__(kThreads, OPS_MIN_CTAS) k_skewed(const DLoop* 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   ChainSmem& S = *reinterpret_cast<ChainSmem*>(smem_raw);
   const bool skip = (int)blockIdx.x == skip_block;
+  if (threadIdx.x == 0) S.own_check = 0;
   int cur = -1;
   for (int ph = 0; ph < nphases; ++ph) {
     const Phase P = phases[ph];
@@ -612,6 +632,110 @@ cudaError_t launch_skewed(const LaunchEnv& env, const DLoop* d_loops, const Phas
   void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10};
   return cudaLaunchCooperativeKernel((const void*)k_skewed, dim3(grid), dim3(kThreads), args, kChainSmem,
                                      env.stream);
+}
+
+// ----------------------------------------------------------------------------
+// overlapped tiles (Sec. 4.D, with CTA tiles in place of MPI ranks): a CTA
+// copies its tile's live-in footprint of every dat of the segment into
+// shared memory, runs the segment's loops there on boxes grown by what later
+// loops of the tile read (recomputing halo points other tiles also compute),
+// and writes its owned box of every written dat to the dat's other buffer.
+// Tiles never wait for one another.
+// ----------------------------------------------------------------------------
+using OvSmem = ChainSmemT<1>;
+constexpr int kOvHeader = (int)((sizeof(OvSmem) + 15) / 16 * 16);
+constexpr int kMaxSmemOptin = 232448;  // sm_103a: per-block opt-in shared memory
+
+// Copy a box between a global dat (strides gp, gq) and a shared footprint
+// whose origin is the box corner fb (strides sp, sq); rows are spread over warps.
+__device__ __forceinline__ void copy_box(const int* box, const int* fb, double* sm, int sp, int sq, const double* g0,
+                                         double* g1, int64_t gp, int64_t gq, bool to_shared) {
+  const int nx = box[1] - box[0], ny = box[3] - box[2], nz = box[5] - box[4];
+  if (nx <= 0 || ny <= 0 || nz <= 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = warp; r < ny * nz; r += nw) {
+    const int y = box[2] + r % ny, z = box[4] + r / ny;
+    double* s = sm + (int64_t)(z - fb[4]) * sq + (int64_t)(y - fb[2]) * sp - fb[0];
+    const int64_t g = (int64_t)y * gp + (int64_t)z * gq;
+    if (to_shared)
+      for (int x = box[0] + lane; x < box[1]; x += 32) s[x] = g0[g + x];
+    else
+      for (int x = box[0] + lane; x < box[1]; x += 32) g1[g + x] = s[x];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_overlap(const DLoop* __restrict__ loops, int nloops,
+                                                      const OvDat* __restrict__ dats, int ndats,
+                                                      const int* __restrict__ own, const int* __restrict__ boxes,
+                                                      const int* __restrict__ foot, int ntiles,
+                                                      const double* __restrict__ scal, DD* part, int stride,
+                                                      int check, int* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  OvSmem& S = *reinterpret_cast<OvSmem*>(smem_raw);
+  double* area = reinterpret_cast<double*>(smem_raw + kOvHeader);
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    __syncthreads();
+    for (int d = 0; d < ndats; ++d) {
+      const OvDat D = dats[d];
+      const int* fb = foot + ((size_t)t * ndats + d) * 6;
+      copy_box(fb, fb, area + D.smem_off, D.spitch, D.splane, D.src, nullptr, D.gpitch, D.gplane, true);
+    }
+    for (int l = 0; l < nloops; ++l) {
+      const int* bx = boxes + ((size_t)t * nloops + l) * 6;
+      if (bx[1] <= bx[0] || bx[3] <= bx[2] || bx[5] <= bx[4]) continue;
+      __syncthreads();
+      stage_loop(&S.L, loops + l);
+      __syncthreads();
+      if ((int)threadIdx.x < S.L.nargs) {
+        DArg& A = S.L.args[threadIdx.x];
+        if (A.kind == OPS_ARG_DAT) {
+          const int d = A.slot;
+          const int* fb = foot + ((size_t)t * ndats + d) * 6;
+          A.ptr0 = area + dats[d].smem_off - (fb[0] + (int64_t)fb[2] * A.pitch + (int64_t)fb[4] * A.plane);
+        }
+      }
+      if (threadIdx.x < 6) S.own[threadIdx.x] = own[(size_t)t * 6 + threadIdx.x];
+      if (threadIdx.x == 0) S.own_check = 1;
+      __syncthreads();
+      red_init(S);
+      run_box(S, bx, scal, 0, 1, check, err);
+      __syncthreads();
+      if (S.L.nreds) flush_partials(S, part, stride, false);
+    }
+    __syncthreads();
+    const int* ob = own + (size_t)t * 6;
+    for (int d = 0; d < ndats; ++d) {
+      const OvDat D = dats[d];
+      if (!D.written) continue;
+      const int* fb = foot + ((size_t)t * ndats + d) * 6;
+      copy_box(ob, fb, area + D.smem_off, D.spitch, D.splane, nullptr, D.dst, D.gpitch, D.gplane, false);
+    }
+  }
+}
+
+int overlap_smem_area_bytes() { return (kMaxSmemOptin - kOvHeader) / 16 * 16; }
+
+int overlap_max_grid(int num_sms, int area_bytes) {
+  int per_sm = 0;
+  if (cudaFuncSetAttribute(k_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, kOvHeader + area_bytes) !=
+      cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_overlap, kThreads, kOvHeader + area_bytes) !=
+      cudaSuccess)
+    return 0;
+  return per_sm * num_sms;
+}
+
+cudaError_t launch_overlap(const LaunchEnv& env, const DLoop* d_loops, int nloops, const OvDat* d_dats, int ndats,
+                           const int* d_own, const int* d_boxes, const int* d_foot, int ntiles, int grid,
+                           int area_bytes) {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_overlap, cudaFuncAttributeMaxDynamicSharedMemorySize, kOvHeader + area_bytes);
+  if (e != cudaSuccess) return e;
+  k_overlap<<<grid, kThreads, kOvHeader + area_bytes, env.stream>>>(d_loops, nloops, d_dats, ndats, d_own, d_boxes,
+                                                                    d_foot, ntiles, env.scal, env.part,
+                                                                    env.part_stride, env.check, env.err);
+  return cudaGetLastError();
 }
 
 }  // namespace opstile

@@ -115,9 +115,32 @@ int ctx_alloc(ops_ctx c, void** p, size_t bytes);  // OPS_OK or OPS_ERR_NOMEM (b
 void ctx_free(ops_ctx c, void* p, size_t bytes);
 int ctx_fail(ops_ctx c, int code, const char* msg);
 
+// Overlapped tiles (Sec. 4.D applied per CTA): one dat of a segment as the
+// overlapped kernel sees it.  Footprints are copied from src (the dat's
+// current buffer) into shared memory at smem_off (doubles) with strides
+// spitch / splane; the owned part of a written dat goes to dst (the dat's
+// other buffer), which becomes current after the kernel.
+struct OvDat {
+  const double* src;   // grid point (0,0,0) of the current buffer
+  double* dst;         // grid point (0,0,0) of the other buffer (written dats)
+  int64_t gpitch, gplane;
+  int written;
+  int smem_off;
+  int spitch, splane;
+};
+
 // Launch helpers implemented in chain_kernels.cu.
 // chain_kernels_setup: once per device (opts the kernels into their shared memory).
 cudaError_t chain_kernels_setup();
+// bytes of shared memory the overlapped kernel may use for footprints
+int overlap_smem_area_bytes();
+int overlap_max_grid(int num_sms, int area_bytes);
+// loops: the segment's descriptors with DAT args in shared-memory layout
+// (pitch/plane/off for the footprint strides, slot = segment dat index);
+// own: 6 ints per tile; boxes: 6 ints per (tile, loop); foot: 6 ints per (tile, dat)
+cudaError_t launch_overlap(const LaunchEnv& env, const DLoop* d_loops, int nloops, const OvDat* d_dats, int ndats,
+                           const int* d_own, const int* d_boxes, const int* d_foot, int ntiles, int grid,
+                           int area_bytes);
 int untiled_grid(const LaunchEnv& env, const int* box);
 cudaError_t launch_untiled(const LaunchEnv& env, const DLoop* d_loop, const int* box, int grid);
 cudaError_t launch_part_init(const LaunchEnv& env, int row0, int nrows);

@@ -33,6 +33,8 @@ struct Dat {
   int size[3], dm[3], dp[3], ext[3];
   double* alloc = nullptr;  // owned allocation (nullptr if borrowed)
   double* ptr0 = nullptr;   // grid point (0,0,0)
+  double* alt = nullptr;    // second buffer for overlapped tiles (allocated on first use)
+  double* alt_ptr0 = nullptr;
   int64_t pitch = 0, plane = 0;
   size_t bytes = 0;
   std::string name;
@@ -58,6 +60,20 @@ struct CachedPlan {
   std::vector<int> key;
   SkewedPlan plan;
   Phase* d_phases = nullptr;
+};
+
+// An overlapped-tile plan of one segment (Sec. 4.D per CTA tile).
+struct OverlapPlan {
+  int tile[3];
+  int ntiles = 0, nloops = 0, ndats = 0;
+  std::vector<int> seg_dats;                // context dat ids, in local order
+  std::vector<int> written, spitch, splane, smem_off;
+  int area_bytes = 0;
+  int64_t redundant = 0;
+  int* d_tab = nullptr;                     // own | boxes | foot
+  size_t tab_ints = 0;
+  int own_off = 0, box_off = 0, foot_off = 0;
+  int first_loop = 0;
 };
 
 // Autotuning state of one segment signature.
@@ -98,6 +114,11 @@ struct ops_ctx_s {
   int skewed_grid = 0;
   std::map<std::vector<int>, std::unique_ptr<CachedPlan>> plans;
   std::map<std::vector<int>, TuneRec> tune;
+  std::map<std::vector<int>, std::unique_ptr<OverlapPlan>> oplans;
+  DLoop* d_oloops = nullptr;  // overlapped segments: descriptors in shared-memory layout
+  int oloops_cap = 0;
+  OvDat* d_ovdat = nullptr;
+  int ovdat_cap = 0;
   int64_t allocated = 0;
   std::string err;
   ops_flush_stats stats;
@@ -406,11 +427,359 @@ int record_event(ops_ctx c) {
   return OPS_OK;
 }
 
+std::vector<int> segment_signature(ops_ctx c, int first, int count);
+
+// Overlapped tiles (Sec. 4.D, CTA tiles in place of MPI ranks).  The tiles
+// partition the dats' allocation box; in each tile the loops run on the boxes
+// of build_overlap_tile and each dat lives in a shared-memory footprint that
+// holds what the tile reads, computes and owns.  A run of loops is eligible
+// when every dat it touches is library-owned with one common size and halo.
+// Halos grow with every loop of a run, so a run is cut into sub-runs short
+// enough that, for tiles of at least kOvMinX points in x, the footprints fit
+// one CTA's shared memory and the points computed stay within
+// kOvMaxRedundancy times the points the loops own.
+constexpr double kOvMaxRedundancy = 2.0;
+constexpr int kOvMinX = 32;
+
+// Plan loops [first, first + n) for tile T (shrunk while needed); nullptr
+// when no tile makes them fit.  Plans, and failures, are cached by the loops'
+// signature and the requested tile.
+int overlap_plan(ops_ctx c, int first, int n, const int* tile_in, OverlapPlan** out) {
+  *out = nullptr;
+  const int ndim = c->queue[first].dims;
+  std::vector<int> seg;
+  std::map<int, int> local;
+  for (int i = 0; i < n; ++i)
+    for (const ops_arg& a : c->queue[first + i].args)
+      if (a.kind == OPS_ARG_DAT && !local.count(a.handle)) {
+        local[a.handle] = (int)seg.size();
+        seg.push_back(a.handle);
+      }
+  if (seg.empty()) return OPS_OK;
+  const Dat& D0 = c->dats[seg[0]];
+  for (int h : seg) {
+    const Dat& D = c->dats[h];
+    if (!D.alloc || D.pitch != D0.pitch || D.plane != D0.plane) return OPS_OK;
+    for (int d = 0; d < 3; ++d)
+      if (D.size[d] != D0.size[d] || D.dm[d] != D0.dm[d] || D.dp[d] != D0.dp[d]) return OPS_OK;
+  }
+  int alo[3], ahi[3];
+  for (int d = 0; d < 3; ++d) {
+    alo[d] = -D0.dm[d];
+    ahi[d] = D0.size[d] + D0.dp[d];
+  }
+  int T[3];
+  const int def[3][3] = {{2048, 1, 1}, {64, 32, 1}, {32, 16, 8}};
+  for (int d = 0; d < 3; ++d) {
+    T[d] = d < ndim ? (tile_in[d] > 0 ? tile_in[d] : def[ndim - 1][d]) : 1;
+    T[d] = std::max(1, std::min(T[d], ahi[d] - alo[d]));
+  }
+  std::vector<int> key = segment_signature(c, first, n);
+  key.push_back(-7);  // overlapped
+  for (int d = 0; d < 3; ++d) key.push_back(T[d]);
+  auto it = c->oplans.find(key);
+  if (it != c->oplans.end()) {
+    *out = it->second.get();
+    if (*out) ++c->stats.plan_cache_hits;
+    return OPS_OK;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<PLoop> pl;
+  for (int i = 0; i < n; ++i) pl.push_back(plan_loop(c, c->queue[first + i]));
+  const int nd = (int)seg.size();
+  std::vector<int> written(nd, 0);
+  for (int i = 0; i < n; ++i)
+    for (const PArg& a : pl[i].args)
+      if (a.kind == OPS_ARG_DAT && a.writes) written[local[a.dat]] = 1;
+  const int area_cap = overlap_smem_area_bytes();
+  // points of each loop's range, for the redundancy of a tile
+  OverlapTile ot;
+  // Geometry of the tile with corner index tt: owned box, loop boxes, footprints.
+  auto eval_tile = [&](const int tt[3], int* own6, int* box6n, int* foot6d, int64_t* computed, int64_t* useful) {
+    int ob[6];
+    for (int d = 0; d < 3; ++d) {
+      ob[2 * d] = alo[d] + tt[d] * T[d];
+      ob[2 * d + 1] = std::min(ahi[d], ob[2 * d] + T[d]);
+    }
+    build_overlap_tile(pl, (int)c->dats.size(), ndim, ob, ot);
+    std::memcpy(own6, ob, sizeof ob);
+    *computed = *useful = 0;
+    for (int l = 0; l < n; ++l) {
+      int64_t pts = 1, upts = 1;
+      for (int d = 0; d < 3; ++d) {
+        box6n[6 * l + 2 * d] = ot.box[(size_t)6 * l + 2 * d];
+        box6n[6 * l + 2 * d + 1] = ot.box[(size_t)6 * l + 2 * d + 1];
+        pts *= std::max(0, ot.box[(size_t)6 * l + 2 * d + 1] - ot.box[(size_t)6 * l + 2 * d]);
+        upts *= std::max(0, std::min(ob[2 * d + 1], pl[l].rng[2 * d + 1]) - std::max(ob[2 * d], pl[l].rng[2 * d]));
+      }
+      *computed += pts;
+      *useful += upts;
+    }
+    for (int k = 0; k < nd; ++k) {
+      const int h = seg[k];
+      int F[6];
+      for (int d = 0; d < 3; ++d) {
+        F[2 * d] = 1 << 30;
+        F[2 * d + 1] = -(1 << 30);
+      }
+      auto hull = [&](const int* b) {
+        for (int d = 0; d < 3; ++d)
+          if (b[2 * d + 1] <= b[2 * d]) return;
+        for (int d = 0; d < 3; ++d) {
+          F[2 * d] = std::min(F[2 * d], b[2 * d]);
+          F[2 * d + 1] = std::max(F[2 * d + 1], b[2 * d + 1]);
+        }
+      };
+      hull(&ot.foot[(size_t)6 * h]);
+      for (int l = 0; l < n; ++l)
+        for (const PArg& a : pl[l].args)
+          if (a.kind == OPS_ARG_DAT && a.writes && a.dat == h) hull(&ot.box[(size_t)6 * l]);
+      if (written[k]) hull(ob);
+      bool empty = false;
+      for (int d = 0; d < 3; ++d) {
+        F[2 * d] = std::max(F[2 * d], alo[d]);
+        F[2 * d + 1] = std::min(F[2 * d + 1], ahi[d]);
+        if (F[2 * d + 1] <= F[2 * d]) empty = true;
+      }
+      if (empty)
+        for (int d = 0; d < 6; ++d) F[d] = 0;
+      std::memcpy(&foot6d[6 * k], F, sizeof F);
+    }
+  };
+  // shared-memory doubles of footprints with extents m (3 per dat), 16-byte aligned regions
+  auto area_of = [&](const std::vector<int>& m, std::vector<int>* sp, std::vector<int>* sq, std::vector<int>* so) {
+    int64_t off = 0;
+    for (int k = 0; k < nd; ++k) {
+      const int p = std::max(1, m[3 * k]), q = p * std::max(1, m[3 * k + 1]);
+      if (sp) {
+        (*sp)[k] = p;
+        (*sq)[k] = q;
+        (*so)[k] = (int)off;
+      }
+      off += ((int64_t)q * std::max(1, m[3 * k + 2]) + 1) / 2 * 2;
+    }
+    return off * 8;
+  };
+  std::unique_ptr<OverlapPlan> np;
+  std::vector<int> one_box((size_t)6 * n), one_foot((size_t)6 * nd), own6(6);
+  for (int attempt = 0; attempt < 32 && !np; ++attempt) {
+    int nt[3];
+    for (int d = 0; d < 3; ++d) nt[d] = (ahi[d] - alo[d] + T[d] - 1) / T[d];
+    // the centre tile first: most halo, no boundary clipping
+    const int tc[3] = {nt[0] / 2, nt[1] / 2, nt[2] / 2};
+    int64_t comp = 0, use = 0;
+    eval_tile(tc, own6.data(), one_box.data(), one_foot.data(), &comp, &use);
+    std::vector<int> m(3 * nd);
+    for (int k = 0; k < nd; ++k)
+      for (int d = 0; d < 3; ++d) m[3 * k + d] = one_foot[6 * k + 2 * d + 1] - one_foot[6 * k + 2 * d];
+    bool ok = area_of(m, nullptr, nullptr, nullptr) <= area_cap && comp <= kOvMaxRedundancy * (double)std::max<int64_t>(1, use);
+    if (ok) {
+      const int ntiles = nt[0] * nt[1] * nt[2];
+      std::vector<int> own((size_t)6 * ntiles), boxes((size_t)6 * ntiles * n), foot((size_t)6 * ntiles * nd);
+      std::fill(m.begin(), m.end(), 0);
+      int64_t computed = 0, useful = 0;
+      for (int tz = 0, t = 0; tz < nt[2]; ++tz)
+        for (int ty = 0; ty < nt[1]; ++ty)
+          for (int tx = 0; tx < nt[0]; ++tx, ++t) {
+            const int tt[3] = {tx, ty, tz};
+            int64_t cp = 0, us = 0;
+            eval_tile(tt, &own[(size_t)6 * t], &boxes[(size_t)6 * t * n], &foot[(size_t)6 * t * nd], &cp, &us);
+            computed += cp;
+            useful += us;
+            for (int k = 0; k < nd; ++k)
+              for (int d = 0; d < 3; ++d)
+                m[3 * k + d] = std::max(m[3 * k + d], foot[(size_t)6 * (t * nd + k) + 2 * d + 1] -
+                                                          foot[(size_t)6 * (t * nd + k) + 2 * d]);
+          }
+      np.reset(new OverlapPlan);
+      np->spitch.assign(nd, 0);
+      np->splane.assign(nd, 0);
+      np->smem_off.assign(nd, 0);
+      const int64_t area = area_of(m, &np->spitch, &np->splane, &np->smem_off);
+      if (area > area_cap) {
+        np.reset();  // a boundary tile is larger than the centre one
+      } else {
+        np->ntiles = ntiles;
+        np->area_bytes = (int)area;
+        np->redundant = computed - useful;
+        np->own_off = 0;
+        np->box_off = (int)own.size();
+        np->foot_off = (int)(own.size() + boxes.size());
+        std::vector<int> tab(own);
+        tab.insert(tab.end(), boxes.begin(), boxes.end());
+        tab.insert(tab.end(), foot.begin(), foot.end());
+        np->tab_ints = tab.size();
+        int rc = dev_alloc(c, (void**)&np->d_tab, sizeof(int) * tab.size());
+        if (rc) return rc;
+        CUDA_TRY(c, cudaMemcpyAsync(np->d_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice,
+                                    c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        break;
+      }
+    }
+    // halve the largest tile dimension that may shrink (x stays >= kOvMinX in 2D / 3D)
+    int big = -1;
+    for (int d = 0; d < ndim; ++d) {
+      const int floor_d = (d == 0 && ndim > 1) ? kOvMinX : 1;
+      if (T[d] > floor_d && (big < 0 || T[d] > T[big])) big = d;
+    }
+    if (big < 0) break;
+    T[big] = std::max((big == 0 && ndim > 1) ? kOvMinX : 1, (T[big] + 1) / 2);
+  }
+  c->stats.plan_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (!np) {
+    c->oplans[key] = nullptr;
+    return OPS_OK;
+  }
+  for (int d = 0; d < 3; ++d) np->tile[d] = T[d];
+  np->first_loop = first;
+  np->nloops = n;
+  np->ndats = nd;
+  np->seg_dats = seg;
+  np->written = written;
+  *out = np.get();
+  c->oplans[key] = std::move(np);
+  return OPS_OK;
+}
+
+// Launch one overlapped plan over loops [first, first + op->nloops).
+int run_overlap_plan(ops_ctx c, int first, const std::vector<DLoop>& hl, const OverlapPlan* op) {
+  const int n = op->nloops;
+  std::map<int, int> local;
+  for (int k = 0; k < op->ndats; ++k) local[op->seg_dats[k]] = k;
+  // descriptors in shared-memory layout
+  std::vector<DLoop> ol(hl.begin() + first, hl.begin() + first + n);
+  for (int i = 0; i < n; ++i) {
+    const QLoop& q = c->queue[first + i];
+    for (int a = 0; a < (int)q.args.size(); ++a) {
+      if (q.args[a].kind != OPS_ARG_DAT) continue;
+      const int k = local[q.args[a].handle];
+      DArg& A = ol[i].args[a];
+      const Stencil& s = c->stencils[q.args[a].stencil];
+      A.ptr0 = nullptr;
+      A.pitch = op->spitch[k];
+      A.plane = op->splane[k];
+      A.slot = k;
+      for (int p = 0; p < A.npts; ++p)
+        A.off[p] = (int32_t)(s.off[3 * p] + (int64_t)s.off[3 * p + 1] * A.pitch + (int64_t)s.off[3 * p + 2] * A.plane);
+    }
+  }
+  int rc = ensure(c, &c->d_oloops, &c->oloops_cap, n);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_oloops, ol.data(), sizeof(DLoop) * n, cudaMemcpyHostToDevice, c->stream));
+  std::vector<OvDat> ov(op->ndats);
+  for (int k = 0; k < op->ndats; ++k) {
+    Dat& D = c->dats[op->seg_dats[k]];
+    if (op->written[k] && !D.alt) {
+      rc = dev_alloc(c, (void**)&D.alt, D.bytes);
+      if (rc) return rc;
+      D.alt_ptr0 = D.alt + (D.ptr0 - D.alloc);
+    }
+    ov[k].src = D.ptr0;
+    ov[k].dst = op->written[k] ? D.alt_ptr0 : nullptr;
+    ov[k].gpitch = D.pitch;
+    ov[k].gplane = D.plane;
+    ov[k].written = op->written[k];
+    ov[k].smem_off = op->smem_off[k];
+    ov[k].spitch = op->spitch[k];
+    ov[k].splane = op->splane[k];
+  }
+  rc = ensure(c, &c->d_ovdat, &c->ovdat_cap, op->ndats);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(c->d_ovdat, ov.data(), sizeof(OvDat) * op->ndats, cudaMemcpyHostToDevice, c->stream));
+  LaunchEnv env = make_env(c);
+  int row0 = -1, nrows = 0;
+  for (int i = 0; i < n; ++i) {
+    const DLoop& L = hl[first + i];
+    if (L.nreds) {
+      if (row0 < 0) row0 = L.part_row;
+      nrows = L.part_row + L.nreds - row0;
+    }
+  }
+  const int grid = std::max(1, std::min({op->ntiles, overlap_max_grid(c->num_sms, op->area_bytes), c->part_stride}));
+  if (nrows) {
+    CUDA_TRY(c, launch_part_init(env, row0, nrows));
+    ++c->stats.launches;
+  }
+  rc = record_event(c);
+  if (rc) return rc;
+  CUDA_TRY(c, launch_overlap(env, c->d_oloops, n, c->d_ovdat, op->ndats, op->d_tab + op->own_off,
+                             op->d_tab + op->box_off, op->d_tab + op->foot_off, op->ntiles, grid, op->area_bytes));
+  rc = record_event(c);
+  if (rc) return rc;
+  ++c->stats.launches;
+  ++c->stats.kernel_launches;
+  if (nrows) {
+    CUDA_TRY(c, launch_fold(env, row0, nrows, grid));
+    ++c->stats.launches;
+  }
+  // the other buffers now hold every written dat
+  for (int k = 0; k < op->ndats; ++k)
+    if (op->written[k]) {
+      Dat& D = c->dats[op->seg_dats[k]];
+      std::swap(D.alloc, D.alt);
+      std::swap(D.ptr0, D.alt_ptr0);
+    }
+  ++c->stats.segments;
+  c->stats.loops += n;
+  c->stats.tiles = op->ntiles;
+  for (int d = 0; d < 3; ++d) c->stats.tile[d] = op->tile[d];
+  c->stats.redundant_points += op->redundant;
+  for (int i = 0; i < n; ++i) {
+    int64_t p = 1;
+    for (int d = 0; d < 3; ++d) p *= std::max(0, hl[first + i].rng[2 * d + 1] - hl[first + i].rng[2 * d]);
+    c->stats.points += p;
+  }
+  return OPS_OK;
+}
+
+// Longest leading run of loops [first, first + count) that has an overlapped
+// plan (halving the run until one fits); *used = 0 when not even one loop does.
+int overlap_prefix(ops_ctx c, int first, int count, const int* tile_in, OverlapPlan** out, int* used) {
+  *used = 0;
+  for (int n = count; n >= 1; n = n / 2) {
+    int rc = overlap_plan(c, first, n, tile_in, out);
+    if (rc) return rc;
+    if (*out) {
+      *used = n;
+      return OPS_OK;
+    }
+  }
+  return OPS_OK;
+}
+
 // Execute a segment in a given mode; tile_in entries <= 0 are chosen automatically.
-int run_segment_mode(ops_ctx c, int first, int count, int dl_base, const std::vector<DLoop>& hl, int mode,
+int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl, int mode,
                      const int* tile_in) {
   const QLoop& q0 = c->queue[first];
   const int ndim = q0.dims;
+  if (mode == OPS_MODE_OVERLAPPED) {
+    // consecutive overlapped runs; what no run covers goes to the skewed path
+    const int dl_first = first;
+    while (count > 0) {
+      OverlapPlan* op = nullptr;
+      int used = 0;
+      int rc = overlap_prefix(c, first, count, tile_in, &op, &used);
+      if (rc) return rc;
+      if (!used) break;
+      c->stats.mode = mode;
+      rc = run_overlap_plan(c, first, hl, op);
+      if (rc) return rc;
+      first += used;
+      dl_base += used;
+      count -= used;
+    }
+    if (count == 0) return OPS_OK;
+    if (first != dl_first) {
+      // earlier runs moved written dats to their other buffers
+      std::vector<FoldRow> unused;
+      for (int k = first; k < first + count; ++k) fill_dloop(c, c->queue[k], hl[k], hl[k].part_row, unused);
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_loops + first, hl.data() + first, sizeof(DLoop) * count,
+                                  cudaMemcpyHostToDevice, c->stream));
+    }
+    mode = OPS_MODE_SKEWED;
+    tile_in = c->cfg.tile;
+  }
   LaunchEnv env = make_env(c);
   c->stats.mode = mode;
   ++c->stats.segments;
@@ -558,7 +927,7 @@ std::vector<int> segment_signature(ops_ctx c, int first, int count) {
 // candidate -- untiled, or skewed with the cache-fitting outer tile size h0
 // and 2, 4, 8, 16 times it -- timed with CUDA events; afterwards the fastest
 // candidate is used for that segment.
-int run_segment_auto(ops_ctx c, int first, int count, int dl_base, const std::vector<DLoop>& hl) {
+int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl) {
   const int ndim = c->queue[first].dims;
   TuneRec& T = c->tune[segment_signature(c, first, count)];
   if (T.cand.empty()) {
@@ -588,6 +957,7 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, const std::ve
       T.cand.push_back(cd);
       if (cd[1 + od] >= ext[od]) break;
     }
+    if (count > 1) T.cand.push_back({OPS_MODE_OVERLAPPED, 0, 0, 0});
     T.ms.assign(T.cand.size(), -1.0);
     CUDA_TRY(c, cudaEventCreate(&T.e0));
     CUDA_TRY(c, cudaEventCreate(&T.e1));
@@ -623,7 +993,7 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, const std::ve
   return OPS_OK;
 }
 
-int run_segment(ops_ctx c, int first, int count, int dl_base, const std::vector<DLoop>& hl) {
+int run_segment(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl) {
   int mode = c->cfg.mode;
   if (mode == OPS_MODE_AUTO && count >= 2) return run_segment_auto(c, first, count, dl_base, hl);
   if (mode == OPS_MODE_AUTO) mode = OPS_MODE_UNTILED;
@@ -638,10 +1008,13 @@ int flush(ops_ctx c) {
   const int n = (int)c->queue.size();
   std::vector<DLoop> hl(n);
   std::vector<FoldRow> rows;
-  for (int i = 0; i < n; ++i) fill_dloop(c, c->queue[i], hl[i], (int)rows.size(), rows);
+  std::vector<int> prow(n);
+  for (int i = 0; i < n; ++i) {
+    prow[i] = (int)rows.size();
+    fill_dloop(c, c->queue[i], hl[i], prow[i], rows);
+  }
   int rc = ensure(c, &c->d_loops, &c->loops_cap, n);
   if (rc) return rc;
-  CUDA_TRY(c, cudaMemcpyAsync(c->d_loops, hl.data(), sizeof(DLoop) * n, cudaMemcpyHostToDevice, c->stream));
   if (!rows.empty()) {
     rc = ensure(c, &c->d_rows, &c->rows_cap, (int)rows.size());
     if (rc) return rc;
@@ -675,6 +1048,12 @@ int flush(ops_ctx c) {
       if (!cut && c->queue[i].block != c->queue[first].block) cut = true;
     }
     if (cut && i > first) {
+      // descriptors are filled right before their segment runs: an earlier
+      // overlapped segment may have swapped dat buffers
+      std::vector<FoldRow> unused;
+      for (int k = first; k < i; ++k) fill_dloop(c, c->queue[k], hl[k], prow[k], unused);
+      CUDA_TRY(c, cudaMemcpyAsync(c->d_loops + first, hl.data() + first, sizeof(DLoop) * (i - first),
+                                  cudaMemcpyHostToDevice, c->stream));
       rc = run_segment(c, first, i - first, first, hl);
       if (rc) {
         c->queue.clear();
@@ -780,9 +1159,16 @@ int ops_finalize(ops_ctx c) {
   if (!c) return OPS_ERR_INVALID_ARG;
   if (!c->host_only) {
     cudaStreamSynchronize(c->stream);
-    for (Dat& d : c->dats) dev_free(c, d.alloc, d.bytes);
+    for (Dat& d : c->dats) {
+      dev_free(c, d.alloc, d.bytes);
+      dev_free(c, d.alt, d.bytes);
+    }
     for (auto& kv : c->plans)
       if (kv.second->d_phases) dev_free(c, kv.second->d_phases, sizeof(Phase) * kv.second->plan.phases.size());
+    for (auto& kv : c->oplans)
+      if (kv.second && kv.second->d_tab) dev_free(c, kv.second->d_tab, sizeof(int) * kv.second->tab_ints);
+    dev_free(c, c->d_oloops, sizeof(DLoop) * (size_t)c->oloops_cap);
+    dev_free(c, c->d_ovdat, sizeof(OvDat) * (size_t)c->ovdat_cap);
     dev_free(c, c->d_scal, sizeof(double) * (size_t)c->scal_cap);
     dev_free(c, c->d_part, sizeof(DD) * (size_t)c->part_rows_cap * c->part_stride);
     dev_free(c, c->d_rows, sizeof(FoldRow) * (size_t)c->rows_cap);
@@ -1064,6 +1450,22 @@ int ops_plan_skewed(ops_ctx c, const int* tile, int* out_ntiles, int* out_ranges
     std::memcpy(out_ranges + pos, P.ranges[d].data(), sizeof(int) * P.ranges[d].size());
     pos += (int64_t)P.ranges[d].size();
   }
+  return OPS_OK;
+}
+
+int ops_plan_overlapped(ops_ctx c, const int owned[6], int* out_boxes, int* out_foot) {
+  if (!c || !owned || !out_boxes || !out_foot) return OPS_ERR_INVALID_ARG;
+  if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
+  const int ndim = c->queue[0].dims;
+  std::vector<PLoop> pl;
+  for (const QLoop& q : c->queue) {
+    if (q.dims != ndim) return fail(c, OPS_ERR_INVALID_ARG, "queued loops of different dimensionality");
+    pl.push_back(plan_loop(c, q));
+  }
+  OverlapTile ot;
+  build_overlap_tile(pl, (int)c->dats.size(), ndim, owned, ot);
+  std::memcpy(out_boxes, ot.box.data(), sizeof(int) * ot.box.size());
+  std::memcpy(out_foot, ot.foot.data(), sizeof(int) * ot.foot.size());
   return OPS_OK;
 }
 

@@ -58,13 +58,15 @@ def assert_same(chain, got, ref, hist=None, ref_hist=None, what=""):
 def test_worked_example_1d():
     c = W.worked_example_1d()
     ref, _ = oracle.run_chain(c)
-    for mode, tile in [("untiled", None), ("skewed", (4,)), ("skewed", (1,)), ("skewed", (3,))]:
+    for mode, tile in [("untiled", None), ("skewed", (4,)), ("skewed", (1,)), ("skewed", (3,)),
+                       ("overlapped", (4,)), ("overlapped", (1,)), ("overlapped", (3,))]:
         got, _, st = run_gpu(c, mode, tile)
         assert_same(c, got, ref, what=f"{mode} {tile}")
 
 
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 0, 0)), ("skewed", (0, 40, 0)),
-                                       ("skewed", (100, 33, 0))])
+                                       ("skewed", (100, 33, 0)), ("overlapped", (0, 0, 0)),
+                                       ("overlapped", (64, 16, 0)), ("overlapped", (100, 33, 0))])
 def test_small2d_chain_bit_exact(mode, tile):
     """8 loops x 10 repetitions on 256^2 (radius-1 stencils, zero halo)."""
     c = W.small2d(n=256, reps=10)
@@ -73,10 +75,16 @@ def test_small2d_chain_bit_exact(mode, tile):
     assert_same(c, got, ref, what=f"{mode} {tile}")
     if mode == "skewed":
         assert st["mode"] == ops.OPS_MODE_SKEWED
+    if mode == "overlapped":
+        # one run of the 8 loops of a step: radius-1 halos grow to 8 points
+        assert st["mode"] == ops.OPS_MODE_OVERLAPPED and st["segments"] >= 1
+        assert st["redundant_points"] > 0 and st["loops"] == len(c.loops)
 
 
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 32, 0)), ("skewed", (0, 17, 0)),
-                                       ("skewed", (37, 23, 0)), ("skewed", (0, 0, 0)), ("auto", None)])
+                                       ("skewed", (37, 23, 0)), ("skewed", (0, 0, 0)), ("auto", None),
+                                       ("overlapped", None), ("overlapped", (32, 8, 0)),
+                                       ("overlapped", (40, 100, 0))])
 def test_cloverleaf_shaped_chain(mode, tile):
     """83-loop CloverLeaf-shaped steps on a 100^2 grid (ragged tiles), with
     node ranges, thin halo strips, RW updates and two reductions per step;
@@ -100,6 +108,19 @@ def test_jacobi_eigenmode_closed_form_on_gpu():
     assert st["barriers"] > 0 and st["tiles"] == 4
 
 
+def test_jacobi_overlapped_closed_form():
+    """Overlapped tiles recompute halo points redundantly; the result is still
+    the program-order one, and the eigenmode decays by the closed form."""
+    n, K, nu = 63, 30, 0.125
+    c = W.jacobi2d(n, K, nu=nu, p=2, q=1)
+    ref, _ = oracle.run_chain(c)
+    got, _, st = run_gpu(c, "overlapped", (32, 16, 0))
+    assert_same(c, got, ref, what="jacobi overlapped")
+    # 60 loops in one flush: cut into runs whose recomputation stays bounded
+    assert st["mode"] == ops.OPS_MODE_OVERLAPPED and st["redundant_points"] > 0
+    assert st["segments"] > 1 and st["loops"] == len(c.loops)
+
+
 def test_constant_and_linear_fields():
     c = W.small2d(n=48, reps=2, constant=0.75)
     got, _, _ = run_gpu(c, "skewed", (0, 10, 0))
@@ -115,7 +136,8 @@ def test_constant_and_linear_fields():
 def test_opensbli_shaped_3d():
     c = W.opensbli3d(n=20, steps=1)
     ref, _ = oracle.run_chain(c)
-    for mode, tile in [("untiled", None), ("skewed", (0, 0, 6)), ("skewed", (0, 7, 5))]:
+    for mode, tile in [("untiled", None), ("skewed", (0, 0, 6)), ("skewed", (0, 7, 5)),
+                       ("overlapped", (0, 0, 0)), ("overlapped", (8, 7, 5))]:
         got, _, st = run_gpu(c, mode, tile)
         assert_same(c, got, ref, what=f"3d {mode} {tile}")
 
@@ -154,7 +176,8 @@ def edge_chain(n=30):
     return Chain("edge", 2, size, d_m, d_p, dats, st, [RSUM, RMIN, RMAX], loops, steps=2)
 
 
-@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 7, 0)), ("skewed", (11, 5, 0))])
+@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 7, 0)), ("skewed", (11, 5, 0)),
+                                       ("overlapped", None), ("overlapped", (11, 5, 0))])
 def test_edge_cases(mode, tile):
     c = edge_chain()
     ref, ref_hist = oracle.run_chain(c)
