@@ -164,6 +164,8 @@ def time_mode(chain, mode, tile, steps, warmup, stream, torch):
         e1 = torch.cuda.Event(enable_timing=True)
         kms, launches, kl = 0.0, 0, 0
         stats = None
+        # an NVTX range marks the timed steps, so a profiler can select them
+        torch.cuda.nvtx.range_push(f"timed_{mode}")
         e0.record(stream)
         for _ in range(steps):
             r.step()
@@ -173,6 +175,7 @@ def time_mode(chain, mode, tile, steps, warmup, stream, torch):
             launches += stats["launches"]
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         ms = e0.elapsed_time(e1)
     finally:
         r.close()
@@ -451,7 +454,7 @@ def main():
     traffic = profile_traffic(chosen_mode, chosen_tile) if args.n == N_DEFAULT else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": "k_skewed" if chosen_mode == "skewed" else "k_untiled",
+                "kernel": {"skewed": "k_skewed", "overlapped": "k_overlap"}.get(chosen_mode, "k_untiled"),
                 "peak_source": f"FP64: {NUM_SMS} SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 flop x {sm_max:.0f} MHz "
                                "(unit count from a GB300 probe; MEASURED_PEAKS.json has no FP64 figure)",
                 "kernel_ms_per_launch": kernel_ms_per_launch,

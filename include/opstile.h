@@ -124,6 +124,8 @@ typedef struct {
   int blocks_per_sm;   /* persistent-kernel CTAs per SM; 0 = as many as fit */
   int test_skip_barrier_block; /* test hook: this CTA never arrives at grid barriers; -1 = off */
   int timing;          /* 1: record CUDA events around the chain kernels (kernel_ms in ops_flush_stats) */
+  int interpret;       /* 1: run loop bodies through the register-IR interpreter kernels instead of
+                          kernels compiled from the IR at the first flush of each segment (NVRTC) */
 } ops_config;
 
 /* Fill *cfg with defaults (device 0, own stream, OPS_MODE_AUTO, automatic tiles). */
@@ -214,6 +216,8 @@ typedef struct {
                             or the per-loop kernels), measured with CUDA events on the context's stream */
   int kernel_launches;   /* chain kernels covered by kernel_ms */
   int tuning;            /* OPS_MODE_AUTO: 1 while the autotuner is still timing candidates */
+  int compiled;          /* 1: the last untiled / skewed segment ran compiled loop bodies */
+  double compile_ms;     /* host time spent generating and compiling loop bodies in this flush */
 } ops_flush_stats;
 /* Statistics of the most recent flush; with timing=1 this waits for that
  * flush's kernels to finish. */
@@ -235,8 +239,16 @@ int ops_plan_skewed(ops_ctx ctx, const int* tile, int* out_ntiles, int* out_rang
  * hi in every dimension when no loop reads it).  Dimensions >= the loops'
  * dimensionality hold the loops' (0, 1). */
 int ops_plan_overlapped(ops_ctx ctx, const int owned[6], int* out_boxes, int* out_foot);
+/* Generate the CUDA source of the compiled loop bodies for the currently
+ * queued loops (as one segment) and compile it for sm_103a with NVRTC,
+ * without loading it: no device is needed.  src_out (cap bytes, may be NULL)
+ * receives the NUL-terminated source, truncated to fit; *src_len its full
+ * length; *compile_ms the compile time.  OPS_ERR_CUDA with the compiler's
+ * log in ops_last_error when it does not compile; OPS_ERR_NO_DEVICE when
+ * NVRTC is not installed.  The queue is left as it was. */
+int ops_compile_queued(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
 
-/* ---- heat-conduction solves (TeaLeaf-shaped, Sec. 5 and Sec. 6.C) ----
+/* ---- heat-conduction solves (TeaLeaf-shaped, Sec. 5 and Sec. 6.D) ----
  * Solve A x = b on an n x n cell grid for the implicit heat-conduction
  * operator (A u)_c = u_c + sum over the four faces f of c of
  * k_f (u_c - u_nb), k_f the harmonic mean 2 ka kb / (ka + kb) of the two

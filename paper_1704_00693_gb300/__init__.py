@@ -48,7 +48,7 @@ class ops_config(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("mode", C.c_int), ("tile", C.c_int * 3),
                 ("segment", C.c_int), ("check", C.c_int), ("l2_bytes", C.c_int64), ("hbm_budget", C.c_int64),
                 ("timeout_ms", C.c_int), ("blocks_per_sm", C.c_int), ("test_skip_barrier_block", C.c_int),
-                ("timing", C.c_int)]
+                ("timing", C.c_int), ("interpret", C.c_int)]
 
 
 class ops_arg(C.Structure):
@@ -60,7 +60,7 @@ class ops_flush_stats(C.Structure):
                 ("phases", C.c_int), ("barriers", C.c_int), ("launches", C.c_int), ("plan_cache_hits", C.c_int),
                 ("mode", C.c_int), ("tile", C.c_int * 3), ("redundant_points", C.c_int64), ("points", C.c_int64),
                 ("skew", C.c_int * 3), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int),
-                ("tuning", C.c_int)]
+                ("tuning", C.c_int), ("compiled", C.c_int), ("compile_ms", C.c_double)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k in ("tile", "skew") else getattr(self, k))
@@ -252,6 +252,20 @@ def ops_plan_overlapped(ctx, owned, nloops: int, ndats: int):
     _check(ctx, load().ops_plan_overlapped(ctx, o.ctypes.data_as(ip), boxes.ctypes.data_as(ip),
                                            foot.ctypes.data_as(ip)))
     return boxes[:6 * nloops].reshape(nloops, 3, 2).copy(), foot[:6 * ndats].reshape(ndats, 3, 2).copy()
+
+
+def ops_compile_queued(ctx, want_source: bool = False):
+    """Generate and compile (NVRTC, sm_103a, no device) the loop bodies of the
+    queued loops; returns (source or None, source length, compile ms)."""
+    n = C.c_int64(0)
+    ms = C.c_double(0.0)
+    buf = None
+    if want_source:
+        _check(ctx, load().ops_compile_queued(ctx, None, C.c_int64(0), C.byref(n), C.byref(ms)))
+        buf = C.create_string_buffer(n.value + 1)
+    _check(ctx, load().ops_compile_queued(ctx, buf, C.c_int64(n.value + 1 if buf is not None else 0), C.byref(n),
+                                          C.byref(ms)))
+    return (buf.value.decode() if buf is not None else None), n.value, ms.value
 
 
 # ------------------------------------------------ one loop, no device allocation

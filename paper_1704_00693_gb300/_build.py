@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.environ.get("OPSTILE_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libopstile.so")
 
-SOURCES = ["runtime.cpp", "plan.cpp", "chain_kernels.cu", "cg.cu", "serve.cpp", "noalloc.cu"]
+SOURCES = ["runtime.cpp", "plan.cpp", "chain_kernels.cu", "cg.cu", "serve.cpp", "noalloc.cu", "jit.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -77,7 +77,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + f".tmp{os.getpid()}"
     libdir = _cuda_lib_dir(nvcc)
-    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared", "-Xlinker", f"-rpath,{libdir}"]
+    cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared", "-ldl", "-Xlinker", f"-rpath,{libdir}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

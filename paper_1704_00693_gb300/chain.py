@@ -21,7 +21,8 @@ from . import (OPS_ARG_DAT, OPS_MODE_AUTO, MODES, ops_config_default, ops_dat_fe
 class ChainRunner:
     def __init__(self, chain, mode: str = "auto", tile=None, segment: int = 0, check: bool = False,
                  stream: int = 0, device: int = 0, ctx=None, blocks_per_sm: int = 0, timeout_ms: int = 0,
-                 skip_barrier_block: int = -1, upload: bool = True, timing: bool = False):
+                 skip_barrier_block: int = -1, upload: bool = True, timing: bool = False,
+                 interpret: bool = False):
         self.chain = chain
         self.own_ctx = ctx is None
         if ctx is None:
@@ -39,6 +40,7 @@ class ChainRunner:
                 cfg.timeout_ms = timeout_ms
             cfg.test_skip_barrier_block = skip_barrier_block
             cfg.timing = 1 if timing else 0
+            cfg.interpret = 1 if interpret else 0
             ctx = ops_init(cfg)
         else:
             ops_set_mode(ctx, MODES[mode], tile, segment)

@@ -1,5 +1,5 @@
 // Batched CG for the 5-point heat-conduction operator (TeaLeaf-shaped solves,
-// Sec. 5 and Sec. 6.C), GB300 design:
+// Sec. 5 and Sec. 6.D), GB300 design:
 //   - the operator is (A u)_c = d_c u_c - sum_f k_f u_nb over the four faces,
 //     k_f the harmonic mean of the two cells' conductivity (a boundary face
 //     takes the cell's own), d_c = 1 + sum_f k_f, neighbours outside are 0;

@@ -1,0 +1,659 @@
+// Run-time compiled loop bodies (see jit.h).
+//
+// Code shape.  For loop i of a segment the generator emits body<i>, which
+// enumerates its CTA's share of a box exactly as the interpreter does (units
+// of 256 consecutive x by 4 consecutive rows for rows of >= 128 points,
+// flattened groups otherwise) and evaluates the loop's IR per point with the
+// same explicitly rounded operations in the same order, so every stored
+// value is bit-identical to the interpreter's and the oracle's.  A unit of 4
+// full rows is evaluated instruction by instruction across its 4 points (the
+// interpreter's order, 4 independent dependency chains per thread); partial
+// units and thin boxes take a one-point path.  The constants, dat pointers
+// and scalar slots of a loop are read from its descriptor at run time, so
+// one compiled segment serves every step whatever the host sets them to.
+//
+// Kernel u<i> runs loop i over a box with grid-stride units.  The untiled
+// form launches it once per loop over the loop's range; the skewed form
+// launches it once per (tile, loop) phase of the plan in plan order, the
+// stream order standing in for the grid barriers of a persistent kernel.
+// The loops of a segment are split over several modules that compile in
+// parallel; compiled code is cached in memory and on disk by its source.
+//
+// NVRTC and the driver's module calls are reached at run time (dlopen and
+// cudaGetDriverEntryPointByVersion), so the library loads on hosts without
+// a GPU driver.
+#include "jit.h"
+
+#include <cuda.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <sstream>
+#include <thread>
+
+namespace opstile {
+
+namespace {
+
+// Shape of the compiled kernels: rows per unit (independent points per
+// thread) and the CTAs per SM the register budget is sized for.  Defaults
+// from measurement on GB300; OPSTILE_JIT_PTS / OPSTILE_JIT_MINB override.
+int env_int(const char* name, int def, int lo, int hi) {
+  const char* e = getenv(name);
+  if (!e || !*e) return def;
+  const int v = atoi(e);
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+const int kJitPts = env_int("OPSTILE_JIT_PTS", 4, 1, 8);
+const int kJitMinCtas = env_int("OPSTILE_JIT_MINB", 2, 1, 8);
+constexpr int kJitChunk = 6;  // loops per compiled module (modules compile in parallel)
+
+// ---------------------------------------------------------------------------
+// entry points reached at run time
+// ---------------------------------------------------------------------------
+struct Api {
+  bool tried = false, ok = false;
+  std::string why;
+  // NVRTC
+  nvrtcResult (*create)(nvrtcProgram*, const char*, const char*, int, const char* const*, const char* const*);
+  nvrtcResult (*compile)(nvrtcProgram, int, const char* const*);
+  nvrtcResult (*log_size)(nvrtcProgram, size_t*);
+  nvrtcResult (*log)(nvrtcProgram, char*);
+  nvrtcResult (*cubin_size)(nvrtcProgram, size_t*);
+  nvrtcResult (*cubin)(nvrtcProgram, char*);
+  nvrtcResult (*destroy)(nvrtcProgram*);
+  // driver
+  CUresult (*load)(CUmodule*, const void*);
+  CUresult (*get_function)(CUfunction*, CUmodule, const char*);
+  CUresult (*launch)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                     void**, void**);
+  CUresult (*launch_coop)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, unsigned, CUstream,
+                          void**);
+  CUresult (*occupancy)(int*, CUfunction, int, size_t);
+  CUresult (*attribute)(int*, CUfunction_attribute, CUfunction);
+};
+
+Api g_api;
+std::mutex g_mu;
+
+template <class F>
+bool sym(void* lib, const char* name, F* f) {
+  *f = reinterpret_cast<F>(dlsym(lib, name));
+  return *f != nullptr;
+}
+
+template <class F>
+bool drv(const char* name, F* f) {
+  void* p = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+      q != cudaDriverEntryPointSuccess || !p) {
+    cudaGetLastError();
+    return false;
+  }
+  *f = reinterpret_cast<F>(p);
+  return true;
+}
+
+// call with g_mu held; nvrtc_only: skip the driver entry points
+bool api_ready(std::string* why, bool nvrtc_only = false) {
+  if (nvrtc_only && g_api.create) return true;
+  if (!g_api.tried) {
+    g_api.tried = !nvrtc_only;
+    void* lib = nullptr;
+    for (const char* n : {"libnvrtc.so.13", "/usr/local/cuda/lib64/libnvrtc.so.13", "libnvrtc.so"}) {
+      lib = dlopen(n, RTLD_NOW | RTLD_LOCAL);
+      if (lib) break;
+    }
+    if (!lib) {
+      g_api.why = "libnvrtc.so.13 not found";
+    } else if (!(sym(lib, "nvrtcCreateProgram", &g_api.create) && sym(lib, "nvrtcCompileProgram", &g_api.compile) &&
+                 sym(lib, "nvrtcGetProgramLogSize", &g_api.log_size) &&
+                 sym(lib, "nvrtcGetProgramLog", &g_api.log) && sym(lib, "nvrtcGetCUBINSize", &g_api.cubin_size) &&
+                 sym(lib, "nvrtcGetCUBIN", &g_api.cubin) && sym(lib, "nvrtcDestroyProgram", &g_api.destroy))) {
+      g_api.why = "libnvrtc lacks an entry point";
+      g_api.create = nullptr;
+    } else if (nvrtc_only) {
+      return true;
+    } else if (!(drv("cuModuleLoadData", &g_api.load) && drv("cuModuleGetFunction", &g_api.get_function) &&
+                 drv("cuLaunchKernel", &g_api.launch) && drv("cuLaunchCooperativeKernel", &g_api.launch_coop) &&
+                 drv("cuOccupancyMaxActiveBlocksPerMultiprocessor", &g_api.occupancy) &&
+                 drv("cuFuncGetAttribute", &g_api.attribute))) {
+      g_api.why = "driver module entry points unavailable";
+    } else {
+      g_api.ok = true;
+    }
+  }
+  if (!g_api.ok && why) *why = g_api.why;
+  return g_api.ok;
+}
+
+cudaError_t to_cuda(CUresult r) {
+  if (r == CUDA_SUCCESS) return cudaSuccess;
+  if (r == CUDA_ERROR_COOPERATIVE_LAUNCH_TOO_LARGE) return cudaErrorCooperativeLaunchTooLarge;
+  if (r == CUDA_ERROR_INVALID_VALUE) return cudaErrorInvalidValue;
+  return cudaErrorLaunchFailure;
+}
+
+// ---------------------------------------------------------------------------
+// device code shared by every module (the generator appends the bodies)
+// ---------------------------------------------------------------------------
+const char* kPrelude = R"PRE(
+typedef long long i64;
+struct DD { double hi, lo; };
+struct DArg {
+  double* ptr0; i64 pitch; i64 plane; int kind, access, npts, slot;
+  int alo[3], ahi[3]; int slo[3], shi[3]; int off[32];
+};
+struct DLoop {
+  int nargs, nins, nreds; int rng[6]; int red_op[4]; int part_row; int zmask; int pad_;
+  int ins[64][6]; double K[128]; DArg args[8];
+};
+struct Phase { int loop; int barrier; int box[6]; };
+
+__device__ __forceinline__ DD dd_add(DD a, double x) {
+  double s = __dadd_rn(a.hi, x);
+  double bp = __dsub_rn(s, a.hi);
+  double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bp)), __dsub_rn(x, bp));
+  DD r; r.hi = s; r.lo = __dadd_rn(a.lo, e); return r;
+}
+__device__ __forceinline__ DD dd_merge(DD a, DD b) { DD t = dd_add(a, b.hi); t.lo = __dadd_rn(t.lo, b.lo); return t; }
+__device__ __forceinline__ DD dd_of(double v) { DD r; r.hi = v; r.lo = 0.0; return r; }
+__device__ __forceinline__ double red_identity(int op) {
+  return op == 0 ? 0.0 : (op == 1 ? __longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0xfff0000000000000ll));
+}
+__device__ __forceinline__ DD red_combine(int op, DD a, DD b) {
+  if (op == 0) return dd_merge(a, b);
+  if (op == 1) return dd_of((b.hi < a.hi) ? b.hi : a.hi);
+  return dd_of((b.hi > a.hi) ? b.hi : a.hi);
+}
+__device__ __forceinline__ DD red_sum(DD a, double x) { return dd_add(a, x); }
+__device__ __forceinline__ DD red_min(DD a, double x) { return dd_of((x < a.hi) ? x : a.hi); }
+__device__ __forceinline__ DD red_max(DD a, double x) { return dd_of((x > a.hi) ? x : a.hi); }
+
+__shared__ DD g_sh[32];
+
+// block-wide combine in a fixed tree, result valid in thread 0
+__device__ DD block_combine(int op, DD v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    DD w; w.hi = __shfl_down_sync(0xffffffffu, v.hi, o); w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+    v = red_combine(op, v, w);
+  }
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) g_sh[wp] = v;
+  __syncthreads();
+  if (wp == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? g_sh[lane] : dd_of(red_identity(op));
+    for (int o = 16; o > 0; o >>= 1) {
+      DD w; w.hi = __shfl_down_sync(0xffffffffu, v.hi, o); w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
+      v = red_combine(op, v, w);
+    }
+  }
+  return v;
+}
+__device__ __forceinline__ void flush_red(int op, DD v, DD* part, int stride, int row, int assign) {
+  v = block_combine(op, v);
+  if (threadIdx.x == 0) {
+    DD* dst = part + (size_t)row * stride + blockIdx.x;
+    *dst = assign ? v : red_combine(op, *dst, v);
+  }
+  __syncthreads();
+}
+
+// A CTA's share of a box: rows of >= 128 points in units of 256 x by P rows
+// (u = part, part + nparts, ...), thinner boxes in flattened groups of P
+// points 256 apart.  full(x, y, z) takes rows y .. y+P-1 at x; one(x, y, z)
+// a single point.
+template <int P, class F1, class FP>
+__device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0, int z1, F1& one, FP& full) {
+  const int nx = x1 - x0, ny = y1 - y0, nz = z1 - z0;
+  if (nx <= 0 || ny <= 0 || nz <= 0) return;
+  const int part = blockIdx.x, nparts = gridDim.x;
+  if (nx >= 128) {
+    const int xch = (nx + 255) / 256;
+    const int nrg = (ny + P - 1) / P;
+    const int nunits = xch * nrg * nz;
+    int u = part;
+    int xc = u % xch, rg = (u / xch) % nrg, z = u / (xch * nrg);
+    const int dxc = nparts % xch, drg = (nparts / xch) % nrg, dz = nparts / (xch * nrg);
+    while (u < nunits) {
+      const int x = x0 + xc * 256 + (int)threadIdx.x;
+      if (x < x1) {
+        const int yb = rg * P;
+        if (yb + P <= ny) {
+          full(x, y0 + yb, z0 + z);
+        } else {
+          for (int p = 0; p < ny - yb; ++p) one(x, y0 + yb + p, z0 + z);
+        }
+      }
+      u += nparts; xc += dxc; rg += drg; z += dz;
+      if (xc >= xch) { xc -= xch; ++rg; }
+      if (rg >= nrg) { rg -= nrg; ++z; }
+    }
+  } else {
+    const int npts = nx * ny * nz;
+    const int step = nparts * 256 * P;
+    for (int i = part * 256 * P + (int)threadIdx.x; i < npts; i += step) {
+      for (int p = 0; p < P; ++p) {
+        const int j = i + p * 256;
+        if (j >= npts) break;
+        const int r = j / nx;
+        one(x0 + (j - r * nx), y0 + r % ny, z0 + r / ny);
+      }
+    }
+  }
+}
+
+)PRE";
+
+// ---------------------------------------------------------------------------
+// generator
+// ---------------------------------------------------------------------------
+std::string dbl_sfx(int reg, int p) { return "r" + std::to_string(reg) + "_" + std::to_string(p); }
+
+struct LoopGen {
+  const DLoop& L;
+  const std::vector<char>& ro;
+  std::vector<int> cls;               // pitch class of each DAT arg (-1 otherwise)
+  std::vector<std::pair<int64_t, int64_t>> classes;
+  std::ostringstream& os;
+
+  LoopGen(const DLoop& l, const std::vector<char>& r, std::ostringstream& o) : L(l), ro(r), os(o) {
+    cls.assign(L.nargs, -1);
+    for (int a = 0; a < L.nargs; ++a) {
+      if (L.args[a].kind != OPS_ARG_DAT) continue;
+      std::pair<int64_t, int64_t> pp(L.args[a].pitch, L.args[a].plane);
+      int k = -1;
+      for (int j = 0; j < (int)classes.size(); ++j)
+        if (classes[j] == pp) k = j;
+      if (k < 0) {
+        k = (int)classes.size();
+        classes.push_back(pp);
+      }
+      cls[a] = k;
+    }
+  }
+
+  std::string idx(int a, int p) const { return "i" + std::to_string(cls[a]) + "_" + std::to_string(p); }
+  std::string load(int a, int q, int p) const {
+    std::string addr = "p" + std::to_string(a) + " + (" + idx(a, p) + " + (" + std::to_string(L.args[a].off[q]) + "))";
+    return ro[a] ? "__ldg(" + addr + ")" : "*(" + addr + ")";
+  }
+
+  // the IR of one loop for points 0..np-1 (instruction-major)
+  void emit_points(int np) const {
+    for (int p = 0; p < np; ++p) {
+      os << "    double";
+      for (int r = 0; r < kNReg; ++r) os << (r ? ", " : " ") << dbl_sfx(r, p) << " = 0.0";
+      os << ";\n";
+    }
+    for (int pc = 0; pc < L.nins; ++pc) {
+      const int* I = L.ins[pc];
+      const int op = I[0], d = I[1], a = I[2], b = I[3], c = I[4], e = I[5];
+      for (int p = 0; p < np; ++p) {
+        auto R = [&](int r) { return dbl_sfx(r, p); };
+        switch (op) {
+          case OPS_IR_LD:
+            if (L.args[a].kind == OPS_ARG_SCALAR)
+              os << "    " << R(d) << " = s" << a << ";\n";
+            else
+              os << "    " << R(d) << " = " << load(a, b, p) << ";\n";
+            break;
+          case OPS_IR_CST: os << "    " << R(d) << " = K" << a << ";\n"; break;
+          case OPS_IR_ADD: os << "    " << R(d) << " = __dadd_rn(" << R(a) << ", " << R(b) << ");\n"; break;
+          case OPS_IR_SUB: os << "    " << R(d) << " = __dsub_rn(" << R(a) << ", " << R(b) << ");\n"; break;
+          case OPS_IR_MUL: os << "    " << R(d) << " = __dmul_rn(" << R(a) << ", " << R(b) << ");\n"; break;
+          case OPS_IR_DIV: os << "    " << R(d) << " = __ddiv_rn(" << R(a) << ", " << R(b) << ");\n"; break;
+          case OPS_IR_FMA:
+            os << "    " << R(d) << " = __fma_rn(" << R(a) << ", " << R(b) << ", " << R(c) << ");\n";
+            break;
+          case OPS_IR_MIN:
+            os << "    " << R(d) << " = (" << R(b) << " < " << R(a) << ") ? " << R(b) << " : " << R(a) << ";\n";
+            break;
+          case OPS_IR_MAX:
+            os << "    " << R(d) << " = (" << R(b) << " > " << R(a) << ") ? " << R(b) << " : " << R(a) << ";\n";
+            break;
+          case OPS_IR_SGT:
+            os << "    " << R(d) << " = (" << R(a) << " > " << R(b) << ") ? " << R(c) << " : " << R(e) << ";\n";
+            break;
+          case OPS_IR_WSUM:
+          case OPS_IR_WACC: {
+            const int n = L.args[a].npts;
+            os << "    { double t = ";
+            int q = 0;
+            if (op == OPS_IR_WSUM) {
+              os << "__dmul_rn(K" << b << ", " << load(a, 0, p) << ");\n";
+              q = 1;
+            } else {
+              os << R(d) << ";\n";
+            }
+            for (; q < n; ++q) os << "      t = __fma_rn(K" << (b + q) << ", " << load(a, q, p) << ", t);\n";
+            os << "      " << R(d) << " = t; }\n";
+            break;
+          }
+          case OPS_IR_POLY: {
+            os << "    { double t = K" << (b + c) << ";\n";
+            for (int i = c - 1; i >= 0; --i) os << "      t = __fma_rn(t, " << R(a) << ", K" << (b + i) << ");\n";
+            os << "      " << R(d) << " = t; }\n";
+            break;
+          }
+          case OPS_IR_ST: {
+            const std::string q = "p" + std::to_string(d) + "[" + idx(d, p) + "]";
+            if (L.args[d].access == OPS_INC)
+              os << "    " << q << " = __dadd_rn(" << q << ", " << R(a) << ");\n";
+            else
+              os << "    " << q << " = " << R(a) << ";\n";
+            break;
+          }
+          case OPS_IR_RED: {
+            const int k = L.args[d].slot;
+            const int rop = L.red_op[k];
+            const char* f = rop == OPS_RED_SUM ? "red_sum" : (rop == OPS_RED_MIN ? "red_min" : "red_max");
+            os << "    acc" << k << " = " << f << "(acc" << k << ", " << R(a) << ");\n";
+            break;
+          }
+          default: break;
+        }
+      }
+    }
+  }
+
+  void emit(int i) const {
+    os << "\n__device__ __forceinline__ void body" << i
+       << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
+          "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n";
+    // hoisted: dat pointers, scalars, constants
+    std::vector<char> kused(OPS_MAX_CONSTS, 0);
+    std::vector<char> sused(L.nargs, 0);
+    for (int pc = 0; pc < L.nins; ++pc) {
+      const int* I = L.ins[pc];
+      const int op = I[0], a = I[2], b = I[3], c = I[4];
+      if (op == OPS_IR_CST) kused[a] = 1;
+      if (op == OPS_IR_LD && L.args[a].kind == OPS_ARG_SCALAR) sused[a] = 1;
+      if (op == OPS_IR_WSUM || op == OPS_IR_WACC)
+        for (int q = 0; q < L.args[a].npts; ++q) kused[b + q] = 1;
+      if (op == OPS_IR_POLY)
+        for (int q = 0; q <= c; ++q) kused[b + q] = 1;
+    }
+    for (int a = 0; a < L.nargs; ++a) {
+      if (L.args[a].kind == OPS_ARG_DAT) {
+        if (ro[a])
+          os << "  const double* __restrict__ p" << a << " = L->args[" << a << "].ptr0;\n";
+        else
+          os << "  double* p" << a << " = L->args[" << a << "].ptr0;\n";
+      }
+      if (sused[a]) os << "  const double s" << a << " = scal[L->args[" << a << "].slot];\n";
+    }
+    for (int k = 0; k < OPS_MAX_CONSTS; ++k)
+      if (kused[k]) os << "  const double K" << k << " = L->K[" << k << "];\n";
+    for (int k = 0; k < L.nreds; ++k) os << "  DD acc" << k << " = dd_of(red_identity(" << L.red_op[k] << "));\n";
+    // one point
+    os << "  auto one = [&](int x, int y, int z) {\n";
+    for (int k = 0; k < (int)classes.size(); ++k)
+      os << "    const i64 i" << k << "_0 = (i64)x + (i64)y * " << classes[k].first << "ll + (i64)z * "
+         << classes[k].second << "ll;\n";
+    emit_points(1);
+    os << "  };\n";
+    // kJitPts consecutive rows
+    os << "  auto full = [&](int x, int y, int z) {\n";
+    for (int k = 0; k < (int)classes.size(); ++k) {
+      os << "    const i64 i" << k << "_0 = (i64)x + (i64)y * " << classes[k].first << "ll + (i64)z * "
+         << classes[k].second << "ll;\n";
+      for (int p = 1; p < kJitPts; ++p)
+        os << "    const i64 i" << k << "_" << p << " = i" << k << "_0 + " << (int64_t)p * classes[k].first
+           << "ll;\n";
+    }
+    emit_points(kJitPts);
+    os << "  };\n";
+    os << "  run_units<" << kJitPts << ">(x0, x1, y0, y1, z0, z1, one, full);\n";
+    for (int k = 0; k < L.nreds; ++k)
+      os << "  flush_red(" << L.red_op[k] << ", acc" << k << ", part, stride, L->part_row + " << k << ", assign);\n";
+    os << "}\n";
+  }
+};
+
+// Source of the kernels u<l0> .. u<l1-1> for loops[l0..l1) of a segment.
+std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::vector<char>>& ro) {
+  std::ostringstream os;
+  os << "// opstile compiled loop bodies: " << kJitPts << " rows per unit, " << kJitMinCtas << " CTAs per SM\n";
+  os << kPrelude;
+  os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
+  os << "static_assert(sizeof(DArg) == " << sizeof(DArg) << ", \"DArg layout\");\n";
+  for (int i = l0; i < l1; ++i) {
+    LoopGen g(loops[i], ro[i], os);
+    g.emit(i);
+    os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas << ") u" << i
+       << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
+          "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n  body"
+       << i << "(L, x0, x1, y0, y1, z0, z1, scal, part, stride, assign);\n}\n";
+  }
+  return os.str();
+}
+
+uint64_t fnv64(const std::string& s) {
+  uint64_t h = 1469598103934665603ull;
+  for (unsigned char ch : s) {
+    h ^= ch;
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+std::string cache_dir() {
+  const char* e = getenv("OPSTILE_JIT_CACHE");
+  if (e && *e) return e;
+  const char* home = getenv("HOME");
+  return std::string(home && *home ? home : "/tmp") + "/.cache/opstile-jit";
+}
+
+bool read_file(const std::string& path, std::string* out) {
+  std::ifstream f(path, std::ios::binary);
+  if (!f) return false;
+  std::ostringstream ss;
+  ss << f.rdbuf();
+  *out = ss.str();
+  return true;
+}
+
+void write_file(const std::string& path, const std::string& data) {
+  const std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+  {
+    std::ofstream f(tmp, std::ios::binary);
+    if (!f) return;
+    f.write(data.data(), (std::streamsize)data.size());
+    if (!f) return;
+  }
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+void mkdirs(const std::string& dir) {
+  std::string cur;
+  std::stringstream ss(dir);
+  std::string part;
+  if (!dir.empty() && dir[0] == '/') cur = "/";
+  while (std::getline(ss, part, '/')) {
+    if (part.empty()) continue;
+    cur += part + "/";
+    mkdir(cur.c_str(), 0755);
+  }
+}
+
+// call with g_mu held
+bool compile(const std::string& src, std::string* cubin, std::string* why) {
+  nvrtcProgram prog;
+  if (g_api.create(&prog, src.c_str(), "opstile_segment.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    *why = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-fmad=false", "--std=c++17", "-default-device"};
+  const nvrtcResult rc = g_api.compile(prog, 4, opts);
+  if (rc != NVRTC_SUCCESS) {
+    size_t n = 0;
+    g_api.log_size(prog, &n);
+    std::string log(n, '\0');
+    if (n) g_api.log(prog, &log[0]);
+    *why = "NVRTC: " + log.substr(0, 2000);
+    g_api.destroy(&prog);
+    return false;
+  }
+  size_t n = 0;
+  g_api.cubin_size(prog, &n);
+  cubin->assign(n, '\0');
+  g_api.cubin(prog, &(*cubin)[0]);
+  g_api.destroy(&prog);
+  return true;
+}
+
+}  // namespace
+
+struct JitSegment {
+  std::vector<CUfunction> u;
+};
+
+namespace {
+// loaded modules by (device, source); segments by (device, concatenated sources)
+std::map<std::pair<int, std::string>, CUmodule> g_modules;
+std::map<std::pair<int, std::string>, std::unique_ptr<JitSegment>> g_segments;
+
+std::string cache_base(const std::string& src) {
+  char hx[17];
+  std::snprintf(hx, sizeof hx, "%016llx", (unsigned long long)fnv64(src));
+  return cache_dir() + "/" + hx;
+}
+}  // namespace
+
+int jit_segment(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro,
+                JitSegment** out, std::string* why, double* compile_ms) {
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!api_ready(why)) return OPS_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<std::string> srcs;
+  std::string all;
+  for (int l0 = 0; l0 < count; l0 += kJitChunk) {
+    srcs.push_back(generate(loops, l0, std::min(count, l0 + kJitChunk), ro));
+    all += srcs.back();
+  }
+  auto skey = std::make_pair(device, all);
+  auto it = g_segments.find(skey);
+  if (it != g_segments.end()) {
+    *out = it->second.get();
+    return OPS_OK;
+  }
+  // cubins from the disk cache, the rest compiled in parallel
+  const int nm = (int)srcs.size();
+  std::vector<std::string> cubin(nm), err(nm);
+  std::vector<char> need(nm, 0);
+  for (int m = 0; m < nm; ++m) {
+    if (g_modules.count(std::make_pair(device, srcs[m]))) continue;
+    std::string cached;
+    const std::string base = cache_base(srcs[m]);
+    if (read_file(base + ".cu", &cached) && cached == srcs[m] && read_file(base + ".cubin", &cubin[m]) &&
+        !cubin[m].empty())
+      continue;
+    need[m] = 1;
+  }
+  {
+    std::vector<std::thread> th;
+    for (int m = 0; m < nm; ++m)
+      if (need[m]) th.emplace_back([&, m] {
+          if (!compile(srcs[m], &cubin[m], &err[m])) cubin[m].clear();
+        });
+    for (std::thread& t : th) t.join();
+  }
+  for (int m = 0; m < nm; ++m) {
+    if (!need[m]) continue;
+    if (cubin[m].empty()) {
+      *why = err[m];
+      return OPS_ERR_CUDA;
+    }
+    mkdirs(cache_dir());
+    const std::string base = cache_base(srcs[m]);
+    write_file(base + ".cubin", cubin[m]);
+    write_file(base + ".cu", srcs[m]);
+  }
+  std::unique_ptr<JitSegment> s(new JitSegment);
+  s->u.resize(count);
+  for (int m = 0; m < nm; ++m) {
+    auto mk = std::make_pair(device, srcs[m]);
+    CUmodule mod;
+    auto mi = g_modules.find(mk);
+    if (mi != g_modules.end()) {
+      mod = mi->second;
+    } else {
+      if (g_api.load(&mod, cubin[m].data()) != CUDA_SUCCESS) {
+        *why = "cuModuleLoadData failed";
+        return OPS_ERR_CUDA;
+      }
+      g_modules[mk] = mod;
+    }
+    for (int i = m * kJitChunk; i < std::min(count, (m + 1) * kJitChunk); ++i) {
+      const std::string name = "u" + std::to_string(i);
+      if (g_api.get_function(&s->u[i], mod, name.c_str()) != CUDA_SUCCESS) {
+        *why = "cuModuleGetFunction failed";
+        return OPS_ERR_CUDA;
+      }
+    }
+  }
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = s.get();
+  g_segments[skey] = std::move(s);
+  return OPS_OK;
+}
+
+int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, std::string* src,
+                     std::string* why, double* compile_ms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  std::vector<std::string> srcs;
+  src->clear();
+  for (int l0 = 0; l0 < count; l0 += kJitChunk) {
+    srcs.push_back(generate(loops, l0, std::min(count, l0 + kJitChunk), ro));
+    *src += srcs.back();
+  }
+  if (!api_ready(why, true)) {
+    if (why->empty()) *why = g_api.why;
+    return OPS_ERR_NO_DEVICE;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  const int nm = (int)srcs.size();
+  std::vector<std::string> cubin(nm), err(nm);
+  std::vector<char> ok(nm, 0);
+  {
+    std::vector<std::thread> th;
+    for (int m = 0; m < nm; ++m) th.emplace_back([&, m] { ok[m] = compile(srcs[m], &cubin[m], &err[m]); });
+    for (std::thread& t : th) t.join();
+  }
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int m = 0; m < nm; ++m)
+    if (!ok[m]) {
+      *why = err[m];
+      return OPS_ERR_CUDA;
+    }
+  return OPS_OK;
+}
+
+cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const DLoop* d_loop, const int* box,
+                       int grid, int assign) {
+  const DLoop* a0 = d_loop;
+  int b0 = box[0], b1 = box[1], b2 = box[2], b3 = box[3], b4 = box[4], b5 = box[5];
+  const double* sc = env.scal;
+  DD* pt = env.part;
+  int st = env.part_stride;
+  int as = assign;
+  void* args[] = {&a0, &b0, &b1, &b2, &b3, &b4, &b5, &sc, &pt, &st, &as};
+  return to_cuda(g_api.launch(s->u[i], (unsigned)grid, 1, 1, kThreads, 1, 1, 0, (CUstream)env.stream, args, nullptr));
+}
+
+}  // namespace opstile

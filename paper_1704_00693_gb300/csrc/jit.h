@@ -1,0 +1,40 @@
+// Compiled loop bodies: the IR of every loop of a segment is turned into
+// straight-line CUDA C (IR registers become machine registers, stencil
+// offsets become immediates) and compiled for sm_103a at run time with
+// NVRTC, once per distinct segment.  OPS generates per-loop code ahead of
+// time from the application source (Sec. 3); here the loop bodies arrive as
+// IR at run time, so the code is generated at the first flush instead.
+// Internal to the library.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace opstile {
+
+struct JitSegment;
+
+// Kernels for the segment whose descriptors are loops[0..count) (as filled
+// for this flush; only the fields that shape the code are used) and whose
+// dat arguments are read-only in the whole segment where ro[l][a] != 0.
+// On success *out is a module shared by every context of the process with
+// the same device and code.  Returns OPS_OK with *out == nullptr, and the
+// reason in *why, when run-time compilation is unavailable.
+int jit_segment(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro,
+                JitSegment** out, std::string* why, double* compile_ms);
+
+// Host only: the generated source of the segment, compiled for sm_103a
+// without loading it (no device needed).  OPS_ERR_CUDA with the compiler's
+// log in *why when it does not compile; OPS_ERR_NO_DEVICE without NVRTC.
+int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, std::string* src,
+                     std::string* why, double* compile_ms);
+
+// One launch of loop i of the segment over box (grid-stride units, the
+// interpreter's enumeration); reductions assign (assign = 1) or combine
+// into the CTA's partial column.
+cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const DLoop* d_loop, const int* box,
+                       int grid, int assign);
+
+}  // namespace opstile

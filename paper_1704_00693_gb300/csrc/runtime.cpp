@@ -12,10 +12,12 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <set>
 #include <string>
 #include <vector>
 
 #include "internal.h"
+#include "jit.h"
 #include "opstile.h"
 #include "plan.h"
 
@@ -119,6 +121,9 @@ struct ops_ctx_s {
   int oloops_cap = 0;
   OvDat* d_ovdat = nullptr;
   int ovdat_cap = 0;
+  // compiled loop bodies per segment (by signature and IR); nullptr: interpret
+  std::map<std::vector<int>, JitSegment*> jit;
+  std::string jit_why;
   int64_t allocated = 0;
   std::string err;
   ops_flush_stats stats;
@@ -748,6 +753,47 @@ int overlap_prefix(ops_ctx c, int first, int count, const int* tile_in, OverlapP
   return OPS_OK;
 }
 
+// Compiled kernels of a segment, generated from its loops' IR at its first
+// flush; *out = nullptr (interpreter kernels) in checked mode, with
+// interpret = 1, or when run-time compilation is unavailable.
+int segment_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitSegment** out) {
+  *out = nullptr;
+  if (c->cfg.interpret || c->cfg.check) return OPS_OK;
+  std::vector<int> key = segment_signature(c, first, count);
+  for (int i = 0; i < count; ++i) {
+    const QLoop& q = c->queue[first + i];
+    key.push_back(-1);
+    key.insert(key.end(), q.code.begin(), q.code.end());
+  }
+  auto it = c->jit.find(key);
+  if (it != c->jit.end()) {
+    *out = it->second;
+    return OPS_OK;
+  }
+  // dats no loop of the segment writes are read through the read-only path
+  std::set<int> written;
+  for (int i = 0; i < count; ++i)
+    for (const ops_arg& a : c->queue[first + i].args)
+      if (a.kind == OPS_ARG_DAT && a.access != OPS_READ) written.insert(a.handle);
+  std::vector<std::vector<char>> ro(count);
+  for (int i = 0; i < count; ++i) {
+    const QLoop& q = c->queue[first + i];
+    ro[i].assign(q.args.size(), 0);
+    for (size_t a = 0; a < q.args.size(); ++a)
+      ro[i][a] = q.args[a].kind == OPS_ARG_DAT && !written.count(q.args[a].handle);
+  }
+  JitSegment* s = nullptr;
+  std::string why;
+  double ms = 0.0;
+  const int rc = jit_segment(c->cfg.device, hl.data() + first, count, ro, &s, &why, &ms);
+  c->stats.compile_ms += ms;
+  if (rc) return fail(c, rc, "compiling loop bodies: %s", why.c_str());
+  if (!s) c->jit_why = why;
+  c->jit[key] = s;
+  *out = s;
+  return OPS_OK;
+}
+
 // Execute a segment in a given mode; tile_in entries <= 0 are chosen automatically.
 int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl, int mode,
                      const int* tile_in) {
@@ -784,6 +830,10 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
   c->stats.mode = mode;
   ++c->stats.segments;
   c->stats.loops += count;
+  JitSegment* js = nullptr;
+  int rcj = segment_code(c, first, count, hl, &js);
+  if (rcj) return rcj;
+  c->stats.compiled = js ? 1 : 0;
   if (mode == OPS_MODE_UNTILED || count == 1) {
     for (int i = 0; i < count; ++i) {
       const QLoop& q = c->queue[first + i];
@@ -805,7 +855,10 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
       const int grid = untiled_grid(env, box);
       int rc = record_event(c);
       if (rc) return rc;
-      CUDA_TRY(c, launch_untiled(env, c->d_loops + dl_base + i, box, grid));
+      if (js)
+        CUDA_TRY(c, jit_launch(js, i, env, c->d_loops + dl_base + i, box, grid, 1));
+      else
+        CUDA_TRY(c, launch_untiled(env, c->d_loops + dl_base + i, box, grid));
       rc = record_event(c);
       if (rc) return rc;
       ++c->stats.launches;
@@ -891,13 +944,27 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
   }
   int rc = record_event(c);
   if (rc) return rc;
-  CUDA_TRY(c, launch_skewed(env, c->d_loops + dl_base, cp->d_phases, (int)P.phases.size(), c->skewed_grid));
+  int sgrid = c->skewed_grid;
+  if (js) {
+    // compiled bodies: one launch per phase in plan order; the stream
+    // orders the phases as the persistent kernel's barriers do
+    sgrid = 1;
+    for (const Phase& ph : P.phases) {
+      const int g = std::min(untiled_grid(env, ph.box), c->part_stride);
+      sgrid = std::max(sgrid, g);
+      CUDA_TRY(c, jit_launch(js, ph.loop, env, c->d_loops + dl_base + ph.loop, ph.box, g, 0));
+      ++c->stats.launches;
+      ++c->stats.kernel_launches;
+    }
+  } else {
+    CUDA_TRY(c, launch_skewed(env, c->d_loops + dl_base, cp->d_phases, (int)P.phases.size(), sgrid));
+    ++c->stats.launches;
+    ++c->stats.kernel_launches;
+  }
   rc = record_event(c);
   if (rc) return rc;
-  ++c->stats.launches;
-  ++c->stats.kernel_launches;
   if (nrows) {
-    CUDA_TRY(c, launch_fold(env, row0, nrows, c->skewed_grid));
+    CUDA_TRY(c, launch_fold(env, row0, nrows, sgrid));
     ++c->stats.launches;
   }
   return OPS_OK;
@@ -1450,6 +1517,39 @@ int ops_plan_skewed(ops_ctx c, const int* tile, int* out_ntiles, int* out_ranges
     std::memcpy(out_ranges + pos, P.ranges[d].data(), sizeof(int) * P.ranges[d].size());
     pos += (int64_t)P.ranges[d].size();
   }
+  return OPS_OK;
+}
+
+int ops_compile_queued(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
+  const int n = (int)c->queue.size();
+  std::vector<DLoop> hl(n);
+  std::vector<FoldRow> rows;
+  std::set<int> written;
+  for (int i = 0; i < n; ++i) {
+    fill_dloop(c, c->queue[i], hl[i], (int)rows.size(), rows);
+    for (const ops_arg& a : c->queue[i].args)
+      if (a.kind == OPS_ARG_DAT && a.access != OPS_READ) written.insert(a.handle);
+  }
+  std::vector<std::vector<char>> ro(n);
+  for (int i = 0; i < n; ++i) {
+    const QLoop& q = c->queue[i];
+    ro[i].assign(q.args.size(), 0);
+    for (size_t a = 0; a < q.args.size(); ++a)
+      ro[i][a] = q.args[a].kind == OPS_ARG_DAT && !written.count(q.args[a].handle);
+  }
+  std::string src, why;
+  double ms = 0.0;
+  const int rc = jit_compile_only(hl.data(), n, ro, &src, &why, &ms);
+  if (src_len) *src_len = (int64_t)src.size();
+  if (src_out && cap > 0) {
+    const size_t k = std::min<size_t>(src.size(), (size_t)cap - 1);
+    std::memcpy(src_out, src.data(), k);
+    src_out[k] = '\0';
+  }
+  if (compile_ms) *compile_ms = ms;
+  if (rc) return fail(c, rc, "%s", why.c_str());
   return OPS_OK;
 }
 

@@ -60,18 +60,20 @@ def test_worked_example_1d():
     ref, _ = oracle.run_chain(c)
     for mode, tile in [("untiled", None), ("skewed", (4,)), ("skewed", (1,)), ("skewed", (3,)),
                        ("overlapped", (4,)), ("overlapped", (1,)), ("overlapped", (3,))]:
-        got, _, st = run_gpu(c, mode, tile)
-        assert_same(c, got, ref, what=f"{mode} {tile}")
+        for interp in (False, True):
+            got, _, st = run_gpu(c, mode, tile, interpret=interp)
+            assert_same(c, got, ref, what=f"{mode} {tile} interpret={interp}")
 
 
+@pytest.mark.parametrize("interpret", [False, True])
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 0, 0)), ("skewed", (0, 40, 0)),
                                        ("skewed", (100, 33, 0)), ("overlapped", (0, 0, 0)),
                                        ("overlapped", (64, 16, 0)), ("overlapped", (100, 33, 0))])
-def test_small2d_chain_bit_exact(mode, tile):
+def test_small2d_chain_bit_exact(mode, tile, interpret):
     """8 loops x 10 repetitions on 256^2 (radius-1 stencils, zero halo)."""
     c = W.small2d(n=256, reps=10)
     ref, _ = oracle.run_chain(c)
-    got, _, st = run_gpu(c, mode, tile)
+    got, _, st = run_gpu(c, mode, tile, interpret=interpret)
     assert_same(c, got, ref, what=f"{mode} {tile}")
     if mode == "skewed":
         assert st["mode"] == ops.OPS_MODE_SKEWED
@@ -81,18 +83,22 @@ def test_small2d_chain_bit_exact(mode, tile):
         assert st["redundant_points"] > 0 and st["loops"] == len(c.loops)
 
 
+@pytest.mark.parametrize("interpret", [False, True])
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 32, 0)), ("skewed", (0, 17, 0)),
                                        ("skewed", (37, 23, 0)), ("skewed", (0, 0, 0)), ("auto", None),
                                        ("overlapped", None), ("overlapped", (32, 8, 0)),
                                        ("overlapped", (40, 100, 0))])
-def test_cloverleaf_shaped_chain(mode, tile):
+def test_cloverleaf_shaped_chain(mode, tile, interpret):
     """83-loop CloverLeaf-shaped steps on a 100^2 grid (ragged tiles), with
     node ranges, thin halo strips, RW updates and two reductions per step;
-    the min reduction feeds the next step's constants."""
+    the min reduction feeds the next step's constants.  Loop bodies run
+    compiled from the IR, or through the interpreter kernels."""
     c = W.cloverleaf2d(n=100, steps=3)
     ref, ref_hist = oracle.run_chain(c)
-    got, hist, st = run_gpu(c, mode, tile)
-    assert_same(c, got, ref, hist, ref_hist, what=f"{mode} {tile}")
+    got, hist, st = run_gpu(c, mode, tile, interpret=interpret)
+    assert_same(c, got, ref, hist, ref_hist, what=f"{mode} {tile} interpret={interpret}")
+    if mode in ("untiled", "skewed"):
+        assert st["compiled"] == (0 if interpret else 1)
 
 
 def test_jacobi_eigenmode_closed_form_on_gpu():
@@ -136,10 +142,11 @@ def test_constant_and_linear_fields():
 def test_opensbli_shaped_3d():
     c = W.opensbli3d(n=20, steps=1)
     ref, _ = oracle.run_chain(c)
-    for mode, tile in [("untiled", None), ("skewed", (0, 0, 6)), ("skewed", (0, 7, 5)),
-                       ("overlapped", (0, 0, 0)), ("overlapped", (8, 7, 5))]:
-        got, _, st = run_gpu(c, mode, tile)
-        assert_same(c, got, ref, what=f"3d {mode} {tile}")
+    for mode, tile, interp in [("untiled", None, False), ("skewed", (0, 0, 6), False), ("skewed", (0, 7, 5), False),
+                               ("untiled", None, True), ("skewed", (0, 7, 5), True),
+                               ("overlapped", (0, 0, 0), False), ("overlapped", (8, 7, 5), False)]:
+        got, _, st = run_gpu(c, mode, tile, interpret=interp)
+        assert_same(c, got, ref, what=f"3d {mode} {tile} interpret={interp}")
 
 
 def edge_chain(n=30):
@@ -176,12 +183,13 @@ def edge_chain(n=30):
     return Chain("edge", 2, size, d_m, d_p, dats, st, [RSUM, RMIN, RMAX], loops, steps=2)
 
 
+@pytest.mark.parametrize("interpret", [False, True])
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 7, 0)), ("skewed", (11, 5, 0)),
                                        ("overlapped", None), ("overlapped", (11, 5, 0))])
-def test_edge_cases(mode, tile):
+def test_edge_cases(mode, tile, interpret):
     c = edge_chain()
     ref, ref_hist = oracle.run_chain(c)
-    got, hist, st = run_gpu(c, mode, tile)
+    got, hist, st = run_gpu(c, mode, tile, interpret=interpret)
     assert_same(c, got, ref, hist, ref_hist, what=f"edge {mode} {tile}")
 
 
@@ -197,7 +205,8 @@ def test_barrier_timeout_reports_and_context_recovers():
     limit, the kernel returns, the host sees OPS_ERR_TIMEOUT; a new context
     on the same device then runs normally."""
     c = W.small2d(n=64, reps=1)
-    r = ChainRunner(c, mode="skewed", tile=(0, 8, 0), timeout_ms=200, skip_barrier_block=0)
+    # the persistent skewed kernel (interpreted bodies) is the one with grid barriers
+    r = ChainRunner(c, mode="skewed", tile=(0, 8, 0), timeout_ms=200, skip_barrier_block=0, interpret=True)
     try:
         r.enqueue_step()
         with pytest.raises(ops.OpsError) as e:
@@ -251,5 +260,8 @@ def test_full_size_cloverleaf_one_step():
     c = W.cloverleaf2d(n=3840, steps=1)
     ref, ref_hist = oracle.run_chain(c)
     got, hist, st = run_gpu(c, "skewed")
-    assert_same(c, got, ref, hist, ref_hist, what="full size")
-    assert st["tiles"] > 1
+    assert_same(c, got, ref, hist, ref_hist, what="full size skewed")
+    assert st["tiles"] > 1 and st["compiled"] == 1
+    got, hist, st = run_gpu(c, "untiled")
+    assert_same(c, got, ref, hist, ref_hist, what="full size untiled")
+    assert st["compiled"] == 1
