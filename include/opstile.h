@@ -137,6 +137,8 @@ int ops_init(ops_ctx* out, const ops_config* cfg);
 /* Flush nothing; free every library-owned buffer and the context. */
 int ops_finalize(ops_ctx ctx);
 const char* ops_last_error(ops_ctx ctx);
+/* Turn the per-kernel timing events (ops_config.timing) on or off for later flushes. */
+int ops_set_timing(ops_ctx ctx, int timing);
 /* Change mode / tile / segment for later flushes (tile may be NULL). */
 int ops_set_mode(ops_ctx ctx, int mode, const int* tile, int segment);
 

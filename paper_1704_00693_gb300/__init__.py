@@ -224,6 +224,10 @@ def ops_last_stats(ctx) -> dict:
     return s.as_dict()
 
 
+def ops_set_timing(ctx, timing: bool):
+    _check(ctx, load().ops_set_timing(ctx, 1 if timing else 0))
+
+
 def ops_plan_skewed(ctx, tile, ndim: int, nloops: int):
     """Algorithm 1 ranges for the queued loops: list over d of arrays
     [ntiles_d, nloops, 2]."""

@@ -56,6 +56,11 @@ class ChainRunner:
         self.dt = 1.0
         self.history: List[List[float]] = []
 
+    def set_timing(self, on: bool):
+        """Per-kernel timing events on or off for later steps (kernel_ms in stats)."""
+        from . import ops_set_timing
+        ops_set_timing(self.ctx, on)
+
     def upload(self):
         for h, d in zip(self.dats, self.chain.dats):
             ops_dat_upload(self.ctx, h, d.init)
@@ -80,7 +85,11 @@ class ChainRunner:
             arr = (ops_arg * max(1, len(args)))(*args)
             code = np.ascontiguousarray(lp.code.astype(np.int32))
             consts = np.ascontiguousarray(lp.consts.astype(np.float64))
-            self._calls.append((lp, r, arr, len(args), code, consts, lp.name.encode()))
+            # ctypes arguments converted once (the arrays stay alive in the tuple)
+            cargs = (C.c_int(self.block), C.c_int(self.chain.ndim), r.ctypes.data_as(C.POINTER(C.c_int)),
+                     C.c_int(len(args)), arr, C.c_int(code.shape[0]), code.ctypes.data_as(C.POINTER(C.c_int32)),
+                     C.c_int(consts.size), consts.ctypes.data_as(C.POINTER(C.c_double)), lp.name.encode())
+            self._calls.append((lp, r, code, consts, cargs))
         self._L = L
 
     def enqueue_step(self, dt: Optional[float] = None):
@@ -90,14 +99,13 @@ class ChainRunner:
             self._marshal()
         dt = self.dt if dt is None else dt
         L = self._L
-        for lp, r, arr, nargs, code, consts, name in self._calls:
+        par_loop, ctx = L.ops_par_loop, self.ctx
+        for lp, r, code, consts, cargs in self._calls:
             if lp.dt_slot >= 0:
                 consts[lp.dt_slot] = lp.dt_scale * dt
-            _check(self.ctx, L.ops_par_loop(self.ctx, C.c_int(self.block), C.c_int(self.chain.ndim),
-                                            r.ctypes.data_as(C.POINTER(C.c_int)), C.c_int(nargs), arr,
-                                            C.c_int(code.shape[0]), code.ctypes.data_as(C.POINTER(C.c_int32)),
-                                            C.c_int(consts.size), consts.ctypes.data_as(C.POINTER(C.c_double)),
-                                            name))
+            rc = par_loop(ctx, *cargs)
+            if rc:
+                _check(ctx, rc)
 
     def step(self) -> List[float]:
         """Queue one step and flush it by reading every reduction."""

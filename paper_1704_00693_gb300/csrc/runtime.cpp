@@ -81,7 +81,8 @@ struct OverlapPlan {
 // Autotuning state of one segment signature.
 struct TuneRec {
   std::vector<std::array<int, 4>> cand;  // (mode, tile x, tile y, tile z)
-  std::vector<double> ms;                // device time of each candidate (-1: not yet run)
+  std::vector<double> ms;                // best device time of each candidate (-1: not yet run)
+  std::vector<int> runs;                 // samples taken of each candidate
   int pending = -1;                      // candidate whose events are outstanding
   int best = -1;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -113,6 +114,11 @@ struct ops_ctx_s {
   unsigned* d_bar = nullptr;
   DLoop* d_loops = nullptr;
   int loops_cap = 0;
+  // host copy of the descriptors d_loops holds (in stream order), so a flush
+  // uploads only the descriptors that changed since the last one
+  std::vector<DLoop> loops_mirror;
+  DLoop* mirror_of = nullptr;
+  uint64_t swap_gen = 0;  // bumped whenever overlapped tiles move dats to their other buffer
   int skewed_grid = 0;
   std::map<std::vector<int>, std::unique_ptr<CachedPlan>> plans;
   std::map<std::vector<int>, TuneRec> tune;
@@ -434,6 +440,36 @@ int record_event(ops_ctx c) {
 
 std::vector<int> segment_signature(ops_ctx c, int first, int count);
 
+// Bring d_loops[first, first + count) up to date with hl, copying only the
+// runs of descriptors that differ from what the device already holds.
+int upload_loops(ops_ctx c, const std::vector<DLoop>& hl, int first, int count) {
+  if (c->mirror_of != c->d_loops) {
+    c->loops_mirror.clear();
+    c->mirror_of = c->d_loops;
+  }
+  if ((int)c->loops_mirror.size() < first + count) {
+    const size_t old = c->loops_mirror.size();
+    c->loops_mirror.resize(first + count);
+    // mark new entries as unknown (a descriptor never has nargs < 0)
+    for (size_t i = old; i < c->loops_mirror.size(); ++i) c->loops_mirror[i].nargs = -1;
+  }
+  int i = first;
+  const int end = first + count;
+  while (i < end) {
+    if (std::memcmp(&c->loops_mirror[i], &hl[i], sizeof(DLoop)) == 0) {
+      ++i;
+      continue;
+    }
+    int j = i + 1;
+    while (j < end && std::memcmp(&c->loops_mirror[j], &hl[j], sizeof(DLoop)) != 0) ++j;
+    CUDA_TRY(c, cudaMemcpyAsync(c->d_loops + i, hl.data() + i, sizeof(DLoop) * (j - i), cudaMemcpyHostToDevice,
+                                c->stream));
+    std::memcpy(&c->loops_mirror[i], &hl[i], sizeof(DLoop) * (j - i));
+    i = j;
+  }
+  return OPS_OK;
+}
+
 // Overlapped tiles (Sec. 4.D, CTA tiles in place of MPI ranks).  The tiles
 // partition the dats' allocation box; in each tile the loops run on the boxes
 // of build_overlap_tile and each dat lives in a shared-memory footprint that
@@ -724,6 +760,7 @@ int run_overlap_plan(ops_ctx c, int first, const std::vector<DLoop>& hl, const O
       Dat& D = c->dats[op->seg_dats[k]];
       std::swap(D.alloc, D.alt);
       std::swap(D.ptr0, D.alt_ptr0);
+      ++c->swap_gen;
     }
   ++c->stats.segments;
   c->stats.loops += n;
@@ -820,8 +857,8 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
       // earlier runs moved written dats to their other buffers
       std::vector<FoldRow> unused;
       for (int k = first; k < first + count; ++k) fill_dloop(c, c->queue[k], hl[k], hl[k].part_row, unused);
-      CUDA_TRY(c, cudaMemcpyAsync(c->d_loops + first, hl.data() + first, sizeof(DLoop) * count,
-                                  cudaMemcpyHostToDevice, c->stream));
+      int rc = upload_loops(c, hl, first, count);
+      if (rc) return rc;
     }
     mode = OPS_MODE_SKEWED;
     tile_in = c->cfg.tile;
@@ -1026,6 +1063,7 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<D
     }
     if (count > 1) T.cand.push_back({OPS_MODE_OVERLAPPED, 0, 0, 0});
     T.ms.assign(T.cand.size(), -1.0);
+    T.runs.assign(T.cand.size(), 0);
     CUDA_TRY(c, cudaEventCreate(&T.e0));
     CUDA_TRY(c, cudaEventCreate(&T.e1));
   }
@@ -1033,13 +1071,16 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<D
     float t = 0.f;
     CUDA_TRY(c, cudaEventSynchronize(T.e1));
     CUDA_TRY(c, cudaEventElapsedTime(&t, T.e0, T.e1));
-    T.ms[T.pending] = t;
+    T.ms[T.pending] = T.ms[T.pending] < 0 ? t : std::min<double>(T.ms[T.pending], t);
+    ++T.runs[T.pending];
     T.pending = -1;
   }
   int pick = T.best;
   if (pick < 0) {
-    for (size_t i = 0; i < T.cand.size() && pick < 0; ++i)
-      if (T.ms[i] < 0) pick = (int)i;
+    // round robin until every candidate has kTuneSamples samples; keep the best of each
+    constexpr int kTuneSamples = 2;
+    for (size_t i = 0; i < T.cand.size(); ++i)
+      if (T.runs[i] < kTuneSamples && (pick < 0 || T.runs[i] < T.runs[pick])) pick = (int)i;
     if (pick < 0) {
       pick = 0;
       for (size_t i = 1; i < T.cand.size(); ++i)
@@ -1080,8 +1121,11 @@ int flush(ops_ctx c) {
     prow[i] = (int)rows.size();
     fill_dloop(c, c->queue[i], hl[i], prow[i], rows);
   }
+  const uint64_t filled_gen = c->swap_gen;
+  const int cap0 = c->loops_cap;
   int rc = ensure(c, &c->d_loops, &c->loops_cap, n);
   if (rc) return rc;
+  if (c->loops_cap != cap0) c->loops_mirror.clear();  // new allocation: contents unknown
   if (!rows.empty()) {
     rc = ensure(c, &c->d_rows, &c->rows_cap, (int)rows.size());
     if (rc) return rc;
@@ -1115,12 +1159,17 @@ int flush(ops_ctx c) {
       if (!cut && c->queue[i].block != c->queue[first].block) cut = true;
     }
     if (cut && i > first) {
-      // descriptors are filled right before their segment runs: an earlier
-      // overlapped segment may have swapped dat buffers
-      std::vector<FoldRow> unused;
-      for (int k = first; k < i; ++k) fill_dloop(c, c->queue[k], hl[k], prow[k], unused);
-      CUDA_TRY(c, cudaMemcpyAsync(c->d_loops + first, hl.data() + first, sizeof(DLoop) * (i - first),
-                                  cudaMemcpyHostToDevice, c->stream));
+      // an earlier overlapped segment of this flush may have moved dats to
+      // their other buffers: refill this segment's descriptors then
+      if (c->swap_gen != filled_gen) {
+        std::vector<FoldRow> unused;
+        for (int k = first; k < i; ++k) fill_dloop(c, c->queue[k], hl[k], prow[k], unused);
+      }
+      rc = upload_loops(c, hl, first, i - first);
+      if (rc) {
+        c->queue.clear();
+        return rc;
+      }
       rc = run_segment(c, first, i - first, first, hl);
       if (rc) {
         c->queue.clear();
@@ -1254,6 +1303,12 @@ int ops_finalize(ops_ctx c) {
 }
 
 const char* ops_last_error(ops_ctx c) { return c ? c->err.c_str() : "null context"; }
+
+int ops_set_timing(ops_ctx c, int timing) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  c->cfg.timing = timing ? 1 : 0;
+  return OPS_OK;
+}
 
 int ops_set_mode(ops_ctx c, int mode, const int* tile, int segment) {
   if (!c) return OPS_ERR_INVALID_ARG;

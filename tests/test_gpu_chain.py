@@ -235,10 +235,11 @@ def test_plan_cache_reuse_and_stats():
 
 
 def test_autotuner_settles_and_stays_exact():
-    """AUTO mode times one candidate schedule per step (untiled, then skewed
-    tiles of growing height), then keeps the fastest; every step's dats stay
-    bit-identical to the oracle whichever candidate ran."""
-    c = W.cloverleaf2d(n=120, steps=10)
+    """AUTO mode times one candidate schedule per step (untiled, skewed tiles
+    of growing height, overlapped), round robin until each has two samples,
+    then keeps the fastest; every step's dats stay bit-identical to the
+    oracle whichever candidate ran."""
+    c = W.cloverleaf2d(n=120, steps=20)
     ref, ref_hist = oracle.run_chain(c)
     r = ChainRunner(c, mode="auto")
     try:
