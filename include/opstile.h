@@ -195,6 +195,13 @@ int ops_dat_fetch(ops_ctx ctx, int dat, double* host_out, int64_t nelems);
 /* Copy a dense host array of the allocation box into the dat (after the
  * queued loops, in stream order). */
 int ops_dat_upload(ops_ctx ctx, int dat, const double* host_in, int64_t nelems);
+/* As ops_dat_fetch / ops_dat_upload, but the copy is only queued on the
+ * context's stream (after the flushed loops): the host array must stay
+ * valid, and unchanged for an upload, until ops_sync (or another waiting
+ * call) returns; fetched values are there from then on.  With pinned host
+ * memory the copy runs while the host continues. */
+int ops_dat_fetch_async(ops_ctx ctx, int dat, double* host_out, int64_t nelems);
+int ops_dat_upload_async(ops_ctx ctx, int dat, const double* host_in, int64_t nelems);
 /* Current device address of grid point (0,0,0) and strides of a dat; ext
  * receives the allocation extents (may be NULL). */
 int ops_dat_info(ops_ctx ctx, int dat, double** dev_ptr0, int64_t* pitch, int64_t* plane, int* ext);

@@ -218,6 +218,22 @@ def ops_dat_upload(ctx, dat: int, host: np.ndarray):
                                       C.c_int64(h.size)))
 
 
+def ops_dat_fetch_async(ctx, dat: int, out: np.ndarray):
+    """Queue a fetch into `out` (C-contiguous float64, pinned for overlap);
+    the values are there once ops_sync returns."""
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    _check(ctx, load().ops_dat_fetch_async(ctx, C.c_int(dat), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                           C.c_int64(out.size)))
+
+
+def ops_dat_upload_async(ctx, dat: int, host: np.ndarray):
+    """Queue an upload from `host` (C-contiguous float64, kept unchanged until
+    ops_sync returns)."""
+    assert host.dtype == np.float64 and host.flags.c_contiguous
+    _check(ctx, load().ops_dat_upload_async(ctx, C.c_int(dat), host.ctypes.data_as(C.POINTER(C.c_double)),
+                                            C.c_int64(host.size)))
+
+
 def ops_last_stats(ctx) -> dict:
     s = ops_flush_stats()
     _check(ctx, load().ops_last_stats(ctx, C.byref(s)))

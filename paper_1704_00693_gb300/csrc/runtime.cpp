@@ -1482,41 +1482,47 @@ int ops_reduction_result(ops_ctx c, int red, double* host_out) {
   return OPS_OK;
 }
 
-int ops_dat_fetch(ops_ctx c, int dat, double* host_out, int64_t nelems) {
-  if (!c || !host_out) return OPS_ERR_INVALID_ARG;
+// Copy a dat between its device allocation box and a dense host array
+// (x fastest), after flushing the queue; to_host selects the direction.
+// wait = 0 leaves the copy queued on the context's stream.
+int dat_copy(ops_ctx c, int dat, double* host, int64_t nelems, bool to_host, bool wait) {
+  if (!c || !host) return OPS_ERR_INVALID_ARG;
   if (dat < 0 || dat >= (int)c->dats.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad dat %d", dat);
-  const Dat& D = c->dats[dat];
-  if (nelems != (int64_t)D.ext[0] * D.ext[1] * D.ext[2])
-    return fail(c, OPS_ERR_INVALID_ARG, "dat '%s': fetch needs %lld elements", D.name.c_str(),
-                (long long)D.ext[0] * D.ext[1] * D.ext[2]);
+  const Dat& D0 = c->dats[dat];
+  if (nelems != (int64_t)D0.ext[0] * D0.ext[1] * D0.ext[2])
+    return fail(c, OPS_ERR_INVALID_ARG, "dat '%s': %s needs %lld elements", D0.name.c_str(),
+                to_host ? "fetch" : "upload", (long long)D0.ext[0] * D0.ext[1] * D0.ext[2]);
+  if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
   int rc = flush(c);
   if (rc) return rc;
-  if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
-  const double* base = D.ptr0 - D.dm[0] - D.pitch * D.dm[1] - D.plane * D.dm[2];
-  for (int z = 0; z < D.ext[2]; ++z)
-    CUDA_TRY(c, cudaMemcpy2DAsync(host_out + (size_t)z * D.ext[0] * D.ext[1], sizeof(double) * D.ext[0],
-                                  base + (size_t)z * D.plane, sizeof(double) * D.pitch, sizeof(double) * D.ext[0],
-                                  D.ext[1], cudaMemcpyDeviceToHost, c->stream));
-  return check_device_error(c);
+  const Dat& D = c->dats[dat];  // the flush may have moved it to its other buffer
+  double* base = D.ptr0 - D.dm[0] - D.pitch * D.dm[1] - D.plane * D.dm[2];
+  const size_t hrow = sizeof(double) * D.ext[0], drow = sizeof(double) * D.pitch;
+  for (int z = 0; z < D.ext[2]; ++z) {
+    double* h = host + (size_t)z * D.ext[0] * D.ext[1];
+    double* d = base + (size_t)z * D.plane;
+    if (to_host)
+      CUDA_TRY(c, cudaMemcpy2DAsync(h, hrow, d, drow, hrow, D.ext[1], cudaMemcpyDeviceToHost, c->stream));
+    else
+      CUDA_TRY(c, cudaMemcpy2DAsync(d, drow, h, hrow, hrow, D.ext[1], cudaMemcpyHostToDevice, c->stream));
+  }
+  return wait ? check_device_error(c) : OPS_OK;
+}
+
+int ops_dat_fetch(ops_ctx c, int dat, double* host_out, int64_t nelems) {
+  return dat_copy(c, dat, host_out, nelems, true, true);
 }
 
 int ops_dat_upload(ops_ctx c, int dat, const double* host_in, int64_t nelems) {
-  if (!c || !host_in) return OPS_ERR_INVALID_ARG;
-  if (dat < 0 || dat >= (int)c->dats.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad dat %d", dat);
-  const Dat& D = c->dats[dat];
-  if (nelems != (int64_t)D.ext[0] * D.ext[1] * D.ext[2])
-    return fail(c, OPS_ERR_INVALID_ARG, "dat '%s': upload needs %lld elements", D.name.c_str(),
-                (long long)D.ext[0] * D.ext[1] * D.ext[2]);
-  if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
-  int rc = flush(c);
-  if (rc) return rc;
-  double* base = D.ptr0 - D.dm[0] - D.pitch * D.dm[1] - D.plane * D.dm[2];
-  for (int z = 0; z < D.ext[2]; ++z)
-    CUDA_TRY(c, cudaMemcpy2DAsync(base + (size_t)z * D.plane, sizeof(double) * D.pitch,
-                                  host_in + (size_t)z * D.ext[0] * D.ext[1], sizeof(double) * D.ext[0],
-                                  sizeof(double) * D.ext[0], D.ext[1], cudaMemcpyHostToDevice, c->stream));
-  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  return OPS_OK;
+  return dat_copy(c, dat, const_cast<double*>(host_in), nelems, false, true);
+}
+
+int ops_dat_fetch_async(ops_ctx c, int dat, double* host_out, int64_t nelems) {
+  return dat_copy(c, dat, host_out, nelems, true, false);
+}
+
+int ops_dat_upload_async(ops_ctx c, int dat, const double* host_in, int64_t nelems) {
+  return dat_copy(c, dat, const_cast<double*>(host_in), nelems, false, false);
 }
 
 int ops_dat_info(ops_ctx c, int dat, double** dev_ptr0, int64_t* pitch, int64_t* plane, int* ext) {

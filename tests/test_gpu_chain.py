@@ -266,3 +266,28 @@ def test_full_size_cloverleaf_one_step():
     got, hist, st = run_gpu(c, "untiled")
     assert_same(c, got, ref, hist, ref_hist, what="full size untiled")
     assert st["compiled"] == 1
+
+
+def test_async_dat_copies_match_blocking_ones():
+    """ops_dat_upload_async / ops_dat_fetch_async queue the same copies as the
+    blocking calls: a step run on asynchronously uploaded dats and fetched
+    asynchronously equals the oracle."""
+    import torch
+    c = W.cloverleaf2d(n=64, steps=1)
+    ref, ref_hist = oracle.run_chain(c)
+    r = ChainRunner(c, mode="untiled", upload=False)
+    try:
+        host_in = [torch.empty(d.init.shape, dtype=torch.float64, pin_memory=True).numpy() for d in c.dats]
+        for a, d in zip(host_in, c.dats):
+            a[...] = d.init
+        for h, a in zip(r.dats, host_in):
+            ops.ops_dat_upload_async(r.ctx, h, a)
+        r.step()
+        out = [torch.empty(d.init.shape, dtype=torch.float64, pin_memory=True).numpy() for d in c.dats]
+        for h, a in zip(r.dats, out):
+            ops.ops_dat_fetch_async(r.ctx, h, a)
+        ops.ops_sync(r.ctx)
+        hist = r.history
+    finally:
+        r.close()
+    assert_same(c, out, ref, hist, ref_hist, what="async copies")
