@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--no-untiled", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the served-solves measurement")
     p.add_argument("--no-cg", action="store_true", help="skip the 4000^2 CG measurement")
+    p.add_argument("--no-3d", action="store_true", help="skip the 320^3 OpenSBLI-shaped chain")
     p.add_argument("--serve-requests", type=int, default=512)
     return p.parse_args()
 
@@ -286,7 +287,7 @@ def mem_available_bytes():
     return 0
 
 
-def bench_serving(nreq=512, seq_sample=32, tol=1e-8, budget=48 << 30):
+def bench_serving(nreq=512, seq_sample=None, tol=1e-8, budget=48 << 30):
     """Served mixed-size diffusion solves (FP32 sweeps + FP64 refinement,
     continuous batching) against sequential untiled FP64 CG solves on the
     same GPU.  Requests: n uniform over multiples of 64 in [64, 2048],
@@ -308,7 +309,9 @@ def bench_serving(nreq=512, seq_sample=32, tol=1e-8, budget=48 << 30):
         return W.cg_problem(n, 1e-1, 1e1, seed=s)
 
     probs = [problem(i) for i in range(nreq)]
-    # sequential untiled FP64 baseline on a bounded sample (same request order)
+    # sequential untiled FP64 baseline: every request, in stream order, one
+    # solve at a time (a smaller sample is scaled to the stream by its cells)
+    seq_sample = nreq if seq_sample is None else min(seq_sample, nreq)
     ctx = ops.ops_init()
     try:
         ops.ops_cg_solve(ctx, *probs[0], tol, ops.OPS_PREC_FP64)  # warm-up
@@ -383,6 +386,23 @@ def bench_cg(n=4000, tol=1e-10):
     best = min((k for k in out if k.startswith("mixed")), key=lambda k: out[k]["seconds"])
     out["best_mixed"] = best
     out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out[best]["seconds"]
+    return out
+
+
+def bench_opensbli3d(stream, torch, n=320, steps=5):
+    """The OpenSBLI-shaped 3D chain (320^3, 15 dats, 40 loops per step):
+    autotuned schedule against the untiled form, effective GB/s of each."""
+    from synth import workloads as W
+    chain = W.opensbli3d(n=n, steps=1)
+    U, flops = workload_numbers(chain)
+    out = {"n": n, "untiled_bytes_per_step": U, "flops_per_step": flops}
+    for mode in ("auto", "untiled"):
+        ms, kms, kl, launches, st = time_mode(chain, mode, None, steps, 3, stream, torch)
+        out[mode] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
+                     "kernel_ms_per_step": kms / steps,
+                     "schedule": {0: "untiled", 1: "skewed", 2: "overlapped"}.get(st["mode"]),
+                     "tile": st["tile"], "compiled": st["compiled"]}
+    out["speedup_auto_vs_untiled"] = out["untiled"]["ms_per_step"] / out["auto"]["ms_per_step"]
     return out
 
 
@@ -534,6 +554,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(args.n)
     cg = bench_cg() if rank == 0 and not args.no_cg else None
+    chain3d = bench_opensbli3d(stream, torch) if rank == 0 and not args.no_3d else None
     serving = bench_serving(args.serve_requests) if rank == 0 and not args.no_serve else None
 
     line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
@@ -547,7 +568,7 @@ def main():
             "speedup_vs_untiled": (untiled["ms_per_step"] / (ms / args.steps)) if untiled else None,
             "untiled": untiled, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
-            "cg_4000": cg, "serving": serving,
+            "cg_4000": cg, "serving": serving, "opensbli3d_320": chain3d,
             "plan": {"phases": st["phases"], "barriers": st["barriers"], "skew": st["skew"],
                      "plan_cache_hits": st["plan_cache_hits"]} if st else None}
     if rank == 0:

@@ -291,3 +291,16 @@ def test_async_dat_copies_match_blocking_ones():
     finally:
         r.close()
     assert_same(c, out, ref, hist, ref_hist, what="async copies")
+
+
+def test_full_size_opensbli_one_step():
+    """The OpenSBLI-shaped chain at its full size (320^3, 15 dats, 40 loops,
+    radius-2 stencils in all three directions) for one step, every point
+    checked, untiled and in the autotuner's first skewed candidate."""
+    c = W.opensbli3d(n=320, steps=1)
+    ref, ref_hist = oracle.run_chain(c)
+    for mode in ("untiled", "skewed"):
+        got, hist, st = run_gpu(c, mode)
+        assert_same(c, got, ref, hist, ref_hist, what=f"opensbli 320^3 {mode}")
+        assert st["compiled"] == 1
+        del got
