@@ -101,6 +101,37 @@ __device__ __forceinline__ void for_unit(const CgUnit& U, F f) {
   }
 }
 
+// The same points, four at a time per thread where the unit allows: point k
+// of a group of four feeds accumulator a[k] (a fixed assignment), so four
+// independent FP64 chains and their loads are in flight per thread.  The
+// callers pass the stored-to arrays as __restrict__ parameters, so the loads
+// of the four points are not held back by the stores.
+template <class F>
+__device__ __forceinline__ void for_unit4(const CgUnit& U, double* a, F f) {
+  if (U.w >= kCgThreads) {
+    for (int r = 0; r < U.nr; ++r) {
+      const int j = U.j0 + r;
+      for (int c = threadIdx.x; c < U.w; c += 4 * kCgThreads) {
+        f(j, U.c0 + c, a[0]);
+        if (c + kCgThreads < U.w) f(j, U.c0 + c + kCgThreads, a[1]);
+        if (c + 2 * kCgThreads < U.w) f(j, U.c0 + c + 2 * kCgThreads, a[2]);
+        if (c + 3 * kCgThreads < U.w) f(j, U.c0 + c + 3 * kCgThreads, a[3]);
+      }
+    }
+  } else {
+    const int rpp = kCgThreads / U.w;
+    const int tr = threadIdx.x / U.w, tc = threadIdx.x - tr * U.w;
+    if (tr < rpp)
+      for (int r = tr; r < U.nr; r += 4 * rpp) {
+        f(U.j0 + r, U.c0 + tc, a[0]);
+        if (r + rpp < U.nr) f(U.j0 + r + rpp, U.c0 + tc, a[1]);
+        if (r + 2 * rpp < U.nr) f(U.j0 + r + 2 * rpp, U.c0 + tc, a[2]);
+        if (r + 3 * rpp < U.nr) f(U.j0 + r + 3 * rpp, U.c0 + tc, a[3]);
+      }
+  }
+}
+__device__ __forceinline__ double sum4(const double* a) { return __dadd_rn(__dadd_rn(a[0], a[1]), __dadd_rn(a[2], a[3])); }
+
 __device__ __forceinline__ double hmean(double a, double b) {
   return __ddiv_rn(__dmul_rn(__dmul_rn(2.0, a), b), __dadd_rn(a, b));
 }
@@ -158,49 +189,97 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_setup2(CgProb* probs, const C
 // ---------------------------------------------------------------------------
 // tick kernels
 // ---------------------------------------------------------------------------
-// A: residual (OUTER/FINISH), w = A p (INNER, CG64); partial dots per unit
+// A sweeps, one function per state (stored-to arrays are __restrict__)
+__device__ __forceinline__ void a_residual(const CgUnit& U, const OpView<double>& A, const double* x,
+                                           const double* b, double* __restrict__ r, int n, double* acc) {
+  for_unit4(U, acc, [&](int j, int i, double& a) {
+    const int64_t c = (int64_t)j * n + i;
+    const double rc = __dsub_rn(b[c], av64(A, x, j, i));
+    r[c] = rc;
+    a = __fma_rn(rc, rc, a);
+  });
+}
+__device__ __forceinline__ void a_inner(const CgUnit& U, const OpView<float>& A, const float* p,
+                                        float* __restrict__ w, int n, double* acc) {
+  for_unit4(U, acc, [&](int j, int i, double& a) {
+    const int64_t c = (int64_t)j * n + i;
+    const float wc = av32(A, p, j, i);
+    w[c] = wc;
+    a = __fma_rn((double)p[c], (double)wc, a);
+  });
+}
+__device__ __forceinline__ void a_cg64(const CgUnit& U, const OpView<double>& A, const double* p,
+                                       double* __restrict__ w, int n, double* acc) {
+  for_unit4(U, acc, [&](int j, int i, double& a) {
+    const int64_t c = (int64_t)j * n + i;
+    const double wc = av64(A, p, j, i);
+    w[c] = wc;
+    a = __fma_rn(p[c], wc, a);
+  });
+}
+
+// A: FP64 residual r = b - A x and |r|^2 (OUTER, FINISH); w = A p and p.w (INNER, CG64)
 __global__ void __launch_bounds__(kCgThreads) k_cg_a(CgProb* probs, const CgUnit* units, int nunits, DD* part) {
   __shared__ double sh[32];
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const CgUnit U = units[u];
     const CgProb& P = probs[U.prob];
     const int st = P.state, n = P.n;
-    double acc = 0.0;  // per-thread FP64 fma accumulation, then a fixed FP64 tree
-    if (st == CG_OUTER || st == CG_FINISH) {
-      const OpView<double> A{P.kx, P.ky, P.dg, n};
-      const double* x = P.x;
-      const double* b = P.b;
-      double* r = P.r;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        const double rc = __dsub_rn(b[c], av64(A, x, j, i));
-        r[c] = rc;
-        acc = __fma_rn(rc, rc, acc);
-      });
-    } else if (st == CG_INNER) {
-      const OpView<float> A{P.kx32, P.ky32, P.dg32, n};
-      const float* p = P.p32;
-      float* w = P.w32;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        const float wc = av32(A, p, j, i);
-        w[c] = wc;
-        acc = __fma_rn((double)p[c], (double)wc, acc);
-      });
-    } else if (st == CG64) {
-      const OpView<double> A{P.kx, P.ky, P.dg, n};
-      const double* p = P.p64;
-      double* w = P.w64;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        const double wc = av64(A, p, j, i);
-        w[c] = wc;
-        acc = __fma_rn(p[c], wc, acc);
-      });
-    }
-    const double tot = cg_block_sum_d(acc, sh);
+    // per-thread FP64 fma accumulation in four fixed chains, then a fixed FP64 tree
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (st == CG_OUTER || st == CG_FINISH)
+      a_residual(U, OpView<double>{P.kx, P.ky, P.dg, n}, P.x, P.b, P.r, n, acc);
+    else if (st == CG_INNER)
+      a_inner(U, OpView<float>{P.kx32, P.ky32, P.dg32, n}, P.p32, P.w32, n, acc);
+    else if (st == CG64)
+      a_cg64(U, OpView<double>{P.kx, P.ky, P.dg, n}, P.p64, P.w64, n, acc);
+    const double tot = cg_block_sum_d(sum4(acc), sh);
     if (threadIdx.x == 0) part[u] = DD{tot, 0.0};
   }
+}
+
+// B sweeps, one function per state
+__device__ __forceinline__ void b_init(const CgUnit& U, double inv, const double* r, float* __restrict__ r32,
+                                       float* __restrict__ p32, float* __restrict__ d32, int n, double* acc) {
+  for_unit4(U, acc, [&](int j, int i, double& a) {
+    const int64_t c = (int64_t)j * n + i;
+    const float rs = (float)__dmul_rn(r[c], inv);
+    r32[c] = rs;
+    p32[c] = rs;
+    d32[c] = 0.0f;
+    a = __fma_rn((double)rs, (double)rs, a);
+  });
+}
+__device__ __forceinline__ void b_inner(const CgUnit& U, float af, const float* p32, const float* w32,
+                                        float* __restrict__ r32, float* __restrict__ d32, int n, double* acc) {
+  for_unit4(U, acc, [&](int j, int i, double& a) {
+    const int64_t c = (int64_t)j * n + i;
+    d32[c] = __fmaf_rn(af, p32[c], d32[c]);
+    const float r = __fmaf_rn(-af, w32[c], r32[c]);
+    r32[c] = r;
+    a = __fma_rn((double)r, (double)r, a);
+  });
+}
+__device__ __forceinline__ void b_cg64_init(const CgUnit& U, const double* b, double* __restrict__ x,
+                                            double* __restrict__ r, double* __restrict__ p, int n, double* acc) {
+  for_unit4(U, acc, [&](int j, int i, double& a) {
+    const int64_t c = (int64_t)j * n + i;
+    const double bc = b[c];
+    x[c] = 0.0;
+    r[c] = bc;
+    p[c] = bc;
+    a = __fma_rn(bc, bc, a);
+  });
+}
+__device__ __forceinline__ void b_cg64(const CgUnit& U, double al, const double* p, const double* w,
+                                       double* __restrict__ x, double* __restrict__ r, int n, double* acc) {
+  for_unit4(U, acc, [&](int j, int i, double& a) {
+    const int64_t c = (int64_t)j * n + i;
+    x[c] = __fma_rn(al, p[c], x[c]);
+    const double rc = __fma_rn(-al, w[c], r[c]);
+    r[c] = rc;
+    a = __fma_rn(rc, rc, a);
+  });
 }
 
 // B: INIT (scaled residual into the FP32 inner vectors), INNER / CG64 updates
@@ -210,56 +289,43 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit
     const CgUnit U = units[u];
     const CgProb& P = probs[U.prob];
     const int st = P.state, n = P.n;
-    double acc = 0.0;  // per-thread FP64 fma accumulation, then a fixed FP64 tree
-    if (st == CG_INIT) {
-      const double inv = __ddiv_rn(1.0, P.nr);
-      const double* r = P.r;
-      float *r32 = P.r32, *p32 = P.p32, *d32 = P.d32;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        const float rs = (float)__dmul_rn(r[c], inv);
-        r32[c] = rs;
-        p32[c] = rs;
-        d32[c] = 0.0f;
-        acc = __fma_rn((double)rs, (double)rs, acc);
-      });
-    } else if (st == CG_INNER) {
-      const float af = (float)P.alpha;
-      const float *p32 = P.p32, *w32 = P.w32;
-      float *r32 = P.r32, *d32 = P.d32;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        d32[c] = __fmaf_rn(af, p32[c], d32[c]);
-        const float r = __fmaf_rn(-af, w32[c], r32[c]);
-        r32[c] = r;
-        acc = __fma_rn((double)r, (double)r, acc);
-      });
-    } else if (st == CG64_INIT) {
-      const double* b = P.b;
-      double *x = P.x, *r = P.r, *p = P.p64;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        const double bc = b[c];
-        x[c] = 0.0;
-        r[c] = bc;
-        p[c] = bc;
-        acc = __fma_rn(bc, bc, acc);
-      });
-    } else if (st == CG64) {
-      const double a = P.alpha;
-      const double *p = P.p64, *w = P.w64;
-      double *x = P.x, *r = P.r;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        x[c] = __fma_rn(a, p[c], x[c]);
-        const double rc = __fma_rn(-a, w[c], r[c]);
-        r[c] = rc;
-        acc = __fma_rn(rc, rc, acc);
-      });
-    }
-    const double tot = cg_block_sum_d(acc, sh);
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    if (st == CG_INIT)
+      b_init(U, __ddiv_rn(1.0, P.nr), P.r, P.r32, P.p32, P.d32, n, acc);
+    else if (st == CG_INNER)
+      b_inner(U, (float)P.alpha, P.p32, P.w32, P.r32, P.d32, n, acc);
+    else if (st == CG64_INIT)
+      b_cg64_init(U, P.b, P.x, P.r, P.p64, n, acc);
+    else if (st == CG64)
+      b_cg64(U, P.alpha, P.p64, P.w64, P.x, P.r, n, acc);
+    const double tot = cg_block_sum_d(sum4(acc), sh);
     if (threadIdx.x == 0) part[u] = DD{tot, 0.0};
   }
+}
+
+// C sweeps, one function per state
+__device__ __forceinline__ void c_inner(const CgUnit& U, float bf, const float* r32, float* __restrict__ p32,
+                                        int n) {
+  double dummy[4];
+  for_unit4(U, dummy, [&](int j, int i, double&) {
+    const int64_t c = (int64_t)j * n + i;
+    p32[c] = __fmaf_rn(bf, p32[c], r32[c]);
+  });
+}
+__device__ __forceinline__ void c_finish(const CgUnit& U, double nr, const float* d32, double* __restrict__ x,
+                                         int n) {
+  double dummy[4];
+  for_unit4(U, dummy, [&](int j, int i, double&) {
+    const int64_t c = (int64_t)j * n + i;
+    x[c] = __fma_rn(nr, (double)d32[c], x[c]);
+  });
+}
+__device__ __forceinline__ void c_cg64(const CgUnit& U, double bt, const double* r, double* __restrict__ p, int n) {
+  double dummy[4];
+  for_unit4(U, dummy, [&](int j, int i, double&) {
+    const int64_t c = (int64_t)j * n + i;
+    p[c] = __fma_rn(bt, p[c], r[c]);
+  });
 }
 
 // C: search-direction update (INNER, CG64) or the refinement correction (FINISH)
@@ -268,31 +334,12 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_c(CgProb* probs, const CgUnit
     const CgUnit U = units[u];
     const CgProb& P = probs[U.prob];
     const int st = P.state, n = P.n;
-    if (st == CG_INNER) {
-      const float bf = (float)P.beta;
-      const float* r32 = P.r32;
-      float* p32 = P.p32;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        p32[c] = __fmaf_rn(bf, p32[c], r32[c]);
-      });
-    } else if (st == CG_FINISH) {
-      const double nr = P.nr;
-      const float* d32 = P.d32;
-      double* x = P.x;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        x[c] = __fma_rn(nr, (double)d32[c], x[c]);
-      });
-    } else if (st == CG64) {
-      const double bt = P.beta;
-      const double* r = P.r;
-      double* p = P.p64;
-      for_unit(U, [&](int j, int i) {
-        const int64_t c = (int64_t)j * n + i;
-        p[c] = __fma_rn(bt, p[c], r[c]);
-      });
-    }
+    if (st == CG_INNER)
+      c_inner(U, (float)P.beta, P.r32, P.p32, n);
+    else if (st == CG_FINISH)
+      c_finish(U, P.nr, P.d32, P.x, n);
+    else if (st == CG64)
+      c_cg64(U, P.beta, P.r, P.p64, n);
   }
 }
 
