@@ -80,6 +80,7 @@ struct Api {
                           void**);
   CUresult (*occupancy)(int*, CUfunction, int, size_t);
   CUresult (*attribute)(int*, CUfunction_attribute, CUfunction);
+  CUresult (*set_attribute)(CUfunction, CUfunction_attribute, int);
 };
 
 Api g_api;
@@ -127,7 +128,8 @@ bool api_ready(std::string* why, bool nvrtc_only = false) {
     } else if (!(drv("cuModuleLoadData", &g_api.load) && drv("cuModuleGetFunction", &g_api.get_function) &&
                  drv("cuLaunchKernel", &g_api.launch) && drv("cuLaunchCooperativeKernel", &g_api.launch_coop) &&
                  drv("cuOccupancyMaxActiveBlocksPerMultiprocessor", &g_api.occupancy) &&
-                 drv("cuFuncGetAttribute", &g_api.attribute))) {
+                 drv("cuFuncGetAttribute", &g_api.attribute) &&
+                 drv("cuFuncSetAttribute", &g_api.set_attribute))) {
       g_api.why = "driver module entry points unavailable";
     } else {
       g_api.ok = true;
@@ -215,10 +217,10 @@ __device__ __forceinline__ void flush_red(int op, DD v, DD* part, int stride, in
 // points 256 apart.  full(x, y, z) takes rows y .. y+P-1 at x; one(x, y, z)
 // a single point.
 template <int P, class F1, class FP>
-__device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0, int z1, F1& one, FP& full) {
+__device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0, int z1, int part, int nparts,
+                                          F1& one, FP& full) {
   const int nx = x1 - x0, ny = y1 - y0, nz = z1 - z0;
   if (nx <= 0 || ny <= 0 || nz <= 0) return;
-  const int part = blockIdx.x, nparts = gridDim.x;
   if (nx >= 128) {
     const int xch = (nx + 255) / 256;
     const int nrg = (ny + P - 1) / P;
@@ -254,6 +256,25 @@ __device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0
   }
 }
 
+
+// overlapped tiles: one dat of a run (the library's OvDat)
+struct OvDat { const double* src; double* dst; i64 gpitch, gplane; int written, smem_off, spitch, splane; };
+// copy a box between a global dat and a shared footprint with corner fb
+__device__ __forceinline__ void copy_box(const int* box, const int* fb, double* sm, int sp, int sq, const double* g0,
+                                         double* g1, i64 gp, i64 gq, bool to_shared) {
+  const int nx = box[1] - box[0], ny = box[3] - box[2], nz = box[5] - box[4];
+  if (nx <= 0 || ny <= 0 || nz <= 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = warp; r < ny * nz; r += nw) {
+    const int y = box[2] + r % ny, z = box[4] + r / ny;
+    double* s = sm + (i64)(z - fb[4]) * sq + (i64)(y - fb[2]) * sp - fb[0];
+    const i64 g = (i64)y * gp + (i64)z * gq;
+    if (to_shared)
+      for (int x = box[0] + lane; x < box[1]; x += 32) s[x] = g0[g + x];
+    else
+      for (int x = box[0] + lane; x < box[1]; x += 32) g1[g + x] = s[x];
+  }
+}
 )PRE";
 
 // ---------------------------------------------------------------------------
@@ -267,8 +288,10 @@ struct LoopGen {
   std::vector<int> cls;               // pitch class of each DAT arg (-1 otherwise)
   std::vector<std::pair<int64_t, int64_t>> classes;
   std::ostringstream& os;
+  bool ov = false;                    // overlapped tile: dats in shared footprints, owned-point reductions
 
-  LoopGen(const DLoop& l, const std::vector<char>& r, std::ostringstream& o) : L(l), ro(r), os(o) {
+  LoopGen(const DLoop& l, const std::vector<char>& r, std::ostringstream& o, bool overlapped = false)
+      : L(l), ro(r), os(o), ov(overlapped) {
     cls.assign(L.nargs, -1);
     for (int a = 0; a < L.nargs; ++a) {
       if (L.args[a].kind != OPS_ARG_DAT) continue;
@@ -296,6 +319,9 @@ struct LoopGen {
       os << "    double";
       for (int r = 0; r < kNReg; ++r) os << (r ? ", " : " ") << dbl_sfx(r, p) << " = 0.0";
       os << ";\n";
+      if (ov && L.nreds)  // redundant points of a tile compute but do not reduce
+        os << "    const bool own" << p << " = x >= ob[0] && x < ob[1] && y + " << p << " >= ob[2] && y + " << p
+           << " < ob[3] && z >= ob[4] && z < ob[5];\n";
     }
     for (int pc = 0; pc < L.nins; ++pc) {
       const int* I = L.ins[pc];
@@ -359,7 +385,10 @@ struct LoopGen {
             const int k = L.args[d].slot;
             const int rop = L.red_op[k];
             const char* f = rop == OPS_RED_SUM ? "red_sum" : (rop == OPS_RED_MIN ? "red_min" : "red_max");
-            os << "    acc" << k << " = " << f << "(acc" << k << ", " << R(a) << ");\n";
+            if (ov)
+              os << "    if (own" << p << ") acc" << k << " = " << f << "(acc" << k << ", " << R(a) << ");\n";
+            else
+              os << "    acc" << k << " = " << f << "(acc" << k << ", " << R(a) << ");\n";
             break;
           }
           default: break;
@@ -368,10 +397,18 @@ struct LoopGen {
     }
   }
 
-  void emit(int i) const {
-    os << "\n__device__ __forceinline__ void body" << i
-       << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
-          "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n";
+  // ndats: dats of an overlapped run (shared footprint pointers fp0 .. fp<ndats-1>)
+  void emit(int i, int ndats = 0) const {
+    if (ov) {
+      os << "\n__device__ __forceinline__ void ovb" << i << "(const DLoop* __restrict__ L, const int* bx";
+      for (int k = 0; k < ndats; ++k) os << ", double* fp" << k;
+      os << ",\n    const double* __restrict__ scal, const int* ob, DD* part, int stride) {\n"
+            "  const int x0 = bx[0], x1 = bx[1], y0 = bx[2], y1 = bx[3], z0 = bx[4], z1 = bx[5];\n";
+    } else {
+      os << "\n__device__ __forceinline__ void body" << i
+         << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
+            "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n";
+    }
     // hoisted: dat pointers, scalars, constants
     std::vector<char> kused(OPS_MAX_CONSTS, 0);
     std::vector<char> sused(L.nargs, 0);
@@ -387,7 +424,9 @@ struct LoopGen {
     }
     for (int a = 0; a < L.nargs; ++a) {
       if (L.args[a].kind == OPS_ARG_DAT) {
-        if (ro[a])
+        if (ov)
+          os << "  double* p" << a << " = fp" << L.args[a].slot << ";\n";
+        else if (ro[a])
           os << "  const double* __restrict__ p" << a << " = L->args[" << a << "].ptr0;\n";
         else
           os << "  double* p" << a << " = L->args[" << a << "].ptr0;\n";
@@ -415,9 +454,13 @@ struct LoopGen {
     }
     emit_points(kJitPts);
     os << "  };\n";
-    os << "  run_units<" << kJitPts << ">(x0, x1, y0, y1, z0, z1, one, full);\n";
+    if (ov)
+      os << "  run_units<" << kJitPts << ">(x0, x1, y0, y1, z0, z1, 0, 1, one, full);\n";
+    else
+      os << "  run_units<" << kJitPts << ">(x0, x1, y0, y1, z0, z1, blockIdx.x, gridDim.x, one, full);\n";
     for (int k = 0; k < L.nreds; ++k)
-      os << "  flush_red(" << L.red_op[k] << ", acc" << k << ", part, stride, L->part_row + " << k << ", assign);\n";
+      os << "  flush_red(" << L.red_op[k] << ", acc" << k << ", part, stride, L->part_row + " << k << ", "
+         << (ov ? "0" : "assign") << ");\n";
     os << "}\n";
   }
 };
@@ -437,6 +480,53 @@ std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::
           "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n  body"
        << i << "(L, x0, x1, y0, y1, z0, z1, scal, part, stride, assign);\n}\n";
   }
+  return os.str();
+}
+
+// Source of the overlapped-tile kernel "ov" for one run of loops with the
+// given shared-memory layout (offsets and strides baked in).
+std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay) {
+  std::ostringstream os;
+  os << "// opstile overlapped tiles: " << kJitPts << " rows per unit\n";
+  os << kPrelude;
+  os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
+  os << "static_assert(sizeof(OvDat) == " << sizeof(OvDat) << ", \"OvDat layout\");\n";
+  const std::vector<char> none(OPS_MAX_ARGS, 0);
+  for (int i = 0; i < count; ++i) {
+    LoopGen g(loops[i], none, os, true);
+    g.emit(i, lay.ndats);
+  }
+  const int nd = lay.ndats;
+  os << "extern \"C\" __global__ void __launch_bounds__(256, 1) ov(const DLoop* __restrict__ loops,\n"
+        "    const OvDat* __restrict__ dats, const int* __restrict__ own, const int* __restrict__ boxes,\n"
+        "    const int* __restrict__ foot, int ntiles, const double* __restrict__ scal, DD* part, int stride) {\n"
+        "  extern __shared__ __align__(16) double area[];\n"
+        "  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {\n"
+        "    __syncthreads();\n"
+     << "    const int* ft = foot + (size_t)t * " << nd * 6 << ";\n";
+  for (int k = 0; k < nd; ++k)
+    os << "    copy_box(ft + " << 6 * k << ", ft + " << 6 * k << ", area + " << lay.smem_off[k] << ", "
+       << lay.spitch[k] << ", " << lay.splane[k] << ", dats[" << k << "].src, nullptr, dats[" << k
+       << "].gpitch, dats[" << k << "].gplane, true);\n";
+  os << "    __syncthreads();\n";
+  for (int k = 0; k < nd; ++k)
+    os << "    double* fp" << k << " = area + " << lay.smem_off[k] << " - (ft[" << 6 * k << "] + (i64)ft["
+       << 6 * k + 2 << "] * " << lay.spitch[k] << " + (i64)ft[" << 6 * k + 4 << "] * " << lay.splane[k] << ");\n";
+  os << "    const int* ob = own + (size_t)t * 6;\n"
+     << "    const int* bt = boxes + (size_t)t * " << count * 6 << ";\n";
+  for (int i = 0; i < count; ++i) {
+    os << "    if (bt[" << 6 * i + 1 << "] > bt[" << 6 * i << "] && bt[" << 6 * i + 3 << "] > bt[" << 6 * i + 2
+       << "] && bt[" << 6 * i + 5 << "] > bt[" << 6 * i + 4 << "]) {\n      ovb" << i << "(loops + " << i
+       << ", bt + " << 6 * i;
+    for (int k = 0; k < nd; ++k) os << ", fp" << k;
+    os << ", scal, ob, part, stride);\n      __syncthreads();\n    }\n";
+  }
+  for (int k = 0; k < nd; ++k)
+    if (lay.written[k])
+      os << "    copy_box(ob, ft + " << 6 * k << ", area + " << lay.smem_off[k] << ", " << lay.spitch[k] << ", "
+         << lay.splane[k] << ", nullptr, dats[" << k << "].dst, dats[" << k << "].gpitch, dats[" << k
+         << "].gplane, false);\n";
+  os << "  }\n}\n";
   return os.str();
 }
 
@@ -495,14 +585,16 @@ bool compile(const std::string& src, std::string* cubin, std::string* why) {
     *why = "nvrtcCreateProgram failed";
     return false;
   }
-  const char* opts[] = {"--gpu-architecture=sm_103a", "-fmad=false", "--std=c++17", "-default-device"};
-  const nvrtcResult rc = g_api.compile(prog, 4, opts);
+  // unused IR registers are declared for every point: silence those notes
+  const char* opts[] = {"--gpu-architecture=sm_103a", "-fmad=false", "--std=c++17", "-default-device",
+                        "--diag-suppress=177,550"};
+  const nvrtcResult rc = g_api.compile(prog, 5, opts);
   if (rc != NVRTC_SUCCESS) {
     size_t n = 0;
     g_api.log_size(prog, &n);
     std::string log(n, '\0');
     if (n) g_api.log(prog, &log[0]);
-    *why = "NVRTC: " + log.substr(0, 2000);
+    *why = "NVRTC: " + log.substr(0, 20000);
     g_api.destroy(&prog);
     return false;
   }
@@ -619,6 +711,141 @@ int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vecto
   src->clear();
   for (int l0 = 0; l0 < count; l0 += kJitChunk) {
     srcs.push_back(generate(loops, l0, std::min(count, l0 + kJitChunk), ro));
+    *src += srcs.back();
+  }
+  if (!api_ready(why, true)) {
+    if (why->empty()) *why = g_api.why;
+    return OPS_ERR_NO_DEVICE;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  const int nm = (int)srcs.size();
+  std::vector<std::string> cubin(nm), err(nm);
+  std::vector<char> ok(nm, 0);
+  {
+    std::vector<std::thread> th;
+    for (int m = 0; m < nm; ++m) th.emplace_back([&, m] { ok[m] = compile(srcs[m], &cubin[m], &err[m]); });
+    for (std::thread& t : th) t.join();
+  }
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  for (int m = 0; m < nm; ++m)
+    if (!ok[m]) {
+      *why = err[m];
+      return OPS_ERR_CUDA;
+    }
+  return OPS_OK;
+}
+
+struct JitOverlap {
+  CUfunction f = nullptr;
+  int area_set = -1;  // dynamic shared memory the function is opted into
+};
+
+namespace {
+std::map<std::pair<int, std::string>, std::unique_ptr<JitOverlap>> g_overlaps;
+
+}  // namespace
+
+int jit_overlap_many(int device, const std::vector<OvRequest>& reqs, std::vector<JitOverlap*>* out, std::string* why,
+                     double* compile_ms) {
+  out->assign(reqs.size(), nullptr);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!api_ready(why)) return OPS_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  const int nr = (int)reqs.size();
+  std::vector<std::string> src(nr), cubin(nr), err(nr);
+  std::vector<char> need(nr, 0), ok(nr, 1);
+  for (int r = 0; r < nr; ++r) {
+    src[r] = generate_overlap(reqs[r].loops, reqs[r].count, reqs[r].lay);
+    auto it = g_overlaps.find(std::make_pair(device, src[r]));
+    if (it != g_overlaps.end()) {
+      (*out)[r] = it->second.get();
+      continue;
+    }
+    std::string cached;
+    const std::string base = cache_base(src[r]);
+    if (read_file(base + ".cu", &cached) && cached == src[r] && read_file(base + ".cubin", &cubin[r]) &&
+        !cubin[r].empty())
+      continue;
+    need[r] = 1;
+  }
+  {
+    std::vector<std::thread> th;
+    for (int r = 0; r < nr; ++r)
+      if (need[r]) th.emplace_back([&, r] { ok[r] = compile(src[r], &cubin[r], &err[r]); });
+    for (std::thread& t : th) t.join();
+  }
+  for (int r = 0; r < nr; ++r) {
+    if ((*out)[r]) continue;
+    if (!ok[r]) {
+      *why = err[r];
+      return OPS_ERR_CUDA;
+    }
+    if (need[r]) {
+      mkdirs(cache_dir());
+      const std::string base = cache_base(src[r]);
+      write_file(base + ".cubin", cubin[r]);
+      write_file(base + ".cu", src[r]);
+    }
+    auto key = std::make_pair(device, src[r]);
+    auto it = g_overlaps.find(key);  // an identical run earlier in this batch
+    if (it != g_overlaps.end()) {
+      (*out)[r] = it->second.get();
+      continue;
+    }
+    CUmodule mod;
+    if (g_api.load(&mod, cubin[r].data()) != CUDA_SUCCESS) {
+      *why = "cuModuleLoadData failed";
+      return OPS_ERR_CUDA;
+    }
+    std::unique_ptr<JitOverlap> o(new JitOverlap);
+    if (g_api.get_function(&o->f, mod, "ov") != CUDA_SUCCESS) {
+      *why = "cuModuleGetFunction failed";
+      return OPS_ERR_CUDA;
+    }
+    (*out)[r] = o.get();
+    g_overlaps[key] = std::move(o);
+  }
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return OPS_OK;
+}
+
+int jit_overlap_max_grid(JitOverlap* o, int num_sms, int area_bytes) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (o->area_set != area_bytes) {
+    if (g_api.set_attribute(o->f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, area_bytes) != CUDA_SUCCESS)
+      return 0;
+    o->area_set = area_bytes;
+  }
+  int per_sm = 0;
+  if (g_api.occupancy(&per_sm, o->f, kThreads, (size_t)area_bytes) != CUDA_SUCCESS) return 0;
+  return per_sm * num_sms;
+}
+
+cudaError_t jit_launch_overlap(const JitOverlap* o, const LaunchEnv& env, const DLoop* d_loops, const OvDat* d_dats,
+                               const int* d_own, const int* d_boxes, const int* d_foot, int ntiles, int grid,
+                               int area_bytes) {
+  const DLoop* a0 = d_loops;
+  const OvDat* a1 = d_dats;
+  const int *a2 = d_own, *a3 = d_boxes, *a4 = d_foot;
+  int a5 = ntiles;
+  const double* a6 = env.scal;
+  DD* a7 = env.part;
+  int a8 = env.part_stride;
+  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
+  return to_cuda(g_api.launch(o->f, (unsigned)grid, 1, 1, kThreads, 1, 1, (unsigned)area_bytes,
+                              (CUstream)env.stream, args, nullptr));
+}
+
+int jit_compile_overlap_only(const DLoop* loops, int count, const OvLayout& lay, std::string* src, std::string* why,
+                             double* compile_ms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  // runs of kJitChunk loops, compiled in parallel (a run's code does not depend on the others)
+  std::vector<std::string> srcs;
+  src->clear();
+  for (int l0 = 0; l0 < count; l0 += kJitChunk) {
+    srcs.push_back(generate_overlap(loops + l0, std::min(kJitChunk, count - l0), lay));
     *src += srcs.back();
   }
   if (!api_ready(why, true)) {

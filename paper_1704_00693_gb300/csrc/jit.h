@@ -37,4 +37,31 @@ int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vecto
 cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const DLoop* d_loop, const int* box,
                        int grid, int assign);
 
+// Overlapped tiles (Sec. 4.D per CTA): one kernel per run of loops, with
+// the run's shared-memory layout compiled in.  loops: the run's descriptors
+// in shared-memory layout (DAT args: pitch / plane / off in footprint
+// strides, slot = the run's dat index).
+struct OvLayout {
+  int ndats = 0;
+  std::vector<int> smem_off, spitch, splane, written;  // per dat of the run
+};
+struct JitOverlap;
+// Kernels for several runs at once: those not compiled yet compile in
+// parallel.  (*out)[i] = nullptr for all when compilation is unavailable.
+struct OvRequest {
+  const DLoop* loops;
+  int count;
+  OvLayout lay;
+};
+int jit_overlap_many(int device, const std::vector<OvRequest>& reqs, std::vector<JitOverlap*>* out, std::string* why,
+                     double* compile_ms);
+// Host only: generate and compile (no load, no device) an overlapped kernel.
+int jit_compile_overlap_only(const DLoop* loops, int count, const OvLayout& lay, std::string* src, std::string* why,
+                             double* compile_ms);
+// CTAs that fit the device at once with area_bytes of dynamic shared memory (0: it does not fit)
+int jit_overlap_max_grid(JitOverlap* o, int num_sms, int area_bytes);
+cudaError_t jit_launch_overlap(const JitOverlap* o, const LaunchEnv& env, const DLoop* d_loops, const OvDat* d_dats,
+                               const int* d_own, const int* d_boxes, const int* d_foot, int ntiles, int grid,
+                               int area_bytes);
+
 }  // namespace opstile

@@ -684,11 +684,12 @@ int overlap_plan(ops_ctx c, int first, int n, const int* tile_in, OverlapPlan** 
 }
 
 // Launch one overlapped plan over loops [first, first + op->nloops).
-int run_overlap_plan(ops_ctx c, int first, const std::vector<DLoop>& hl, const OverlapPlan* op) {
+// The run's descriptors in shared-memory layout: DAT args get the
+// footprint strides, stencil offsets in those strides, slot = run dat index.
+std::vector<DLoop> overlap_descriptors(ops_ctx c, int first, const std::vector<DLoop>& hl, const OverlapPlan* op) {
   const int n = op->nloops;
   std::map<int, int> local;
   for (int k = 0; k < op->ndats; ++k) local[op->seg_dats[k]] = k;
-  // descriptors in shared-memory layout
   std::vector<DLoop> ol(hl.begin() + first, hl.begin() + first + n);
   for (int i = 0; i < n; ++i) {
     const QLoop& q = c->queue[first + i];
@@ -705,6 +706,23 @@ int run_overlap_plan(ops_ctx c, int first, const std::vector<DLoop>& hl, const O
         A.off[p] = (int32_t)(s.off[3 * p] + (int64_t)s.off[3 * p + 1] * A.pitch + (int64_t)s.off[3 * p + 2] * A.plane);
     }
   }
+  return ol;
+}
+
+OvLayout overlap_layout(const OverlapPlan* op) {
+  OvLayout lay;
+  lay.ndats = op->ndats;
+  lay.smem_off = op->smem_off;
+  lay.spitch = op->spitch;
+  lay.splane = op->splane;
+  lay.written = op->written;
+  return lay;
+}
+
+// Launch one overlapped run: jo = its compiled kernel, or nullptr for the interpreter kernel.
+int run_overlap_plan(ops_ctx c, int first, const std::vector<DLoop>& hl, const OverlapPlan* op,
+                     const std::vector<DLoop>& ol, JitOverlap* jo) {
+  const int n = op->nloops;
   int rc = ensure(c, &c->d_oloops, &c->oloops_cap, n);
   if (rc) return rc;
   CUDA_TRY(c, cudaMemcpyAsync(c->d_oloops, ol.data(), sizeof(DLoop) * n, cudaMemcpyHostToDevice, c->stream));
@@ -737,15 +755,23 @@ int run_overlap_plan(ops_ctx c, int first, const std::vector<DLoop>& hl, const O
       nrows = L.part_row + L.nreds - row0;
     }
   }
-  const int grid = std::max(1, std::min({op->ntiles, overlap_max_grid(c->num_sms, op->area_bytes), c->part_stride}));
+  int grid = 0;
+  if (jo) grid = std::min({op->ntiles, jit_overlap_max_grid(jo, c->num_sms, op->area_bytes), c->part_stride});
+  if (grid <= 0) jo = nullptr;
+  if (!jo) grid = std::max(1, std::min({op->ntiles, overlap_max_grid(c->num_sms, op->area_bytes), c->part_stride}));
+  c->stats.compiled = jo ? 1 : 0;
   if (nrows) {
     CUDA_TRY(c, launch_part_init(env, row0, nrows));
     ++c->stats.launches;
   }
   rc = record_event(c);
   if (rc) return rc;
-  CUDA_TRY(c, launch_overlap(env, c->d_oloops, n, c->d_ovdat, op->ndats, op->d_tab + op->own_off,
-                             op->d_tab + op->box_off, op->d_tab + op->foot_off, op->ntiles, grid, op->area_bytes));
+  if (jo)
+    CUDA_TRY(c, jit_launch_overlap(jo, env, c->d_oloops, c->d_ovdat, op->d_tab + op->own_off, op->d_tab + op->box_off,
+                                   op->d_tab + op->foot_off, op->ntiles, grid, op->area_bytes));
+  else
+    CUDA_TRY(c, launch_overlap(env, c->d_oloops, n, c->d_ovdat, op->ndats, op->d_tab + op->own_off,
+                               op->d_tab + op->box_off, op->d_tab + op->foot_off, op->ntiles, grid, op->area_bytes));
   rc = record_event(c);
   if (rc) return rc;
   ++c->stats.launches;
@@ -839,18 +865,36 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
   if (mode == OPS_MODE_OVERLAPPED) {
     // consecutive overlapped runs; what no run covers goes to the skewed path
     const int dl_first = first;
+    std::vector<std::pair<int, OverlapPlan*>> runs;
+    std::vector<std::vector<DLoop>> ols;
     while (count > 0) {
       OverlapPlan* op = nullptr;
       int used = 0;
       int rc = overlap_prefix(c, first, count, tile_in, &op, &used);
       if (rc) return rc;
       if (!used) break;
-      c->stats.mode = mode;
-      rc = run_overlap_plan(c, first, hl, op);
-      if (rc) return rc;
+      runs.emplace_back(first, op);
+      ols.push_back(overlap_descriptors(c, first, hl, op));
       first += used;
       dl_base += used;
       count -= used;
+    }
+    // compiled kernels of every run (compiled together, in parallel), else the interpreter's
+    std::vector<JitOverlap*> jos(runs.size(), nullptr);
+    if (!runs.empty() && !c->cfg.interpret && !c->cfg.check) {
+      std::vector<OvRequest> reqs;
+      for (size_t r = 0; r < runs.size(); ++r)
+        reqs.push_back(OvRequest{ols[r].data(), runs[r].second->nloops, overlap_layout(runs[r].second)});
+      std::string why;
+      double ms = 0.0;
+      int rc = jit_overlap_many(c->cfg.device, reqs, &jos, &why, &ms);
+      c->stats.compile_ms += ms;
+      if (rc) return fail(c, rc, "compiling overlapped tiles: %s", why.c_str());
+    }
+    for (size_t r = 0; r < runs.size(); ++r) {
+      c->stats.mode = mode;
+      int rc = run_overlap_plan(c, runs[r].first, hl, runs[r].second, ols[r], jos[r]);
+      if (rc) return rc;
     }
     if (count == 0) return OPS_OK;
     if (first != dl_first) {
@@ -1602,7 +1646,33 @@ int ops_compile_queued(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, 
   }
   std::string src, why;
   double ms = 0.0;
-  const int rc = jit_compile_only(hl.data(), n, ro, &src, &why, &ms);
+  int rc = jit_compile_only(hl.data(), n, ro, &src, &why, &ms);
+  if (!rc) {
+    // the overlapped-tile form of the same loops, with each dat's own strides as its footprint strides
+    std::map<int, int> local;
+    OvLayout lay;
+    std::vector<DLoop> ol(hl);
+    for (int i = 0; i < n; ++i) {
+      const QLoop& q = c->queue[i];
+      for (size_t a = 0; a < q.args.size(); ++a) {
+        if (q.args[a].kind != OPS_ARG_DAT) continue;
+        auto it = local.find(q.args[a].handle);
+        if (it == local.end()) {
+          const Dat& D = c->dats[q.args[a].handle];
+          it = local.emplace(q.args[a].handle, lay.ndats++).first;
+          lay.smem_off.push_back(0);
+          lay.spitch.push_back((int)D.pitch);
+          lay.splane.push_back((int)D.plane);
+          lay.written.push_back(0);
+        }
+        ol[i].args[a].slot = it->second;
+        if (q.args[a].access != OPS_READ) lay.written[it->second] = 1;
+      }
+    }
+    std::string osrc;
+    rc = jit_compile_overlap_only(ol.data(), n, lay, &osrc, &why, &ms);
+    src += osrc;
+  }
   if (src_len) *src_len = (int64_t)src.size();
   if (src_out && cap > 0) {
     const size_t k = std::min<size_t>(src.size(), (size_t)cap - 1);
