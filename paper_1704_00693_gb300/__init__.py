@@ -33,6 +33,9 @@ OPS_ARG_DAT, OPS_ARG_SCALAR, OPS_ARG_RED = 0, 1, 2
 OPS_READ, OPS_WRITE, OPS_RW, OPS_INC = 0, 1, 2, 3
 OPS_RED_SUM, OPS_RED_MIN, OPS_RED_MAX = 0, 1, 2
 OPS_DEVICE_NONE = -1
+# loop-body IR opcodes (include/opstile.h)
+(OPS_IR_LD, OPS_IR_CST, OPS_IR_ADD, OPS_IR_SUB, OPS_IR_MUL, OPS_IR_FMA, OPS_IR_DIV, OPS_IR_MIN, OPS_IR_MAX,
+ OPS_IR_SGT, OPS_IR_WSUM, OPS_IR_WACC, OPS_IR_POLY, OPS_IR_ST, OPS_IR_RED) = range(1, 16)
 
 MODES = {"untiled": OPS_MODE_UNTILED, "skewed": OPS_MODE_SKEWED, "overlapped": OPS_MODE_OVERLAPPED,
          "auto": OPS_MODE_AUTO}

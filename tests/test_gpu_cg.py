@@ -104,3 +104,27 @@ def test_full_size_mixed_solve():
         ops.ops_finalize(c)
     assert st["converged"] == 1
     assert oracle.relres(kappa, b, x) <= 1e-10
+
+
+@pytest.mark.parametrize("n", [1, 33, 128])
+def test_chain_cg_matches_oracle(n):
+    """CG written as a loop chain (setup loops for the faces and diagonal,
+    three loops per iteration, host-read reductions) converges like the
+    oracle's FP64 CG, and its operator is the engine's bit for bit (one
+    iteration from x = 0 gives w = A b)."""
+    from paper_1704_00693_gb300.cgchain import ChainCG
+    kappa, b = W.cg_problem(n, 1e-2, 1e2)
+    x_ref, it_ref, _ = oracle.cg64(kappa, b, tol=1e-10)
+    for mode in ("untiled", "skewed"):
+        cg = ChainCG(n, mode=mode)
+        try:
+            x, it, rel = cg.solve(kappa, b, 1e-10)
+            assert rel <= 1e-10
+            assert abs(it - it_ref) <= max(2, it_ref // 50)
+            assert oracle.relres(kappa, b, x) <= 1.5e-10
+            assert np.abs(x - x_ref).max() <= 1e-8 * np.abs(x_ref).max()
+            cg.solve(kappa, b, 1e-10, maxit=1)
+            w = ops.ops_dat_fetch(cg.ctx, cg.d["w"]).reshape(n + 2, n + 2)[1:n + 1, 1:n + 1]
+            assert np.array_equal(w, oracle.matvec(kappa, b))
+        finally:
+            cg.close()
