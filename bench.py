@@ -62,6 +62,23 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(ms: float, device: str = "cuda") -> float:
+    """The slowest rank's time (every rank gets it); ranks are independent
+    replicas, so this is the only collective of the benchmark."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(untiled_bytes: float, steps: int, world: int, ms: float) -> float:
+    """Whole-job effective GB/s: every rank runs the same chain (weak scaling)."""
+    return untiled_bytes * steps * world / (ms * 1e-3) / 1e9
+
+
 # --------------------------------------------------------------------------
 # clocks during the timed region
 # --------------------------------------------------------------------------
@@ -406,6 +423,18 @@ def bench_cg(n=4000, tol=1e-10):
                          "ms_per_iteration": dt * 1e3 / max(1, st["iterations"])}
     finally:
         ops.ops_finalize(ctx)
+    # the same solve as a loop chain (three loops per iteration, host-read reductions)
+    from paper_1704_00693_gb300.cgchain import ChainCG
+    cg = ChainCG(n, mode="untiled")
+    try:
+        cg.solve(kappa, b, tol, maxit=2)  # compiled code and plans
+        t0 = time.perf_counter()
+        x, it, rel = cg.solve(kappa, b, tol)
+        dt = time.perf_counter() - t0
+        out["fp64_loop_chain_untiled"] = {"seconds": dt, "iterations": it, "relres": rel,
+                                          "ms_per_iteration": dt * 1e3 / max(1, it)}
+    finally:
+        cg.close()
     best = min((k for k in out if k.startswith("mixed")), key=lambda k: out[k]["seconds"])
     out["best_mixed"] = best
     out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out[best]["seconds"]
@@ -474,7 +503,7 @@ def run_reference(args):
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     v = U * args.steps / t / 1e9
     line = {"metric": "loop-chain effective GB/s", "value": v, "unit": "GB/s", "impl": "reference",
-            "n_gpus": 0, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "sample": f"each step: the chain at {n}^2 (1/4 of the points)"},
             "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
@@ -517,12 +546,8 @@ def main():
     with ClockSampler(local) as clk:
         ms, kms, kl, launches, st = time_mode(chain, args.mode, tile, args.steps, args.warmup, stream, torch)
     barrier()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = U * args.steps * world / (ms * 1e-3) / 1e9
+    ms = max_over_ranks(ms)
+    value = whole_job_gbs(U, args.steps, world, ms)
 
     untiled = None
     if not args.no_untiled and args.mode != "untiled":
