@@ -53,7 +53,7 @@ def parse():
     p.add_argument("--no-untiled", action="store_true")
     p.add_argument("--no-serve", action="store_true", help="skip the served-solves measurement")
     p.add_argument("--no-cg", action="store_true", help="skip the 4000^2 CG measurement")
-    p.add_argument("--no-3d", action="store_true", help="skip the 320^3 OpenSBLI-shaped chain")
+    p.add_argument("--no-3d", action="store_true", help="skip the other chains (OpenSBLI 3D, CloverLeaf 3D, PPCG)")
     p.add_argument("--serve-requests", type=int, default=512)
     return p.parse_args()
 
@@ -441,11 +441,9 @@ def bench_cg(n=4000, tol=1e-10):
     return out
 
 
-def bench_opensbli3d(stream, torch, n=320, steps=5):
-    """The OpenSBLI-shaped 3D chain (320^3, 15 dats, 40 loops per step):
-    autotuned schedule against the untiled form, effective GB/s of each."""
-    from synth import workloads as W
-    chain = W.opensbli3d(n=n, steps=1)
+def bench_chain(chain, stream, torch, steps=5):
+    """Autotuned schedule against the untiled form on one chain, effective GB/s of each."""
+    n = chain.size[0]
     U, flops = workload_numbers(chain)
     out = {"n": n, "untiled_bytes_per_step": U, "flops_per_step": flops}
     for mode in ("auto", "untiled"):
@@ -456,6 +454,36 @@ def bench_opensbli3d(stream, torch, n=320, steps=5):
                      "tile": st["tile"], "compiled": st["compiled"]}
     out["speedup_auto_vs_untiled"] = out["untiled"]["ms_per_step"] / out["auto"]["ms_per_step"]
     return out
+
+
+def bench_opensbli3d(stream, torch, n=320, steps=5):
+    """The OpenSBLI-shaped 3D chain (320^3, 15 dats, 40 loops per step)."""
+    from synth import workloads as W
+    return bench_chain(W.opensbli3d(n=n, steps=1), stream, torch, steps)
+
+
+def bench_ppcg(stream, torch, n=4000, inner=10, steps=5):
+    """The TeaLeaf-PPCG-shaped chain (one preconditioner application: 7
+    setup loops, 10 Chebyshev iterations of three loops, z.r): every
+    schedule, effective GB/s of each."""
+    from synth import workloads as W
+    chain = W.ppcg2d(n=n, inner=inner)
+    U, flops = workload_numbers(chain)
+    out = {"n": n, "inner": inner, "untiled_bytes_per_step": U, "flops_per_step": flops}
+    for mode in ("untiled", "skewed", "overlapped", "auto"):
+        ms, kms, kl, launches, st = time_mode(chain, mode, None, steps, 3, stream, torch)
+        out[mode] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
+                     "schedule": {0: "untiled", 1: "skewed", 2: "overlapped"}.get(st["mode"]),
+                     "tile": st["tile"], "tiles": st["tiles"]}
+    for mode in ("skewed", "overlapped", "auto"):
+        out[f"speedup_{mode}_vs_untiled"] = out["untiled"]["ms_per_step"] / out[mode]["ms_per_step"]
+    return out
+
+
+def bench_cloverleaf3d(stream, torch, n=330, steps=3):
+    """The CloverLeaf-3D-shaped chain (330^3 as in the paper, 30 dats, 141 loops per step)."""
+    from synth import workloads as W
+    return bench_chain(W.cloverleaf3d(n=n, steps=1), stream, torch, steps)
 
 
 def cpu_baseline(n_full, seconds=12.0):
@@ -603,6 +631,8 @@ def main():
         cpu = cpu_baseline(args.n)
     cg = bench_cg() if rank == 0 and not args.no_cg else None
     chain3d = bench_opensbli3d(stream, torch) if rank == 0 and not args.no_3d else None
+    hydro3d = bench_cloverleaf3d(stream, torch) if rank == 0 and not args.no_3d else None
+    ppcg = bench_ppcg(stream, torch) if rank == 0 and not args.no_3d else None
     serving = bench_serving(args.serve_requests) if rank == 0 and not args.no_serve else None
 
     line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
@@ -616,7 +646,7 @@ def main():
             "speedup_vs_untiled": (untiled["ms_per_step"] / (ms / args.steps)) if untiled else None,
             "untiled": untiled, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
-            "cg_4000": cg, "serving": serving, "opensbli3d_320": chain3d,
+            "cg_4000": cg, "serving": serving, "opensbli3d_320": chain3d, "cloverleaf3d_330": hydro3d, "ppcg_4000": ppcg,
             "plan": {"phases": st["phases"], "barriers": st["barriers"], "skew": st["skew"],
                      "plan_cache_hits": st["plan_cache_hits"]} if st else None}
     if rank == 0:

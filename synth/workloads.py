@@ -199,22 +199,54 @@ def cloverleaf2d(n: int = 3840, steps: int = 20, seed: int = None, nloops: int =
     after the step, scales two loops of the next step (the time step).
     """
     seed = R.subseed(R.BASE_SEED, "cloverleaf2d") if seed is None else seed
+    return _hydro_chain(2, n, steps, seed, nloops, ndats, nstatic, {3, 45})
+
+
+S7 = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1)]
+S27 = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)]
+S8P = [(0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0), (0, 0, 1), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+S8M = [(-x, -y, -z) for x, y, z in S8P]
+
+
+def cloverleaf3d(n: int = 330, steps: int = 10, seed: int = None, nloops: int = 141,
+                 ndats: int = 30, nstatic: int = 5) -> Chain:
+    """A CloverLeaf-3D-shaped step (the paper's 3D hydro code has 141
+    distinct loops): 30 dats U(0.5, 1.5), 141 loops built like the 2D step
+    with the 3D stencils (point, 7-point, 27-point, the one-sided 8-point
+    node stencil {0,1}^3 and its mirror), cell, node ([0, n+1)^3) and
+    halo-plane ranges, a sum reduction mid-step and a min reduction (the
+    time step) at the end."""
+    seed = R.subseed(R.BASE_SEED, "cloverleaf3d") if seed is None else seed
+    return _hydro_chain(3, n, steps, seed, nloops, ndats, nstatic, {3, 45, 90})
+
+
+def _hydro_chain(ndim, n, steps, seed, nloops, ndats, nstatic, dt_users) -> Chain:
     rnd = random.Random(seed)
     h = 2
-    size, d_m, d_p = (n, n, 1), (h, h, 0), (h, h, 0)
+    if ndim == 2:
+        size, d_m, d_p = (n, n, 1), (h, h, 0), (h, h, 0)
+        st = [P0, S5, S9, S4P, S4M]
+        stname = {0: "P", 1: "S5", 2: "S9", 3: "S4P", 4: "S4M"}
+        cell = ((0, n), (0, n))
+        node = ((0, n + 1), (0, n + 1))
+        strips = [((0, n), (-2, 0)), ((0, n), (n, n + 2)), ((-2, 0), (0, n)), ((n, n + 2), (0, n))]
+    else:
+        size, d_m, d_p = (n, n, n), (h, h, h), (h, h, h)
+        st = [P0, S7, S27, S8P, S8M]
+        stname = {0: "P", 1: "S7", 2: "S27", 3: "S8P", 4: "S8M"}
+        cell = ((0, n), (0, n), (0, n))
+        node = ((0, n + 1), (0, n + 1), (0, n + 1))
+        strips = []
+        for d in range(3):
+            for lo, hi in ((-2, 0), (n, n + 2)):
+                strips.append(tuple((lo, hi) if e == d else (0, n) for e in range(3)))
     shp = _alloc_shape(size, d_m, d_p)
     dats = [DatSpec(f"d{k:02d}", R.uniform(R.subseed(seed, "dat", k), shp, 0.5, 1.5))
             for k in range(ndats)]
-    st = [P0, S5, S9, S4P, S4M]
-    stname = {0: "P", 1: "S5", 2: "S9", 3: "S4P", 4: "S4M"}
     evolving = list(range(nstatic, ndats))
     recent: List[int] = []
     loops: List[Loop] = []
-    cell = ((0, n), (0, n))
-    node = ((0, n + 1), (0, n + 1))
-    strips = [((0, n), (-2, 0)), ((0, n), (n, n + 2)), ((-2, 0), (0, n)), ((n, n + 2), (0, n))]
     sum_at = nloops // 2
-    dt_users = {3, 45}
 
     def pick_reads(count, exclude):
         pool = [k for k in range(ndats) if k not in exclude]
@@ -347,7 +379,7 @@ def cloverleaf2d(n: int = 3840, steps: int = 20, seed: int = None, nloops: int =
         lp.stencil_names = [stname.get(a.stencil, "-") for a in args]
         loops.append(lp)
         recent.extend(writes)
-    return Chain(f"cloverleaf2d_{n}", 2, size, d_m, d_p, dats, st, [RSUM, RMIN], loops,
+    return Chain(f"cloverleaf{ndim}d_{n}", ndim, size, d_m, d_p, dats, st, [RSUM, RMIN], loops,
                  steps=steps, dt_red=1)
 
 
@@ -426,6 +458,101 @@ def opensbli3d(n: int = 320, steps: int = 10, seed: int = None) -> Chain:
             loops.append(Loop(f"rk{s}q{k}", cells, [Arg(DAT, Q[k], 0, RW), Arg(DAT, QS[k], 0, READ),
                                                     Arg(DAT, RES, 0, READ)], c, kk))
     return Chain(f"opensbli3d_{n}", 3, size, d_m, d_p, dats, st, [], loops, steps=steps)
+
+
+# --------------------------------------------------------------------------
+# TeaLeaf-PPCG-shaped chain: the polynomial preconditioner's inner loops
+# --------------------------------------------------------------------------
+def ppcg2d(n: int = 4000, inner: int = 10, steps: int = 1, seed: int = None, kappa_const: float = None,
+           r_mode: Tuple[int, int] = None) -> Chain:
+    """A TeaLeaf-PPCG-shaped chain (Sec. 6.D): one application of a Chebyshev
+    polynomial preconditioner to a residual r on the 5-point heat operator.
+    Setup loops build the negated face coefficients and the diagonal from a
+    conductivity log-uniform in [0.1, 10] (harmonic means inside, the cell's
+    own at the boundary; d = 1 + sum of the faces); then sd = r / theta,
+    rt = r, z = sd, and `inner` iterations of
+        w = A sd;   rt = rt - w;   sd = alpha_k sd + beta_k rt, z = z + sd
+    with the Chebyshev coefficients for the spectrum bound [1, 81]; a last
+    loop reduces z.r for the outer CG.  No loop before it reduces, so the
+    whole application is one segment.  kappa_const and r_mode = (p, q) (the
+    Dirichlet eigenmode sin(pi p (i+1)/(n+1)) sin(pi q (j+1)/(n+1))) give a
+    case with a closed form."""
+    seed = R.subseed(R.BASE_SEED, "ppcg2d", n) if seed is None else seed
+    h = 1
+    size, d_m, d_p = (n, n, 1), (h, h, 0), (h, h, 0)
+    shp = _alloc_shape(size, d_m, d_p)
+    if kappa_const is None:
+        u = R.uniform(R.subseed(seed, "kappa"), shp, 0.0, 1.0)
+        kappa = _zero_halo(np.exp(np.log(0.1) + (np.log(10.0) - np.log(0.1)) * u), size, d_m)
+    else:
+        kappa = _zero_halo(np.full(shp, float(kappa_const)), size, d_m)
+    if r_mode is None:
+        r = _zero_halo(R.uniform(R.subseed(seed, "r"), shp, 0.0, 1.0), size, d_m)
+    else:
+        p, q = r_mode
+        i = np.arange(n)
+        sx = np.array([math.sin(math.pi * p * (k + 1) / (n + 1)) for k in i])
+        sy = np.array([math.sin(math.pi * q * (k + 1) / (n + 1)) for k in i])
+        r = np.zeros(shp)
+        r[0, h:n + h, h:n + h] = np.outer(sy, sx)
+    names = ["kappa", "r", "rt", "sd", "w", "z", "nkx", "nky", "dg"]
+    init = {"kappa": kappa, "r": r}
+    dats = [DatSpec(nm, init.get(nm, np.zeros(shp))) for nm in names]
+    K, Rr, RT, SD, Wd, Z, NKX, NKY, DG = range(len(names))
+    st = [P0, S5, [(0, 0, 0), (1, 0, 0)], [(0, 0, 0), (0, 1, 0)], [(0, 0, 0), (-1, 0, 0)], [(0, 0, 0), (0, -1, 0)]]
+    SP, SS5, SEX, SEY, SWX, SSY = range(len(st))
+    cells = ((0, n), (0, n))
+    loops: List[Loop] = []
+
+    def face_loops(dat, sten, interior, west, east):
+        bb = BodyBuilder().ld(0, 0, 1).ld(1, 0, 0).cst(2, 2.0).emit(MUL, 3, 2, 0).emit(MUL, 3, 3, 1)
+        bb.emit(ADD, 4, 0, 1).emit(7, 5, 3, 4).cst(6, 0.0).emit(SUB, 7, 6, 5).st(1, 7)
+        c, k = bb.build()
+        args = [Arg(DAT, K, sten, READ), Arg(DAT, dat, SP, WRITE)]
+        loops.append(Loop(f"face_in{dat}", interior, args, c, k))
+        c, k = BodyBuilder().ld(0, 0, 0).cst(6, 0.0).emit(SUB, 7, 6, 0).st(1, 7).build()
+        loops.append(Loop(f"face_lo{dat}", west, args, c, k))
+        c, k = BodyBuilder().ld(0, 0, 1).cst(6, 0.0).emit(SUB, 7, 6, 0).st(1, 7).build()
+        loops.append(Loop(f"face_hi{dat}", east, args, c, k))
+
+    face_loops(NKX, SWX, ((1, n), (0, n)), ((0, 1), (0, n)), ((n, n + 1), (0, n)))
+    face_loops(NKY, SSY, ((0, n), (1, n)), ((0, n), (0, 1)), ((0, n), (n, n + 1)))
+    bb = BodyBuilder().cst(0, 1.0)
+    for a, pt in ((0, 0), (0, 1), (1, 0), (1, 1)):
+        bb.ld(1, a, pt).emit(SUB, 0, 0, 1)
+    c, k = bb.st(2, 0).build()
+    loops.append(Loop("diag", cells, [Arg(DAT, NKX, SEX, READ), Arg(DAT, NKY, SEY, READ), Arg(DAT, DG, SP, WRITE)],
+                      c, k))
+    lmin, lmax = 1.0, 81.0
+    theta, delta = (lmax + lmin) / 2, (lmax - lmin) / 2
+    c, k = BodyBuilder().ld(0, 0, 0).cst(1, 1.0 / theta).emit(MUL, 2, 0, 1).st(1, 2).st(2, 0).st(3, 2).build()
+    loops.append(Loop("init", cells, [Arg(DAT, Rr, SP, READ), Arg(DAT, SD, SP, WRITE), Arg(DAT, RT, SP, WRITE),
+                                      Arg(DAT, Z, SP, WRITE)], c, k))
+    sigma = theta / delta
+    rho_old = 1.0 / sigma
+    for it in range(inner):
+        # w = A sd, the engine's term order
+        bb = BodyBuilder().ld(0, 1, 0).ld(1, 0, 0).emit(MUL, 2, 0, 1)
+        for a, pa, pp in ((2, 0, 1), (2, 1, 2), (3, 0, 3), (3, 1, 4)):
+            bb.ld(0, a, pa).ld(1, 0, pp).emit(FMA, 2, 0, 1, 2)
+        c, k = bb.st(4, 2).build()
+        loops.append(Loop(f"matvec{it}", cells, [Arg(DAT, SD, SS5, READ), Arg(DAT, DG, SP, READ),
+                                                   Arg(DAT, NKX, SEX, READ), Arg(DAT, NKY, SEY, READ),
+                                                   Arg(DAT, Wd, SP, WRITE)], c, k))
+        c, k = BodyBuilder().ld(0, 0, 0).ld(1, 1, 0).emit(SUB, 2, 0, 1).st(0, 2).build()
+        loops.append(Loop(f"resid{it}", cells, [Arg(DAT, RT, SP, RW), Arg(DAT, Wd, SP, READ)], c, k))
+        rho = 1.0 / (2.0 * sigma - rho_old)
+        alpha, beta = rho * rho_old, 2.0 * rho / delta
+        rho_old = rho
+        bb = BodyBuilder().cst(0, alpha).ld(1, 0, 0).emit(MUL, 2, 0, 1).cst(3, beta).ld(4, 1, 0)
+        bb.emit(FMA, 2, 3, 4, 2).st(0, 2).ld(5, 2, 0).emit(ADD, 5, 5, 2).st(2, 5)
+        c, k = bb.build()
+        loops.append(Loop(f"cheby{it}", cells, [Arg(DAT, SD, SP, RW), Arg(DAT, RT, SP, READ), Arg(DAT, Z, SP, RW)],
+                          c, k))
+    c, k = BodyBuilder().ld(0, 0, 0).ld(1, 1, 0).emit(MUL, 2, 0, 1).red(2, 2).build()
+    loops.append(Loop("zr", cells, [Arg(DAT, Z, SP, READ), Arg(DAT, Rr, SP, READ), Arg(REDARG, 0, -1, READ)], c, k))
+    return Chain(f"ppcg2d_{n}", 2, size, d_m, d_p, dats, st, [RSUM], loops, steps=steps,
+                 meta=dict(inner=inner, theta=theta, delta=delta))
 
 
 # --------------------------------------------------------------------------

@@ -211,7 +211,7 @@ def test_library_overlapped_tiles_match_oracle(lib, ndim):
                     assert all(foot[k, d, 1] < foot[k, d, 0] for d in range(ndim)), f"tile {owned} dat {k} unread"
 
 
-@pytest.mark.parametrize("name", ["small2d", "cloverleaf2d", "opensbli3d", "edge"])
+@pytest.mark.parametrize("name", ["small2d", "cloverleaf2d", "cloverleaf3d", "opensbli3d", "edge"])
 def test_generated_loop_bodies_compile(lib, name):
     """The CUDA generated from each workload's IR compiles for sm_103a
     (NVRTC, no device needed), and every loop gets its kernel."""
@@ -223,6 +223,8 @@ def test_generated_loop_bodies_compile(lib, name):
         c = W.small2d(n=40, reps=1)
     elif name == "cloverleaf2d":
         c = W.cloverleaf2d(n=40, steps=1)
+    elif name == "cloverleaf3d":
+        c = W.cloverleaf3d(n=12, steps=1)
     else:
         c = W.opensbli3d(n=12, steps=1)
     ctx = host_ctx()

@@ -101,6 +101,28 @@ def test_cloverleaf_shaped_chain(mode, tile, interpret):
         assert st["compiled"] == (0 if interpret else 1)
 
 
+@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 0, 0)), ("skewed", (0, 9, 7)),
+                                       ("overlapped", None), ("auto", None)])
+def test_cloverleaf3d_shaped_chain(mode, tile):
+    """141-loop CloverLeaf-3D-shaped steps on 40^3 (7-, 27- and one-sided
+    8-point stencils, node ranges, halo planes, two reductions per step)."""
+    c = W.cloverleaf3d(n=40, steps=2)
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist, st = run_gpu(c, mode, tile)
+    assert_same(c, got, ref, hist, ref_hist, what=f"3d hydro {mode} {tile}")
+
+
+@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 0, 0)), ("skewed", (0, 16, 0)),
+                                       ("overlapped", None), ("overlapped", (64, 16, 0)), ("auto", None)])
+def test_ppcg_shaped_chain(mode, tile):
+    """The TeaLeaf-PPCG-shaped chain: setup loops, then 10 Chebyshev inner
+    iterations (three loops each, no reduction) in one segment, and z.r."""
+    c = W.ppcg2d(n=100, inner=10, steps=2)
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist, st = run_gpu(c, mode, tile)
+    assert_same(c, got, ref, hist, ref_hist, what=f"ppcg {mode} {tile}")
+
+
 def test_jacobi_eigenmode_closed_form_on_gpu():
     n, K, nu = 63, 30, 0.125
     c = W.jacobi2d(n, K, nu=nu, p=2, q=1)

@@ -190,3 +190,31 @@ def test_overlapped_plan_bruteforce(ndim):
         for lows in itertools.product(*cuts):
             tiles.append(tuple((lo, min(lo + ts[d], n[d] + 2)) for d, lo in enumerate(lows)))
         check_overlapped(loops, st, ndim, tiles, oplan.overlapped_plan)
+
+
+def test_ppcg_chain_eigenmode_closed_form():
+    """The TeaLeaf-PPCG-shaped chain with constant conductivity k applied to
+    the Dirichlet eigenmode v of I + k L (eigenvalue lam = 1 + k (4 sin^2 +
+    4 sin^2)) keeps every vector a multiple of v: sd_0 = v / theta, rt = v,
+    z = sd, then rt -= lam sd, sd = alpha sd + beta rt, z += sd.  The oracle's
+    z must be that scalar recurrence times v, and z.r its sum."""
+    n, kap, p, q, inner = 24, 0.7, 3, 2, 8
+    c = W.ppcg2d(n=n, inner=inner, kappa_const=kap, r_mode=(p, q))
+    ref, hist = oracle.run_chain(c)
+    lam = 1 + kap * (4 * math.sin(math.pi * p / (2 * (n + 1))) ** 2 + 4 * math.sin(math.pi * q / (2 * (n + 1))) ** 2)
+    theta, delta = c.meta["theta"], c.meta["delta"]
+    sigma = theta / delta
+    sd, rt = 1.0 / theta, 1.0
+    z = sd
+    rho_old = 1.0 / sigma
+    for _ in range(inner):
+        rt = rt - lam * sd
+        rho = 1.0 / (2 * sigma - rho_old)
+        alpha, beta = rho * rho_old, 2 * rho / delta
+        rho_old = rho
+        sd = alpha * sd + beta * rt
+        z = z + sd
+    v = c.dats[1].init
+    zz = ref[5]
+    assert np.abs(zz - z * v).max() <= 1e-13 * np.abs(v).max()
+    assert abs(hist[0][0] - z * float((v * v).sum())) <= 1e-12 * abs(z * float((v * v).sum()))
