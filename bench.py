@@ -505,9 +505,19 @@ def cpu_baseline(n_full, seconds=12.0):
             break
     t = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": U * nsteps / t / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
-            "sample": f"{nsteps} step(s) of the same chain at {n}^2 (1/4 of the points), untiled FP64 oracle",
-            "seconds": t}
+    out = {"value": U * nsteps / t / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+           "sample": f"{nsteps} step(s) of the same chain at {n}^2 (1/4 of the points), untiled FP64 oracle",
+           "seconds": t}
+    # context: the paper's CPU scheme (Algorithms 1-2, OpenMP inside each tile) on the same cores,
+    # tiles of whole rows sized so a tile's 25 dats fill about 32 MB
+    rows = max(8, (32 << 20) // (8 * 25 * (n + 4)))
+    tchain = W.cloverleaf2d(n=n, steps=nsteps)
+    t0 = time.perf_counter()
+    oracle.run_chain_tiled(tchain, (n + 4, rows))
+    tt = time.perf_counter() - t0
+    out["skewed_tiled_cpu"] = {"value": U * nsteps / tt / 1e9, "unit": "GB/s", "tile": [n + 4, rows],
+                               "speedup_vs_untiled_cpu": t / tt}
+    return out
 
 
 def run_reference(args):

@@ -157,6 +157,48 @@ def run_chain(chain, steps: Optional[int] = None, nthreads: int = 0):
     return dats, hist
 
 
+def run_chain_tiled(chain, tile: Sequence[int], steps: Optional[int] = None, nthreads: int = 0):
+    """The paper's CPU execution of the same steps: each step's loops get
+    Algorithm 1's skewed ranges (oracle.plan.skewed_plan) for the tile sizes
+    `tile`, then run as Algorithm 2 does, tile by tile in lexicographic
+    order (x fastest) and loop by loop within a tile, with the rows of each
+    (tile, loop) box spread over the host cores.  Every point is evaluated
+    as in run_chain and reductions are exact, so the results are identical."""
+    from . import plan as oplan
+    import itertools
+    dats = [np.ascontiguousarray(d.init.copy()) for d in chain.dats]
+    nsteps = chain.steps if steps is None else steps
+    nd = chain.ndim
+    dt = 1.0
+    hist = []
+    for s in range(nsteps):
+        loops = [_with_consts(lp, lp.consts_for(dt)) for lp in chain.loops]
+        ntiles, ranges, _ = oplan.skewed_plan(loops, chain.stencils, nd, list(tile)[:nd])
+        phases = []
+        for rev in itertools.product(*[range(ntiles[d]) for d in reversed(range(nd))]):
+            t = tuple(reversed(rev))
+            for l, lp in enumerate(loops):
+                box = [ranges[d][t[d]][l] for d in range(nd)]
+                if all(hi > lo for lo, hi in box):
+                    phases.append(_BoxView(lp, box))
+        vals = run_loops(chain, dats, phases, [red_identity(op) for op in chain.reductions], nthreads)
+        hist.append(vals)
+        if chain.dt_red >= 0:
+            dt = vals[chain.dt_red]
+    return dats, hist
+
+
+class _BoxView:
+    """A loop restricted to one (tile, loop) box."""
+
+    def __init__(self, lp, box):
+        self._lp = lp
+        self.rng = tuple(box)
+
+    def __getattr__(self, k):
+        return getattr(self._lp, k)
+
+
 class _LoopView:
     def __init__(self, lp, consts):
         self._lp = lp

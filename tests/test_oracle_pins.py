@@ -218,3 +218,20 @@ def test_ppcg_chain_eigenmode_closed_form():
     zz = ref[5]
     assert np.abs(zz - z * v).max() <= 1e-13 * np.abs(v).max()
     assert abs(hist[0][0] - z * float((v * v).sum())) <= 1e-12 * abs(z * float((v * v).sum()))
+
+
+@pytest.mark.parametrize("name,tile", [("cloverleaf2d", (64, 9)), ("cloverleaf2d", (17, 64)), ("small2d", (40, 7)),
+                                       ("opensbli3d", (12, 5, 4)), ("ppcg2d", (50, 6))])
+def test_tiled_execution_equals_program_order(name, tile):
+    """Algorithm 1's ranges executed as Algorithm 2 does (tile by tile, loops
+    in order within a tile) give the program-order result bit for bit and
+    the same exact reductions: the oracle's plan and executor agree with the
+    definition of the method on whole workloads, not only on the brute-force
+    grids."""
+    c = {"cloverleaf2d": lambda: W.cloverleaf2d(n=48, steps=2), "small2d": lambda: W.small2d(n=60, reps=3),
+         "opensbli3d": lambda: W.opensbli3d(n=14, steps=1), "ppcg2d": lambda: W.ppcg2d(n=50, inner=4)}[name]()
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist = oracle.run_chain_tiled(c, tile)
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    assert hist == ref_hist
