@@ -1,9 +1,9 @@
 // Run-time compiled loop bodies (see jit.h).
 //
 // Code shape.  For loop i of a segment the generator emits body<i>, which
-// enumerates its CTA's share of a box exactly as the interpreter does (units
-// of 256 consecutive x by 4 consecutive rows for rows of >= 128 points,
-// flattened groups otherwise) and evaluates the loop's IR per point with the
+// enumerates its CTA's share of a box as the interpreter does (units of 256
+// consecutive x by 4 consecutive rows for rows of >= 128 points, flattened
+// groups otherwise) and evaluates the loop's IR per point with the
 // same explicitly rounded operations in the same order, so every stored
 // value is bit-identical to the interpreter's and the oracle's.  A unit of 4
 // full rows is evaluated instruction by instruction across its 4 points (the
@@ -55,6 +55,12 @@ int env_int(const char* name, int def, int lo, int hi) {
 }
 const int kJitPts = env_int("OPSTILE_JIT_PTS", 4, 1, 8);
 const int kJitMinCtas = env_int("OPSTILE_JIT_MINB", 2, 1, 8);
+// Overlapped tiles: one CTA per SM holds the footprints, so it takes twice
+// the threads of the untiled kernels; one point per thread at a time keeps
+// the bodies within the 128 registers that 512 threads leave (1024 threads
+// would spill them).
+constexpr int kOvThreads = 512;
+constexpr int kOvPts = 1;
 constexpr int kJitChunk = 6;  // loops per compiled module (modules compile in parallel)
 
 // ---------------------------------------------------------------------------
@@ -212,24 +218,24 @@ __device__ __forceinline__ void flush_red(int op, DD v, DD* part, int stride, in
   __syncthreads();
 }
 
-// A CTA's share of a box: rows of >= 128 points in units of 256 x by P rows
+// A CTA's share of a box: rows of >= 128 points in units of NT x by P rows
 // (u = part, part + nparts, ...), thinner boxes in flattened groups of P
-// points 256 apart.  full(x, y, z) takes rows y .. y+P-1 at x; one(x, y, z)
-// a single point.
-template <int P, class F1, class FP>
+// points NT apart (NT = threads per CTA).  full(x, y, z) takes rows
+// y .. y+P-1 at x; one(x, y, z) a single point.
+template <int P, int NT, class F1, class FP>
 __device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0, int z1, int part, int nparts,
                                           F1& one, FP& full) {
   const int nx = x1 - x0, ny = y1 - y0, nz = z1 - z0;
   if (nx <= 0 || ny <= 0 || nz <= 0) return;
   if (nx >= 128) {
-    const int xch = (nx + 255) / 256;
+    const int xch = (nx + NT - 1) / NT;
     const int nrg = (ny + P - 1) / P;
     const int nunits = xch * nrg * nz;
     int u = part;
     int xc = u % xch, rg = (u / xch) % nrg, z = u / (xch * nrg);
     const int dxc = nparts % xch, drg = (nparts / xch) % nrg, dz = nparts / (xch * nrg);
     while (u < nunits) {
-      const int x = x0 + xc * 256 + (int)threadIdx.x;
+      const int x = x0 + xc * NT + (int)threadIdx.x;
       if (x < x1) {
         const int yb = rg * P;
         if (yb + P <= ny) {
@@ -244,10 +250,10 @@ __device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0
     }
   } else {
     const int npts = nx * ny * nz;
-    const int step = nparts * 256 * P;
-    for (int i = part * 256 * P + (int)threadIdx.x; i < npts; i += step) {
+    const int step = nparts * NT * P;
+    for (int i = part * NT * P + (int)threadIdx.x; i < npts; i += step) {
       for (int p = 0; p < P; ++p) {
-        const int j = i + p * 256;
+        const int j = i + p * NT;
         if (j >= npts) break;
         const int r = j / nx;
         one(x0 + (j - r * nx), y0 + r % ny, z0 + r / ny);
@@ -397,12 +403,13 @@ struct LoopGen {
     }
   }
 
-  // ndats: dats of an overlapped run (shared footprint pointers fp0 .. fp<ndats-1>)
-  void emit(int i, int ndats = 0) const {
+  // lay: shared-memory layout of an overlapped run (footprint of dat slot k
+  // at area + smem_off[k], strides spitch[k] / splane[k], corner ft[6k..])
+  void emit(int i, const OvLayout* lay = nullptr) const {
     if (ov) {
-      os << "\n__device__ __forceinline__ void ovb" << i << "(const DLoop* __restrict__ L, const int* bx";
-      for (int k = 0; k < ndats; ++k) os << ", double* fp" << k;
-      os << ",\n    const double* __restrict__ scal, const int* ob, DD* part, int stride) {\n"
+      os << "\n__device__ __forceinline__ void ovb" << i
+         << "(const DLoop* __restrict__ L, const int* bx, double* area, const int* ft,\n"
+            "    const double* __restrict__ scal, const int* ob, DD* part, int stride) {\n"
             "  const int x0 = bx[0], x1 = bx[1], y0 = bx[2], y1 = bx[3], z0 = bx[4], z1 = bx[5];\n";
     } else {
       os << "\n__device__ __forceinline__ void body" << i
@@ -424,8 +431,12 @@ struct LoopGen {
     }
     for (int a = 0; a < L.nargs; ++a) {
       if (L.args[a].kind == OPS_ARG_DAT) {
-        if (ov)
-          os << "  double* p" << a << " = fp" << L.args[a].slot << ";\n";
+        if (ov) {
+          const int k = L.args[a].slot;
+          os << "  double* p" << a << " = area + " << lay->smem_off[k] << " - (ft[" << 6 * k << "] + (i64)ft["
+             << 6 * k + 2 << "] * " << lay->spitch[k] << " + (i64)ft[" << 6 * k + 4 << "] * " << lay->splane[k]
+             << ");\n";
+        }
         else if (ro[a])
           os << "  const double* __restrict__ p" << a << " = L->args[" << a << "].ptr0;\n";
         else
@@ -443,21 +454,23 @@ struct LoopGen {
          << classes[k].second << "ll;\n";
     emit_points(1);
     os << "  };\n";
-    // kJitPts consecutive rows
+    // P consecutive rows
+    const int P = ov ? kOvPts : kJitPts;
     os << "  auto full = [&](int x, int y, int z) {\n";
     for (int k = 0; k < (int)classes.size(); ++k) {
       os << "    const i64 i" << k << "_0 = (i64)x + (i64)y * " << classes[k].first << "ll + (i64)z * "
          << classes[k].second << "ll;\n";
-      for (int p = 1; p < kJitPts; ++p)
+      for (int p = 1; p < P; ++p)
         os << "    const i64 i" << k << "_" << p << " = i" << k << "_0 + " << (int64_t)p * classes[k].first
            << "ll;\n";
     }
-    emit_points(kJitPts);
+    emit_points(P);
     os << "  };\n";
     if (ov)
-      os << "  run_units<" << kJitPts << ">(x0, x1, y0, y1, z0, z1, 0, 1, one, full);\n";
+      os << "  run_units<" << P << ", " << kOvThreads << ">(x0, x1, y0, y1, z0, z1, 0, 1, one, full);\n";
     else
-      os << "  run_units<" << kJitPts << ">(x0, x1, y0, y1, z0, z1, blockIdx.x, gridDim.x, one, full);\n";
+      os << "  run_units<" << P << ", " << kThreads
+         << ">(x0, x1, y0, y1, z0, z1, blockIdx.x, gridDim.x, one, full);\n";
     for (int k = 0; k < L.nreds; ++k)
       os << "  flush_red(" << L.red_op[k] << ", acc" << k << ", part, stride, L->part_row + " << k << ", "
          << (ov ? "0" : "assign") << ");\n";
@@ -487,17 +500,17 @@ std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::
 // given shared-memory layout (offsets and strides baked in).
 std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay) {
   std::ostringstream os;
-  os << "// opstile overlapped tiles: " << kJitPts << " rows per unit\n";
+  os << "// opstile overlapped tiles: " << kOvThreads << " threads, " << kOvPts << " rows per unit\n";
   os << kPrelude;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
   os << "static_assert(sizeof(OvDat) == " << sizeof(OvDat) << ", \"OvDat layout\");\n";
   const std::vector<char> none(OPS_MAX_ARGS, 0);
   for (int i = 0; i < count; ++i) {
     LoopGen g(loops[i], none, os, true);
-    g.emit(i, lay.ndats);
+    g.emit(i, &lay);
   }
   const int nd = lay.ndats;
-  os << "extern \"C\" __global__ void __launch_bounds__(256, 1) ov(const DLoop* __restrict__ loops,\n"
+  os << "extern \"C\" __global__ void __launch_bounds__(" << kOvThreads << ", 1) ov(const DLoop* __restrict__ loops,\n"
         "    const OvDat* __restrict__ dats, const int* __restrict__ own, const int* __restrict__ boxes,\n"
         "    const int* __restrict__ foot, int ntiles, const double* __restrict__ scal, DD* part, int stride) {\n"
         "  extern __shared__ __align__(16) double area[];\n"
@@ -509,17 +522,12 @@ std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay)
        << lay.spitch[k] << ", " << lay.splane[k] << ", dats[" << k << "].src, nullptr, dats[" << k
        << "].gpitch, dats[" << k << "].gplane, true);\n";
   os << "    __syncthreads();\n";
-  for (int k = 0; k < nd; ++k)
-    os << "    double* fp" << k << " = area + " << lay.smem_off[k] << " - (ft[" << 6 * k << "] + (i64)ft["
-       << 6 * k + 2 << "] * " << lay.spitch[k] << " + (i64)ft[" << 6 * k + 4 << "] * " << lay.splane[k] << ");\n";
   os << "    const int* ob = own + (size_t)t * 6;\n"
      << "    const int* bt = boxes + (size_t)t * " << count * 6 << ";\n";
   for (int i = 0; i < count; ++i) {
     os << "    if (bt[" << 6 * i + 1 << "] > bt[" << 6 * i << "] && bt[" << 6 * i + 3 << "] > bt[" << 6 * i + 2
        << "] && bt[" << 6 * i + 5 << "] > bt[" << 6 * i + 4 << "]) {\n      ovb" << i << "(loops + " << i
-       << ", bt + " << 6 * i;
-    for (int k = 0; k < nd; ++k) os << ", fp" << k;
-    os << ", scal, ob, part, stride);\n      __syncthreads();\n    }\n";
+       << ", bt + " << 6 * i << ", area, ft, scal, ob, part, stride);\n      __syncthreads();\n    }\n";
   }
   for (int k = 0; k < nd; ++k)
     if (lay.written[k])
@@ -819,7 +827,7 @@ int jit_overlap_max_grid(JitOverlap* o, int num_sms, int area_bytes) {
     o->area_set = area_bytes;
   }
   int per_sm = 0;
-  if (g_api.occupancy(&per_sm, o->f, kThreads, (size_t)area_bytes) != CUDA_SUCCESS) return 0;
+  if (g_api.occupancy(&per_sm, o->f, kOvThreads, (size_t)area_bytes) != CUDA_SUCCESS) return 0;
   return per_sm * num_sms;
 }
 
@@ -834,7 +842,7 @@ cudaError_t jit_launch_overlap(const JitOverlap* o, const LaunchEnv& env, const 
   DD* a7 = env.part;
   int a8 = env.part_stride;
   void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
-  return to_cuda(g_api.launch(o->f, (unsigned)grid, 1, 1, kThreads, 1, 1, (unsigned)area_bytes,
+  return to_cuda(g_api.launch(o->f, (unsigned)grid, 1, 1, kOvThreads, 1, 1, (unsigned)area_bytes,
                               (CUstream)env.stream, args, nullptr));
 }
 

@@ -326,3 +326,39 @@ def test_full_size_opensbli_one_step():
         assert_same(c, got, ref, hist, ref_hist, what=f"opensbli 320^3 {mode}")
         assert st["compiled"] == 1
         del got
+
+
+@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 16, 0)), ("overlapped", None),
+                                       ("auto", None)])
+def test_borrowed_device_dats(mode, tile):
+    """Dats declared on caller-owned device memory (torch tensors with a pitch
+    of their own): the chain reads and writes them in place in every mode
+    (overlapped tiles need library-owned dats and run the segment skewed)."""
+    import torch
+    c = W.cloverleaf2d(n=70, steps=2)
+    ref, ref_hist = oracle.run_chain(c)
+    ez, ey, ex = c.dats[0].init.shape
+    pitch = ex + 5  # rows padded unlike the library's own layout
+    ctx = ops.ops_init()
+    try:
+        ts = []
+        for d in c.dats:
+            t = torch.zeros((ez, ey, pitch), dtype=torch.float64, device="cuda")
+            t[:, :, :ex] = torch.from_numpy(d.init)
+            ts.append(t)
+        torch.cuda.synchronize()
+        r = ChainRunner(c, mode=mode, tile=tile, ctx=ctx, upload=False)
+        # replace the library's dats by borrowed ones (same order, same shapes)
+        r.dats = []
+        for t in ts:
+            p0 = t.data_ptr() + 8 * (c.d_m[0] + pitch * c.d_m[1])
+            r.dats.append(ops.ops_decl_dat(ctx, r.block, c.size, c.d_m, c.d_p, p0, pitch, pitch * ey))
+        hist = r.run()
+        torch.cuda.synchronize()
+        got = [t[:, :, :ex].cpu().numpy() for t in ts]
+        st = r.stats()
+    finally:
+        ops.ops_finalize(ctx)
+    assert_same(c, got, ref, hist, ref_hist, what=f"borrowed {mode}")
+    if mode == "overlapped":
+        assert st["mode"] == ops.OPS_MODE_SKEWED
