@@ -46,9 +46,21 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    deps = sources() + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps.append(os.path.join(INCLUDE, "opstile.h"))
     return any(os.path.getmtime(p) > t for p in deps)
+
+
+def _embed_device_common(gen_dir: str) -> None:
+    """device_common.cuh as a C++ raw string literal, for the run-time compiler."""
+    os.makedirs(gen_dir, exist_ok=True)
+    text = open(os.path.join(CSRC, "device_common.cuh")).read()
+    assert ')DCOMMON"' not in text
+    out = os.path.join(gen_dir, "device_common.inc")
+    body = "// generated by _build.py from csrc/device_common.cuh\nR\"DCOMMON(" + text + ")DCOMMON\"\n"
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as f:
+            f.write(body)
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -56,10 +68,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     nvcc = _nvcc()
     obj_dir = os.path.join(BUILD, "obj")
+    gen_dir = os.path.join(BUILD, "gen")
     os.makedirs(obj_dir, exist_ok=True)
+    _embed_device_common(gen_dir)
     common = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "--extended-lambda", "-Xcompiler",
               "-fPIC,-O2,-ffp-contract=off",
-              "-I", INCLUDE, "-I", CSRC] + ARCH
+              "-I", INCLUDE, "-I", CSRC, "-I", gen_dir] + ARCH
     # optional tuning macros, e.g. OPSTILE_NVCC_DEFS="OPS_PTS=2 OPS_MIN_CTAS=2"
     common += ["-D" + d for d in os.environ.get("OPSTILE_NVCC_DEFS", "").split()]
 

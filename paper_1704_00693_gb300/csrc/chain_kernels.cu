@@ -46,52 +46,8 @@ struct ChainSmemT {
 using ChainSmem = ChainSmemT<kPts>;
 constexpr size_t kChainSmem = sizeof(ChainSmem);
 
-// ----------------------------------------------------------------------------
-// compensated accumulation (Knuth's two-sum; order fixed by the launch shape)
-// ----------------------------------------------------------------------------
-__device__ __forceinline__ DD dd_add(DD a, double x) {
-  double s = __dadd_rn(a.hi, x);
-  double bp = __dsub_rn(s, a.hi);
-  double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bp)), __dsub_rn(x, bp));
-  return DD{s, __dadd_rn(a.lo, e)};
-}
-__device__ __forceinline__ DD dd_merge(DD a, DD b) {
-  DD t = dd_add(a, b.hi);
-  t.lo = __dadd_rn(t.lo, b.lo);
-  return t;
-}
-__device__ __forceinline__ double red_identity(int op) {
-  return op == OPS_RED_SUM ? 0.0 : (op == OPS_RED_MIN ? __longlong_as_double(0x7ff0000000000000ll)
-                                                       : __longlong_as_double(0xfff0000000000000ll));
-}
-__device__ __forceinline__ DD red_combine(int op, DD a, DD b) {
-  if (op == OPS_RED_SUM) return dd_merge(a, b);
-  if (op == OPS_RED_MIN) return DD{(b.hi < a.hi) ? b.hi : a.hi, 0.0};
-  return DD{(b.hi > a.hi) ? b.hi : a.hi, 0.0};
-}
-__device__ __forceinline__ DD red_add(int op, DD a, double x) {
-  if (op == OPS_RED_SUM) return dd_add(a, x);
-  if (op == OPS_RED_MIN) return DD{(x < a.hi) ? x : a.hi, 0.0};
-  return DD{(x > a.hi) ? x : a.hi, 0.0};
-}
-__device__ __forceinline__ DD shfl_down_dd(DD v, int o) {
-  return DD{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
-}
-
-// Block-wide combine in a fixed tree; result valid in thread 0.
-__device__ DD block_combine(int op, DD v, DD* sh) {
-  for (int o = 16; o > 0; o >>= 1) v = red_combine(op, v, shfl_down_dd(v, o));
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    v = lane < nw ? sh[lane] : DD{red_identity(op), 0.0};
-    for (int o = 16; o > 0; o >>= 1) v = red_combine(op, v, shfl_down_dd(v, o));
-  }
-  return v;
-}
+#include "device_common.cuh"
+static_assert(OPS_RED_SUM == 0 && OPS_RED_MIN == 1 && OPS_RED_MAX == 2, "device_common.cuh reduction codes");
 
 template <int P>
 __device__ __forceinline__ void red_init(ChainSmemT<P>& S) {
@@ -645,24 +601,6 @@ cudaError_t launch_skewed(const LaunchEnv& env, const DLoop* d_loops, const Phas
 using OvSmem = ChainSmemT<1>;
 constexpr int kOvHeader = (int)((sizeof(OvSmem) + 15) / 16 * 16);
 constexpr int kMaxSmemOptin = 232448;  // sm_103a: per-block opt-in shared memory
-
-// Copy a box between a global dat (strides gp, gq) and a shared footprint
-// whose origin is the box corner fb (strides sp, sq); rows are spread over warps.
-__device__ __forceinline__ void copy_box(const int* box, const int* fb, double* sm, int sp, int sq, const double* g0,
-                                         double* g1, int64_t gp, int64_t gq, bool to_shared) {
-  const int nx = box[1] - box[0], ny = box[3] - box[2], nz = box[5] - box[4];
-  if (nx <= 0 || ny <= 0 || nz <= 0) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r = warp; r < ny * nz; r += nw) {
-    const int y = box[2] + r % ny, z = box[4] + r / ny;
-    double* s = sm + (int64_t)(z - fb[4]) * sq + (int64_t)(y - fb[2]) * sp - fb[0];
-    const int64_t g = (int64_t)y * gp + (int64_t)z * gq;
-    if (to_shared)
-      for (int x = box[0] + lane; x < box[1]; x += 32) s[x] = g0[g + x];
-    else
-      for (int x = box[0] + lane; x < box[1]; x += 32) g1[g + x] = s[x];
-  }
-}
 
 __global__ void __launch_bounds__(kThreads) k_overlap(const DLoop* __restrict__ loops, int nloops,
                                                       const OvDat* __restrict__ dats, int ndats,

@@ -167,50 +167,18 @@ struct DLoop {
   int ins[64][6]; double K[128]; DArg args[8];
 };
 struct Phase { int loop; int barrier; int box[6]; };
+)PRE";
 
-__device__ __forceinline__ DD dd_add(DD a, double x) {
-  double s = __dadd_rn(a.hi, x);
-  double bp = __dsub_rn(s, a.hi);
-  double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bp)), __dsub_rn(x, bp));
-  DD r; r.hi = s; r.lo = __dadd_rn(a.lo, e); return r;
-}
-__device__ __forceinline__ DD dd_merge(DD a, DD b) { DD t = dd_add(a, b.hi); t.lo = __dadd_rn(t.lo, b.lo); return t; }
-__device__ __forceinline__ DD dd_of(double v) { DD r; r.hi = v; r.lo = 0.0; return r; }
-__device__ __forceinline__ double red_identity(int op) {
-  return op == 0 ? 0.0 : (op == 1 ? __longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0xfff0000000000000ll));
-}
-__device__ __forceinline__ DD red_combine(int op, DD a, DD b) {
-  if (op == 0) return dd_merge(a, b);
-  if (op == 1) return dd_of((b.hi < a.hi) ? b.hi : a.hi);
-  return dd_of((b.hi > a.hi) ? b.hi : a.hi);
-}
-__device__ __forceinline__ DD red_sum(DD a, double x) { return dd_add(a, x); }
-__device__ __forceinline__ DD red_min(DD a, double x) { return dd_of((x < a.hi) ? x : a.hi); }
-__device__ __forceinline__ DD red_max(DD a, double x) { return dd_of((x > a.hi) ? x : a.hi); }
+// device_common.cuh, embedded at build time (the interpreter kernels include the same file)
+const char* kDeviceCommon =
+#include "device_common.inc"
+    ;
 
+const char* kPreludeTail = R"PRE(
 __shared__ DD g_sh[32];
 
-// block-wide combine in a fixed tree, result valid in thread 0
-__device__ DD block_combine(int op, DD v) {
-  for (int o = 16; o > 0; o >>= 1) {
-    DD w; w.hi = __shfl_down_sync(0xffffffffu, v.hi, o); w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
-    v = red_combine(op, v, w);
-  }
-  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) g_sh[wp] = v;
-  __syncthreads();
-  if (wp == 0) {
-    v = lane < (int)(blockDim.x >> 5) ? g_sh[lane] : dd_of(red_identity(op));
-    for (int o = 16; o > 0; o >>= 1) {
-      DD w; w.hi = __shfl_down_sync(0xffffffffu, v.hi, o); w.lo = __shfl_down_sync(0xffffffffu, v.lo, o);
-      v = red_combine(op, v, w);
-    }
-  }
-  return v;
-}
 __device__ __forceinline__ void flush_red(int op, DD v, DD* part, int stride, int row, int assign) {
-  v = block_combine(op, v);
+  v = block_combine(op, v, g_sh);
   if (threadIdx.x == 0) {
     DD* dst = part + (size_t)row * stride + blockIdx.x;
     *dst = assign ? v : red_combine(op, *dst, v);
@@ -265,22 +233,6 @@ __device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0
 
 // overlapped tiles: one dat of a run (the library's OvDat)
 struct OvDat { const double* src; double* dst; i64 gpitch, gplane; int written, smem_off, spitch, splane; };
-// copy a box between a global dat and a shared footprint with corner fb
-__device__ __forceinline__ void copy_box(const int* box, const int* fb, double* sm, int sp, int sq, const double* g0,
-                                         double* g1, i64 gp, i64 gq, bool to_shared) {
-  const int nx = box[1] - box[0], ny = box[3] - box[2], nz = box[5] - box[4];
-  if (nx <= 0 || ny <= 0 || nz <= 0) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r = warp; r < ny * nz; r += nw) {
-    const int y = box[2] + r % ny, z = box[4] + r / ny;
-    double* s = sm + (i64)(z - fb[4]) * sq + (i64)(y - fb[2]) * sp - fb[0];
-    const i64 g = (i64)y * gp + (i64)z * gq;
-    if (to_shared)
-      for (int x = box[0] + lane; x < box[1]; x += 32) s[x] = g0[g + x];
-    else
-      for (int x = box[0] + lane; x < box[1]; x += 32) g1[g + x] = s[x];
-  }
-}
 )PRE";
 
 // ---------------------------------------------------------------------------
@@ -482,7 +434,7 @@ struct LoopGen {
 std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::vector<char>>& ro) {
   std::ostringstream os;
   os << "// opstile compiled loop bodies: " << kJitPts << " rows per unit, " << kJitMinCtas << " CTAs per SM\n";
-  os << kPrelude;
+  os << kPrelude << kDeviceCommon << kPreludeTail;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
   os << "static_assert(sizeof(DArg) == " << sizeof(DArg) << ", \"DArg layout\");\n";
   for (int i = l0; i < l1; ++i) {
@@ -501,7 +453,7 @@ std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::
 std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay) {
   std::ostringstream os;
   os << "// opstile overlapped tiles: " << kOvThreads << " threads, " << kOvPts << " rows per unit\n";
-  os << kPrelude;
+  os << kPrelude << kDeviceCommon << kPreludeTail;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
   os << "static_assert(sizeof(OvDat) == " << sizeof(OvDat) << ", \"OvDat layout\");\n";
   const std::vector<char> none(OPS_MAX_ARGS, 0);

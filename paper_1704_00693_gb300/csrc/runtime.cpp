@@ -80,7 +80,7 @@ struct OverlapPlan {
 
 // Autotuning state of one segment signature.
 struct TuneRec {
-  std::vector<std::array<int, 4>> cand;  // (mode, tile x, tile y, tile z)
+  std::vector<std::array<int, 5>> cand;  // (mode, tile x, tile y, tile z, loops per sub-segment; 0 = all)
   std::vector<double> ms;                // best device time of each candidate (-1: not yet run)
   std::vector<int> runs;                 // samples taken of each candidate
   int pending = -1;                      // candidate whose events are outstanding
@@ -1098,14 +1098,17 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<D
         od = d;
         break;
       }
-    T.cand.push_back({OPS_MODE_UNTILED, 0, 0, 0});
+    T.cand.push_back({OPS_MODE_UNTILED, 0, 0, 0, 0});
     for (int f = 1; f <= 16; f *= 2) {
-      std::array<int, 4> cd = {OPS_MODE_SKEWED, at[0], at[1], at[2]};
+      std::array<int, 5> cd = {OPS_MODE_SKEWED, at[0], at[1], at[2], 0};
       cd[1 + od] = (int)std::min<int64_t>((int64_t)at[od] * f, ext[od]);
       T.cand.push_back(cd);
       if (cd[1 + od] >= ext[od]) break;
     }
-    if (count > 1) T.cand.push_back({OPS_MODE_OVERLAPPED, 0, 0, 0});
+    // shorter segments: less skew, so the automatic tile of each part is larger
+    for (int parts = 2; parts <= 4 && count / parts >= 4; parts *= 2)
+      T.cand.push_back({OPS_MODE_SKEWED, 0, 0, 0, (count + parts - 1) / parts});
+    if (count > 1) T.cand.push_back({OPS_MODE_OVERLAPPED, 0, 0, 0, 0});
     T.ms.assign(T.cand.size(), -1.0);
     T.runs.assign(T.cand.size(), 0);
     CUDA_TRY(c, cudaEventCreate(&T.e0));
@@ -1135,8 +1138,11 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<D
   const bool tuning = T.best < 0;
   c->stats.tuning |= tuning ? 1 : 0;
   if (tuning) CUDA_TRY(c, cudaEventRecord(T.e0, c->stream));
-  const std::array<int, 4>& cd = T.cand[pick];
-  int rc = run_segment_mode(c, first, count, dl_base, hl, cd[0], &cd[1]);
+  const std::array<int, 5>& cd = T.cand[pick];
+  int rc = OPS_OK;
+  const int part = cd[4] > 0 ? cd[4] : count;
+  for (int f = 0; f < count && !rc; f += part)
+    rc = run_segment_mode(c, first + f, std::min(part, count - f), dl_base + f, hl, cd[0], &cd[1]);
   if (rc) return rc;
   if (tuning) {
     CUDA_TRY(c, cudaEventRecord(T.e1, c->stream));
