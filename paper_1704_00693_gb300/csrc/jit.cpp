@@ -450,10 +450,44 @@ std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::
 
 // Source of the overlapped-tile kernel "ov" for one run of loops with the
 // given shared-memory layout (offsets and strides baked in).
+// Bulk copies (the TMA unit) of footprint rows into shared memory, counted
+// on one mbarrier; waits are bounded by wall-clock time.
+const char* kOvTma = R"OVT(
+__shared__ __align__(8) unsigned long long g_mbar;
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(bar)) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_to_shared(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// true once the barrier's phase `parity` completed; false after timeout_ns
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long timeout_ns) {
+  const unsigned long long t0 = now_ns();
+  for (;;) {
+    unsigned done;
+    asm volatile("{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+                 : "=r"(done) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    if (done) return true;
+    if ((long long)(now_ns() - t0) > timeout_ns) return false;
+  }
+}
+)OVT";
+
 std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay) {
   std::ostringstream os;
   os << "// opstile overlapped tiles: " << kOvThreads << " threads, " << kOvPts << " rows per unit\n";
-  os << kPrelude << kDeviceCommon << kPreludeTail;
+  os << kPrelude << kDeviceCommon << kPreludeTail << kOvTma;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
   os << "static_assert(sizeof(OvDat) == " << sizeof(OvDat) << ", \"OvDat layout\");\n";
   const std::vector<char> none(OPS_MAX_ARGS, 0);
@@ -464,16 +498,47 @@ std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay)
   const int nd = lay.ndats;
   os << "extern \"C\" __global__ void __launch_bounds__(" << kOvThreads << ", 1) ov(const DLoop* __restrict__ loops,\n"
         "    const OvDat* __restrict__ dats, const int* __restrict__ own, const int* __restrict__ boxes,\n"
-        "    const int* __restrict__ foot, int ntiles, const double* __restrict__ scal, DD* part, int stride) {\n"
-        "  extern __shared__ __align__(16) double area[];\n"
+        "    const int* __restrict__ foot, int ntiles, const double* __restrict__ scal, DD* part, int stride,\n"
+        "    int* err, long long timeout_ns) {\n"
+        "  extern __shared__ __align__(128) double area[];\n"
+        "  if (threadIdx.x == 0) mbar_init(&g_mbar);\n"
+        "  __syncthreads();\n"
+        "  unsigned phase = 0;\n"
         "  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {\n"
-        "    __syncthreads();\n"
      << "    const int* ft = foot + (size_t)t * " << nd * 6 << ";\n";
+  // Footprint rows start on even x (16-byte aligned in global memory; the
+  // shared regions, pitches and planes are even) and hold an even number
+  // of doubles, so every row is one bulk copy.  Every thread counts the
+  // bytes the same way; one thread announces them on the mbarrier before
+  // any copy is issued.
+  os << "    unsigned bytes = 0;\n";
   for (int k = 0; k < nd; ++k)
-    os << "    copy_box(ft + " << 6 * k << ", ft + " << 6 * k << ", area + " << lay.smem_off[k] << ", "
-       << lay.spitch[k] << ", " << lay.splane[k] << ", dats[" << k << "].src, nullptr, dats[" << k
-       << "].gpitch, dats[" << k << "].gplane, true);\n";
-  os << "    __syncthreads();\n";
+    os << "    bytes += (unsigned)(ft[" << 6 * k + 1 << "] - ft[" << 6 * k << "]) * (unsigned)(ft[" << 6 * k + 3
+       << "] - ft[" << 6 * k + 2 << "]) * (unsigned)(ft[" << 6 * k + 5 << "] - ft[" << 6 * k + 4 << "]) * 8u;\n";
+  os << "    __syncthreads();  // the previous tile's reads and write-back are done\n"
+        "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n"
+        "    if (threadIdx.x == 0) mbar_expect_tx(&g_mbar, bytes);\n"
+        "    __syncthreads();\n";
+  for (int k = 0; k < nd; ++k) {
+    const int o = 6 * k;
+    os << "    {\n      const int nx = ft[" << o + 1 << "] - ft[" << o << "], ny = ft[" << o + 3 << "] - ft[" << o + 2
+       << "], nz = ft[" << o + 5 << "] - ft[" << o + 4 << "];\n"
+       << "      if (nx > 0 && ny > 0 && nz > 0)\n"
+       << "        for (int r = threadIdx.x; r < ny * nz; r += blockDim.x) {\n"
+       << "          const int y = ft[" << o + 2 << "] + r % ny, z = ft[" << o + 4 << "] + r / ny;\n"
+       << "          bulk_to_shared(area + " << lay.smem_off[k] << " + (i64)(z - ft[" << o + 4 << "]) * "
+       << lay.splane[k] << " + (i64)(y - ft[" << o + 2 << "]) * " << lay.spitch[k] << ",\n"
+       << "                         dats[" << k << "].src + (i64)y * dats[" << k << "].gpitch + (i64)z * dats[" << k
+       << "].gplane + ft[" << o << "], (unsigned)nx * 8u, &g_mbar);\n"
+       << "        }\n    }\n";
+  }
+  os << "    bool late = !mbar_wait(&g_mbar, phase, timeout_ns);\n"
+        "    if (late) {\n"
+        "      atomicCAS(err, 0, 1);\n"
+        "      mbar_wait(&g_mbar, phase, timeout_ns);  // the copies still in flight\n"
+        "    }\n"
+        "    if (__syncthreads_or(late)) return;\n"
+        "    phase ^= 1u;\n";
   os << "    const int* ob = own + (size_t)t * 6;\n"
      << "    const int* bt = boxes + (size_t)t * " << count * 6 << ";\n";
   for (int i = 0; i < count; ++i) {
@@ -793,7 +858,9 @@ cudaError_t jit_launch_overlap(const JitOverlap* o, const LaunchEnv& env, const 
   const double* a6 = env.scal;
   DD* a7 = env.part;
   int a8 = env.part_stride;
-  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8};
+  int* a9 = env.err;
+  long long a10 = env.timeout_ns;
+  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10};
   return to_cuda(g_api.launch(o->f, (unsigned)grid, 1, 1, kOvThreads, 1, 1, (unsigned)area_bytes,
                               (CUstream)env.stream, args, nullptr));
 }

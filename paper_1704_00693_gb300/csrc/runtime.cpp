@@ -582,8 +582,18 @@ int overlap_plan(ops_ctx c, int first, int n, const int* tile_in, OverlapPlan** 
         F[2 * d + 1] = std::min(F[2 * d + 1], ahi[d]);
         if (F[2 * d + 1] <= F[2 * d]) empty = true;
       }
-      if (empty)
+      if (empty) {
         for (int d = 0; d < 6; ++d) F[d] = 0;
+      } else {
+        // x widened to even grid coordinates: grid x = 0 starts a 128-byte
+        // line and pitch and plane are multiples of 16, so footprint rows
+        // then move as whole 16-byte bulk copies.  The widening reaches at
+        // most one double into the row padding on either side, which the
+        // library's layout always holds (x = 0 sits at the rounded-up front
+        // halo; the pitch rounds the row up to 16 doubles).
+        F[0] -= F[0] & 1;
+        F[1] += F[1] & 1;
+      }
       std::memcpy(&foot6d[6 * k], F, sizeof F);
     }
   };
