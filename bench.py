@@ -169,12 +169,12 @@ def profile_traffic(schedule, tile):
         return None
 
 
-def time_mode(chain, mode, tile, steps, warmup, stream, torch):
+def time_mode(chain, mode, tile, steps, warmup, stream, torch, fp32=False):
     """Timed steps without per-kernel events (the value), then as many steps
     of the same settled schedule with per-kernel CUDA events on the launching
     stream (the kernels' durations for the roofline)."""
     from paper_1704_00693_gb300.chain import ChainRunner
-    r = ChainRunner(chain, mode=mode, tile=tile, stream=stream.cuda_stream, timing=False)
+    r = ChainRunner(chain, mode=mode, tile=tile, stream=stream.cuda_stream, timing=False, fp32=fp32)
     try:
         for _ in range(warmup):
             r.step()
@@ -480,6 +480,27 @@ def bench_ppcg(stream, torch, n=4000, inner=10, steps=5):
     return out
 
 
+def bench_fp32(stream, torch, n=3840, steps=5):
+    """The CloverLeaf-shaped chain in an OPS_REAL_F32 context (float dats and
+    arithmetic): every schedule, effective GB/s at 4 bytes per element.  With
+    single-precision arithmetic the chain is bound by HBM, not by the FP64
+    pipe, which is where tiling pays."""
+    from synth import workloads as W
+    chain = W.cloverleaf2d(n=n, steps=1)
+    U, flops = workload_numbers(chain)
+    U = U // 2  # 4-byte elements
+    out = {"n": n, "untiled_bytes_per_step": U, "dtype": "f32"}
+    for mode, tile in (("untiled", None), ("skewed", None), ("skewed", [0, 1024, 0]), ("overlapped", None),
+                       ("auto", None)):
+        ms, kms, kl, launches, st = time_mode(chain, mode, tile, steps, 3, stream, torch, fp32=True)
+        key = mode if tile is None else f"{mode}_{tile[1]}"
+        out[key] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
+                    "schedule": {0: "untiled", 1: "skewed", 2: "overlapped"}.get(st["mode"]), "tile": st["tile"]}
+    for key in [k for k in out if isinstance(out[k], dict) and k != "untiled"]:
+        out[f"speedup_{key}_vs_untiled"] = out["untiled"]["ms_per_step"] / out[key]["ms_per_step"]
+    return out
+
+
 def bench_cloverleaf3d(stream, torch, n=330, steps=3):
     """The CloverLeaf-3D-shaped chain (330^3 as in the paper, 30 dats, 141 loops per step)."""
     from synth import workloads as W
@@ -643,6 +664,7 @@ def main():
     chain3d = bench_opensbli3d(stream, torch) if rank == 0 and not args.no_3d else None
     hydro3d = bench_cloverleaf3d(stream, torch) if rank == 0 and not args.no_3d else None
     ppcg = bench_ppcg(stream, torch) if rank == 0 and not args.no_3d else None
+    fp32 = bench_fp32(stream, torch) if rank == 0 and not args.no_3d else None
     serving = bench_serving(args.serve_requests) if rank == 0 and not args.no_serve else None
 
     line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
@@ -656,7 +678,7 @@ def main():
             "speedup_vs_untiled": (untiled["ms_per_step"] / (ms / args.steps)) if untiled else None,
             "untiled": untiled, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
-            "cg_4000": cg, "serving": serving, "opensbli3d_320": chain3d, "cloverleaf3d_330": hydro3d, "ppcg_4000": ppcg,
+            "cg_4000": cg, "serving": serving, "opensbli3d_320": chain3d, "cloverleaf3d_330": hydro3d, "ppcg_4000": ppcg, "cloverleaf2d_3840_fp32": fp32,
             "plan": {"phases": st["phases"], "barriers": st["barriers"], "skew": st["skew"],
                      "plan_cache_hits": st["plan_cache_hits"]} if st else None}
     if rank == 0:

@@ -126,7 +126,14 @@ typedef struct {
   int timing;          /* 1: record CUDA events around the chain kernels (kernel_ms in ops_flush_stats) */
   int interpret;       /* 1: run loop bodies through the register-IR interpreter kernels instead of
                           kernels compiled from the IR at the first flush of each segment (NVRTC) */
+  int real;            /* OPS_REAL_F64 (default) or OPS_REAL_F32: the element type of every dat of
+                          the context and the precision of every loop's arithmetic.  FP32 loops
+                          run compiled bodies only (no checked or interpreted mode); constants
+                          and scalar arguments are rounded to float on load; reductions take the
+                          float values exactly and accumulate as in FP64 */
 } ops_config;
+#define OPS_REAL_F64 0
+#define OPS_REAL_F32 1
 
 /* Fill *cfg with defaults (device 0, own stream, OPS_MODE_AUTO, automatic tiles). */
 void ops_config_default(ops_config* cfg);
@@ -145,7 +152,7 @@ int ops_set_mode(ops_ctx ctx, int mode, const int* tile, int segment);
 /* ---- declarations (Sec. 3) ---- */
 /* A structured block of 1, 2 or 3 dimensions. */
 int ops_decl_block(ops_ctx ctx, int dims, const char* name, int* out);
-/* A FP64 dat of size[0..dims) interior points with halo depths d_m (below)
+/* A dat (FP64, or FP32 in an OPS_REAL_F32 context) of size[0..dims) interior points with halo depths d_m (below)
  * and d_p (above) per dimension (unused dimensions: size 1, halos 0).
  * dev_ptr0 == NULL: the library allocates a zeroed, padded array (x rows
  * start 128-byte aligned) and owns it.  Otherwise dev_ptr0 is borrowed: it
@@ -190,18 +197,19 @@ int ops_sync(ops_ctx ctx);
 
 /* ---- data movement ---- */
 /* Flush, then copy the dat's whole allocation box (halos included) into the
- * dense host array host_out of ex*ey*ez doubles, x fastest. */
-int ops_dat_fetch(ops_ctx ctx, int dat, double* host_out, int64_t nelems);
+ * dense host array host_out of ex*ey*ez elements of the context's type
+ * (doubles, or floats with OPS_REAL_F32), x fastest. */
+int ops_dat_fetch(ops_ctx ctx, int dat, void* host_out, int64_t nelems);
 /* Copy a dense host array of the allocation box into the dat (after the
  * queued loops, in stream order). */
-int ops_dat_upload(ops_ctx ctx, int dat, const double* host_in, int64_t nelems);
+int ops_dat_upload(ops_ctx ctx, int dat, const void* host_in, int64_t nelems);
 /* As ops_dat_fetch / ops_dat_upload, but the copy is only queued on the
  * context's stream (after the flushed loops): the host array must stay
  * valid, and unchanged for an upload, until ops_sync (or another waiting
  * call) returns; fetched values are there from then on.  With pinned host
  * memory the copy runs while the host continues. */
-int ops_dat_fetch_async(ops_ctx ctx, int dat, double* host_out, int64_t nelems);
-int ops_dat_upload_async(ops_ctx ctx, int dat, const double* host_in, int64_t nelems);
+int ops_dat_fetch_async(ops_ctx ctx, int dat, void* host_out, int64_t nelems);
+int ops_dat_upload_async(ops_ctx ctx, int dat, const void* host_in, int64_t nelems);
 /* Current device address of grid point (0,0,0) and strides of a dat; ext
  * receives the allocation extents (may be NULL). */
 int ops_dat_info(ops_ctx ctx, int dat, double** dev_ptr0, int64_t* pitch, int64_t* plane, int* ext);

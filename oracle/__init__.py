@@ -99,9 +99,10 @@ def run_loops(chain, dats: List[np.ndarray], loops: Sequence, red_vals: List[flo
     reduction values after the loops, starting from `red_vals`."""
     L = lib()
     nd = len(dats)
+    f32 = nd > 0 and dats[0].dtype == np.float32
     for a in dats:
-        assert a.dtype == np.float64 and a.flags.c_contiguous
-    ptrs = (C.POINTER(C.c_double) * max(nd, 1))(*[_dp(a) for a in dats])
+        assert a.dtype == (np.float32 if f32 else np.float64) and a.flags.c_contiguous
+    ptrs = (C.POINTER(C.c_double) * max(nd, 1))(*[C.cast(a.ctypes.data, C.POINTER(C.c_double)) for a in dats])
     ext = np.array([[a.shape[2], a.shape[1], a.shape[0]] for a in dats], dtype=np.int32).ravel()
     dm = np.array([list(chain.d_m) for _ in dats], dtype=np.int32).ravel()
     st_npts = np.array([len(s) for s in chain.stencils], dtype=np.int32)
@@ -126,7 +127,7 @@ def run_loops(chain, dats: List[np.ndarray], loops: Sequence, red_vals: List[flo
     rc = L.ora_run_loops(C.c_int(nd), ptrs, _ip(ext), _ip(dm), _ip(st_npts), _ip(st_start), _ip(st_off),
                          C.c_int(len(chain.reductions)), _ip(red_op), _dp(red_val),
                          C.c_int(nl), _ip(rngs), _ip(nargs), _ip(arg0), _ip(args), _ip(nins), _ip(ins0),
-                         _ip(ins), _ip(k0), _ip(nk), _dp(K), C.c_int(nthreads), err)
+                         _ip(ins), _ip(k0), _ip(nk), _dp(K), C.c_int(nthreads), C.c_int(1 if f32 else 0), err)
     if rc != 0:
         raise OracleError(err.value.decode())
     return [float(v) for v in red_val[:len(chain.reductions)]]
@@ -136,12 +137,14 @@ def red_identity(op: int) -> float:
     return 0.0 if op == 0 else (np.inf if op == 1 else -np.inf)
 
 
-def run_chain(chain, steps: Optional[int] = None, nthreads: int = 0):
+def run_chain(chain, steps: Optional[int] = None, nthreads: int = 0, fp32: bool = False):
     """Run the chain's steps untiled in program order.
 
     Returns (dats, history): the final dats (dense arrays) and, per step,
-    the reduction values the host reads at the end of that step."""
-    dats = [np.ascontiguousarray(d.init.copy()) for d in chain.dats]
+    the reduction values the host reads at the end of that step.  fp32: the
+    dats start as the initial values rounded to float and every operation
+    is an IEEE single one."""
+    dats = [np.ascontiguousarray(d.init.astype(np.float32 if fp32 else np.float64)) for d in chain.dats]
     nsteps = chain.steps if steps is None else steps
     dt = 1.0
     hist = []
@@ -157,7 +160,8 @@ def run_chain(chain, steps: Optional[int] = None, nthreads: int = 0):
     return dats, hist
 
 
-def run_chain_tiled(chain, tile: Sequence[int], steps: Optional[int] = None, nthreads: int = 0):
+def run_chain_tiled(chain, tile: Sequence[int], steps: Optional[int] = None, nthreads: int = 0,
+                    fp32: bool = False):
     """The paper's CPU execution of the same steps: each step's loops get
     Algorithm 1's skewed ranges (oracle.plan.skewed_plan) for the tile sizes
     `tile`, then run as Algorithm 2 does, tile by tile in lexicographic
@@ -166,7 +170,7 @@ def run_chain_tiled(chain, tile: Sequence[int], steps: Optional[int] = None, nth
     as in run_chain and reductions are exact, so the results are identical."""
     from . import plan as oplan
     import itertools
-    dats = [np.ascontiguousarray(d.init.copy()) for d in chain.dats]
+    dats = [np.ascontiguousarray(d.init.astype(np.float32 if fp32 else np.float64)) for d in chain.dats]
     nsteps = chain.steps if steps is None else steps
     nd = chain.ndim
     dt = 1.0

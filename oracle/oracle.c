@@ -10,7 +10,7 @@
  *
  * What it computes:
  *  - ora_run_loops: the plain untiled program-order execution of a chain of
- *    parallel loops.  A parallel loop's result must not depend on the order
+ *    parallel loops, in FP64 or (f32) in FP32.  A parallel loop's result must not depend on the order
  *    of its points (Sec. 3), and tiling only reorders such work (Sec. 4.B,
  *    Algorithm 2), so the untiled result is what every tiled schedule must
  *    reproduce.  Each point evaluates the IR in its fixed statement and term
@@ -123,7 +123,7 @@ static double xdot32(const float* x, const float* y, int64_t n) {
  * ------------------------------------------------------------------------- */
 typedef struct {
   int ndats;
-  double** dat;           /* dense, x fastest, allocated box incl. halos */
+  double** dat;           /* dense, x fastest, allocated box incl. halos (float* when f32) */
   const int* ext;         /* 3 per dat: allocated extents ex, ey, ez */
   const int* dm;          /* 3 per dat: index of grid point 0 inside the allocation */
   const int* st_npts;
@@ -131,6 +131,7 @@ typedef struct {
   const int* st_off;      /* 3 ints per stencil point */
   int nred;
   const int* red_op;
+  int f32;                /* 1: FP32 dats and FP32 arithmetic (IEEE single, explicit fmaf) */
 } env_t;
 
 typedef struct {
@@ -253,6 +254,97 @@ static void run_point(const env_t* E, const loop_t* L, const double* scal, long 
   }
 }
 
+/* ---- FP32: the same interpreter on float dats, every operation an IEEE
+ * single operation (C float arithmetic, fmaf), constants and scalars rounded
+ * to float on load; reductions take the float values exactly ---- */
+static float* at32(const env_t* E, int dat, long x, long y, long z) {
+  const int* e = E->ext + 3 * dat;
+  const int* m = E->dm + 3 * dat;
+  long ix = x + m[0], iy = y + m[1], iz = z + m[2];
+  if (ix < 0 || iy < 0 || iz < 0 || ix >= e[0] || iy >= e[1] || iz >= e[2]) return NULL;
+  return ((float*)E->dat[dat]) + ix + (long)e[0] * (iy + (long)e[1] * iz);
+}
+
+static int fetch32(const env_t* E, const loop_t* L, int a, int p, long x, long y, long z,
+                   float* out, status_t* st) {
+  const int* ar = L->args + 4 * a;
+  if (ar[0] != K_DAT) { fail(st, "LD of a non-dat argument %ld", a, 0, 0); return 0; }
+  int s = ar[2];
+  if (p < 0 || p >= E->st_npts[s]) { fail(st, "stencil point %ld out of range for arg %ld", p, a, 0); return 0; }
+  const int* o = E->st_off + 3 * (E->st_start[s] + p);
+  float* q = at32(E, ar[1], x + o[0], y + o[1], z + o[2]);
+  if (!q) { fail(st, "out-of-allocation read at (%ld,%ld,%ld)", x + o[0], y + o[1], z + o[2]); return 0; }
+  *out = *q;
+  return 1;
+}
+
+static void run_point32(const env_t* E, const loop_t* L, const double* scal, long x, long y, long z,
+                        redacc_t* acc, status_t* st) {
+  float r[NREG];
+  for (int i = 0; i < NREG; ++i) r[i] = 0.0f;
+  for (int pc = 0; pc < L->nins; ++pc) {
+    const int* I = L->ins + 6 * pc;
+    int op = I[0], d = I[1], a = I[2], b = I[3], c = I[4], e = I[5];
+    float v;
+    switch (op) {
+      case I_LD:
+        if (L->args[4 * a] == K_SCALAR) { r[d] = (float)scal[L->args[4 * a + 1]]; break; }
+        if (!fetch32(E, L, a, b, x, y, z, &v, st)) return;
+        r[d] = v;
+        break;
+      case I_CST: r[d] = (float)L->K[a]; break;
+      case I_ADD: r[d] = r[a] + r[b]; break;
+      case I_SUB: r[d] = r[a] - r[b]; break;
+      case I_MUL: r[d] = r[a] * r[b]; break;
+      case I_FMA: r[d] = fmaf(r[a], r[b], r[c]); break;
+      case I_DIV: r[d] = r[a] / r[b]; break;
+      case I_MIN: r[d] = (r[b] < r[a]) ? r[b] : r[a]; break;
+      case I_MAX: r[d] = (r[b] > r[a]) ? r[b] : r[a]; break;
+      case I_SGT: r[d] = (r[a] > r[b]) ? r[c] : r[e]; break;
+      case I_WSUM:
+      case I_WACC: {
+        int s = L->args[4 * a + 2];
+        int np = E->st_npts[s];
+        float t = r[d];
+        for (int p = 0; p < np; ++p) {
+          if (!fetch32(E, L, a, p, x, y, z, &v, st)) return;
+          if (op == I_WSUM && p == 0) t = (float)L->K[b] * v;
+          else t = fmaf((float)L->K[b + p], v, t);
+        }
+        r[d] = t;
+        break;
+      }
+      case I_POLY: {
+        float t = (float)L->K[b + c];
+        for (int i = c - 1; i >= 0; --i) t = fmaf(t, r[a], (float)L->K[b + i]);
+        r[d] = t;
+        break;
+      }
+      case I_ST: {
+        const int* ar = L->args + 4 * d;
+        float* q = at32(E, ar[1], x, y, z);
+        if (!q) { fail(st, "out-of-allocation write at (%ld,%ld,%ld)", x, y, z); return; }
+        if (ar[3] == A_INC) *q = *q + r[a];
+        else *q = r[a];
+        break;
+      }
+      case I_RED: {
+        int h = L->args[4 * d + 1];
+        int rop = E->red_op[h];
+        double w = (double)r[a];
+        acc->touched[h] = 1;
+        if (rop == R_SUM) xs_add(&acc->sums[h], w);
+        else if (rop == R_MIN) acc->mm[h] = (w < acc->mm[h]) ? w : acc->mm[h];
+        else acc->mm[h] = (w > acc->mm[h]) ? w : acc->mm[h];
+        break;
+      }
+      default:
+        fail(st, "bad opcode %ld at %ld", op, pc, 0);
+        return;
+    }
+  }
+}
+
 /* reduction state: an exact sum per SUM handle, a running value per MIN/MAX */
 typedef struct { xsum* sums; double* mm; } redstate_t;
 
@@ -294,7 +386,10 @@ static void run_loop(const env_t* E, const loop_t* L, redstate_t* RS, int nthrea
     long z = z0 + o / ny, y = y0 + o % ny;
     for (long x = x0; x < x1; ++x) {
       if (st->err) break;
-      run_point(E, L, scal, x, y, z, &accs[tid], st);
+      if (E->f32)
+        run_point32(E, L, scal, x, y, z, &accs[tid], st);
+      else
+        run_point(E, L, scal, x, y, z, &accs[tid], st);
     }
   }
   /* fold per-thread reduction state into the handles (exact for sums) */
@@ -321,7 +416,7 @@ static void run_loop(const env_t* E, const loop_t* L, redstate_t* RS, int nthrea
 
 /*
  * Run `nloops` loops in program order over the given dats (modified in
- * place).  red_val[h] holds each reduction's value on entry (the identity
+ * place; float arrays and FP32 arithmetic when f32 != 0).  red_val[h] holds each reduction's value on entry (the identity
  * after a host read) and its exactly rounded / exact value on return.
  * Returns 0, or 1 with a message in errbuf (>= 256 bytes).
  */
@@ -331,8 +426,8 @@ int ora_run_loops(int ndats, double** dat, const int* ext, const int* dm,
                   int nloops, const int* loop_rng, const int* loop_nargs, const int* loop_arg0,
                   const int* args, const int* loop_nins, const int* loop_ins0, const int* ins,
                   const int* loop_k0, const int* loop_nk, const double* K,
-                  int nthreads, char* errbuf) {
-  env_t E = {ndats, dat, ext, dm, st_npts, st_start, st_off, nred, red_op};
+                  int nthreads, int f32, char* errbuf) {
+  env_t E = {ndats, dat, ext, dm, st_npts, st_start, st_off, nred, red_op, f32};
   status_t st;
   st.err = 0;
   st.msg[0] = 0;

@@ -33,6 +33,7 @@ OPS_ARG_DAT, OPS_ARG_SCALAR, OPS_ARG_RED = 0, 1, 2
 OPS_READ, OPS_WRITE, OPS_RW, OPS_INC = 0, 1, 2, 3
 OPS_RED_SUM, OPS_RED_MIN, OPS_RED_MAX = 0, 1, 2
 OPS_DEVICE_NONE = -1
+OPS_REAL_F64, OPS_REAL_F32 = 0, 1
 # loop-body IR opcodes (include/opstile.h)
 (OPS_IR_LD, OPS_IR_CST, OPS_IR_ADD, OPS_IR_SUB, OPS_IR_MUL, OPS_IR_FMA, OPS_IR_DIV, OPS_IR_MIN, OPS_IR_MAX,
  OPS_IR_SGT, OPS_IR_WSUM, OPS_IR_WACC, OPS_IR_POLY, OPS_IR_ST, OPS_IR_RED) = range(1, 16)
@@ -51,7 +52,7 @@ class ops_config(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("mode", C.c_int), ("tile", C.c_int * 3),
                 ("segment", C.c_int), ("check", C.c_int), ("l2_bytes", C.c_int64), ("hbm_budget", C.c_int64),
                 ("timeout_ms", C.c_int), ("blocks_per_sm", C.c_int), ("test_skip_barrier_block", C.c_int),
-                ("timing", C.c_int), ("interpret", C.c_int)]
+                ("timing", C.c_int), ("interpret", C.c_int), ("real", C.c_int)]
 
 
 class ops_arg(C.Structure):
@@ -205,36 +206,34 @@ def ops_dat_info(ctx, dat: int):
     return (p.value or 0), pitch.value, plane.value, tuple(ext)
 
 
-def ops_dat_fetch(ctx, dat: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+def ops_dat_fetch(ctx, dat: int, out: Optional[np.ndarray] = None, dtype=np.float64) -> np.ndarray:
+    """The dat's allocation box as a dense (ez, ey, ex) array of the
+    context's element type (dtype float32 for an OPS_REAL_F32 context)."""
     _, _, _, ext = ops_dat_info(ctx, dat)
     if out is None:
-        out = np.empty((ext[2], ext[1], ext[0]), dtype=np.float64)
-    assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == ext[0] * ext[1] * ext[2]
-    _check(ctx, load().ops_dat_fetch(ctx, C.c_int(dat), out.ctypes.data_as(C.POINTER(C.c_double)),
-                                     C.c_int64(out.size)))
+        out = np.empty((ext[2], ext[1], ext[0]), dtype=dtype)
+    assert out.dtype in (np.float64, np.float32) and out.flags.c_contiguous and out.size == ext[0] * ext[1] * ext[2]
+    _check(ctx, load().ops_dat_fetch(ctx, C.c_int(dat), C.c_void_p(out.ctypes.data), C.c_int64(out.size)))
     return out
 
 
-def ops_dat_upload(ctx, dat: int, host: np.ndarray):
-    h = np.ascontiguousarray(host, dtype=np.float64)
-    _check(ctx, load().ops_dat_upload(ctx, C.c_int(dat), h.ctypes.data_as(C.POINTER(C.c_double)),
-                                      C.c_int64(h.size)))
+def ops_dat_upload(ctx, dat: int, host: np.ndarray, dtype=np.float64):
+    h = np.ascontiguousarray(host, dtype=dtype)
+    _check(ctx, load().ops_dat_upload(ctx, C.c_int(dat), C.c_void_p(h.ctypes.data), C.c_int64(h.size)))
 
 
 def ops_dat_fetch_async(ctx, dat: int, out: np.ndarray):
     """Queue a fetch into `out` (C-contiguous float64, pinned for overlap);
     the values are there once ops_sync returns."""
-    assert out.dtype == np.float64 and out.flags.c_contiguous
-    _check(ctx, load().ops_dat_fetch_async(ctx, C.c_int(dat), out.ctypes.data_as(C.POINTER(C.c_double)),
-                                           C.c_int64(out.size)))
+    assert out.dtype in (np.float64, np.float32) and out.flags.c_contiguous
+    _check(ctx, load().ops_dat_fetch_async(ctx, C.c_int(dat), C.c_void_p(out.ctypes.data), C.c_int64(out.size)))
 
 
 def ops_dat_upload_async(ctx, dat: int, host: np.ndarray):
     """Queue an upload from `host` (C-contiguous float64, kept unchanged until
     ops_sync returns)."""
-    assert host.dtype == np.float64 and host.flags.c_contiguous
-    _check(ctx, load().ops_dat_upload_async(ctx, C.c_int(dat), host.ctypes.data_as(C.POINTER(C.c_double)),
-                                            C.c_int64(host.size)))
+    assert host.dtype in (np.float64, np.float32) and host.flags.c_contiguous
+    _check(ctx, load().ops_dat_upload_async(ctx, C.c_int(dat), C.c_void_p(host.ctypes.data), C.c_int64(host.size)))
 
 
 def ops_last_stats(ctx) -> dict:

@@ -22,8 +22,9 @@ class ChainRunner:
     def __init__(self, chain, mode: str = "auto", tile=None, segment: int = 0, check: bool = False,
                  stream: int = 0, device: int = 0, ctx=None, blocks_per_sm: int = 0, timeout_ms: int = 0,
                  skip_barrier_block: int = -1, upload: bool = True, timing: bool = False,
-                 interpret: bool = False):
+                 interpret: bool = False, fp32: bool = False):
         self.chain = chain
+        self.dtype = np.float32 if fp32 else np.float64
         self.own_ctx = ctx is None
         if ctx is None:
             cfg = ops_config_default()
@@ -41,6 +42,7 @@ class ChainRunner:
             cfg.test_skip_barrier_block = skip_barrier_block
             cfg.timing = 1 if timing else 0
             cfg.interpret = 1 if interpret else 0
+            cfg.real = 1 if fp32 else 0
             ctx = ops_init(cfg)
         else:
             ops_set_mode(ctx, MODES[mode], tile, segment)
@@ -50,7 +52,7 @@ class ChainRunner:
         self.dats = [ops_decl_dat(ctx, self.block, c.size, c.d_m, c.d_p, name=d.name) for d in c.dats]
         if upload:
             for h, d in zip(self.dats, c.dats):
-                ops_dat_upload(ctx, h, d.init)
+                ops_dat_upload(ctx, h, d.init, self.dtype)
         self.stencils = [ops_decl_stencil(ctx, c.ndim, pts) for pts in c.stencils]
         self.reds = [ops_decl_reduction(ctx, op) for op in c.reductions]
         self.dt = 1.0
@@ -63,7 +65,7 @@ class ChainRunner:
 
     def upload(self):
         for h, d in zip(self.dats, self.chain.dats):
-            ops_dat_upload(self.ctx, h, d.init)
+            ops_dat_upload(self.ctx, h, d.init, self.dtype)
 
     def _marshal(self):
         """ctypes arguments of every loop, built once; only constants change per step."""
@@ -128,7 +130,7 @@ class ChainRunner:
         return self.history
 
     def fetch(self) -> List[np.ndarray]:
-        return [ops_dat_fetch(self.ctx, h) for h in self.dats]
+        return [ops_dat_fetch(self.ctx, h, dtype=self.dtype) for h in self.dats]
 
     def stats(self) -> dict:
         return ops_last_stats(self.ctx)

@@ -616,7 +616,7 @@ __global__ void __launch_bounds__(kThreads) k_overlap(const DLoop* __restrict__ 
     for (int d = 0; d < ndats; ++d) {
       const OvDat D = dats[d];
       const int* fb = foot + ((size_t)t * ndats + d) * 6;
-      copy_box(fb, fb, area + D.smem_off, D.spitch, D.splane, D.src, nullptr, D.gpitch, D.gplane, true);
+      copy_box<double>(fb, fb, area + D.smem_off, D.spitch, D.splane, D.src, nullptr, D.gpitch, D.gplane, true);
     }
     for (int l = 0; l < nloops; ++l) {
       const int* bx = boxes + ((size_t)t * nloops + l) * 6;
@@ -646,7 +646,7 @@ __global__ void __launch_bounds__(kThreads) k_overlap(const DLoop* __restrict__ 
       const OvDat D = dats[d];
       if (!D.written) continue;
       const int* fb = foot + ((size_t)t * ndats + d) * 6;
-      copy_box(ob, fb, area + D.smem_off, D.spitch, D.splane, nullptr, D.dst, D.gpitch, D.gplane, false);
+      copy_box<double>(ob, fb, area + D.smem_off, D.spitch, D.splane, nullptr, D.dst, D.gpitch, D.gplane, false);
     }
   }
 }

@@ -66,14 +66,15 @@ __device__ __forceinline__ DD block_combine(int op, DD v, DD* sh) {
 // Copy a box between a global dat (strides gp, gq) and a shared footprint
 // whose origin is the box corner fb (strides sp, sq); rows are spread over
 // the warps, x over the lanes (coalesced).
-__device__ __forceinline__ void copy_box(const int* box, const int* fb, double* sm, int sp, int sq, const double* g0,
-                                         double* g1, long long gp, long long gq, bool to_shared) {
+template <class T>
+__device__ __forceinline__ void copy_box(const int* box, const int* fb, T* sm, int sp, int sq, const T* g0, T* g1,
+                                         long long gp, long long gq, bool to_shared) {
   const int nx = box[1] - box[0], ny = box[3] - box[2], nz = box[5] - box[4];
   if (nx <= 0 || ny <= 0 || nz <= 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int r = warp; r < ny * nz; r += nw) {
     const int y = box[2] + r % ny, z = box[4] + r / ny;
-    double* s = sm + (long long)(z - fb[4]) * sq + (long long)(y - fb[2]) * sp - fb[0];
+    T* s = sm + (long long)(z - fb[4]) * sq + (long long)(y - fb[2]) * sp - fb[0];
     const long long g = (long long)y * gp + (long long)z * gq;
     if (to_shared)
       for (int x = box[0] + lane; x < box[1]; x += 32) s[x] = g0[g + x];

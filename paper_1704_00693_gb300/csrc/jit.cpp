@@ -247,9 +247,21 @@ struct LoopGen {
   std::vector<std::pair<int64_t, int64_t>> classes;
   std::ostringstream& os;
   bool ov = false;                    // overlapped tile: dats in shared footprints, owned-point reductions
+  bool f32 = false;                   // FP32 dats and arithmetic
+  const char* T = "double";
+  const char *fadd = "__dadd_rn", *fsub = "__dsub_rn", *fmul = "__dmul_rn", *fdiv = "__ddiv_rn", *ffma = "__fma_rn";
 
-  LoopGen(const DLoop& l, const std::vector<char>& r, std::ostringstream& o, bool overlapped = false)
-      : L(l), ro(r), os(o), ov(overlapped) {
+  LoopGen(const DLoop& l, const std::vector<char>& r, std::ostringstream& o, bool overlapped = false,
+          bool single = false)
+      : L(l), ro(r), os(o), ov(overlapped), f32(single) {
+    if (f32) {
+      T = "float";
+      fadd = "__fadd_rn";
+      fsub = "__fsub_rn";
+      fmul = "__fmul_rn";
+      fdiv = "__fdiv_rn";
+      ffma = "__fmaf_rn";
+    }
     cls.assign(L.nargs, -1);
     for (int a = 0; a < L.nargs; ++a) {
       if (L.args[a].kind != OPS_ARG_DAT) continue;
@@ -274,8 +286,8 @@ struct LoopGen {
   // the IR of one loop for points 0..np-1 (instruction-major)
   void emit_points(int np) const {
     for (int p = 0; p < np; ++p) {
-      os << "    double";
-      for (int r = 0; r < kNReg; ++r) os << (r ? ", " : " ") << dbl_sfx(r, p) << " = 0.0";
+      os << "    " << T;
+      for (int r = 0; r < kNReg; ++r) os << (r ? ", " : " ") << dbl_sfx(r, p) << " = 0";
       os << ";\n";
       if (ov && L.nreds)  // redundant points of a tile compute but do not reduce
         os << "    const bool own" << p << " = x >= ob[0] && x < ob[1] && y + " << p << " >= ob[2] && y + " << p
@@ -294,12 +306,12 @@ struct LoopGen {
               os << "    " << R(d) << " = " << load(a, b, p) << ";\n";
             break;
           case OPS_IR_CST: os << "    " << R(d) << " = K" << a << ";\n"; break;
-          case OPS_IR_ADD: os << "    " << R(d) << " = __dadd_rn(" << R(a) << ", " << R(b) << ");\n"; break;
-          case OPS_IR_SUB: os << "    " << R(d) << " = __dsub_rn(" << R(a) << ", " << R(b) << ");\n"; break;
-          case OPS_IR_MUL: os << "    " << R(d) << " = __dmul_rn(" << R(a) << ", " << R(b) << ");\n"; break;
-          case OPS_IR_DIV: os << "    " << R(d) << " = __ddiv_rn(" << R(a) << ", " << R(b) << ");\n"; break;
+          case OPS_IR_ADD: os << "    " << R(d) << " = " << fadd << "(" << R(a) << ", " << R(b) << ");\n"; break;
+          case OPS_IR_SUB: os << "    " << R(d) << " = " << fsub << "(" << R(a) << ", " << R(b) << ");\n"; break;
+          case OPS_IR_MUL: os << "    " << R(d) << " = " << fmul << "(" << R(a) << ", " << R(b) << ");\n"; break;
+          case OPS_IR_DIV: os << "    " << R(d) << " = " << fdiv << "(" << R(a) << ", " << R(b) << ");\n"; break;
           case OPS_IR_FMA:
-            os << "    " << R(d) << " = __fma_rn(" << R(a) << ", " << R(b) << ", " << R(c) << ");\n";
+            os << "    " << R(d) << " = " << ffma << "(" << R(a) << ", " << R(b) << ", " << R(c) << ");\n";
             break;
           case OPS_IR_MIN:
             os << "    " << R(d) << " = (" << R(b) << " < " << R(a) << ") ? " << R(b) << " : " << R(a) << ";\n";
@@ -313,28 +325,29 @@ struct LoopGen {
           case OPS_IR_WSUM:
           case OPS_IR_WACC: {
             const int n = L.args[a].npts;
-            os << "    { double t = ";
+            os << "    { " << T << " t = ";
             int q = 0;
             if (op == OPS_IR_WSUM) {
-              os << "__dmul_rn(K" << b << ", " << load(a, 0, p) << ");\n";
+              os << fmul << "(K" << b << ", " << load(a, 0, p) << ");\n";
               q = 1;
             } else {
               os << R(d) << ";\n";
             }
-            for (; q < n; ++q) os << "      t = __fma_rn(K" << (b + q) << ", " << load(a, q, p) << ", t);\n";
+            for (; q < n; ++q) os << "      t = " << ffma << "(K" << (b + q) << ", " << load(a, q, p) << ", t);\n";
             os << "      " << R(d) << " = t; }\n";
             break;
           }
           case OPS_IR_POLY: {
-            os << "    { double t = K" << (b + c) << ";\n";
-            for (int i = c - 1; i >= 0; --i) os << "      t = __fma_rn(t, " << R(a) << ", K" << (b + i) << ");\n";
+            os << "    { " << T << " t = K" << (b + c) << ";\n";
+            for (int i = c - 1; i >= 0; --i)
+              os << "      t = " << ffma << "(t, " << R(a) << ", K" << (b + i) << ");\n";
             os << "      " << R(d) << " = t; }\n";
             break;
           }
           case OPS_IR_ST: {
             const std::string q = "p" + std::to_string(d) + "[" + idx(d, p) + "]";
             if (L.args[d].access == OPS_INC)
-              os << "    " << q << " = __dadd_rn(" << q << ", " << R(a) << ");\n";
+              os << "    " << q << " = " << fadd << "(" << q << ", " << R(a) << ");\n";
             else
               os << "    " << q << " = " << R(a) << ";\n";
             break;
@@ -343,10 +356,11 @@ struct LoopGen {
             const int k = L.args[d].slot;
             const int rop = L.red_op[k];
             const char* f = rop == OPS_RED_SUM ? "red_sum" : (rop == OPS_RED_MIN ? "red_min" : "red_max");
+            // a float value converts to double exactly
             if (ov)
-              os << "    if (own" << p << ") acc" << k << " = " << f << "(acc" << k << ", " << R(a) << ");\n";
+              os << "    if (own" << p << ") acc" << k << " = " << f << "(acc" << k << ", (double)" << R(a) << ");\n";
             else
-              os << "    acc" << k << " = " << f << "(acc" << k << ", " << R(a) << ");\n";
+              os << "    acc" << k << " = " << f << "(acc" << k << ", (double)" << R(a) << ");\n";
             break;
           }
           default: break;
@@ -385,19 +399,19 @@ struct LoopGen {
       if (L.args[a].kind == OPS_ARG_DAT) {
         if (ov) {
           const int k = L.args[a].slot;
-          os << "  double* p" << a << " = area + " << lay->smem_off[k] << " - (ft[" << 6 * k << "] + (i64)ft["
+          os << "  " << T << "* p" << a << " = (" << T << "*)area + " << lay->smem_off[k] << " - (ft[" << 6 * k << "] + (i64)ft["
              << 6 * k + 2 << "] * " << lay->spitch[k] << " + (i64)ft[" << 6 * k + 4 << "] * " << lay->splane[k]
              << ");\n";
         }
         else if (ro[a])
-          os << "  const double* __restrict__ p" << a << " = L->args[" << a << "].ptr0;\n";
+          os << "  const " << T << "* __restrict__ p" << a << " = (const " << T << "*)L->args[" << a << "].ptr0;\n";
         else
-          os << "  double* p" << a << " = L->args[" << a << "].ptr0;\n";
+          os << "  " << T << "* p" << a << " = (" << T << "*)L->args[" << a << "].ptr0;\n";
       }
-      if (sused[a]) os << "  const double s" << a << " = scal[L->args[" << a << "].slot];\n";
+      if (sused[a]) os << "  const " << T << " s" << a << " = (" << T << ")scal[L->args[" << a << "].slot];\n";
     }
     for (int k = 0; k < OPS_MAX_CONSTS; ++k)
-      if (kused[k]) os << "  const double K" << k << " = L->K[" << k << "];\n";
+      if (kused[k]) os << "  const " << T << " K" << k << " = (" << T << ")L->K[" << k << "];\n";
     for (int k = 0; k < L.nreds; ++k) os << "  DD acc" << k << " = dd_of(red_identity(" << L.red_op[k] << "));\n";
     // one point
     os << "  auto one = [&](int x, int y, int z) {\n";
@@ -431,14 +445,15 @@ struct LoopGen {
 };
 
 // Source of the kernels u<l0> .. u<l1-1> for loops[l0..l1) of a segment.
-std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::vector<char>>& ro) {
+std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::vector<char>>& ro, int es) {
   std::ostringstream os;
-  os << "// opstile compiled loop bodies: " << kJitPts << " rows per unit, " << kJitMinCtas << " CTAs per SM\n";
+  os << "// opstile compiled loop bodies: " << kJitPts << " rows per unit, " << kJitMinCtas << " CTAs per SM, "
+     << (es == 4 ? "fp32" : "fp64") << "\n";
   os << kPrelude << kDeviceCommon << kPreludeTail;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
   os << "static_assert(sizeof(DArg) == " << sizeof(DArg) << ", \"DArg layout\");\n";
   for (int i = l0; i < l1; ++i) {
-    LoopGen g(loops[i], ro[i], os);
+    LoopGen g(loops[i], ro[i], os, false, es == 4);
     g.emit(i);
     os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas << ") u" << i
        << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
@@ -486,13 +501,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 
 std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay) {
   std::ostringstream os;
-  os << "// opstile overlapped tiles: " << kOvThreads << " threads, " << kOvPts << " rows per unit\n";
+  const bool f32 = lay.es == 4;
+  const char* T = f32 ? "float" : "double";
+  os << "// opstile overlapped tiles: " << kOvThreads << " threads, " << kOvPts << " rows per unit, "
+     << (f32 ? "fp32" : "fp64") << "\n";
   os << kPrelude << kDeviceCommon << kPreludeTail << kOvTma;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
   os << "static_assert(sizeof(OvDat) == " << sizeof(OvDat) << ", \"OvDat layout\");\n";
   const std::vector<char> none(OPS_MAX_ARGS, 0);
   for (int i = 0; i < count; ++i) {
-    LoopGen g(loops[i], none, os, true);
+    LoopGen g(loops[i], none, os, true, f32);
     g.emit(i, &lay);
   }
   const int nd = lay.ndats;
@@ -514,7 +532,8 @@ std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay)
   os << "    unsigned bytes = 0;\n";
   for (int k = 0; k < nd; ++k)
     os << "    bytes += (unsigned)(ft[" << 6 * k + 1 << "] - ft[" << 6 * k << "]) * (unsigned)(ft[" << 6 * k + 3
-       << "] - ft[" << 6 * k + 2 << "]) * (unsigned)(ft[" << 6 * k + 5 << "] - ft[" << 6 * k + 4 << "]) * 8u;\n";
+       << "] - ft[" << 6 * k + 2 << "]) * (unsigned)(ft[" << 6 * k + 5 << "] - ft[" << 6 * k + 4 << "]) * "
+       << lay.es << "u;\n";
   os << "    __syncthreads();  // the previous tile's reads and write-back are done\n"
         "    asm volatile(\"fence.proxy.async.shared::cta;\" ::: \"memory\");\n"
         "    if (threadIdx.x == 0) mbar_expect_tx(&g_mbar, bytes);\n"
@@ -526,10 +545,11 @@ std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay)
        << "      if (nx > 0 && ny > 0 && nz > 0)\n"
        << "        for (int r = threadIdx.x; r < ny * nz; r += blockDim.x) {\n"
        << "          const int y = ft[" << o + 2 << "] + r % ny, z = ft[" << o + 4 << "] + r / ny;\n"
-       << "          bulk_to_shared(area + " << lay.smem_off[k] << " + (i64)(z - ft[" << o + 4 << "]) * "
-       << lay.splane[k] << " + (i64)(y - ft[" << o + 2 << "]) * " << lay.spitch[k] << ",\n"
-       << "                         dats[" << k << "].src + (i64)y * dats[" << k << "].gpitch + (i64)z * dats[" << k
-       << "].gplane + ft[" << o << "], (unsigned)nx * 8u, &g_mbar);\n"
+       << "          bulk_to_shared((" << T << "*)area + " << lay.smem_off[k] << " + (i64)(z - ft[" << o + 4
+       << "]) * " << lay.splane[k] << " + (i64)(y - ft[" << o + 2 << "]) * " << lay.spitch[k] << ",\n"
+       << "                         (const " << T << "*)dats[" << k << "].src + (i64)y * dats[" << k
+       << "].gpitch + (i64)z * dats[" << k << "].gplane + ft[" << o << "], (unsigned)nx * " << lay.es
+       << "u, &g_mbar);\n"
        << "        }\n    }\n";
   }
   os << "    bool late = !mbar_wait(&g_mbar, phase, timeout_ns);\n"
@@ -548,9 +568,9 @@ std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay)
   }
   for (int k = 0; k < nd; ++k)
     if (lay.written[k])
-      os << "    copy_box(ob, ft + " << 6 * k << ", area + " << lay.smem_off[k] << ", " << lay.spitch[k] << ", "
-         << lay.splane[k] << ", nullptr, dats[" << k << "].dst, dats[" << k << "].gpitch, dats[" << k
-         << "].gplane, false);\n";
+      os << "    copy_box<" << T << ">(ob, ft + " << 6 * k << ", (" << T << "*)area + " << lay.smem_off[k] << ", "
+         << lay.spitch[k] << ", " << lay.splane[k] << ", nullptr, (" << T << "*)dats[" << k << "].dst, dats[" << k
+         << "].gpitch, dats[" << k << "].gplane, false);\n";
   os << "  }\n}\n";
   return os.str();
 }
@@ -649,7 +669,7 @@ std::string cache_base(const std::string& src) {
 }
 }  // namespace
 
-int jit_segment(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro,
+int jit_segment(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
                 JitSegment** out, std::string* why, double* compile_ms) {
   *out = nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
@@ -658,7 +678,7 @@ int jit_segment(int device, const DLoop* loops, int count, const std::vector<std
   std::vector<std::string> srcs;
   std::string all;
   for (int l0 = 0; l0 < count; l0 += kJitChunk) {
-    srcs.push_back(generate(loops, l0, std::min(count, l0 + kJitChunk), ro));
+    srcs.push_back(generate(loops, l0, std::min(count, l0 + kJitChunk), ro, es));
     all += srcs.back();
   }
   auto skey = std::make_pair(device, all);
@@ -729,13 +749,13 @@ int jit_segment(int device, const DLoop* loops, int count, const std::vector<std
   return OPS_OK;
 }
 
-int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, std::string* src,
-                     std::string* why, double* compile_ms) {
+int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                     std::string* src, std::string* why, double* compile_ms) {
   std::lock_guard<std::mutex> lk(g_mu);
   std::vector<std::string> srcs;
   src->clear();
   for (int l0 = 0; l0 < count; l0 += kJitChunk) {
-    srcs.push_back(generate(loops, l0, std::min(count, l0 + kJitChunk), ro));
+    srcs.push_back(generate(loops, l0, std::min(count, l0 + kJitChunk), ro, es));
     *src += srcs.back();
   }
   if (!api_ready(why, true)) {

@@ -18,18 +18,19 @@ struct JitSegment;
 
 // Kernels for the segment whose descriptors are loops[0..count) (as filled
 // for this flush; only the fields that shape the code are used) and whose
-// dat arguments are read-only in the whole segment where ro[l][a] != 0.
+// dat arguments are read-only in the whole segment where ro[l][a] != 0;
+// es = 4 generates FP32 dats and arithmetic, 8 FP64.
 // On success *out is a module shared by every context of the process with
 // the same device and code.  Returns OPS_OK with *out == nullptr, and the
 // reason in *why, when run-time compilation is unavailable.
-int jit_segment(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro,
+int jit_segment(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
                 JitSegment** out, std::string* why, double* compile_ms);
 
 // Host only: the generated source of the segment, compiled for sm_103a
 // without loading it (no device needed).  OPS_ERR_CUDA with the compiler's
 // log in *why when it does not compile; OPS_ERR_NO_DEVICE without NVRTC.
-int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, std::string* src,
-                     std::string* why, double* compile_ms);
+int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                     std::string* src, std::string* why, double* compile_ms);
 
 // One launch of loop i of the segment over box (grid-stride units, the
 // interpreter's enumeration); reductions assign (assign = 1) or combine
@@ -42,6 +43,7 @@ cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const D
 // in shared-memory layout (DAT args: pitch / plane / off in footprint
 // strides, slot = the run's dat index).
 struct OvLayout {
+  int es = 8;  // bytes per element (8: FP64, 4: FP32); offsets and strides count elements
   int ndats = 0;
   std::vector<int> smem_off, spitch, splane, written;  // per dat of the run
 };

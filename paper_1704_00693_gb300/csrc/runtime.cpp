@@ -92,6 +92,7 @@ struct TuneRec {
 
 struct ops_ctx_s {
   ops_config cfg;
+  int es = 8;  // bytes per dat element: 8 (FP64) or 4 (FP32)
   bool host_only = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
@@ -161,6 +162,10 @@ int cuda_fail(ops_ctx c, cudaError_t e, const char* what) {
     cudaError_t e_ = (expr);                           \
     if (e_ != cudaSuccess) return cuda_fail(c, e_, #expr); \
   } while (0)
+
+// Address `n` elements of `es` bytes from p (dat pointers are kept as double*
+// whatever the element type).
+inline double* elem_at(double* p, int64_t n, int es) { return (double*)((char*)p + (int64_t)es * n); }
 
 int dev_alloc(ops_ctx c, void** p, size_t bytes) {
   if (c->cfg.hbm_budget > 0 && c->allocated + (int64_t)bytes > c->cfg.hbm_budget)
@@ -389,7 +394,7 @@ PLoop plan_loop(ops_ctx c, const QLoop& q) {
   return p;
 }
 
-// Automatic tile size (Sec. 4.C, adapted): bytes per grid point = 8 x the
+// Automatic tile size (Sec. 4.C, adapted): bytes per grid point = element size x the
 // number of distinct dats of the segment; rows stay whole (x untiled, so
 // every access is a long coalesced row) and the outermost tiled dimension
 // gets as many points as fit the L2 budget.
@@ -409,7 +414,7 @@ void auto_tile(ops_ctx c, const std::vector<PLoop>& pl, int ndim, int tile[3]) {
     }
   }
   const int64_t budget = c->cfg.l2_bytes > 0 ? c->cfg.l2_bytes : (c->l2_size > 0 ? c->l2_size * 3 / 4 : 96ll << 20);
-  const int64_t bpp = 8ll * std::max(1, ndat);
+  const int64_t bpp = (int64_t)c->es * std::max(1, ndat);
   int64_t pts = std::max<int64_t>(1, budget / bpp);
   for (int d = 0; d < 3; ++d) tile[d] = std::max(1, hi[d] - lo[d]);
   // shrink the outermost dimensions first until a tile fits the budget
@@ -585,14 +590,15 @@ int overlap_plan(ops_ctx c, int first, int n, const int* tile_in, OverlapPlan** 
       if (empty) {
         for (int d = 0; d < 6; ++d) F[d] = 0;
       } else {
-        // x widened to even grid coordinates: grid x = 0 starts a 128-byte
-        // line and pitch and plane are multiples of 16, so footprint rows
-        // then move as whole 16-byte bulk copies.  The widening reaches at
-        // most one double into the row padding on either side, which the
-        // library's layout always holds (x = 0 sits at the rounded-up front
-        // halo; the pitch rounds the row up to 16 doubles).
-        F[0] -= F[0] & 1;
-        F[1] += F[1] & 1;
+        // x widened to multiples of v = 16 bytes / element: grid x = 0
+        // starts a 128-byte line and pitch and plane are whole lines, so
+        // footprint rows then move as whole 16-byte bulk copies.  The
+        // widening stays inside the row's 128-byte lines, which the
+        // library's layout always holds (x = 0 sits at the line-rounded
+        // front halo; the pitch rounds the row up to whole lines).
+        const int v = 16 / c->es;
+        F[0] -= ((F[0] % v) + v) % v;
+        F[1] += (v - ((F[1] % v) + v) % v) % v;
       }
       std::memcpy(&foot6d[6 * k], F, sizeof F);
     }
@@ -607,9 +613,10 @@ int overlap_plan(ops_ctx c, int first, int n, const int* tile_in, OverlapPlan** 
         (*sq)[k] = q;
         (*so)[k] = (int)off;
       }
-      off += ((int64_t)q * std::max(1, m[3 * k + 2]) + 1) / 2 * 2;
+      const int64_t v = 16 / c->es;  // regions start on 16-byte boundaries
+      off += ((int64_t)q * std::max(1, m[3 * k + 2]) + v - 1) / v * v;
     }
-    return off * 8;
+    return off * c->es;
   };
   std::unique_ptr<OverlapPlan> np;
   std::vector<int> one_box((size_t)6 * n), one_foot((size_t)6 * nd), own6(6);
@@ -719,8 +726,9 @@ std::vector<DLoop> overlap_descriptors(ops_ctx c, int first, const std::vector<D
   return ol;
 }
 
-OvLayout overlap_layout(const OverlapPlan* op) {
+OvLayout overlap_layout(const OverlapPlan* op, int es) {
   OvLayout lay;
+  lay.es = es;
   lay.ndats = op->ndats;
   lay.smem_off = op->smem_off;
   lay.spitch = op->spitch;
@@ -742,7 +750,7 @@ int run_overlap_plan(ops_ctx c, int first, const std::vector<DLoop>& hl, const O
     if (op->written[k] && !D.alt) {
       rc = dev_alloc(c, (void**)&D.alt, D.bytes);
       if (rc) return rc;
-      D.alt_ptr0 = D.alt + (D.ptr0 - D.alloc);
+      D.alt_ptr0 = (double*)((char*)D.alt + ((char*)D.ptr0 - (char*)D.alloc));
     }
     ov[k].src = D.ptr0;
     ov[k].dst = op->written[k] ? D.alt_ptr0 : nullptr;
@@ -768,6 +776,7 @@ int run_overlap_plan(ops_ctx c, int first, const std::vector<DLoop>& hl, const O
   int grid = 0;
   if (jo) grid = std::min({op->ntiles, jit_overlap_max_grid(jo, c->num_sms, op->area_bytes), c->part_stride});
   if (grid <= 0) jo = nullptr;
+  if (!jo && c->es == 4) return fail(c, OPS_ERR_INVALID_ARG, "FP32 overlapped tiles run compiled bodies only");
   if (!jo) grid = std::max(1, std::min({op->ntiles, overlap_max_grid(c->num_sms, op->area_bytes), c->part_stride}));
   c->stats.compiled = jo ? 1 : 0;
   if (nrows) {
@@ -858,7 +867,7 @@ int segment_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, 
   JitSegment* s = nullptr;
   std::string why;
   double ms = 0.0;
-  const int rc = jit_segment(c->cfg.device, hl.data() + first, count, ro, &s, &why, &ms);
+  const int rc = jit_segment(c->cfg.device, hl.data() + first, count, ro, c->es, &s, &why, &ms);
   c->stats.compile_ms += ms;
   if (rc) return fail(c, rc, "compiling loop bodies: %s", why.c_str());
   if (!s) c->jit_why = why;
@@ -894,7 +903,7 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
     if (!runs.empty() && !c->cfg.interpret && !c->cfg.check) {
       std::vector<OvRequest> reqs;
       for (size_t r = 0; r < runs.size(); ++r)
-        reqs.push_back(OvRequest{ols[r].data(), runs[r].second->nloops, overlap_layout(runs[r].second)});
+        reqs.push_back(OvRequest{ols[r].data(), runs[r].second->nloops, overlap_layout(runs[r].second, c->es)});
       std::string why;
       double ms = 0.0;
       int rc = jit_overlap_many(c->cfg.device, reqs, &jos, &why, &ms);
@@ -925,6 +934,9 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
   int rcj = segment_code(c, first, count, hl, &js);
   if (rcj) return rcj;
   c->stats.compiled = js ? 1 : 0;
+  if (!js && c->es == 4)
+    return fail(c, OPS_ERR_INVALID_ARG, "FP32 loops run compiled bodies only (no checked or interpreted mode%s%s)",
+                c->jit_why.empty() ? "" : "; ", c->jit_why.c_str());
   if (mode == OPS_MODE_UNTILED || count == 1) {
     for (int i = 0; i < count; ++i) {
       const QLoop& q = c->queue[first + i];
@@ -1293,6 +1305,8 @@ int ops_init(ops_ctx* out, const ops_config* cfg) {
   std::unique_ptr<ops_ctx_s> c(new ops_ctx_s);
   if (cfg) c->cfg = *cfg;
   else ops_config_default(&c->cfg);
+  if (c->cfg.real != OPS_REAL_F64 && c->cfg.real != OPS_REAL_F32) return OPS_ERR_INVALID_ARG;
+  c->es = c->cfg.real == OPS_REAL_F32 ? 4 : 8;
   std::memset(&c->stats, 0, sizeof c->stats);
   if (c->cfg.device < 0) {  // host-only: declarations, validation and planning
     c->host_only = true;
@@ -1411,16 +1425,18 @@ int ops_decl_dat(ops_ctx c, int block, const int size[3], const int d_m[3], cons
     D.pitch = pitch;
     D.plane = plane;
   } else {
-    // point x = 0 starts a 128-byte line: pad the row front to round_up(d_m, 16)
-    const int64_t xo = (D.dm[0] + 15) / 16 * 16;
-    D.pitch = (xo + D.size[0] + D.dp[0] + 15) / 16 * 16;
+    // point x = 0 starts a 128-byte line: pad the row front to a whole
+    // number of lines, and the row to whole lines
+    const int64_t line = 128 / c->es;
+    const int64_t xo = (D.dm[0] + line - 1) / line * line;
+    D.pitch = (xo + D.size[0] + D.dp[0] + line - 1) / line * line;
     D.plane = D.pitch * D.ext[1];
-    D.bytes = sizeof(double) * (size_t)(D.plane * D.ext[2]);
+    D.bytes = (size_t)c->es * (size_t)(D.plane * D.ext[2]);
     if (!c->host_only) {
       int rc = dev_alloc(c, (void**)&D.alloc, D.bytes);
       if (rc) return rc;
       CUDA_TRY(c, cudaMemsetAsync(D.alloc, 0, D.bytes, c->stream));
-      D.ptr0 = D.alloc + xo + D.pitch * D.dm[1] + D.plane * D.dm[2];
+      D.ptr0 = elem_at(D.alloc, xo + D.pitch * D.dm[1] + D.plane * D.dm[2], c->es);
     }
   }
   c->dats.push_back(D);
@@ -1545,7 +1561,7 @@ int ops_reduction_result(ops_ctx c, int red, double* host_out) {
 // Copy a dat between its device allocation box and a dense host array
 // (x fastest), after flushing the queue; to_host selects the direction.
 // wait = 0 leaves the copy queued on the context's stream.
-int dat_copy(ops_ctx c, int dat, double* host, int64_t nelems, bool to_host, bool wait) {
+int dat_copy(ops_ctx c, int dat, void* host, int64_t nelems, bool to_host, bool wait) {
   if (!c || !host) return OPS_ERR_INVALID_ARG;
   if (dat < 0 || dat >= (int)c->dats.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad dat %d", dat);
   const Dat& D0 = c->dats[dat];
@@ -1556,11 +1572,11 @@ int dat_copy(ops_ctx c, int dat, double* host, int64_t nelems, bool to_host, boo
   int rc = flush(c);
   if (rc) return rc;
   const Dat& D = c->dats[dat];  // the flush may have moved it to its other buffer
-  double* base = D.ptr0 - D.dm[0] - D.pitch * D.dm[1] - D.plane * D.dm[2];
-  const size_t hrow = sizeof(double) * D.ext[0], drow = sizeof(double) * D.pitch;
+  char* base = (char*)elem_at(D.ptr0, -(D.dm[0] + D.pitch * D.dm[1] + D.plane * D.dm[2]), c->es);
+  const size_t es = (size_t)c->es, hrow = es * D.ext[0], drow = es * D.pitch;
   for (int z = 0; z < D.ext[2]; ++z) {
-    double* h = host + (size_t)z * D.ext[0] * D.ext[1];
-    double* d = base + (size_t)z * D.plane;
+    char* h = (char*)host + es * (size_t)z * D.ext[0] * D.ext[1];
+    char* d = base + es * (size_t)z * D.plane;
     if (to_host)
       CUDA_TRY(c, cudaMemcpy2DAsync(h, hrow, d, drow, hrow, D.ext[1], cudaMemcpyDeviceToHost, c->stream));
     else
@@ -1569,20 +1585,20 @@ int dat_copy(ops_ctx c, int dat, double* host, int64_t nelems, bool to_host, boo
   return wait ? check_device_error(c) : OPS_OK;
 }
 
-int ops_dat_fetch(ops_ctx c, int dat, double* host_out, int64_t nelems) {
+int ops_dat_fetch(ops_ctx c, int dat, void* host_out, int64_t nelems) {
   return dat_copy(c, dat, host_out, nelems, true, true);
 }
 
-int ops_dat_upload(ops_ctx c, int dat, const double* host_in, int64_t nelems) {
-  return dat_copy(c, dat, const_cast<double*>(host_in), nelems, false, true);
+int ops_dat_upload(ops_ctx c, int dat, const void* host_in, int64_t nelems) {
+  return dat_copy(c, dat, const_cast<void*>(host_in), nelems, false, true);
 }
 
-int ops_dat_fetch_async(ops_ctx c, int dat, double* host_out, int64_t nelems) {
+int ops_dat_fetch_async(ops_ctx c, int dat, void* host_out, int64_t nelems) {
   return dat_copy(c, dat, host_out, nelems, true, false);
 }
 
-int ops_dat_upload_async(ops_ctx c, int dat, const double* host_in, int64_t nelems) {
-  return dat_copy(c, dat, const_cast<double*>(host_in), nelems, false, false);
+int ops_dat_upload_async(ops_ctx c, int dat, const void* host_in, int64_t nelems) {
+  return dat_copy(c, dat, const_cast<void*>(host_in), nelems, false, false);
 }
 
 int ops_dat_info(ops_ctx c, int dat, double** dev_ptr0, int64_t* pitch, int64_t* plane, int* ext) {
@@ -1662,11 +1678,12 @@ int ops_compile_queued(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, 
   }
   std::string src, why;
   double ms = 0.0;
-  int rc = jit_compile_only(hl.data(), n, ro, &src, &why, &ms);
+  int rc = jit_compile_only(hl.data(), n, ro, c->es, &src, &why, &ms);
   if (!rc) {
     // the overlapped-tile form of the same loops, with each dat's own strides as its footprint strides
     std::map<int, int> local;
     OvLayout lay;
+    lay.es = c->es;
     std::vector<DLoop> ol(hl);
     for (int i = 0; i < n; ++i) {
       const QLoop& q = c->queue[i];

@@ -211,10 +211,13 @@ def test_library_overlapped_tiles_match_oracle(lib, ndim):
                     assert all(foot[k, d, 1] < foot[k, d, 0] for d in range(ndim)), f"tile {owned} dat {k} unread"
 
 
-@pytest.mark.parametrize("name", ["small2d", "cloverleaf2d", "cloverleaf3d", "opensbli3d", "edge"])
-def test_generated_loop_bodies_compile(lib, name):
-    """The CUDA generated from each workload's IR compiles for sm_103a
-    (NVRTC, no device needed), and every loop gets its kernel."""
+@pytest.mark.parametrize("name,fp32", [("small2d", False), ("cloverleaf2d", False), ("cloverleaf3d", False),
+                                       ("opensbli3d", False), ("edge", False), ("cloverleaf2d", True),
+                                       ("edge", True)])
+def test_generated_loop_bodies_compile(lib, name, fp32):
+    """The CUDA generated from each workload's IR (untiled / skewed kernels
+    and overlapped-tile kernels, FP64 or FP32) compiles for sm_103a (NVRTC,
+    no device needed), and every loop gets its kernel."""
     from paper_1704_00693_gb300.chain import ChainRunner
     if name == "edge":
         from test_gpu_chain import edge_chain
@@ -227,7 +230,10 @@ def test_generated_loop_bodies_compile(lib, name):
         c = W.cloverleaf3d(n=12, steps=1)
     else:
         c = W.opensbli3d(n=12, steps=1)
-    ctx = host_ctx()
+    cfg = ops.ops_config_default()
+    cfg.device = ops.OPS_DEVICE_NONE
+    cfg.real = ops.OPS_REAL_F32 if fp32 else ops.OPS_REAL_F64
+    ctx = ops.ops_init(cfg)
     r = ChainRunner(c, ctx=ctx, upload=False, mode="untiled")
     r.enqueue_step()
     try:
@@ -239,5 +245,6 @@ def test_generated_loop_bodies_compile(lib, name):
     assert n == len(src)
     for i in range(len(c.loops)):
         assert f" u{i}(" in src
+    assert ("fp32" in src) == fp32 and ("__fmaf_rn" in src) == fp32
     ops.ops_queue_clear(ctx)
     ops.ops_finalize(ctx)

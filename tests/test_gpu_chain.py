@@ -362,3 +362,29 @@ def test_borrowed_device_dats(mode, tile):
     assert_same(c, got, ref, hist, ref_hist, what=f"borrowed {mode}")
     if mode == "overlapped":
         assert st["mode"] == ops.OPS_MODE_SKEWED
+
+
+@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 17, 0)), ("skewed", (0, 0, 0)),
+                                       ("overlapped", None), ("auto", None)])
+def test_fp32_chains_bit_exact(mode, tile):
+    """An OPS_REAL_F32 context: float dats, single-precision arithmetic with
+    explicit rounding on both sides, constants rounded to float on load; the
+    compiled kernels match the oracle's FP32 execution bit for bit in every
+    schedule (reductions of the float values within the usual bound)."""
+    for c in (W.cloverleaf2d(n=100, steps=3), W.small2d(n=256, reps=4), edge_chain()):
+        ref, ref_hist = oracle.run_chain(c, fp32=True)
+        got, hist, st = run_gpu(c, mode, tile, fp32=True)
+        assert got[0].dtype == np.float32
+        assert_same(c, got, ref, hist, ref_hist, what=f"fp32 {c.name} {mode} {tile}")
+        assert st["compiled"] == 1
+
+
+def test_fp32_refuses_interpreted_and_checked_modes():
+    c = W.small2d(n=32, reps=1)
+    for kw in (dict(interpret=True), dict(check=True)):
+        r = ChainRunner(c, mode="untiled", fp32=True, **kw)
+        try:
+            with pytest.raises(ops.OpsError):
+                r.step()
+        finally:
+            r.close()

@@ -235,3 +235,24 @@ def test_tiled_execution_equals_program_order(name, tile):
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
     assert hist == ref_hist
+
+
+def test_fp32_oracle_pins():
+    """The oracle's FP32 execution: constants preserved exactly (dyadic
+    weights), linear fields reproduced exactly by symmetric stencils, and
+    every result within a few float roundings per loop of the FP64 one."""
+    c = W.small2d(n=48, reps=2, constant=0.75)
+    got, _ = oracle.run_chain(c, fp32=True)
+    assert all(d.dtype == np.float32 and (d == np.float32(0.75)).all() for d in got)
+    a0, bx, by = 0.5, 0.25, -0.375
+    c = W.linear2d(40, a0, bx, by)
+    got32, _ = oracle.run_chain(c, fp32=True)
+    got64, _ = oracle.run_chain(c)
+    for a, b in zip(got32, got64):
+        assert np.array_equal(a.astype(np.float64), b)
+    c = W.small2d(n=64, reps=3)
+    r32, _ = oracle.run_chain(c, fp32=True)
+    r64, _ = oracle.run_chain(c)
+    nloops = len(c.loops) * c.steps
+    for a, b in zip(r32, r64):
+        assert np.abs(a.astype(np.float64) - b).max() <= 20 * nloops * 2.0 ** -24 * max(1.0, np.abs(b).max())
