@@ -11,8 +11,14 @@
 //     make the solver FP64-latency-bound on GB300); the residual
 //     r = b - A x, its norm and the correction x += |r| d are FP64
 //     (iterative refinement);
+//   - in the FP32 inner iterations the direction update p = r + beta p is
+//     fused into the next matvec: each thread recomputes it at the five
+//     stencil points from r and the previous direction (double-buffered), so
+//     an inner iteration is two sweeps (FP64 iterations keep a third sweep:
+//     the recomputation would cost FP64 fma on GB300's narrow FP64 pipe);
 //   - every problem is a state machine advanced by one CG iteration per
-//     "tick" of five kernels (sweep, scalars, sweep, scalars, sweep), so many
+//     "tick" of five kernels (sweep, scalars, sweep, scalars, and a third
+//     sweep that only applies the refinement correction), so many
 //     grids of different sizes share every launch; a problem's reductions use
 //     only its own work units in a fixed order, so its result does not depend
 //     on what else is in the batch.
@@ -79,6 +85,20 @@ __device__ __forceinline__ float av32(const OpView<float>& A, const float* u, in
   const float uN = j < n - 1 ? u[c + n] : 0.0f;
   const int64_t fx = (int64_t)j * (n + 1) + i, fy = (int64_t)j * n + i;
   float t = __fmul_rn(A.dg[c], u[c]);
+  t = __fmaf_rn(-A.kx[fx], uW, t);
+  t = __fmaf_rn(-A.kx[fx + 1], uE, t);
+  t = __fmaf_rn(-A.ky[fy], uS, t);
+  t = __fmaf_rn(-A.ky[fy + n], uN, t);
+  return t;
+}
+
+// The operator at one cell from the five values of its stencil (outside: 0),
+// in the term order of av32.
+__device__ __forceinline__ float av32v(const OpView<float>& A, int j, int i, float uC, float uW, float uE, float uS,
+                                       float uN) {
+  const int n = A.n;
+  const int64_t c = (int64_t)j * n + i, fx = (int64_t)j * (n + 1) + i, fy = (int64_t)j * n + i;
+  float t = __fmul_rn(A.dg[c], uC);
   t = __fmaf_rn(-A.kx[fx], uW, t);
   t = __fmaf_rn(-A.kx[fx + 1], uE, t);
   t = __fmaf_rn(-A.ky[fy], uS, t);
@@ -216,15 +236,28 @@ __device__ __forceinline__ void a_residual(const CgUnit& U, const OpView<double>
     a = __fma_rn(rc, rc, a);
   });
 }
-__device__ __forceinline__ void a_inner(const CgUnit& U, const OpView<float>& A, const float* p,
-                                        float* __restrict__ w, int n, double* acc) {
+// The direction update p = r + beta p_old is fused into the matvec: every
+// thread recomputes it at the five stencil points (the same fma the owner
+// of each point evaluates, so the values are identical), writes the new
+// direction of its own cell to the other buffer, and applies A to it.
+__device__ __forceinline__ void a_inner(const CgUnit& U, const OpView<float>& A, float bf, const float* po,
+                                        const float* r, float* __restrict__ pn, float* __restrict__ w, int n,
+                                        double* acc) {
   for_unit4(U, acc, [&](int j, int i, double& a) {
     const int64_t c = (int64_t)j * n + i;
-    const float wc = av32(A, p, j, i);
+    const float pC = __fmaf_rn(bf, po[c], r[c]);
+    const float pW = i > 0 ? __fmaf_rn(bf, po[c - 1], r[c - 1]) : 0.0f;
+    const float pE = i < n - 1 ? __fmaf_rn(bf, po[c + 1], r[c + 1]) : 0.0f;
+    const float pS = j > 0 ? __fmaf_rn(bf, po[c - n], r[c - n]) : 0.0f;
+    const float pN = j < n - 1 ? __fmaf_rn(bf, po[c + n], r[c + n]) : 0.0f;
+    const float wc = av32v(A, j, i, pC, pW, pE, pS, pN);
+    pn[c] = pC;
     w[c] = wc;
-    a = __fma_rn(widen(p[c]), widen(wc), a);
+    a = __fma_rn(widen(pC), widen(wc), a);
   });
 }
+// FP64 iterations keep the update in its own sweep: recomputing it at five
+// points would add four FP64 fma per cell on GB300's narrow FP64 pipe.
 __device__ __forceinline__ void a_cg64(const CgUnit& U, const OpView<double>& A, const double* p,
                                        double* __restrict__ w, int n, double* acc) {
   for_unit4(U, acc, [&](int j, int i, double& a) {
@@ -247,7 +280,8 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_a(CgProb* probs, const CgUnit
     if (st == CG_OUTER || st == CG_FINISH)
       a_residual(U, OpView<double>{P.kx, P.ky, P.dg, n}, P.x, P.b, P.r, n, acc);
     else if (st == CG_INNER)
-      a_inner(U, OpView<float>{P.kx32, P.ky32, P.dg32, n}, P.p32, P.w32, n, acc);
+      a_inner(U, OpView<float>{P.kx32, P.ky32, P.dg32, n}, (float)P.beta, P.pp ? P.p32b : P.p32, P.r32,
+              P.pp ? P.p32 : P.p32b, P.w32, n, acc);
     else if (st == CG64)
       a_cg64(U, OpView<double>{P.kx, P.ky, P.dg, n}, P.p64, P.w64, n, acc);
     const double tot = cg_block_sum_d(sum4(acc), sh);
@@ -312,7 +346,7 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit
     if (st == CG_INIT)
       b_init(U, __ddiv_rn(1.0, P.nr), P.r, P.r32, P.p32, P.d32, n, acc);
     else if (st == CG_INNER)
-      b_inner(U, (float)P.alpha, P.p32, P.w32, P.r32, P.d32, n, acc);
+      b_inner(U, (float)P.alpha, P.pp ? P.p32 : P.p32b, P.w32, P.r32, P.d32, n, acc);
     else if (st == CG64_INIT)
       b_cg64_init(U, P.b, P.x, P.r, P.p64, n, acc);
     else if (st == CG64)
@@ -322,13 +356,14 @@ __global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit
   }
 }
 
-// C sweeps, one function per state
-__device__ __forceinline__ void c_inner(const CgUnit& U, float bf, const float* r32, float* __restrict__ p32,
-                                        int n) {
+// C sweep: the refinement correction x += |r| d (FINISH) and the FP64
+// direction update p = r + beta p (CG64); the inner (FP32) direction update
+// is fused into the next A sweep
+__device__ __forceinline__ void c_cg64(const CgUnit& U, double bt, const double* r, double* __restrict__ p, int n) {
   double dummy[4];
   for_unit4(U, dummy, [&](int j, int i, double&) {
     const int64_t c = (int64_t)j * n + i;
-    p32[c] = __fmaf_rn(bf, p32[c], r32[c]);
+    p[c] = __fma_rn(bt, p[c], r[c]);
   });
 }
 __device__ __forceinline__ void c_finish(const CgUnit& U, double nr, const float* d32, double* __restrict__ x,
@@ -339,26 +374,15 @@ __device__ __forceinline__ void c_finish(const CgUnit& U, double nr, const float
     x[c] = __fma_rn(nr, (double)d32[c], x[c]);
   });
 }
-__device__ __forceinline__ void c_cg64(const CgUnit& U, double bt, const double* r, double* __restrict__ p, int n) {
-  double dummy[4];
-  for_unit4(U, dummy, [&](int j, int i, double&) {
-    const int64_t c = (int64_t)j * n + i;
-    p[c] = __fma_rn(bt, p[c], r[c]);
-  });
-}
 
-// C: search-direction update (INNER, CG64) or the refinement correction (FINISH)
 __global__ void __launch_bounds__(kCgThreads) k_cg_c(CgProb* probs, const CgUnit* units, int nunits) {
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const CgUnit U = units[u];
     const CgProb& P = probs[U.prob];
-    const int st = P.state, n = P.n;
-    if (st == CG_INNER)
-      c_inner(U, (float)P.beta, P.r32, P.p32, n);
-    else if (st == CG_FINISH)
-      c_finish(U, P.nr, P.d32, P.x, n);
-    else if (st == CG64)
-      c_cg64(U, P.beta, P.r, P.p64, n);
+    if (P.state == CG_FINISH)
+      c_finish(U, P.nr, P.d32, P.x, P.n);
+    else if (P.state == CG64)
+      c_cg64(U, P.beta, P.r, P.p64, P.n);
   }
 }
 
@@ -416,6 +440,7 @@ __global__ void k_cg_s1(CgProb* probs, const int2* ranges, int nslots, const DD*
     } else {
       P.nr = nr;
       P.state = CG_INIT;
+      P.pp = 0;  // the inner solve starts from buffer 0, which the INIT sweep fills with r
     }
   } else {
     P.alpha = P.rho / s;
@@ -435,6 +460,7 @@ __global__ void k_cg_s2(CgProb* probs, const int2* ranges, int nslots, const DD*
   if (st == CG_INIT) {
     P.rho = s;
     P.rho0 = s;
+    P.beta = 0.0;  // the first direction of every inner solve is r itself
     P.state = s > 0.0 ? CG_INNER : CG_FINISH;
   } else if (st == CG_INNER) {
     ++P.it;
@@ -443,6 +469,7 @@ __global__ void k_cg_s2(CgProb* probs, const int2* ranges, int nslots, const DD*
     } else {
       P.beta = s / P.rho;
       P.rho = s;
+      P.pp ^= 1;  // the direction the A sweep wrote becomes the old one
     }
   } else if (st == CG64_INIT) {
     P.rho = s;
@@ -478,7 +505,7 @@ size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
 int64_t cg_problem_bytes(int n) {
   const size_t N = (size_t)n * n, F = (size_t)n * (n + 1);
-  return (int64_t)(5 * al256(8 * N) + 2 * al256(8 * F) + al256(8 * N) + 2 * al256(4 * F) + 5 * al256(4 * N));
+  return (int64_t)(5 * al256(8 * N) + 2 * al256(8 * F) + al256(8 * N) + 2 * al256(4 * F) + 6 * al256(4 * N));
 }
 
 CgBatch::CgBatch(cudaStream_t stream, int num_sms) : stream_(stream), num_sms_(num_sms) {}
@@ -549,6 +576,7 @@ int CgBatch::add(int n, const double* kappa, const double* rhs, double tol, int 
   P.p32 = (float*)take(4 * N);
   P.w32 = (float*)take(4 * N);
   P.d32 = (float*)take(4 * N);
+  P.p32b = (float*)take(4 * N);
   hprob_[slot] = P;
   live_[slot] = 1;
   reported_[slot] = 0;

@@ -27,12 +27,14 @@ enum CgState : int {
 struct CgProb {
   int n, state, prec, conv;   // prec: 0 FP64 CG, 1 FP32 inner + FP64 refinement
   int it, outer, maxit, maxouter;
-  int u0, u1, pad0, pad1;     // its work units [u0, u1)
+  int u0, u1, pp, pad1;       // its work units [u0, u1); pp: which p buffer holds the current direction
   double tol, inner_tol;
   double nb, nr, rho, rho0, alpha, beta, rel, pad2;
   double *b, *x, *r, *p64, *w64, *kx, *ky, *dg;      // FP64: N, N, N, N, N, n(n+1), (n+1)n, N
   float *kx32, *ky32, *dg32, *r32, *p32, *w32, *d32;  // FP32 copies and inner vectors
-  float* pad3;
+  float* p32b;                                        // second FP32 direction buffer
+  double* pad3;
+  double* pad4;
 };
 
 // A work unit: rows [j0, j0 + nr) x columns [c0, c0 + w) of one problem.
