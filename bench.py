@@ -31,9 +31,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 N_DEFAULT = 3840
-WORKLOAD = "cloverleaf2d-shaped chain: 3840^2 FP64, halo 2, 25 dats U(0.5,1.5), 83 loops + 1 sum + 1 min reduction per step"
+def workload(n: int) -> str:
+    return (f"cloverleaf2d-shaped chain: {n}^2 FP64, halo 2, 25 dats U(0.5,1.5), 83 loops + 1 sum + 1 min "
+            "reduction per step")
 PROFILE = os.path.join(ROOT, "profiles", "chain_cloverleaf2d_3840.md")
-KERNEL_SRC = [os.path.join(ROOT, "paper_1704_00693_gb300", "csrc", f) for f in ("jit.cpp", "chain_kernels.cu")]
+KERNEL_SRC = [os.path.join(ROOT, "paper_1704_00693_gb300", "csrc", f) for f in ("jit.cpp", "chain_kernels.cu", "device_common.cuh")]
 # FP64: 2 DFMA per clock per SM on GB300 (measured 1.97 at 1995 MHz), fma = 2 flops
 FP64_DFMA_PER_CLK_SM = 2
 NUM_SMS = 152
@@ -564,7 +566,7 @@ def run_reference(args):
     line = {"metric": "loop-chain effective GB/s", "value": v, "unit": "GB/s", "impl": "reference",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"each step: the chain at {n}^2 (1/4 of the points)"},
+            "config": {"workload": workload(args.n), "sample": f"each step: the chain at {n}^2 (1/4 of the points)"},
             "cpu_baseline": {"value": v, "unit": "GB/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step the same chain at {n}^2"},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -670,7 +672,7 @@ def main():
     line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "mode": args.mode, "schedule": chosen_mode,
+            "config": {"workload": workload(n), "mode": args.mode, "schedule": chosen_mode,
                        "tile": st["tile"] if st else None,
                        "tiles": st["tiles"] if st else None, "l2": "inputs larger than L2 (25 dats, 3.0 GB)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
