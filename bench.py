@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--mode", default="auto", choices=["skewed", "untiled", "overlapped", "auto"])
+    p.add_argument("--mode", default="auto", choices=["skewed", "untiled", "overlapped", "wavefront", "auto"])
     p.add_argument("--tile", default="", help="x,y tile (0 = automatic)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")

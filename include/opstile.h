@@ -63,6 +63,19 @@ extern "C" {
  * writes every written dat into a second buffer of the same shape, which then
  * becomes the dat's storage: ops_dat_info returns the new address. */
 #define OPS_MODE_AUTO 3       /* library picks per segment */
+#define OPS_MODE_WAVEFRONT 4  /* Algorithm 1 tiles run as a dependence-driven wavefront (Sec. 4.B leaves
+                                 wavefront scheduling of the tiles to future work) */
+/* OPS_MODE_WAVEFRONT cuts the outermost dimension into thin tiles (tile[ndim-1]
+ * points; 0 = about 32768 points per tile) and leaves the other dimensions
+ * whole unless tile[] sets them.  Algorithm 1 gives every (tile, loop) phase
+ * its range; each phase then depends only on the earlier phases it conflicts
+ * with (a shared dat that one of the two writes, in intersecting regions,
+ * reads widened by their stencils).  One persistent kernel holding every loop
+ * body of the segment (compiled at run time, so this mode needs NVRTC) hands
+ * out chunks of phases in order of their dependency level, and each chunk
+ * waits only on its phase's dependencies -- no grid-wide barrier.  A segment
+ * of one loop runs untiled; with check = 1 or interpret = 1 the segment runs
+ * in OPS_MODE_SKEWED.  Results are identical to every other mode. */
 
 /* ---- argument kinds, access modes, reduction operators ---- */
 #define OPS_ARG_DAT 0    /* a dat accessed through a stencil */
@@ -122,7 +135,8 @@ typedef struct {
   int64_t hbm_budget;  /* cap on bytes the library allocates; 0 = no cap */
   int timeout_ms;      /* limit of every device-side wait (grid barriers); 0 = 2000 */
   int blocks_per_sm;   /* persistent-kernel CTAs per SM; 0 = as many as fit */
-  int test_skip_barrier_block; /* test hook: this CTA never arrives at grid barriers; -1 = off */
+  int test_skip_barrier_block; /* test hook: this CTA never arrives at grid barriers (skewed), this
+                                  work unit's completion is never counted (wavefront); -1 = off */
   int timing;          /* 1: record CUDA events around the chain kernels (kernel_ms in ops_flush_stats) */
   int interpret;       /* 1: run loop bodies through the register-IR interpreter kernels instead of
                           kernels compiled from the IR at the first flush of each segment (NVRTC) */
@@ -256,6 +270,17 @@ int ops_plan_skewed(ops_ctx ctx, const int* tile, int* out_ntiles, int* out_rang
  * hi in every dimension when no loop reads it).  Dimensions >= the loops'
  * dimensionality hold the loops' (0, 1). */
 int ops_plan_overlapped(ops_ctx ctx, const int owned[6], int* out_boxes, int* out_foot);
+/* Build the wavefront plan (OPS_MODE_WAVEFRONT) of the currently queued loops
+ * for the given tile sizes, without executing them.  counts[0..3] receive the
+ * number of (tile, loop) phases, of dependency entries, of work units and of
+ * dependency levels.  With out_phases != NULL (phase_cap ints, >= 12 per
+ * phase) phase q, in Algorithm 2 order, is described by
+ *   out_phases[12 q ..] = loop, chunks, first work unit, first dependency
+ *   entry, dependency count, level, box (x0 x1 y0 y1 z0 z1),
+ * and with out_deps != NULL (dep_cap ints) the dependency entries are the
+ * indices of earlier phases.  Call with NULL arrays to learn the sizes. */
+int ops_plan_wavefront(ops_ctx ctx, const int* tile, int64_t* counts, int* out_phases, int64_t phase_cap,
+                       int* out_deps, int64_t dep_cap);
 /* Generate the CUDA source of the compiled loop bodies for the currently
  * queued loops (as one segment) and compile it for sm_103a with NVRTC,
  * without loading it: no device is needed.  src_out (cap bytes, may be NULL)
@@ -264,6 +289,9 @@ int ops_plan_overlapped(ops_ctx ctx, const int owned[6], int* out_boxes, int* ou
  * log in ops_last_error when it does not compile; OPS_ERR_NO_DEVICE when
  * NVRTC is not installed.  The queue is left as it was. */
 int ops_compile_queued(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
+/* The same for the wavefront kernel of the queued loops (OPS_MODE_WAVEFRONT:
+ * every loop body in one kernel). */
+int ops_compile_queued_wavefront(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
 
 /* ---- heat-conduction solves (TeaLeaf-shaped, Sec. 5 and Sec. 6.D) ----
  * Solve A x = b on an n x n cell grid for the implicit heat-conduction

@@ -192,6 +192,55 @@ def run_chain_tiled(chain, tile: Sequence[int], steps: Optional[int] = None, nth
     return dats, hist
 
 
+def run_chain_wavefront(chain, tile: Sequence[int], steps: Optional[int] = None, seed: int = 0,
+                        fp32: bool = False, drop=None):
+    """The phases of each step's skewed plan (Algorithm 1 ranges for the tile
+    sizes `tile`) executed in a random order that keeps every pair of
+    conflicting phases (oracle.plan.phase_conflicts) in plan order: at each
+    point one of the phases whose earlier conflicting phases are all done is
+    drawn at random.  This is the freedom a wavefront schedule of the tiles
+    uses (Sec. 4.B leaves such schedules to future work); the results are
+    those of program order.  drop(q, deps) -> deps, if given, edits the
+    dependency list of phase q before the order is drawn (tests use it to
+    show that the relation is needed)."""
+    import random
+    from . import plan as oplan
+    rnd = random.Random(seed)
+    dats = [np.ascontiguousarray(d.init.astype(np.float32 if fp32 else np.float64)) for d in chain.dats]
+    nsteps = chain.steps if steps is None else steps
+    nd = chain.ndim
+    dt = 1.0
+    hist = []
+    for s in range(nsteps):
+        loops = [_with_consts(lp, lp.consts_for(dt)) for lp in chain.loops]
+        ntiles, ranges, _ = oplan.skewed_plan(loops, chain.stencils, nd, list(tile)[:nd])
+        phases = oplan.phases_in_order(loops, ntiles, ranges, nd)
+        deps = oplan.phase_conflicts(loops, chain.stencils, nd, phases)
+        if drop is not None:
+            deps = [drop(q, list(d)) for q, d in enumerate(deps)]
+        waiting = [len(d) for d in deps]
+        users = [[] for _ in phases]
+        for q, d in enumerate(deps):
+            for p in d:
+                users[p].append(q)
+        ready = [q for q in range(len(phases)) if waiting[q] == 0]
+        order = []
+        while ready:
+            q = ready.pop(rnd.randrange(len(ready)))
+            order.append(q)
+            for u in users[q]:
+                waiting[u] -= 1
+                if waiting[u] == 0:
+                    ready.append(u)
+        assert len(order) == len(phases)
+        views = [_BoxView(loops[phases[q][0]], phases[q][1]) for q in order]
+        vals = run_loops(chain, dats, views, [red_identity(op) for op in chain.reductions])
+        hist.append(vals)
+        if chain.dt_red >= 0:
+            dt = vals[chain.dt_red]
+    return dats, hist
+
+
 class _BoxView:
     """A loop restricted to one (tile, loop) box."""
 

@@ -171,3 +171,70 @@ def overlapped_plan(loops: Sequence, stencils: Sequence, ndim: int, owned: Seque
     for dat, rb in readbox.items():
         footprint[dat] = tuple((rb[d][0], rb[d][1]) for d in range(ndim))
     return boxes, footprint
+
+
+def phases_in_order(loops: Sequence, ntiles, ranges, ndim: int):
+    """Algorithm 2's execution order of a skewed plan: tiles in lexicographic
+    order (x fastest), the loops in program order inside a tile; phases with
+    an empty box are dropped.  Returns [(loop index, box)], box a tuple of
+    per-dimension (lo, hi)."""
+    import itertools
+    out = []
+    for rev in itertools.product(*[range(ntiles[d]) for d in reversed(range(ndim))]):
+        t = tuple(reversed(rev))
+        for l in range(len(loops)):
+            box = tuple(ranges[d][t[d]][l] for d in range(ndim))
+            if all(hi > lo for lo, hi in box):
+                out.append((l, box))
+    return out
+
+
+def phase_conflicts(loops: Sequence, stencils: Sequence, ndim: int, phases):
+    """For every phase q (in the given order) the sorted list of earlier
+    phases p that must stay before it: p and q touch a common point of some
+    dat and at least one of them writes that point.  A phase reads, for each
+    reading argument, the points of its box shifted by each point of the
+    argument's stencil, and writes the points of its box for each writing
+    argument (the exact point sets, not bounding boxes).  Any execution that
+    keeps every such pair in order computes what the given order computes
+    (program order, for the phases of a skewed plan).  Brute force over
+    boolean masks: small problems only."""
+    import numpy as np
+    n = len(phases)
+    lo, hi = [0] * ndim, [1] * ndim
+    for l, box in phases:
+        for a in loops[l].args:
+            if a.kind != DAT:
+                continue
+            for d in range(ndim):
+                m, p = _ext(stencils[a.stencil], d)
+                lo[d] = min(lo[d], box[d][0] + m)
+                hi[d] = max(hi[d], box[d][1] + p)
+    shape = tuple(hi[d] - lo[d] for d in reversed(range(ndim)))  # z, y, x
+    dats = sorted({a.handle for lp in loops for a in lp.args if a.kind == DAT})
+    conf = np.zeros((n, n), dtype=bool)
+    for k in dats:
+        idx = [i for i, (l, _) in enumerate(phases) if any(a.kind == DAT and a.handle == k for a in loops[l].args)]
+        R = np.zeros((len(idx), int(np.prod(shape))), dtype=np.float32)
+        Wm = np.zeros_like(R)
+        for j, i in enumerate(idx):
+            l, box = phases[i]
+            for a in loops[l].args:
+                if a.kind != DAT or a.handle != k:
+                    continue
+                pts = stencils[a.stencil] if _reads(a) else []
+                for p in pts:
+                    m = np.zeros(shape, dtype=bool)
+                    sl = tuple(slice(box[d][0] + p[d] - lo[d], box[d][1] + p[d] - lo[d]) for d in reversed(range(ndim)))
+                    m[sl] = True
+                    R[j] = np.maximum(R[j], m.reshape(-1))
+                if _writes(a):
+                    m = np.zeros(shape, dtype=bool)
+                    sl = tuple(slice(box[d][0] - lo[d], box[d][1] - lo[d]) for d in reversed(range(ndim)))
+                    m[sl] = True
+                    Wm[j] = np.maximum(Wm[j], m.reshape(-1))
+        T = np.maximum(R, Wm)
+        c = (Wm @ T.T > 0) | (T @ Wm.T > 0)
+        ix = np.array(idx, dtype=np.int64)
+        conf[np.ix_(ix, ix)] |= c
+    return [sorted(int(p) for p in np.nonzero(conf[q, :q])[0]) for q in range(n)]

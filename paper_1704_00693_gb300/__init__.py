@@ -28,7 +28,7 @@ OPS_ERR_CUDA = -7
 OPS_ERR_STATE = -8
 OPS_ERR_NO_DEVICE = -9
 
-OPS_MODE_UNTILED, OPS_MODE_SKEWED, OPS_MODE_OVERLAPPED, OPS_MODE_AUTO = 0, 1, 2, 3
+OPS_MODE_UNTILED, OPS_MODE_SKEWED, OPS_MODE_OVERLAPPED, OPS_MODE_AUTO, OPS_MODE_WAVEFRONT = 0, 1, 2, 3, 4
 OPS_ARG_DAT, OPS_ARG_SCALAR, OPS_ARG_RED = 0, 1, 2
 OPS_READ, OPS_WRITE, OPS_RW, OPS_INC = 0, 1, 2, 3
 OPS_RED_SUM, OPS_RED_MIN, OPS_RED_MAX = 0, 1, 2
@@ -39,7 +39,7 @@ OPS_REAL_F64, OPS_REAL_F32 = 0, 1
  OPS_IR_SGT, OPS_IR_WSUM, OPS_IR_WACC, OPS_IR_POLY, OPS_IR_ST, OPS_IR_RED) = range(1, 16)
 
 MODES = {"untiled": OPS_MODE_UNTILED, "skewed": OPS_MODE_SKEWED, "overlapped": OPS_MODE_OVERLAPPED,
-         "auto": OPS_MODE_AUTO}
+         "auto": OPS_MODE_AUTO, "wavefront": OPS_MODE_WAVEFRONT}
 
 
 class OpsError(RuntimeError):
@@ -276,17 +276,37 @@ def ops_plan_overlapped(ctx, owned, nloops: int, ndats: int):
     return boxes[:6 * nloops].reshape(nloops, 3, 2).copy(), foot[:6 * ndats].reshape(ndats, 3, 2).copy()
 
 
-def ops_compile_queued(ctx, want_source: bool = False):
+def ops_plan_wavefront(ctx, tile):
+    """Wavefront plan of the queued loops for the given tile sizes:
+    (phases, deps, nunits, nlevels), phases an int32 array [nphases, 12] of
+    (loop, chunks, first work unit, first dependency entry, dependency count,
+    level, x0, x1, y0, y1, z0, z1) in Algorithm 2 order and deps the
+    dependency entries (indices of earlier phases)."""
+    counts = (C.c_int64 * 4)()
+    t = _i3(list(tile) + [1] * (3 - len(tile)))
+    _check(ctx, load().ops_plan_wavefront(ctx, t, counts, None, C.c_int64(0), None, C.c_int64(0)))
+    nph, ndep = counts[0], counts[1]
+    ph = np.zeros((max(1, nph), 12), dtype=np.int32)
+    dp = np.zeros(max(1, ndep), dtype=np.int32)
+    ip = C.POINTER(C.c_int)
+    _check(ctx, load().ops_plan_wavefront(ctx, t, counts, ph.ctypes.data_as(ip), C.c_int64(ph.size),
+                                          dp.ctypes.data_as(ip), C.c_int64(dp.size)))
+    return ph[:nph].copy(), dp[:ndep].copy(), int(counts[2]), int(counts[3])
+
+
+def ops_compile_queued(ctx, want_source: bool = False, wavefront: bool = False):
     """Generate and compile (NVRTC, sm_103a, no device) the loop bodies of the
-    queued loops; returns (source or None, source length, compile ms)."""
+    queued loops -- the per-loop and overlapped-tile kernels, or with
+    wavefront=True the wavefront kernel; returns (source or None, source
+    length, compile ms)."""
+    f = load().ops_compile_queued_wavefront if wavefront else load().ops_compile_queued
     n = C.c_int64(0)
     ms = C.c_double(0.0)
     buf = None
     if want_source:
-        _check(ctx, load().ops_compile_queued(ctx, None, C.c_int64(0), C.byref(n), C.byref(ms)))
+        _check(ctx, f(ctx, None, C.c_int64(0), C.byref(n), C.byref(ms)))
         buf = C.create_string_buffer(n.value + 1)
-    _check(ctx, load().ops_compile_queued(ctx, buf, C.c_int64(n.value + 1 if buf is not None else 0), C.byref(n),
-                                          C.byref(ms)))
+    _check(ctx, f(ctx, buf, C.c_int64(n.value + 1 if buf is not None else 0), C.byref(n), C.byref(ms)))
     return (buf.value.decode() if buf is not None else None), n.value, ms.value
 
 

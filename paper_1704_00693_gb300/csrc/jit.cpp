@@ -177,6 +177,12 @@ const char* kDeviceCommon =
 const char* kPreludeTail = R"PRE(
 __shared__ DD g_sh[32];
 
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 __device__ __forceinline__ void flush_red(int op, DD v, DD* part, int stride, int row, int assign) {
   v = block_combine(op, v, g_sh);
   if (threadIdx.x == 0) {
@@ -379,7 +385,7 @@ struct LoopGen {
             "  const int x0 = bx[0], x1 = bx[1], y0 = bx[2], y1 = bx[3], z0 = bx[4], z1 = bx[5];\n";
     } else {
       os << "\n__device__ __forceinline__ void body" << i
-         << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
+         << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1, int ck, int nck,\n"
             "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n";
     }
     // hoisted: dat pointers, scalars, constants
@@ -435,8 +441,7 @@ struct LoopGen {
     if (ov)
       os << "  run_units<" << P << ", " << kOvThreads << ">(x0, x1, y0, y1, z0, z1, 0, 1, one, full);\n";
     else
-      os << "  run_units<" << P << ", " << kThreads
-         << ">(x0, x1, y0, y1, z0, z1, blockIdx.x, gridDim.x, one, full);\n";
+      os << "  run_units<" << P << ", " << kThreads << ">(x0, x1, y0, y1, z0, z1, ck, nck, one, full);\n";
     for (int k = 0; k < L.nreds; ++k)
       os << "  flush_red(" << L.red_op[k] << ", acc" << k << ", part, stride, L->part_row + " << k << ", "
          << (ov ? "0" : "assign") << ");\n";
@@ -458,7 +463,7 @@ std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::
     os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas << ") u" << i
        << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
           "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n  body"
-       << i << "(L, x0, x1, y0, y1, z0, z1, scal, part, stride, assign);\n}\n";
+       << i << "(L, x0, x1, y0, y1, z0, z1, blockIdx.x, gridDim.x, scal, part, stride, assign);\n}\n";
   }
   return os.str();
 }
@@ -480,11 +485,6 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned
 __device__ __forceinline__ void bulk_to_shared(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ unsigned long long now_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
 }
 // true once the barrier's phase `parity` completed; false after timeout_ns
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long timeout_ns) {
@@ -572,6 +572,93 @@ std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay)
          << lay.spitch[k] << ", " << lay.splane[k] << ", nullptr, (" << T << "*)dats[" << k << "].dst, dats[" << k
          << "].gpitch, dats[" << k << "].gplane, false);\n";
   os << "  }\n}\n";
+  return os.str();
+}
+
+// Source of the wavefront kernel "wf" for the loops of a segment.  Work
+// units (a chunk of one phase) are taken in plan order from a ticket
+// counter; before running its chunk a CTA waits until every phase its phase
+// depends on has all its chunks done.  Every dependency points to an earlier
+// phase, whose units were handed out before, to CTAs that are running: the
+// earliest unfinished unit can always proceed, so the waits end.  The first
+// warp polls up to 32 dependency counters at once; each wait is bounded in
+// wall-clock time and a CTA that gives up sets the error word and leaves, as
+// does every CTA that finds the word set.
+const char* kWfPrelude = R"WFP(
+struct WfPhase { int loop, nchunk, ustart, dep0, ndep, pad; int box[6]; };
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+)WFP";
+
+std::string generate_wavefront(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es) {
+  std::ostringstream os;
+  os << "// opstile wavefront kernel: " << kJitPts << " rows per unit, " << kJitMinCtas << " CTAs per SM, "
+     << (es == 4 ? "fp32" : "fp64") << "\n";
+  os << kPrelude << kDeviceCommon << kPreludeTail << kWfPrelude;
+  os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
+  os << "static_assert(sizeof(WfPhase) == " << sizeof(WfPhase) << ", \"WfPhase layout\");\n";
+  for (int i = 0; i < count; ++i) {
+    LoopGen g(loops[i], ro[i], os, false, es == 4);
+    g.emit(i);
+  }
+  os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas
+     << ") wf(const DLoop* __restrict__ L,\n"
+        "    const WfPhase* __restrict__ ph, const int* __restrict__ deps, const int* __restrict__ uphase,\n"
+        "    int nunits, int* done, int* ticket, const double* __restrict__ scal, DD* part, int stride, int* err,\n"
+        "    long long timeout_ns, int skip_unit) {\n"
+        "  __shared__ int s_u, s_ok;\n"
+        "  for (;;) {\n"
+        "    if (threadIdx.x == 0) s_u = *(volatile int*)err ? nunits : atomicAdd(ticket, 1);\n"
+        "    __syncthreads();\n"
+        "    const int u = s_u;\n"
+        "    if (u >= nunits) return;\n"
+        "    const int q = uphase[u];\n"
+        "    const WfPhase P = ph[q];\n"
+        "    if (threadIdx.x < 32) {\n"
+        "      bool ok = true;\n"
+        "      unsigned long long t0 = 0;\n"
+        "      for (int j = threadIdx.x; ok && j < P.ndep; j += 32) {\n"
+        "        const int d = deps[P.dep0 + j];\n"
+        "        const int want = ph[d].nchunk;\n"
+        "        unsigned spins = 0;\n"
+        "        while (ld_acquire(done + d) < want) {\n"
+        "          if ((++spins & 63u) == 0) {\n"
+        "            if (t0 == 0) {\n"
+        "              t0 = now_ns();\n"
+        "            } else if (*(volatile int*)err || (long long)(now_ns() - t0) > timeout_ns) {\n"
+        "              ok = false;\n"
+        "              break;\n"
+        "            }\n"
+        "          }\n"
+        "        }\n"
+        "      }\n"
+        "      ok = __all_sync(0xffffffffu, ok);\n"
+        "      if (threadIdx.x == 0) {\n"
+        "        if (!ok) atomicCAS(err, 0, 1);\n"
+        "        __threadfence();\n"
+        "        s_ok = ok;\n"
+        "      }\n"
+        "    }\n"
+        "    __syncthreads();\n"
+        "    if (!s_ok) return;\n"
+        "    const int ck = u - P.ustart;\n"
+        "    switch (P.loop) {\n";
+  for (int i = 0; i < count; ++i)
+    os << "      case " << i << ": body" << i << "(L + " << i
+       << ", P.box[0], P.box[1], P.box[2], P.box[3], P.box[4], P.box[5], ck, P.nchunk, scal, part, stride, 0); "
+          "break;\n";
+  os << "      default: break;\n"
+        "    }\n"
+        "    __syncthreads();\n"
+        "    if (threadIdx.x == 0 && u != skip_unit) {\n"
+        "      __threadfence();\n"
+        "      atomicAdd(done + q, 1);\n"
+        "    }\n"
+        "  }\n"
+        "}\n";
   return os.str();
 }
 
@@ -928,6 +1015,112 @@ cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const D
   int as = assign;
   void* args[] = {&a0, &b0, &b1, &b2, &b3, &b4, &b5, &sc, &pt, &st, &as};
   return to_cuda(g_api.launch(s->u[i], (unsigned)grid, 1, 1, kThreads, 1, 1, 0, (CUstream)env.stream, args, nullptr));
+}
+
+
+int jit_rows_per_unit() { return kJitPts; }
+
+int jit_wave_units_per_chunk() {
+  static const int v = env_int("OPSTILE_WF_UNITS", 8, 1, 1 << 20);
+  return v;
+}
+
+int jit_wave_slope() {
+  static const int v = env_int("OPSTILE_WF_SLOPE", 1, 0, 1 << 20);
+  return v;
+}
+
+struct JitWave {
+  CUfunction f = nullptr;
+};
+
+namespace {
+std::map<std::pair<int, std::string>, std::unique_ptr<JitWave>> g_waves;
+
+bool cubin_for(const std::string& src, std::string* cubin, std::string* why) {
+  std::string cached;
+  const std::string base = cache_base(src);
+  if (read_file(base + ".cu", &cached) && cached == src && read_file(base + ".cubin", cubin) && !cubin->empty())
+    return true;
+  if (!compile(src, cubin, why)) return false;
+  mkdirs(cache_dir());
+  write_file(base + ".cubin", *cubin);
+  write_file(base + ".cu", src);
+  return true;
+}
+}  // namespace
+
+int jit_wavefront(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                  JitWave** out, std::string* why, double* compile_ms) {
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!api_ready(why)) return OPS_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  const std::string src = generate_wavefront(loops, count, ro, es);
+  auto key = std::make_pair(device, src);
+  auto it = g_waves.find(key);
+  if (it != g_waves.end()) {
+    *out = it->second.get();
+    return OPS_OK;
+  }
+  std::string cubin;
+  if (!cubin_for(src, &cubin, why)) return OPS_ERR_CUDA;
+  CUmodule mod;
+  if (g_api.load(&mod, cubin.data()) != CUDA_SUCCESS) {
+    *why = "cuModuleLoadData failed";
+    return OPS_ERR_CUDA;
+  }
+  std::unique_ptr<JitWave> w(new JitWave);
+  if (g_api.get_function(&w->f, mod, "wf") != CUDA_SUCCESS) {
+    *why = "cuModuleGetFunction failed";
+    return OPS_ERR_CUDA;
+  }
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = w.get();
+  g_waves[key] = std::move(w);
+  return OPS_OK;
+}
+
+int jit_compile_wavefront_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                               std::string* src, std::string* why, double* compile_ms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  *src = generate_wavefront(loops, count, ro, es);
+  if (!api_ready(why, true)) {
+    if (why->empty()) *why = g_api.why;
+    return OPS_ERR_NO_DEVICE;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  std::string cubin;
+  const bool ok = compile(*src, &cubin, why);
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return ok ? OPS_OK : OPS_ERR_CUDA;
+}
+
+int jit_wavefront_max_grid(JitWave* w, int num_sms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int per_sm = 0;
+  if (g_api.occupancy(&per_sm, w->f, kThreads, 0) != CUDA_SUCCESS) return 0;
+  return per_sm * num_sms;
+}
+
+cudaError_t jit_launch_wavefront(const JitWave* w, const LaunchEnv& env, const DLoop* d_loops,
+                                 const WfPhase* d_phases, const int* d_deps, const int* d_uphase, int nunits,
+                                 int* d_done, int* d_ticket, int grid) {
+  const DLoop* a0 = d_loops;
+  const WfPhase* a1 = d_phases;
+  const int *a2 = d_deps, *a3 = d_uphase;
+  int a4 = nunits;
+  int *a5 = d_done, *a6 = d_ticket;
+  const double* a7 = env.scal;
+  DD* a8 = env.part;
+  int a9 = env.part_stride;
+  int* a10 = env.err;
+  long long a11 = env.timeout_ns;
+  int a12 = env.skip_block;
+  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10, &a11, &a12};
+  return to_cuda(g_api.launch(w->f, (unsigned)grid, 1, 1, kThreads, 1, 1, 0, (CUstream)env.stream, args, nullptr));
 }
 
 }  // namespace opstile

@@ -66,4 +66,33 @@ cudaError_t jit_launch_overlap(const JitOverlap* o, const LaunchEnv& env, const 
                                const int* d_own, const int* d_boxes, const int* d_foot, int ntiles, int grid,
                                int area_bytes);
 
+// Wavefront execution of a skewed plan (Sec. 4.B tiles; the wavefront
+// scheduling the paper leaves to future work): one persistent kernel with
+// every loop body of the segment, taking (phase, chunk) work units in plan
+// order and waiting on per-phase completion counters.
+struct WfPhase {
+  int loop, nchunk, ustart, dep0, ndep, pad;
+  int box[6];
+};
+struct JitWave;
+// P of the compiled enumeration (rows per unit); enumeration units per
+// wavefront work unit (OPSTILE_WF_UNITS, default 8)
+int jit_rows_per_unit();
+int jit_wave_units_per_chunk();
+// slope of the wavefront's ticket order (OPSTILE_WF_SLOPE, default 1; see build_wavefront)
+int jit_wave_slope();
+int jit_wavefront(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                  JitWave** out, std::string* why, double* compile_ms);
+// Host only: generate and compile (no load, no device) the wavefront kernel.
+int jit_compile_wavefront_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                               std::string* src, std::string* why, double* compile_ms);
+// CTAs of the wavefront kernel resident on the device at once
+int jit_wavefront_max_grid(JitWave* w, int num_sms);
+// d_done: one counter per phase, zero before the launch; d_ticket: zero.
+// env.skip_block >= 0 (test hook): that work unit's completion is never
+// counted, so the phases waiting on it give up after env.timeout_ns.
+cudaError_t jit_launch_wavefront(const JitWave* w, const LaunchEnv& env, const DLoop* d_loops,
+                                 const WfPhase* d_phases, const int* d_deps, const int* d_uphase, int nunits,
+                                 int* d_done, int* d_ticket, int grid);
+
 }  // namespace opstile

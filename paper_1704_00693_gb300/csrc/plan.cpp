@@ -20,6 +20,7 @@
 #include "plan.h"
 
 #include <algorithm>
+#include <array>
 #include <climits>
 
 namespace opstile {
@@ -144,6 +145,7 @@ bool conflict(const PLoop& lp, const int* bp, const PLoop& lq, const int* bq) {
 void build_phases(const std::vector<PLoop>& loops, SkewedPlan& plan) {
   const int L = (int)loops.size();
   plan.phases.clear();
+  plan.phase_tile.clear();
   plan.nbarriers = 0;
   plan.points = 0;
   std::vector<int> epoch;  // phases since the last barrier
@@ -186,7 +188,95 @@ void build_phases(const std::vector<PLoop>& loops, SkewedPlan& plan) {
           for (int d = 0; d < 3; ++d) n *= (int64_t)(P.box[2 * d + 1] - P.box[2 * d]);
           plan.points += n;
           plan.phases.push_back(P);
+          plan.phase_tile.push_back((tz * plan.ntiles[1] + ty) * plan.ntiles[0] + tx);
         }
+}
+
+namespace {
+// enumeration units of one box, as the kernels count them (see run_units)
+int64_t box_units(const int* b, int P, int NT) {
+  const int64_t nx = b[1] - b[0], ny = b[3] - b[2], nz = b[5] - b[4];
+  if (nx <= 0 || ny <= 0 || nz <= 0) return 0;
+  if (nx >= 128) return ((nx + NT - 1) / NT) * ((ny + P - 1) / P) * nz;
+  const int64_t g = (int64_t)NT * P;
+  return (nx * ny * nz + g - 1) / g;
+}
+}  // namespace
+
+void build_wavefront(const std::vector<PLoop>& loops, int ndats, const SkewedPlan& plan, int axis, int P, int NT,
+                     int per_unit, int slope, WavePlan& out) {
+  const int nph = (int)plan.phases.size();
+  out.axis = axis;
+  out.dep_off.assign(nph + 1, 0);
+  out.deps.clear();
+  out.nchunk.assign(nph, 0);
+  out.ustart.assign(nph, 0);
+  out.nunits = 0;
+  // the index range along the axis that any phase touches
+  int lo = kFar, hi = -kFar;
+  for (const Phase& ph : plan.phases)
+    for (const PArg& a : loops[ph.loop].args) {
+      if (a.kind != OPS_ARG_DAT) continue;
+      lo = std::min(lo, ph.box[2 * axis] + a.slo[axis]);
+      hi = std::max(hi, ph.box[2 * axis + 1] + a.shi[axis]);
+    }
+  const int n = hi > lo ? hi - lo : 0;
+  // acc[dat * n + i]: phases so far that touch index i of the dat along the axis
+  std::vector<std::vector<int>> acc((size_t)ndats * n);
+  std::vector<int> seen(nph, -1), cand;
+  for (int q = 0; q < nph; ++q) {
+    const Phase& Q = plan.phases[q];
+    const PLoop& lq = loops[Q.loop];
+    cand.clear();
+    for (const PArg& a : lq.args) {
+      if (a.kind != OPS_ARG_DAT) continue;
+      const int r0 = Q.box[2 * axis] + (a.reads ? a.slo[axis] : 0) - lo;
+      const int r1 = Q.box[2 * axis + 1] + (a.reads ? a.shi[axis] : 0) - lo;
+      for (int i = r0; i < r1; ++i)
+        for (int p : acc[(size_t)a.dat * n + i])
+          if (seen[p] != q) {
+            seen[p] = q;
+            cand.push_back(p);
+          }
+    }
+    std::sort(cand.begin(), cand.end());
+    for (int p : cand)
+      if (conflict(loops[plan.phases[p].loop], plan.phases[p].box, lq, Q.box)) out.deps.push_back(p);
+    out.dep_off[q + 1] = (int)out.deps.size();
+    for (const PArg& a : lq.args) {
+      if (a.kind != OPS_ARG_DAT) continue;
+      const int r0 = Q.box[2 * axis] + (a.reads ? a.slo[axis] : 0) - lo;
+      const int r1 = Q.box[2 * axis + 1] + (a.reads ? a.shi[axis] : 0) - lo;
+      for (int i = r0; i < r1; ++i) {
+        std::vector<int>& v = acc[(size_t)a.dat * n + i];
+        if (v.empty() || v.back() != q) v.push_back(q);
+      }
+    }
+    const int64_t u = box_units(Q.box, P, NT);
+    out.nchunk[q] = (int)std::max<int64_t>(1, (u + per_unit - 1) / std::max(1, per_unit));
+  }
+  // levels, then the units by (level + slope * tile, tile, plan order)
+  out.level.assign(nph, 0);
+  out.nlevels = 0;
+  for (int q = 0; q < nph; ++q) {
+    for (int k = out.dep_off[q]; k < out.dep_off[q + 1]; ++k)
+      out.level[q] = std::max(out.level[q], out.level[out.deps[k]] + 1);
+    out.nlevels = std::max(out.nlevels, out.level[q] + 1);
+  }
+  std::vector<std::array<int64_t, 3>> keyed(nph);
+  for (int q = 0; q < nph; ++q) {
+    const int64_t t = plan.phase_tile[q];
+    keyed[q] = {out.level[q] + (int64_t)std::max(0, slope) * t, t, q};
+  }
+  std::sort(keyed.begin(), keyed.end());
+  std::vector<int> order(nph);
+  for (int q = 0; q < nph; ++q) order[q] = (int)keyed[q][2];
+  out.uphase.clear();
+  for (int q : order) {
+    out.ustart[q] = (int)out.uphase.size();
+    out.uphase.insert(out.uphase.end(), out.nchunk[q], q);
+  }
+  out.nunits = (int64_t)out.uphase.size();
 }
 
 // Overlapped tile (Sec. 4.D, read dependencies only): the last loops keep the

@@ -31,6 +31,7 @@ struct SkewedPlan {
   // ranges[d][2 * (t * nloops + l)] = start, [... + 1] = end of loop l in tile t along d
   std::vector<int> ranges[3];
   std::vector<Phase> phases;
+  std::vector<int> phase_tile;  // linear tile index (x fastest) of each phase
   int nbarriers = 0;
   int skew[3] = {0, 0, 0};
   int64_t points = 0;
@@ -42,6 +43,37 @@ void build_skewed_ranges(const std::vector<PLoop>& loops, int ndats, int ndim, c
 // tile) with a grid barrier only before a phase that conflicts with a phase
 // since the previous barrier.
 void build_phases(const std::vector<PLoop>& loops, SkewedPlan& plan);
+
+// Wavefront execution of a skewed plan: the phases of plan.phases, each
+// waiting only for the earlier phases it conflicts with.  deps[dep_off[q] ..
+// dep_off[q + 1]) are the phases before q in plan order that touch a dat q
+// touches, where at least one of the two writes it and the touched regions
+// (reads widened by the stencil) intersect.  Candidates are found through a
+// per-(dat, index) access list along dimension `axis` and then checked
+// exactly, so the list is complete (every conflicting earlier phase) and
+// holds nothing else.  Phase q is split into nchunk[q] work units of at most
+// `per_unit` of the kernel's enumeration units (P rows of NT points, or
+// flattened groups of NT x P points for boxes narrower than 128).
+// Work units are numbered (the order a kernel hands them out) by the key
+// level + slope * tile, then tile, then plan order, where the level of a
+// phase is the longest dependency path that ends at it and tile is its
+// linear tile index.  Every dependency has a smaller key (its level is
+// smaller and its tile no later), so this is a topological order for any
+// slope >= 0.  Slope 0 runs level by level over all tiles (loop by loop, as
+// untiled); a slope >= the number of levels is Algorithm 2's tile-by-tile
+// order; in between, about nlevels / slope tiles are in flight at once, each
+// at a different level -- a wavefront over the tiles.
+struct WavePlan {
+  int axis = 0;
+  std::vector<int> dep_off, deps;
+  std::vector<int> nchunk, ustart;  // per phase
+  std::vector<int> level;           // per phase
+  int nlevels = 0;
+  std::vector<int> uphase;          // per work unit: its phase
+  int64_t nunits = 0;
+};
+void build_wavefront(const std::vector<PLoop>& loops, int ndats, const SkewedPlan& plan, int axis, int P, int NT,
+                     int per_unit, int slope, WavePlan& out);
 
 // Overlapped tiling (Sec. 4.D applied to one tile): grow each loop's part of
 // the tile backwards by what later loops of the tile read.

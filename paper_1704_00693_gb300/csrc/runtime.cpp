@@ -62,6 +62,13 @@ struct CachedPlan {
   std::vector<int> key;
   SkewedPlan plan;
   Phase* d_phases = nullptr;
+  // wavefront form: phase table, dependency lists and the ticket order on
+  // the device (one allocation), per-phase completion counters + ticket
+  WavePlan wave;
+  int nlevels = 0;
+  void* d_wave = nullptr;
+  size_t wave_bytes = 0;
+  int* d_wdone = nullptr;
 };
 
 // An overlapped-tile plan of one segment (Sec. 4.D per CTA tile).
@@ -130,6 +137,7 @@ struct ops_ctx_s {
   int ovdat_cap = 0;
   // compiled loop bodies per segment (by signature and IR); nullptr: interpret
   std::map<std::vector<int>, JitSegment*> jit;
+  std::map<std::vector<int>, JitWave*> jitw;  // wavefront kernels, same keys
   std::string jit_why;
   int64_t allocated = 0;
   std::string err;
@@ -838,21 +846,18 @@ int overlap_prefix(ops_ctx c, int first, int count, const int* tile_in, OverlapP
 // Compiled kernels of a segment, generated from its loops' IR at its first
 // flush; *out = nullptr (interpreter kernels) in checked mode, with
 // interpret = 1, or when run-time compilation is unavailable.
-int segment_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitSegment** out) {
-  *out = nullptr;
-  if (c->cfg.interpret || c->cfg.check) return OPS_OK;
+std::vector<int> code_key(ops_ctx c, int first, int count) {
   std::vector<int> key = segment_signature(c, first, count);
   for (int i = 0; i < count; ++i) {
     const QLoop& q = c->queue[first + i];
     key.push_back(-1);
     key.insert(key.end(), q.code.begin(), q.code.end());
   }
-  auto it = c->jit.find(key);
-  if (it != c->jit.end()) {
-    *out = it->second;
-    return OPS_OK;
-  }
-  // dats no loop of the segment writes are read through the read-only path
+  return key;
+}
+
+// dats no loop of the segment writes are read through the read-only path
+std::vector<std::vector<char>> read_only_args(ops_ctx c, int first, int count) {
   std::set<int> written;
   for (int i = 0; i < count; ++i)
     for (const ops_arg& a : c->queue[first + i].args)
@@ -864,6 +869,19 @@ int segment_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, 
     for (size_t a = 0; a < q.args.size(); ++a)
       ro[i][a] = q.args[a].kind == OPS_ARG_DAT && !written.count(q.args[a].handle);
   }
+  return ro;
+}
+
+int segment_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitSegment** out) {
+  *out = nullptr;
+  if (c->cfg.interpret || c->cfg.check) return OPS_OK;
+  std::vector<int> key = code_key(c, first, count);
+  auto it = c->jit.find(key);
+  if (it != c->jit.end()) {
+    *out = it->second;
+    return OPS_OK;
+  }
+  std::vector<std::vector<char>> ro = read_only_args(c, first, count);
   JitSegment* s = nullptr;
   std::string why;
   double ms = 0.0;
@@ -873,6 +891,181 @@ int segment_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, 
   if (!s) c->jit_why = why;
   c->jit[key] = s;
   *out = s;
+  return OPS_OK;
+}
+
+// Wavefront kernel of a segment (every loop body in one module), compiled
+// at the segment's first wavefront flush; nullptr when run-time compilation
+// is unavailable (reason in jit_why).
+int wave_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitWave** out) {
+  *out = nullptr;
+  std::vector<int> key = code_key(c, first, count);
+  auto it = c->jitw.find(key);
+  if (it != c->jitw.end()) {
+    *out = it->second;
+    return OPS_OK;
+  }
+  std::vector<std::vector<char>> ro = read_only_args(c, first, count);
+  JitWave* w = nullptr;
+  std::string why;
+  double ms = 0.0;
+  const int rc = jit_wavefront(c->cfg.device, hl.data() + first, count, ro, c->es, &w, &why, &ms);
+  c->stats.compile_ms += ms;
+  if (rc) return fail(c, rc, "compiling the wavefront kernel: %s", why.c_str());
+  if (!w) c->jit_why = why;
+  c->jitw[key] = w;
+  *out = w;
+  return OPS_OK;
+}
+
+// Points of one wavefront tile along the outermost dimension when the tile
+// size is automatic: about eight full 4096-point rows.
+constexpr int64_t kWavePoints = 8 * 4096;
+
+// The plan of a wavefront segment (cached like the skewed plans): Algorithm
+// 1's ranges for thin tiles along the outermost dimension (the others
+// untiled unless a tile size is given), Algorithm 2's phase order, and the
+// dependency lists and work units of build_wavefront, uploaded once.
+int wave_plan(ops_ctx c, int first, int count, const int* tile_in, CachedPlan** out) {
+  const int ndim = c->queue[first].dims;
+  std::vector<PLoop> pl;
+  pl.reserve(count);
+  for (int i = 0; i < count; ++i) pl.push_back(plan_loop(c, c->queue[first + i]));
+  int ext[3] = {1, 1, 1};
+  for (int d = 0; d < ndim; ++d) {
+    int lo = 1 << 30, hi = -(1 << 30);
+    for (const PLoop& p : pl) {
+      lo = std::min(lo, p.rng[2 * d]);
+      hi = std::max(hi, p.rng[2 * d + 1]);
+    }
+    ext[d] = std::max(1, hi - lo);
+  }
+  int tile[3] = {1, 1, 1};
+  int64_t inner = 1;
+  for (int d = 0; d + 1 < ndim; ++d) {
+    tile[d] = tile_in[d] > 0 ? tile_in[d] : ext[d];
+    inner *= tile[d];
+  }
+  tile[ndim - 1] =
+      tile_in[ndim - 1] > 0 ? tile_in[ndim - 1] : (int)std::max<int64_t>(1, kWavePoints / std::max<int64_t>(1, inner));
+  const int P = jit_rows_per_unit(), upc = jit_wave_units_per_chunk(), slope = jit_wave_slope();
+  std::vector<int> key = {-OPS_MODE_WAVEFRONT, ndim, tile[0], tile[1], tile[2], P, upc, slope};
+  for (int i = 0; i < count; ++i) {
+    const QLoop& q = c->queue[first + i];
+    for (int k = 0; k < 6; ++k) key.push_back(q.rng[k]);
+    key.push_back((int)q.args.size());
+    for (const ops_arg& a : q.args) {
+      key.push_back(a.kind);
+      key.push_back(a.handle);
+      key.push_back(a.kind == OPS_ARG_DAT ? a.stencil : -1);
+      key.push_back(a.access);
+    }
+  }
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    ++c->stats.plan_cache_hits;
+    *out = it->second.get();
+    return OPS_OK;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  std::unique_ptr<CachedPlan> np(new CachedPlan);
+  np->key = key;
+  build_skewed_ranges(pl, (int)c->dats.size(), ndim, tile, np->plan);
+  build_phases(pl, np->plan);
+  WavePlan& W = np->wave;
+  build_wavefront(pl, (int)c->dats.size(), np->plan, ndim - 1, P, kThreads, upc, slope, W);
+  c->stats.plan_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  const size_t nph = np->plan.phases.size();
+  if (W.nunits >= (1ll << 31) || W.deps.size() >= (1ull << 31))
+    return fail(c, OPS_ERR_INVALID_ARG, "wavefront plan too large (%lld work units)", (long long)W.nunits);
+  if (nph) {
+    std::vector<WfPhase> tab(nph);
+    for (size_t q = 0; q < nph; ++q) {
+      WfPhase& f = tab[q];
+      f.loop = np->plan.phases[q].loop;
+      f.nchunk = W.nchunk[q];
+      f.ustart = W.ustart[q];
+      f.dep0 = W.dep_off[q];
+      f.ndep = W.dep_off[q + 1] - W.dep_off[q];
+      f.pad = W.level[q];
+      for (int k = 0; k < 6; ++k) f.box[k] = np->plan.phases[q].box[k];
+    }
+    const size_t b0 = sizeof(WfPhase) * nph, b1 = sizeof(int) * W.deps.size(), b2 = sizeof(int) * W.uphase.size();
+    np->wave_bytes = b0 + b1 + b2 + 16;
+    int rc = dev_alloc(c, &np->d_wave, np->wave_bytes);
+    if (!rc) rc = dev_alloc(c, (void**)&np->d_wdone, sizeof(int) * (nph + 1));
+    if (rc) return rc;
+    char* d = (char*)np->d_wave;
+    CUDA_TRY(c, cudaMemcpyAsync(d, tab.data(), b0, cudaMemcpyHostToDevice, c->stream));
+    if (b1) CUDA_TRY(c, cudaMemcpyAsync(d + b0, W.deps.data(), b1, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(d + b0 + b1, W.uphase.data(), b2, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host tables are temporaries
+  }
+  np->nlevels = W.nlevels;
+  *out = np.get();
+  c->plans[key] = std::move(np);
+  return OPS_OK;
+}
+
+// Wavefront execution of a segment (OPS_MODE_WAVEFRONT): one persistent
+// kernel takes the plan's work units in level order and waits, per unit,
+// only on the phases it conflicts with.
+int run_wavefront(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl, const int* tile_in) {
+  JitWave* w = nullptr;
+  int rc = wave_code(c, first, count, hl, &w);
+  if (rc) return rc;
+  if (!w)
+    return fail(c, OPS_ERR_INVALID_ARG, "wavefront mode runs compiled loop bodies only (%s)", c->jit_why.c_str());
+  CachedPlan* cp = nullptr;
+  rc = wave_plan(c, first, count, tile_in, &cp);
+  if (rc) return rc;
+  const SkewedPlan& P = cp->plan;
+  LaunchEnv env = make_env(c);
+  c->stats.mode = OPS_MODE_WAVEFRONT;
+  c->stats.compiled = 1;
+  ++c->stats.segments;
+  c->stats.loops += count;
+  int ntiles = 1;
+  for (int d = 0; d < 3; ++d) {
+    ntiles *= P.ntiles[d];
+    c->stats.tile[d] = P.tile[d];
+    c->stats.skew[d] = P.skew[d];
+  }
+  c->stats.tiles = ntiles;
+  c->stats.phases += (int)P.phases.size();
+  c->stats.points += P.points;
+  if (P.phases.empty()) return OPS_OK;
+  const size_t nph = P.phases.size();
+  int row0 = -1, nrows = 0;
+  for (int i = 0; i < count; ++i) {
+    const DLoop& L = hl[dl_base + i];
+    if (L.nreds) {
+      if (row0 < 0) row0 = L.part_row;
+      nrows = L.part_row + L.nreds - row0;
+    }
+  }
+  const int grid = std::min(std::max(1, jit_wavefront_max_grid(w, c->num_sms)), c->part_stride);
+  if (nrows) {
+    CUDA_TRY(c, launch_part_init(env, row0, nrows));
+    ++c->stats.launches;
+  }
+  CUDA_TRY(c, cudaMemsetAsync(cp->d_wdone, 0, sizeof(int) * (nph + 1), c->stream));
+  rc = record_event(c);
+  if (rc) return rc;
+  const char* d = (const char*)cp->d_wave;
+  const WfPhase* d_ph = (const WfPhase*)d;
+  const int* d_deps = (const int*)(d + sizeof(WfPhase) * nph);
+  const int* d_uphase = d_deps + cp->wave.deps.size();
+  CUDA_TRY(c, jit_launch_wavefront(w, env, c->d_loops + dl_base, d_ph, d_deps, d_uphase, (int)cp->wave.nunits,
+                                   cp->d_wdone, cp->d_wdone + nph, grid));
+  ++c->stats.launches;
+  ++c->stats.kernel_launches;
+  rc = record_event(c);
+  if (rc) return rc;
+  if (nrows) {
+    CUDA_TRY(c, launch_fold(env, row0, nrows, grid));
+    ++c->stats.launches;
+  }
   return OPS_OK;
 }
 
@@ -925,6 +1118,12 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
     }
     mode = OPS_MODE_SKEWED;
     tile_in = c->cfg.tile;
+  }
+  if (mode == OPS_MODE_WAVEFRONT) {
+    // one loop has no dependencies to schedule; checked and interpreted
+    // runs go through the persistent skewed kernel instead
+    if (count > 1 && !c->cfg.interpret && !c->cfg.check) return run_wavefront(c, first, count, dl_base, hl, tile_in);
+    mode = count > 1 ? OPS_MODE_SKEWED : OPS_MODE_UNTILED;
   }
   LaunchEnv env = make_env(c);
   c->stats.mode = mode;
@@ -1353,8 +1552,11 @@ int ops_finalize(ops_ctx c) {
       dev_free(c, d.alloc, d.bytes);
       dev_free(c, d.alt, d.bytes);
     }
-    for (auto& kv : c->plans)
+    for (auto& kv : c->plans) {
       if (kv.second->d_phases) dev_free(c, kv.second->d_phases, sizeof(Phase) * kv.second->plan.phases.size());
+      if (kv.second->d_wave) dev_free(c, kv.second->d_wave, kv.second->wave_bytes);
+      if (kv.second->d_wdone) dev_free(c, kv.second->d_wdone, sizeof(int) * (kv.second->plan.phases.size() + 1));
+    }
     for (auto& kv : c->oplans)
       if (kv.second && kv.second->d_tab) dev_free(c, kv.second->d_tab, sizeof(int) * kv.second->tab_ints);
     dev_free(c, c->d_oloops, sizeof(DLoop) * (size_t)c->oloops_cap);
@@ -1386,7 +1588,7 @@ int ops_set_timing(ops_ctx c, int timing) {
 
 int ops_set_mode(ops_ctx c, int mode, const int* tile, int segment) {
   if (!c) return OPS_ERR_INVALID_ARG;
-  if (mode < OPS_MODE_UNTILED || mode > OPS_MODE_AUTO) return fail(c, OPS_ERR_INVALID_ARG, "bad mode %d", mode);
+  if (mode < OPS_MODE_UNTILED || mode > OPS_MODE_WAVEFRONT) return fail(c, OPS_ERR_INVALID_ARG, "bad mode %d", mode);
   c->cfg.mode = mode;
   if (tile)
     for (int d = 0; d < 3; ++d) c->cfg.tile[d] = tile[d];
@@ -1657,6 +1859,74 @@ int ops_plan_skewed(ops_ctx c, const int* tile, int* out_ntiles, int* out_ranges
   return OPS_OK;
 }
 
+int ops_compile_queued_wavefront(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
+  const int n = (int)c->queue.size();
+  std::vector<DLoop> hl(n);
+  std::vector<FoldRow> rows;
+  for (int i = 0; i < n; ++i) fill_dloop(c, c->queue[i], hl[i], (int)rows.size(), rows);
+  std::string src, why;
+  double ms = 0.0;
+  const int rc = jit_compile_wavefront_only(hl.data(), n, read_only_args(c, 0, n), c->es, &src, &why, &ms);
+  if (src_len) *src_len = (int64_t)src.size();
+  if (src_out && cap > 0) {
+    const size_t k = std::min<size_t>(src.size(), (size_t)cap - 1);
+    std::memcpy(src_out, src.data(), k);
+    src_out[k] = '\0';
+  }
+  if (compile_ms) *compile_ms = ms;
+  if (rc) return fail(c, rc, "%s", why.c_str());
+  return OPS_OK;
+}
+
+int ops_plan_wavefront(ops_ctx c, const int* tile, int64_t* counts, int* out_phases, int64_t phase_cap,
+                       int* out_deps, int64_t dep_cap) {
+  if (!c || !tile || !counts) return OPS_ERR_INVALID_ARG;
+  if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
+  const int ndim = c->queue[0].dims;
+  std::vector<PLoop> pl;
+  for (const QLoop& q : c->queue) {
+    if (q.dims != ndim) return fail(c, OPS_ERR_INVALID_ARG, "queued loops of different dimensionality");
+    pl.push_back(plan_loop(c, q));
+  }
+  int t[3] = {1, 1, 1};
+  for (int d = 0; d < ndim; ++d) {
+    if (tile[d] < 1) return fail(c, OPS_ERR_INVALID_ARG, "tile sizes must be >= 1");
+    t[d] = tile[d];
+  }
+  SkewedPlan P;
+  build_skewed_ranges(pl, (int)c->dats.size(), ndim, t, P);
+  build_phases(pl, P);
+  WavePlan W;
+  build_wavefront(pl, (int)c->dats.size(), P, ndim - 1, jit_rows_per_unit(), kThreads, jit_wave_units_per_chunk(),
+                  jit_wave_slope(), W);
+  const int64_t nph = (int64_t)P.phases.size();
+  counts[0] = nph;
+  counts[1] = (int64_t)W.deps.size();
+  counts[2] = W.nunits;
+  counts[3] = W.nlevels;
+  if (out_phases) {
+    if (12 * nph > phase_cap) return fail(c, OPS_ERR_INVALID_ARG, "out_phases needs %lld ints", (long long)(12 * nph));
+    for (int64_t q = 0; q < nph; ++q) {
+      int* o = out_phases + 12 * q;
+      o[0] = P.phases[q].loop;
+      o[1] = W.nchunk[q];
+      o[2] = W.ustart[q];
+      o[3] = W.dep_off[q];
+      o[4] = W.dep_off[q + 1] - W.dep_off[q];
+      o[5] = W.level[q];
+      for (int k = 0; k < 6; ++k) o[6 + k] = P.phases[q].box[k];
+    }
+  }
+  if (out_deps) {
+    if ((int64_t)W.deps.size() > dep_cap)
+      return fail(c, OPS_ERR_INVALID_ARG, "out_deps needs %lld ints", (long long)W.deps.size());
+    if (!W.deps.empty()) std::memcpy(out_deps, W.deps.data(), sizeof(int) * W.deps.size());
+  }
+  return OPS_OK;
+}
+
 int ops_compile_queued(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms) {
   if (!c) return OPS_ERR_INVALID_ARG;
   if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
@@ -1706,6 +1976,7 @@ int ops_compile_queued(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, 
     rc = jit_compile_overlap_only(ol.data(), n, lay, &osrc, &why, &ms);
     src += osrc;
   }
+
   if (src_len) *src_len = (int64_t)src.size();
   if (src_out && cap > 0) {
     const size_t k = std::min<size_t>(src.size(), (size_t)cap - 1);

@@ -82,6 +82,49 @@ def check_skewed(loops, stencils, ndim, ntiles, ranges):
     assert ver == ref_ver, "final versions differ"
 
 
+def check_phase_order(loops, stencils, ndim, phases, order):
+    """phases: [(loop, box)]; order: the sequence of phase indices actually
+    executed.  Every (loop, point) of every loop's range must run exactly
+    once, every read must see its program-order version and every cell must
+    end with its program-order version."""
+    ref_ver, ref_seen = untiled(loops, stencils, ndim)
+    ver, seen = {}, {}
+    done = set()
+    for q in order:
+        l, box = phases[q]
+        for rev in _points(box):
+            P = _pt(rev)
+            assert (l, P) not in done, f"loop {l} point {P} executed twice"
+            done.add((l, P))
+            run_point(loops[l], l, P, stencils, ndim, ver, seen)
+    for l, lp in enumerate(loops):
+        for rev in _points(lp.rng[:ndim]):
+            assert (l, _pt(rev)) in done, f"loop {l} point {_pt(rev)} never executed"
+    for k, v in ref_seen.items():
+        assert seen[k] == v, f"read {k}: sees version {seen[k]}, program order {v}"
+    assert ver == ref_ver, "final versions differ"
+
+
+def random_topological(deps, rnd: random.Random):
+    """A random order of range(len(deps)) that puts every p in deps[q] before q."""
+    waiting = [len(d) for d in deps]
+    users = [[] for _ in deps]
+    for q, d in enumerate(deps):
+        for p in d:
+            users[p].append(q)
+    ready = [q for q in range(len(deps)) if waiting[q] == 0]
+    order = []
+    while ready:
+        q = ready.pop(rnd.randrange(len(ready)))
+        order.append(q)
+        for u in users[q]:
+            waiting[u] -= 1
+            if waiting[u] == 0:
+                ready.append(u)
+    assert len(order) == len(deps), "dependency cycle"
+    return order
+
+
 def check_overlapped(loops, stencils, ndim, tiles: Sequence, plan_fn):
     """Every tile runs on a private copy of the pre-segment state; every point
     it computes must see program-order inputs, every live-in read must lie in

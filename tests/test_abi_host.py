@@ -1,5 +1,6 @@
 """Host-side checks of the C ABI: no GPU needed (host-only contexts)."""
 import ctypes as C
+import json
 import os
 import random
 import re
@@ -13,7 +14,7 @@ from oracle import plan as oplan
 from synth import workloads as W
 from synth.program import DAT, READ, WRITE, RW, INC, BodyBuilder
 
-from bruteforce import check_skewed, random_chain
+from bruteforce import check_phase_order, check_skewed, random_chain, random_topological
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -111,7 +112,7 @@ def test_validation_errors(lib):
     ops.ops_finalize(ctx)
 
 
-def _abi_plan(chain_like, loops, stencils, ndim, tile, overlapped_owned=None):
+def _abi_plan(chain_like, loops, stencils, ndim, tile, overlapped_owned=None, wavefront=False):
     ctx = host_ctx()
     b = ops.ops_decl_block(ctx, ndim)
     ndats = 1 + max(a.handle for lp in loops for a in lp.args if a.kind == DAT)
@@ -135,6 +136,8 @@ def _abi_plan(chain_like, loops, stencils, ndim, tile, overlapped_owned=None):
         ops.ops_par_loop(ctx, b, ndim, lp.rng[:ndim], args, code, K, lp.name)
     if overlapped_owned is not None:
         out = [ops.ops_plan_overlapped(ctx, o, len(loops), ndats) for o in overlapped_owned]
+    elif wavefront:
+        out = ops.ops_plan_wavefront(ctx, tile)
     else:
         out = ops.ops_plan_skewed(ctx, tile, ndim, len(loops))
     ops.ops_queue_clear(ctx)
@@ -177,6 +180,70 @@ def test_cloverleaf_shaped_plan_matches_oracle(lib):
         for d in range(2):
             want = np.array([[list(rg[d][t][l]) for l in range(len(c.loops))] for t in range(nt[d])])
             assert (got[d] == want).all()
+
+
+def _check_wavefront(loops, st, ndim, tile, rnd):
+    """The library's wavefront plan against the oracle: the same phases in
+    Algorithm 2 order, every exact conflict among its dependencies, levels
+    and work units as documented, and random orders of its dependency DAG
+    valid under the brute-force version check."""
+    ph, deps, nunits, nlevels = _abi_plan(None, loops, st, ndim, tile, wavefront=True)
+    nt, rg, _ = oplan.skewed_plan(loops, st, ndim, tile)
+    want = oplan.phases_in_order(loops, nt, rg, ndim)
+    assert len(ph) == len(want)
+    for q, (l, box) in enumerate(want):
+        assert ph[q, 0] == l
+        assert [(int(ph[q, 6 + 2 * d]), int(ph[q, 7 + 2 * d])) for d in range(ndim)] == list(box)
+    lib_deps = [deps[ph[q, 3]:ph[q, 3] + ph[q, 4]].tolist() for q in range(len(ph))]
+    exact = oplan.phase_conflicts(loops, st, ndim, want)
+    for q in range(len(ph)):
+        assert all(p < q for p in lib_deps[q])
+        assert set(exact[q]) <= set(lib_deps[q]), f"phase {q}: missing {set(exact[q]) - set(lib_deps[q])}"
+        lv = max([ph[p, 5] + 1 for p in lib_deps[q]] + [0])
+        assert ph[q, 5] == lv
+        assert ph[q, 1] >= 1
+    assert nlevels == (int(ph[:, 5].max()) + 1 if len(ph) else 0)
+    assert nunits == int(ph[:, 1].sum())
+    # units: each phase's chunks contiguous, every dependency handed out first
+    order = sorted(range(len(ph)), key=lambda q: ph[q, 2])
+    pos = 0
+    for q in order:
+        assert ph[q, 2] == pos
+        pos += ph[q, 1]
+        assert all(ph[p, 2] < ph[q, 2] for p in lib_deps[q])
+    if len(ph) <= 400:
+        for k in range(2):
+            check_phase_order(loops, st, ndim, want, random_topological(lib_deps, rnd))
+    return ph, lib_deps
+
+
+def test_wavefront_plan_worked_example(lib):
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "worked_example_1d_wavefront.json")))
+    c = W.worked_example_1d()
+    ph, deps = _check_wavefront(c.loops, c.stencils, 1, g["tile"], random.Random(1))
+    assert deps == g["deps"]
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_library_wavefront_plan(lib, ndim):
+    rnd = random.Random(5000 + ndim)
+    sizes = {1: (30,), 2: (12, 10), 3: (7, 6, 5)}[ndim]
+    for trial in range({1: 40, 2: 20, 3: 8}[ndim]):
+        n = [rnd.randint(max(3, s // 2), s) for s in sizes]
+        loops, st = random_chain(rnd, ndim, n, ndats=rnd.randint(3, 5), nloops=rnd.randint(2, 7))
+        ts = [rnd.randint(1, n[d] + 2) for d in range(ndim)]
+        _check_wavefront(loops, st, ndim, ts, rnd)
+
+
+def test_cloverleaf_shaped_wavefront_plan(lib):
+    """The bench chain's shape at 40^2 with 4-row tiles: the library finds
+    every conflict, and the phases of a level are many (the wavefront's
+    parallelism)."""
+    c = W.cloverleaf2d(n=40, steps=1)
+    ph, deps = _check_wavefront(c.loops, c.stencils, 2, [44, 4], random.Random(2))
+    levels = np.bincount(ph[:, 5])
+    assert levels.max() >= 8
+    assert len(levels) < len(ph) // 4
 
 
 @pytest.mark.parametrize("ndim", [1, 2, 3])
@@ -246,5 +313,33 @@ def test_generated_loop_bodies_compile(lib, name, fp32):
     for i in range(len(c.loops)):
         assert f" u{i}(" in src
     assert ("fp32" in src) == fp32 and ("__fmaf_rn" in src) == fp32
+    ops.ops_queue_clear(ctx)
+    ops.ops_finalize(ctx)
+
+
+@pytest.mark.parametrize("name,fp32", [("small2d", False), ("edge", False), ("edge", True)])
+def test_generated_wavefront_kernel_compiles(lib, name, fp32):
+    """The wavefront kernel (every loop body of the segment behind one
+    dispatch on the phase's loop) compiles for sm_103a, FP64 or FP32."""
+    from paper_1704_00693_gb300.chain import ChainRunner
+    if name == "edge":
+        from test_gpu_chain import edge_chain
+        c = edge_chain()
+    else:
+        c = W.small2d(n=40, reps=1)
+    cfg = ops.ops_config_default()
+    cfg.device = ops.OPS_DEVICE_NONE
+    cfg.real = ops.OPS_REAL_F32 if fp32 else ops.OPS_REAL_F64
+    ctx = ops.ops_init(cfg)
+    r = ChainRunner(c, ctx=ctx, upload=False, mode="wavefront")
+    r.enqueue_step()
+    try:
+        src, n, ms = ops.ops_compile_queued(ctx, want_source=True, wavefront=True)
+    except ops.OpsError as e:
+        if e.code == ops.OPS_ERR_NO_DEVICE:
+            pytest.skip("NVRTC is not installed")
+        raise
+    assert " wf(" in src and src.count("      case ") == len(c.loops)
+    assert ("fp32" in src) == fp32
     ops.ops_queue_clear(ctx)
     ops.ops_finalize(ctx)

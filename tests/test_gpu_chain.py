@@ -59,7 +59,8 @@ def test_worked_example_1d():
     c = W.worked_example_1d()
     ref, _ = oracle.run_chain(c)
     for mode, tile in [("untiled", None), ("skewed", (4,)), ("skewed", (1,)), ("skewed", (3,)),
-                       ("overlapped", (4,)), ("overlapped", (1,)), ("overlapped", (3,))]:
+                       ("overlapped", (4,)), ("overlapped", (1,)), ("overlapped", (3,)),
+                       ("wavefront", (4,)), ("wavefront", (1,)), ("wavefront", (3,))]:
         for interp in (False, True):
             got, _, st = run_gpu(c, mode, tile, interpret=interp)
             assert_same(c, got, ref, what=f"{mode} {tile} interpret={interp}")
@@ -68,7 +69,9 @@ def test_worked_example_1d():
 @pytest.mark.parametrize("interpret", [False, True])
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 0, 0)), ("skewed", (0, 40, 0)),
                                        ("skewed", (100, 33, 0)), ("overlapped", (0, 0, 0)),
-                                       ("overlapped", (64, 16, 0)), ("overlapped", (100, 33, 0))])
+                                       ("overlapped", (64, 16, 0)), ("overlapped", (100, 33, 0)),
+                                       ("wavefront", (0, 0, 0)), ("wavefront", (0, 4, 0)),
+                                       ("wavefront", (100, 33, 0))])
 def test_small2d_chain_bit_exact(mode, tile, interpret):
     """8 loops x 10 repetitions on 256^2 (radius-1 stencils, zero halo)."""
     c = W.small2d(n=256, reps=10)
@@ -77,6 +80,9 @@ def test_small2d_chain_bit_exact(mode, tile, interpret):
     assert_same(c, got, ref, what=f"{mode} {tile}")
     if mode == "skewed":
         assert st["mode"] == ops.OPS_MODE_SKEWED
+    if mode == "wavefront":
+        # interpreted bodies take the persistent skewed kernel instead
+        assert st["mode"] == (ops.OPS_MODE_SKEWED if interpret else ops.OPS_MODE_WAVEFRONT)
     if mode == "overlapped":
         # one run of the 8 loops of a step: radius-1 halos grow to 8 points
         assert st["mode"] == ops.OPS_MODE_OVERLAPPED and st["segments"] >= 1
@@ -87,7 +93,8 @@ def test_small2d_chain_bit_exact(mode, tile, interpret):
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 32, 0)), ("skewed", (0, 17, 0)),
                                        ("skewed", (37, 23, 0)), ("skewed", (0, 0, 0)), ("auto", None),
                                        ("overlapped", None), ("overlapped", (32, 8, 0)),
-                                       ("overlapped", (40, 100, 0))])
+                                       ("overlapped", (40, 100, 0)), ("wavefront", (0, 0, 0)),
+                                       ("wavefront", (0, 5, 0)), ("wavefront", (37, 8, 0))])
 def test_cloverleaf_shaped_chain(mode, tile, interpret):
     """83-loop CloverLeaf-shaped steps on a 100^2 grid (ragged tiles), with
     node ranges, thin halo strips, RW updates and two reductions per step;
@@ -102,7 +109,7 @@ def test_cloverleaf_shaped_chain(mode, tile, interpret):
 
 
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 0, 0)), ("skewed", (0, 9, 7)),
-                                       ("overlapped", None), ("auto", None)])
+                                       ("overlapped", None), ("auto", None), ("wavefront", (0, 0, 3))])
 def test_cloverleaf3d_shaped_chain(mode, tile):
     """141-loop CloverLeaf-3D-shaped steps on 40^3 (7-, 27- and one-sided
     8-point stencils, node ranges, halo planes, two reductions per step)."""
@@ -113,7 +120,8 @@ def test_cloverleaf3d_shaped_chain(mode, tile):
 
 
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 0, 0)), ("skewed", (0, 16, 0)),
-                                       ("overlapped", None), ("overlapped", (64, 16, 0)), ("auto", None)])
+                                       ("overlapped", None), ("overlapped", (64, 16, 0)), ("auto", None),
+                                       ("wavefront", (0, 0, 0)), ("wavefront", (0, 3, 0))])
 def test_ppcg_shaped_chain(mode, tile):
     """The TeaLeaf-PPCG-shaped chain: setup loops, then 10 Chebyshev inner
     iterations (three loops each, no reduction) in one segment, and z.r."""
@@ -166,7 +174,8 @@ def test_opensbli_shaped_3d():
     ref, _ = oracle.run_chain(c)
     for mode, tile, interp in [("untiled", None, False), ("skewed", (0, 0, 6), False), ("skewed", (0, 7, 5), False),
                                ("untiled", None, True), ("skewed", (0, 7, 5), True),
-                               ("overlapped", (0, 0, 0), False), ("overlapped", (8, 7, 5), False)]:
+                               ("overlapped", (0, 0, 0), False), ("overlapped", (8, 7, 5), False),
+                               ("wavefront", (0, 0, 0), False), ("wavefront", (0, 7, 2), False)]:
         got, _, st = run_gpu(c, mode, tile, interpret=interp)
         assert_same(c, got, ref, what=f"3d {mode} {tile} interpret={interp}")
 
@@ -207,7 +216,8 @@ def edge_chain(n=30):
 
 @pytest.mark.parametrize("interpret", [False, True])
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 7, 0)), ("skewed", (11, 5, 0)),
-                                       ("overlapped", None), ("overlapped", (11, 5, 0))])
+                                       ("overlapped", None), ("overlapped", (11, 5, 0)), ("wavefront", (0, 3, 0)),
+                                       ("wavefront", (11, 5, 0))])
 def test_edge_cases(mode, tile, interpret):
     c = edge_chain()
     ref, ref_hist = oracle.run_chain(c)
@@ -239,6 +249,52 @@ def test_barrier_timeout_reports_and_context_recovers():
     ref, _ = oracle.run_chain(c)
     got, _, _ = run_gpu(c, "skewed", (0, 8, 0))
     assert_same(c, got, ref, what="after timeout")
+
+
+def test_wavefront_timeout_reports_and_context_recovers():
+    """The wavefront kernel's first work unit never reports completion: the
+    phases waiting on it give up after the limit, every CTA leaves, the host
+    sees OPS_ERR_TIMEOUT; a new context on the same device then runs the
+    same chain in wavefront mode normally."""
+    c = W.small2d(n=64, reps=1)
+    r = ChainRunner(c, mode="wavefront", tile=(0, 4, 0), timeout_ms=200, skip_barrier_block=0)
+    try:
+        r.enqueue_step()
+        with pytest.raises(ops.OpsError) as e:
+            ops.ops_sync(r.ctx)
+        assert e.value.code == ops.OPS_ERR_TIMEOUT
+    finally:
+        r.close()
+    ref, _ = oracle.run_chain(c)
+    got, _, st = run_gpu(c, "wavefront", (0, 4, 0))
+    assert st["mode"] == ops.OPS_MODE_WAVEFRONT
+    assert_same(c, got, ref, what="after timeout")
+
+
+def test_wavefront_jacobi_closed_form_and_stats():
+    """Jacobi steps in wavefront mode reproduce the Dirichlet eigenmode's
+    closed-form decay; the plan is cached and one kernel runs per flush."""
+    import math
+    n, K, nu = 62, 30, 0.125
+    c = W.jacobi2d(n, K, nu=nu, p=2, q=1)
+    ref, _ = oracle.run_chain(c)
+    r = ChainRunner(c, mode="wavefront", tile=(0, 4, 0))
+    try:
+        r.run()
+        got = r.fetch()
+        st = r.stats()
+        r.run()
+        st2 = r.stats()
+    finally:
+        r.close()
+    assert_same(c, got, ref, what="jacobi wavefront")
+    assert st["mode"] == ops.OPS_MODE_WAVEFRONT and st["barriers"] == 0
+    assert st["kernel_launches"] == st["segments"] >= 1
+    assert st["tiles"] == math.ceil(n / 4) and st["tile"][1] == 4
+    assert st2["plan_cache_hits"] >= 1
+    lam = -4 * math.sin(math.pi * 2 / (2 * (n + 1))) ** 2 - 4 * math.sin(math.pi * 1 / (2 * (n + 1))) ** 2
+    want = c.dats[0].init * (1 + nu * lam) ** K
+    assert np.abs(got[0] - want).max() <= 1e-13 * np.abs(want).max()
 
 
 def test_plan_cache_reuse_and_stats():
@@ -365,7 +421,8 @@ def test_borrowed_device_dats(mode, tile):
 
 
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 17, 0)), ("skewed", (0, 0, 0)),
-                                       ("overlapped", None), ("auto", None)])
+                                       ("overlapped", None), ("auto", None), ("wavefront", (0, 0, 0)),
+                                       ("wavefront", (0, 6, 0))])
 def test_fp32_chains_bit_exact(mode, tile):
     """An OPS_REAL_F32 context: float dats, single-precision arithmetic with
     explicit rounding on both sides, constants rounded to float on load; the

@@ -14,7 +14,7 @@ from oracle import plan as oplan
 from synth import workloads as W
 from synth import rng as R
 
-from bruteforce import check_overlapped, check_skewed, random_chain
+from bruteforce import check_overlapped, check_phase_order, check_skewed, random_chain, random_topological
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -235,6 +235,76 @@ def test_tiled_execution_equals_program_order(name, tile):
     for a, b in zip(got, ref):
         assert np.array_equal(a, b)
     assert hist == ref_hist
+
+
+# ---------------------------------------------------------- wavefront orders
+def test_phase_conflicts_worked_example():
+    """The conflict relation of the Sec. 4.B worked example, derived by hand
+    in the golden file: loop 1 of tile 1 depends on nothing of tile 0."""
+    g = json.load(open(os.path.join(GOLDEN, "worked_example_1d_wavefront.json")))
+    c = W.worked_example_1d()
+    nt, rg, _ = oplan.skewed_plan(c.loops, c.stencils, 1, g["tile"])
+    ph = oplan.phases_in_order(c.loops, nt, rg, 1)
+    assert [[l, list(b[0])] for l, b in ph] == g["phases"]
+    assert oplan.phase_conflicts(c.loops, c.stencils, 1, ph) == g["deps"]
+
+
+@pytest.mark.parametrize("ndim", [1, 2, 3])
+def test_phase_conflicts_allow_any_topological_order(ndim):
+    """Brute force on tiny random chains: every order of a skewed plan's
+    phases that respects phase_conflicts gives program-order versions at
+    every read and every cell (random orders and the order that runs each
+    phase as late as possible)."""
+    rnd = random.Random(7000 + ndim)
+    sizes = {1: (24,), 2: (10, 9), 3: (6, 5, 5)}[ndim]
+    for trial in range({1: 40, 2: 20, 3: 8}[ndim]):
+        n = [rnd.randint(max(3, s // 2), s) for s in sizes]
+        loops, st = random_chain(rnd, ndim, n, ndats=rnd.randint(3, 5), nloops=rnd.randint(2, 7))
+        ts = [rnd.randint(1, n[d] + 2) for d in range(ndim)]
+        nt, rg, _ = oplan.skewed_plan(loops, st, ndim, ts)
+        ph = oplan.phases_in_order(loops, nt, rg, ndim)
+        deps = oplan.phase_conflicts(loops, st, ndim, ph)
+        assert all(p < q for q, d in enumerate(deps) for p in d)
+        for k in range(3):
+            check_phase_order(loops, st, ndim, ph, random_topological(deps, rnd))
+        # latest first: always take the highest-numbered ready phase
+        users = [[] for _ in ph]
+        for q, d in enumerate(deps):
+            for p in d:
+                users[p].append(q)
+        waiting, ready, order = [len(d) for d in deps], [q for q, d in enumerate(deps) if not d], []
+        while ready:
+            ready.sort()
+            q = ready.pop()
+            order.append(q)
+            for u in users[q]:
+                waiting[u] -= 1
+                if waiting[u] == 0:
+                    ready.append(u)
+        check_phase_order(loops, st, ndim, ph, order)
+
+
+@pytest.mark.parametrize("name,tile", [("cloverleaf2d", (44, 5)), ("small2d", (40, 4)), ("jacobi2d", (26, 3)),
+                                       ("opensbli3d", (14, 14, 2))])
+def test_wavefront_order_equals_program_order(name, tile):
+    """Whole workloads in random conflict-respecting orders of their phases
+    give the program-order dats bit for bit and the same exact reductions;
+    with every dependency list cut to its first half (a planted mistake) some
+    order goes wrong."""
+    c = {"cloverleaf2d": lambda: W.cloverleaf2d(n=40, steps=1), "small2d": lambda: W.small2d(n=36, reps=2),
+         "jacobi2d": lambda: W.jacobi2d(n=24, iters=4, init="random"),
+         "opensbli3d": lambda: W.opensbli3d(n=10, steps=1)}[name]()
+    ref, ref_hist = oracle.run_chain(c)
+    for seed in range(2):
+        got, hist = oracle.run_chain_wavefront(c, tile, seed=seed)
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+        assert hist == ref_hist
+    wrong = 0
+    for seed in range(4):
+        got, _ = oracle.run_chain_wavefront(c, tile, seed=seed, drop=lambda q, d: d[:len(d) // 2])
+        wrong += any(not np.array_equal(a, b) for a, b in zip(got, ref))
+    assert wrong > 0
 
 
 def test_fp32_oracle_pins():
