@@ -452,7 +452,7 @@ def bench_chain(chain, stream, torch, steps=5):
         ms, kms, kl, launches, st = time_mode(chain, mode, None, steps, 3, stream, torch)
         out[mode] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
                      "kernel_ms_per_step": kms / steps,
-                     "schedule": {0: "untiled", 1: "skewed", 2: "overlapped"}.get(st["mode"]),
+                     "schedule": {0: "untiled", 1: "skewed", 2: "overlapped", 4: "wavefront"}.get(st["mode"]),
                      "tile": st["tile"], "compiled": st["compiled"]}
     out["speedup_auto_vs_untiled"] = out["untiled"]["ms_per_step"] / out["auto"]["ms_per_step"]
     return out
@@ -472,12 +472,12 @@ def bench_ppcg(stream, torch, n=4000, inner=10, steps=5):
     chain = W.ppcg2d(n=n, inner=inner)
     U, flops = workload_numbers(chain)
     out = {"n": n, "inner": inner, "untiled_bytes_per_step": U, "flops_per_step": flops}
-    for mode in ("untiled", "skewed", "overlapped", "auto"):
+    for mode in ("untiled", "skewed", "overlapped", "wavefront", "auto"):
         ms, kms, kl, launches, st = time_mode(chain, mode, None, steps, 3, stream, torch)
         out[mode] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
-                     "schedule": {0: "untiled", 1: "skewed", 2: "overlapped"}.get(st["mode"]),
+                     "schedule": {0: "untiled", 1: "skewed", 2: "overlapped", 4: "wavefront"}.get(st["mode"]),
                      "tile": st["tile"], "tiles": st["tiles"]}
-    for mode in ("skewed", "overlapped", "auto"):
+    for mode in ("skewed", "overlapped", "wavefront", "auto"):
         out[f"speedup_{mode}_vs_untiled"] = out["untiled"]["ms_per_step"] / out[mode]["ms_per_step"]
     return out
 
@@ -493,11 +493,11 @@ def bench_fp32(stream, torch, n=3840, steps=5):
     U = U // 2  # 4-byte elements
     out = {"n": n, "untiled_bytes_per_step": U, "dtype": "f32"}
     for mode, tile in (("untiled", None), ("skewed", None), ("skewed", [0, 1024, 0]), ("overlapped", None),
-                       ("auto", None)):
+                       ("wavefront", None), ("auto", None)):
         ms, kms, kl, launches, st = time_mode(chain, mode, tile, steps, 3, stream, torch, fp32=True)
         key = mode if tile is None else f"{mode}_{tile[1]}"
         out[key] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
-                    "schedule": {0: "untiled", 1: "skewed", 2: "overlapped"}.get(st["mode"]), "tile": st["tile"]}
+                    "schedule": {0: "untiled", 1: "skewed", 2: "overlapped", 4: "wavefront"}.get(st["mode"]), "tile": st["tile"]}
     for key in [k for k in out if isinstance(out[k], dict) and k != "untiled"]:
         out[f"speedup_{key}_vs_untiled"] = out["untiled"]["ms_per_step"] / out[key]["ms_per_step"]
     return out
@@ -615,9 +615,16 @@ def main():
         ums, ukms, ukl, _, _ = time_mode(chain, "untiled", None, args.steps, args.warmup, stream, torch)
         untiled = {"value": U * args.steps / (ums * 1e-3) / 1e9, "ms_per_step": ums / args.steps,
                    "kernel_ms_per_step": ukms / args.steps, "kernel_launches_per_step": ukl / args.steps}
+    wavefront = None
+    if not args.no_untiled and args.mode != "wavefront":
+        wms, wkms, wkl, _, wst = time_mode(chain, "wavefront", None, args.steps, args.warmup, stream, torch)
+        wavefront = {"value": U * args.steps / (wms * 1e-3) / 1e9, "ms_per_step": wms / args.steps,
+                     "kernel_ms_per_step": wkms / args.steps, "tile": wst["tile"], "phases": wst["phases"],
+                     "how": "OPS_MODE_WAVEFRONT: Algorithm 1 tiles of about 64 rows, one persistent kernel that "
+                            "runs (tile, loop) phases as their dependencies complete"}
 
     # the schedule the timed steps ran (the autotuner's pick in auto mode)
-    chosen_mode = {0: "untiled", 1: "skewed", 2: "overlapped"}.get(st["mode"], "skewed") if st else args.mode
+    chosen_mode = {0: "untiled", 1: "skewed", 2: "overlapped", 4: "wavefront"}.get(st["mode"], "skewed") if st else args.mode
     chosen_tile = list(st["tile"]) if st and chosen_mode != "untiled" else None
     e2e = None
     if not args.no_e2e:
@@ -646,7 +653,8 @@ def main():
     traffic = profile_traffic(chosen_mode, chosen_tile) if args.n == N_DEFAULT else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                 "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": ("u<i>: the loop bodies compiled from the IR, one kernel per loop, averaged over the "
+                "kernel": "wf: the wavefront kernel, one launch per step" if chosen_mode == "wavefront" else
+                          ("u<i>: the loop bodies compiled from the IR, one kernel per loop, averaged over the "
                            "step's launches") if st and st.get("compiled") else
                           {"skewed": "k_skewed", "overlapped": "k_overlap"}.get(chosen_mode, "k_untiled"),
                 "peak_source": f"FP64: {NUM_SMS} SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 flop x {sm_max:.0f} MHz "
@@ -672,13 +680,13 @@ def main():
     line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload(n), "mode": args.mode, "schedule": chosen_mode,
+            "config": {"workload": workload(args.n), "mode": args.mode, "schedule": chosen_mode,
                        "tile": st["tile"] if st else None,
                        "tiles": st["tiles"] if st else None, "l2": "inputs larger than L2 (25 dats, 3.0 GB)",
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "untiled_bytes_per_step": U, "flops_per_step": flops},
             "speedup_vs_untiled": (untiled["ms_per_step"] / (ms / args.steps)) if untiled else None,
-            "untiled": untiled, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "untiled": untiled, "wavefront": wavefront, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
             "cg_4000": cg, "serving": serving, "opensbli3d_320": chain3d, "cloverleaf3d_330": hydro3d, "ppcg_4000": ppcg, "cloverleaf2d_3840_fp32": fp32,
             "plan": {"phases": st["phases"], "barriers": st["barriers"], "skew": st["skew"],

@@ -66,7 +66,7 @@ extern "C" {
 #define OPS_MODE_WAVEFRONT 4  /* Algorithm 1 tiles run as a dependence-driven wavefront (Sec. 4.B leaves
                                  wavefront scheduling of the tiles to future work) */
 /* OPS_MODE_WAVEFRONT cuts the outermost dimension into thin tiles (tile[ndim-1]
- * points; 0 = about 32768 points per tile) and leaves the other dimensions
+ * points; 0 = about 262144 points per tile) and leaves the other dimensions
  * whole unless tile[] sets them.  Algorithm 1 gives every (tile, loop) phase
  * its range; each phase then depends only on the earlier phases it conflicts
  * with (a shared dat that one of the two writes, in intersecting regions,
@@ -74,8 +74,9 @@ extern "C" {
  * body of the segment (compiled at run time, so this mode needs NVRTC) hands
  * out chunks of phases in order of their dependency level, and each chunk
  * waits only on its phase's dependencies -- no grid-wide barrier.  A segment
- * of one loop runs untiled; with check = 1 or interpret = 1 the segment runs
- * in OPS_MODE_SKEWED.  Results are identical to every other mode. */
+ * of one loop runs untiled; with check = 1 or interpret = 1, or without
+ * NVRTC, the segment runs in OPS_MODE_SKEWED.  Results are identical to every
+ * other mode.  OPS_MODE_AUTO does not try this mode. */
 
 /* ---- argument kinds, access modes, reduction operators ---- */
 #define OPS_ARG_DAT 0    /* a dat accessed through a stencil */

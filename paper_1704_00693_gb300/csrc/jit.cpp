@@ -254,6 +254,7 @@ struct LoopGen {
   std::ostringstream& os;
   bool ov = false;                    // overlapped tile: dats in shared footprints, owned-point reductions
   bool f32 = false;                   // FP32 dats and arithmetic
+  int nt = kThreads;                  // threads per CTA of the enumeration (not overlapped)
   const char* T = "double";
   const char *fadd = "__dadd_rn", *fsub = "__dsub_rn", *fmul = "__dmul_rn", *fdiv = "__ddiv_rn", *ffma = "__fma_rn";
 
@@ -441,7 +442,7 @@ struct LoopGen {
     if (ov)
       os << "  run_units<" << P << ", " << kOvThreads << ">(x0, x1, y0, y1, z0, z1, 0, 1, one, full);\n";
     else
-      os << "  run_units<" << P << ", " << kThreads << ">(x0, x1, y0, y1, z0, z1, ck, nck, one, full);\n";
+      os << "  run_units<" << P << ", " << nt << ">(x0, x1, y0, y1, z0, z1, ck, nck, one, full);\n";
     for (int k = 0; k < L.nreds; ++k)
       os << "  flush_red(" << L.red_op[k] << ", acc" << k << ", part, stride, L->part_row + " << k << ", "
          << (ov ? "0" : "assign") << ");\n";
@@ -583,80 +584,99 @@ std::string generate_overlap(const DLoop* loops, int count, const OvLayout& lay)
 // earliest unfinished unit can always proceed, so the waits end.  The first
 // warp polls up to 32 dependency counters at once; each wait is bounded in
 // wall-clock time and a CTA that gives up sets the error word and leaves, as
-// does every CTA that finds the word set.
+// does every CTA that finds the word set.  A CTA draws its next ticket while
+// the current body runs, and its first warp reports the unit done and waits
+// for the next one's dependencies in the same step.
 const char* kWfPrelude = R"WFP(
 struct WfPhase { int loop, nchunk, ustart, dep0, ndep, pad; int box[6]; };
-__device__ __forceinline__ int ld_acquire(const int* p) {
+// Polls are relaxed loads; one acquire fence follows the last of them (an
+// acquire on every poll would keep invalidating the SM's L1, which the
+// stencil loads of every CTA on the SM rely on).
+__device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+// add with release semantics: the CTA's writes before the preceding barrier
+// are visible to any thread that acquires the new value
+__device__ __forceinline__ void red_release(int* p, int v) {
+  asm volatile("red.release.gpu.global.add.s32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
 )WFP";
 
 std::string generate_wavefront(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es) {
+  const int nt = jit_wave_threads();
   std::ostringstream os;
-  os << "// opstile wavefront kernel: " << kJitPts << " rows per unit, " << kJitMinCtas << " CTAs per SM, "
+  os << "// opstile wavefront kernel: " << kJitPts << " rows per unit, " << nt << " threads, "
+     << jit_wave_min_ctas() << " CTAs per SM, "
      << (es == 4 ? "fp32" : "fp64") << "\n";
   os << kPrelude << kDeviceCommon << kPreludeTail << kWfPrelude;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
   os << "static_assert(sizeof(WfPhase) == " << sizeof(WfPhase) << ", \"WfPhase layout\");\n";
   for (int i = 0; i < count; ++i) {
     LoopGen g(loops[i], ro[i], os, false, es == 4);
+    g.nt = nt;
     g.emit(i);
   }
-  os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas
+  // Per work unit: the body, a barrier, then the first warp reports the
+  // unit done (release), and waits for the dependencies of the next unit,
+  // whose ticket thread 0 drew while the body ran.
+  os << "extern \"C\" __global__ void __launch_bounds__(" << nt << ", " << jit_wave_min_ctas()
      << ") wf(const DLoop* __restrict__ L,\n"
         "    const WfPhase* __restrict__ ph, const int* __restrict__ deps, const int* __restrict__ uphase,\n"
         "    int nunits, int* done, int* ticket, const double* __restrict__ scal, DD* part, int stride, int* err,\n"
         "    long long timeout_ns, int skip_unit) {\n"
         "  __shared__ int s_u, s_ok;\n"
-        "  for (;;) {\n"
-        "    if (threadIdx.x == 0) s_u = *(volatile int*)err ? nunits : atomicAdd(ticket, 1);\n"
-        "    __syncthreads();\n"
-        "    const int u = s_u;\n"
-        "    if (u >= nunits) return;\n"
-        "    const int q = uphase[u];\n"
-        "    const WfPhase P = ph[q];\n"
+        "  int nxt = 0;\n"
+        "  if (threadIdx.x == 0) nxt = atomicAdd(ticket, 1);\n"
+        "  for (int u = -1;;) {\n"
         "    if (threadIdx.x < 32) {\n"
+        "      if (u >= 0 && threadIdx.x == 0 && u != skip_unit) red_release(done + uphase[u], 1);\n"
+        "      const int v = __shfl_sync(0xffffffffu, nxt, 0);\n"
         "      bool ok = true;\n"
-        "      unsigned long long t0 = 0;\n"
-        "      for (int j = threadIdx.x; ok && j < P.ndep; j += 32) {\n"
-        "        const int d = deps[P.dep0 + j];\n"
-        "        const int want = ph[d].nchunk;\n"
-        "        unsigned spins = 0;\n"
-        "        while (ld_acquire(done + d) < want) {\n"
-        "          if ((++spins & 63u) == 0) {\n"
-        "            if (t0 == 0) {\n"
-        "              t0 = now_ns();\n"
-        "            } else if (*(volatile int*)err || (long long)(now_ns() - t0) > timeout_ns) {\n"
-        "              ok = false;\n"
-        "              break;\n"
+        "      if (v < nunits) {\n"
+        "        const WfPhase& Q = ph[uphase[v]];\n"
+        "        const int dep0 = Q.dep0, ndep = Q.ndep;\n"
+        "        unsigned long long t0 = 0;\n"
+        "        for (int j = threadIdx.x; ok && j < ndep; j += 32) {\n"
+        "          const int d = deps[dep0 + j];\n"
+        "          const int want = ph[d].nchunk;\n"
+        "          unsigned spins = 0;\n"
+        "          while (ld_relaxed(done + d) < want) {\n"
+        "            if ((++spins & 63u) == 0) {\n"
+        "              if (t0 == 0) {\n"
+        "                t0 = now_ns();\n"
+        "              } else if (*(volatile int*)err || (long long)(now_ns() - t0) > timeout_ns) {\n"
+        "                ok = false;\n"
+        "                break;\n"
+        "              }\n"
         "            }\n"
         "          }\n"
         "        }\n"
         "      }\n"
         "      ok = __all_sync(0xffffffffu, ok);\n"
+        "      fence_acq_rel();\n"
         "      if (threadIdx.x == 0) {\n"
         "        if (!ok) atomicCAS(err, 0, 1);\n"
-        "        __threadfence();\n"
-        "        s_ok = ok;\n"
+        "        s_u = v;\n"
+        "        s_ok = ok && !*(volatile int*)err;\n"
         "      }\n"
         "    }\n"
         "    __syncthreads();\n"
-        "    if (!s_ok) return;\n"
+        "    u = s_u;\n"
+        "    if (u >= nunits || !s_ok) return;\n"
+        "    if (threadIdx.x == 0) nxt = atomicAdd(ticket, 1);\n"
+        "    const WfPhase P = ph[uphase[u]];\n"
         "    const int ck = u - P.ustart;\n"
         "    switch (P.loop) {\n";
   for (int i = 0; i < count; ++i)
-    os << "      case " << i << ": body" << i << "(L + " << i
-       << ", P.box[0], P.box[1], P.box[2], P.box[3], P.box[4], P.box[5], ck, P.nchunk, scal, part, stride, 0); "
-          "break;\n";
+    os << "      case " << i << ": body" << i
+       << "(L + " << i << ", P.box[0], P.box[1], P.box[2], P.box[3], P.box[4], P.box[5], ck, P.nchunk, scal, part, "
+          "stride, 0); break;\n";
   os << "      default: break;\n"
         "    }\n"
         "    __syncthreads();\n"
-        "    if (threadIdx.x == 0 && u != skip_unit) {\n"
-        "      __threadfence();\n"
-        "      atomicAdd(done + q, 1);\n"
-        "    }\n"
         "  }\n"
         "}\n";
   return os.str();
@@ -1021,7 +1041,22 @@ cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const D
 int jit_rows_per_unit() { return kJitPts; }
 
 int jit_wave_units_per_chunk() {
-  static const int v = env_int("OPSTILE_WF_UNITS", 8, 1, 1 << 20);
+  static const int v = env_int("OPSTILE_WF_UNITS", 16, 1, 1 << 20);
+  return v;
+}
+
+int jit_wave_threads() {
+  // 32, 64, 128 or 256 (OPSTILE_WF_THREADS rounds down to one of them)
+  static const int v = [] {
+    int t = env_int("OPSTILE_WF_THREADS", 128, 32, 256), p = 32;
+    while (p * 2 <= t) p *= 2;
+    return p;
+  }();
+  return v;
+}
+
+int jit_wave_min_ctas() {
+  static const int v = env_int("OPSTILE_WF_MINB", (kJitMinCtas * kThreads) / jit_wave_threads(), 1, 32);
   return v;
 }
 
@@ -1101,7 +1136,7 @@ int jit_compile_wavefront_only(const DLoop* loops, int count, const std::vector<
 int jit_wavefront_max_grid(JitWave* w, int num_sms) {
   std::lock_guard<std::mutex> lk(g_mu);
   int per_sm = 0;
-  if (g_api.occupancy(&per_sm, w->f, kThreads, 0) != CUDA_SUCCESS) return 0;
+  if (g_api.occupancy(&per_sm, w->f, jit_wave_threads(), 0) != CUDA_SUCCESS) return 0;
   return per_sm * num_sms;
 }
 
@@ -1120,7 +1155,8 @@ cudaError_t jit_launch_wavefront(const JitWave* w, const LaunchEnv& env, const D
   long long a11 = env.timeout_ns;
   int a12 = env.skip_block;
   void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10, &a11, &a12};
-  return to_cuda(g_api.launch(w->f, (unsigned)grid, 1, 1, kThreads, 1, 1, 0, (CUstream)env.stream, args, nullptr));
+  return to_cuda(
+      g_api.launch(w->f, (unsigned)grid, 1, 1, jit_wave_threads(), 1, 1, 0, (CUstream)env.stream, args, nullptr));
 }
 
 }  // namespace opstile

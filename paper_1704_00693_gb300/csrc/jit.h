@@ -76,9 +76,14 @@ struct WfPhase {
 };
 struct JitWave;
 // P of the compiled enumeration (rows per unit); enumeration units per
-// wavefront work unit (OPSTILE_WF_UNITS, default 8)
+// wavefront work unit (OPSTILE_WF_UNITS, default 16)
 int jit_rows_per_unit();
 int jit_wave_units_per_chunk();
+// threads per CTA of the wavefront kernel (OPSTILE_WF_THREADS, default 128)
+int jit_wave_threads();
+// CTAs per SM the wavefront kernel's registers are sized for (OPSTILE_WF_MINB,
+// default: the per-loop kernels' thread count per SM)
+int jit_wave_min_ctas();
 // slope of the wavefront's ticket order (OPSTILE_WF_SLOPE, default 1; see build_wavefront)
 int jit_wave_slope();
 int jit_wavefront(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,

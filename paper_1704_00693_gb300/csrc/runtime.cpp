@@ -919,8 +919,9 @@ int wave_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, Jit
 }
 
 // Points of one wavefront tile along the outermost dimension when the tile
-// size is automatic: about eight full 4096-point rows.
-constexpr int64_t kWavePoints = 8 * 4096;
+// size is automatic: about 64 full 4096-point rows (the fastest of 4-64 rows
+// on the 3840^2 CloverLeaf-shaped chain, FP32 and FP64).
+constexpr int64_t kWavePoints = 64 * 4096;
 
 // The plan of a wavefront segment (cached like the skewed plans): Algorithm
 // 1's ranges for thin tiles along the outermost dimension (the others
@@ -949,7 +950,7 @@ int wave_plan(ops_ctx c, int first, int count, const int* tile_in, CachedPlan** 
   tile[ndim - 1] =
       tile_in[ndim - 1] > 0 ? tile_in[ndim - 1] : (int)std::max<int64_t>(1, kWavePoints / std::max<int64_t>(1, inner));
   const int P = jit_rows_per_unit(), upc = jit_wave_units_per_chunk(), slope = jit_wave_slope();
-  std::vector<int> key = {-OPS_MODE_WAVEFRONT, ndim, tile[0], tile[1], tile[2], P, upc, slope};
+  std::vector<int> key = {-OPS_MODE_WAVEFRONT, ndim, tile[0], tile[1], tile[2], P, upc, slope, jit_wave_threads()};
   for (int i = 0; i < count; ++i) {
     const QLoop& q = c->queue[first + i];
     for (int k = 0; k < 6; ++k) key.push_back(q.rng[k]);
@@ -973,7 +974,7 @@ int wave_plan(ops_ctx c, int first, int count, const int* tile_in, CachedPlan** 
   build_skewed_ranges(pl, (int)c->dats.size(), ndim, tile, np->plan);
   build_phases(pl, np->plan);
   WavePlan& W = np->wave;
-  build_wavefront(pl, (int)c->dats.size(), np->plan, ndim - 1, P, kThreads, upc, slope, W);
+  build_wavefront(pl, (int)c->dats.size(), np->plan, ndim - 1, P, jit_wave_threads(), upc, slope, W);
   c->stats.plan_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   const size_t nph = np->plan.phases.size();
   if (W.nunits >= (1ll << 31) || W.deps.size() >= (1ull << 31))
@@ -1010,14 +1011,10 @@ int wave_plan(ops_ctx c, int first, int count, const int* tile_in, CachedPlan** 
 // Wavefront execution of a segment (OPS_MODE_WAVEFRONT): one persistent
 // kernel takes the plan's work units in level order and waits, per unit,
 // only on the phases it conflicts with.
-int run_wavefront(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl, const int* tile_in) {
-  JitWave* w = nullptr;
-  int rc = wave_code(c, first, count, hl, &w);
-  if (rc) return rc;
-  if (!w)
-    return fail(c, OPS_ERR_INVALID_ARG, "wavefront mode runs compiled loop bodies only (%s)", c->jit_why.c_str());
+int run_wavefront(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl, const int* tile_in,
+                  JitWave* w) {
   CachedPlan* cp = nullptr;
-  rc = wave_plan(c, first, count, tile_in, &cp);
+  int rc = wave_plan(c, first, count, tile_in, &cp);
   if (rc) return rc;
   const SkewedPlan& P = cp->plan;
   LaunchEnv env = make_env(c);
@@ -1121,8 +1118,13 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
   }
   if (mode == OPS_MODE_WAVEFRONT) {
     // one loop has no dependencies to schedule; checked and interpreted
-    // runs go through the persistent skewed kernel instead
-    if (count > 1 && !c->cfg.interpret && !c->cfg.check) return run_wavefront(c, first, count, dl_base, hl, tile_in);
+    // runs, and runs without run-time compilation, go through the skewed path
+    if (count > 1 && !c->cfg.interpret && !c->cfg.check) {
+      JitWave* w = nullptr;
+      int rc = wave_code(c, first, count, hl, &w);
+      if (rc) return rc;
+      if (w) return run_wavefront(c, first, count, dl_base, hl, tile_in, w);
+    }
     mode = count > 1 ? OPS_MODE_SKEWED : OPS_MODE_UNTILED;
   }
   LaunchEnv env = make_env(c);
@@ -1899,8 +1901,8 @@ int ops_plan_wavefront(ops_ctx c, const int* tile, int64_t* counts, int* out_pha
   build_skewed_ranges(pl, (int)c->dats.size(), ndim, t, P);
   build_phases(pl, P);
   WavePlan W;
-  build_wavefront(pl, (int)c->dats.size(), P, ndim - 1, jit_rows_per_unit(), kThreads, jit_wave_units_per_chunk(),
-                  jit_wave_slope(), W);
+  build_wavefront(pl, (int)c->dats.size(), P, ndim - 1, jit_rows_per_unit(), jit_wave_threads(),
+                  jit_wave_units_per_chunk(), jit_wave_slope(), W);
   const int64_t nph = (int64_t)P.phases.size();
   counts[0] = nph;
   counts[1] = (int64_t)W.deps.size();
