@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "cg.h"
@@ -33,7 +34,26 @@
 namespace opstile {
 
 constexpr int kCgThreads = 256;
-constexpr int kCgUnitPts = 8192;  // points per work unit (whole rows where they fit)
+
+// Work-unit size in points (whole rows where they fit) and the sweep grid:
+// CTAs per SM, 0 = as many as are resident at once.  OPSTILE_CG_UNIT and
+// OPSTILE_CG_GRID override the defaults, 4096 points and 16 CTAs per SM:
+// more CTAs than fit at once let the block scheduler even out the last wave
+// (measured on GB300 for one 4000^2 solve and for the served mix).
+static int cg_env(const char* name, int def, int lo, int hi) {
+  const char* e = getenv(name);
+  if (!e || !*e) return def;
+  const int v = atoi(e);
+  return v < lo ? lo : (v > hi ? hi : v);
+}
+static int cg_unit_pts() {
+  static const int v = cg_env("OPSTILE_CG_UNIT", 4096, 256, 1 << 20);
+  return v;
+}
+static int cg_grid_per_sm() {
+  static const int v = cg_env("OPSTILE_CG_GRID", 16, 0, 64);
+  return v;
+}
 
 // ---------------------------------------------------------------------------
 // reductions
@@ -519,14 +539,15 @@ CgBatch::~CgBatch() {
   cudaFree(dpart_);
 }
 
-// Units of whole rows holding about kCgUnitPts cells (rows wider than that
-// are cut into column chunks); they depend only on n, never on the batch.
+// Units of whole rows holding about cg_unit_pts() cells (rows wider than
+// that are cut into column chunks); they depend only on n, never on the batch.
 static void units_for(int slot, int n, std::vector<CgUnit>& out) {
-  if (n > kCgUnitPts) {
+  const int pts = cg_unit_pts();
+  if (n > pts) {
     for (int j = 0; j < n; ++j)
-      for (int c0 = 0; c0 < n; c0 += kCgUnitPts) out.push_back(CgUnit{slot, j, 1, c0, std::min(kCgUnitPts, n - c0)});
+      for (int c0 = 0; c0 < n; c0 += pts) out.push_back(CgUnit{slot, j, 1, c0, std::min(pts, n - c0)});
   } else {
-    const int nr = std::max(1, kCgUnitPts / n);
+    const int nr = std::max(1, pts / n);
     for (int j = 0; j < n; j += nr) out.push_back(CgUnit{slot, j, std::min(nr, n - j), 0, n});
   }
 }
@@ -689,7 +710,13 @@ cudaError_t CgBatch::run(int ticks) {
   if (nunits_ == 0) return cudaSuccess;
   const int nslots = (int)hprob_.size();
   const int2* ranges = dranges_;
-  const int g = std::max(1, std::min(nunits_, num_sms_ * 8));
+  int per_sm = cg_grid_per_sm();
+  if (per_sm == 0) {
+    // as many CTAs as the A sweep keeps resident (the B and C sweeps keep at least as many)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_a, kCgThreads, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 4;
+  }
+  const int g = std::max(1, std::min(nunits_, num_sms_ * per_sm));
   const int gs = nslots;  // scalar kernels: one block per problem slot
   // the tick sequence is captured once per batch composition and replayed
   if (!gexec_ || gticks_ != ticks) {

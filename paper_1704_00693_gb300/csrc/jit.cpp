@@ -762,6 +762,7 @@ bool compile(const std::string& src, std::string* cubin, std::string* why) {
 
 struct JitSegment {
   std::vector<CUfunction> u;
+  std::vector<int> per_sm;  // resident CTAs per SM of each kernel (0: not queried yet)
 };
 
 namespace {
@@ -1023,6 +1024,22 @@ int jit_compile_overlap_only(const DLoop* loops, int count, const OvLayout& lay,
       return OPS_ERR_CUDA;
     }
   return OPS_OK;
+}
+
+int jit_grid_policy() {
+  static const int v = env_int("OPSTILE_JIT_GRID", 0, 0, 64);
+  return v;
+}
+
+int jit_resident(JitSegment* s, int i) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (s->per_sm.size() != s->u.size()) s->per_sm.assign(s->u.size(), 0);
+  if (!s->per_sm[i]) {
+    int per_sm = 0;
+    if (g_api.occupancy(&per_sm, s->u[i], kThreads, 0) != CUDA_SUCCESS || per_sm < 1) per_sm = 1;
+    s->per_sm[i] = per_sm;
+  }
+  return s->per_sm[i];
 }
 
 cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const DLoop* d_loop, const int* box,

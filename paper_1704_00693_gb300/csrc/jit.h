@@ -32,6 +32,13 @@ int jit_segment(int device, const DLoop* loops, int count, const std::vector<std
 int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
                      std::string* src, std::string* why, double* compile_ms);
 
+// CTAs of kernel u<i> resident per SM (queried once per kernel).
+int jit_resident(JitSegment* s, int i);
+// Grid policy of the compiled per-loop kernels (OPSTILE_JIT_GRID): 0 = the
+// kernel's resident CTAs x SMs (one wave of CTAs striding over the units),
+// k > 0 = up to k CTAs per SM.
+int jit_grid_policy();
+
 // One launch of loop i of the segment over box (grid-stride units, the
 // interpreter's enumeration); reductions assign (assign = 1) or combine
 // into the CTA's partial column.

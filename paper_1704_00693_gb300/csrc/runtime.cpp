@@ -1066,6 +1066,17 @@ int run_wavefront(ops_ctx c, int first, int count, int dl_base, std::vector<DLoo
   return OPS_OK;
 }
 
+// Grid of a compiled per-loop kernel over a box: by default one wave of the
+// CTAs that stay resident (the kernel's occupancy x SMs), each striding over
+// the box's units, so no partly filled last wave of CTAs idles SMs;
+// OPSTILE_JIT_GRID = k caps the grid at k CTAs per SM instead.
+int compiled_grid(ops_ctx c, JitSegment* js, int i, const LaunchEnv& env, const int* box) {
+  const int units = untiled_grid(env, box);  // enumeration units, capped at 8 CTAs per SM
+  const int k = jit_grid_policy();
+  const int cap = k > 0 ? k * c->num_sms : jit_resident(js, i) * c->num_sms;
+  return std::max(1, std::min(units, std::min(cap, c->part_stride)));
+}
+
 // Execute a segment in a given mode; tile_in entries <= 0 are chosen automatically.
 int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl, int mode,
                      const int* tile_in) {
@@ -1156,7 +1167,7 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
       const DLoop& L = hl[dl_base + i];
       if (empty) continue;
       c->stats.points += n;
-      const int grid = untiled_grid(env, box);
+      const int grid = js ? compiled_grid(c, js, i, env, box) : untiled_grid(env, box);
       int rc = record_event(c);
       if (rc) return rc;
       if (js)
@@ -1254,7 +1265,7 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
     // orders the phases as the persistent kernel's barriers do
     sgrid = 1;
     for (const Phase& ph : P.phases) {
-      const int g = std::min(untiled_grid(env, ph.box), c->part_stride);
+      const int g = std::min(compiled_grid(c, js, ph.loop, env, ph.box), c->part_stride);
       sgrid = std::max(sgrid, g);
       CUDA_TRY(c, jit_launch(js, ph.loop, env, c->d_loops + dl_base + ph.loop, ph.box, g, 0));
       ++c->stats.launches;
