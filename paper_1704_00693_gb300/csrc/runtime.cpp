@@ -1066,10 +1066,9 @@ int run_wavefront(ops_ctx c, int first, int count, int dl_base, std::vector<DLoo
   return OPS_OK;
 }
 
-// Grid of a compiled per-loop kernel over a box: by default one wave of the
-// CTAs that stay resident (the kernel's occupancy x SMs), each striding over
-// the box's units, so no partly filled last wave of CTAs idles SMs;
-// OPSTILE_JIT_GRID = k caps the grid at k CTAs per SM instead.
+// Grid of a compiled per-loop kernel over a box: the box's enumeration
+// units, capped at OPSTILE_JIT_GRID CTAs per SM (default 8), or with
+// OPSTILE_JIT_GRID = 0 at one wave of the CTAs that stay resident.
 int compiled_grid(ops_ctx c, JitSegment* js, int i, const LaunchEnv& env, const int* box) {
   const int units = untiled_grid(env, box);  // enumeration units, capped at 8 CTAs per SM
   const int k = jit_grid_policy();
