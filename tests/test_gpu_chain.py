@@ -297,6 +297,20 @@ def test_wavefront_jacobi_closed_form_and_stats():
     assert np.abs(got[0] - want).max() <= 1e-13 * np.abs(want).max()
 
 
+def test_wavefront_segments_and_single_loop_segments():
+    """A flush cut into segments of at most 10 loops runs one wavefront
+    kernel per segment of several loops; a segment length of 1 runs every
+    loop untiled.  Both give the program-order result."""
+    c = W.cloverleaf2d(n=90, steps=2)
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist, st = run_gpu(c, "wavefront", (0, 8, 0), segment=10)
+    assert_same(c, got, ref, hist, ref_hist, what="wavefront segments")
+    assert st["segments"] >= 8 and st["kernel_launches"] == st["segments"]
+    got, hist, st = run_gpu(c, "wavefront", (0, 8, 0), segment=1)
+    assert_same(c, got, ref, hist, ref_hist, what="wavefront one-loop segments")
+    assert st["mode"] == ops.OPS_MODE_UNTILED
+
+
 def test_plan_cache_reuse_and_stats():
     c = W.cloverleaf2d(n=80, steps=3)
     r = ChainRunner(c, mode="skewed", tile=(0, 20, 0))
@@ -385,7 +399,7 @@ def test_full_size_opensbli_one_step():
 
 
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 16, 0)), ("overlapped", None),
-                                       ("auto", None)])
+                                       ("auto", None), ("wavefront", (0, 8, 0))])
 def test_borrowed_device_dats(mode, tile):
     """Dats declared on caller-owned device memory (torch tensors with a pitch
     of their own): the chain reads and writes them in place in every mode
@@ -418,6 +432,8 @@ def test_borrowed_device_dats(mode, tile):
     assert_same(c, got, ref, hist, ref_hist, what=f"borrowed {mode}")
     if mode == "overlapped":
         assert st["mode"] == ops.OPS_MODE_SKEWED
+    if mode == "wavefront":
+        assert st["mode"] == ops.OPS_MODE_WAVEFRONT
 
 
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 17, 0)), ("skewed", (0, 0, 0)),
