@@ -410,7 +410,9 @@ def bench_serving(nreq=512, seq_sample=None, tol=1e-8, budget=48 << 30):
 
 def bench_cg(n=4000, tol=1e-10):
     """TeaLeaf-shaped solve: conductivity log-uniform in [1e-2, 1e2], RHS
-    U(0,1); FP64 CG against FP32 sweeps with FP64 residual and refinement."""
+    U(0,1); FP64 CG against FP32 sweeps with FP64 residual and refinement.
+    Each form: one untimed full-size solve, then the best of two timed ones
+    (host wall clock, uploads of kappa and b and the fetch of x included)."""
     import paper_1704_00693_gb300 as ops
     from synth import workloads as W
     kappa, b = W.cg_problem(n, 1e-2, 1e2)
@@ -420,10 +422,13 @@ def bench_cg(n=4000, tol=1e-10):
         runs = [("fp64", ops.OPS_PREC_FP64, 0.0), ("mixed_inner1e-4", ops.OPS_PREC_MIXED, 1e-4),
                 ("mixed_inner1e-5", ops.OPS_PREC_MIXED, 1e-5), ("mixed_inner1e-6", ops.OPS_PREC_MIXED, 1e-6)]
         for name, prec, itol in runs:
-            ops.ops_cg_solve(ctx, kappa[:512, :512].copy(), b[:512, :512].copy(), tol, prec, inner_tol=itol)
-            t0 = time.perf_counter()
-            x, st = ops.ops_cg_solve(ctx, kappa, b, tol, prec, inner_tol=itol)
-            dt = time.perf_counter() - t0
+            # a full-size solve first (allocation, graph capture), then the best of two timed ones
+            ops.ops_cg_solve(ctx, kappa, b, tol, prec, inner_tol=itol)
+            dt = float("inf")
+            for _ in range(2):
+                t0 = time.perf_counter()
+                x, st = ops.ops_cg_solve(ctx, kappa, b, tol, prec, inner_tol=itol)
+                dt = min(dt, time.perf_counter() - t0)
             out[name] = {"seconds": dt, "iterations": st["iterations"], "outer": st["outer"],
                          "converged": st["converged"], "relres": st["relres"],
                          "ms_per_iteration": dt * 1e3 / max(1, st["iterations"])}
@@ -434,9 +439,11 @@ def bench_cg(n=4000, tol=1e-10):
     cg = ChainCG(n, mode="untiled")
     try:
         cg.solve(kappa, b, tol, maxit=2)  # compiled code and plans
-        t0 = time.perf_counter()
-        x, it, rel = cg.solve(kappa, b, tol)
-        dt = time.perf_counter() - t0
+        dt = float("inf")
+        for _ in range(2):
+            t0 = time.perf_counter()
+            x, it, rel = cg.solve(kappa, b, tol)
+            dt = min(dt, time.perf_counter() - t0)
         out["fp64_loop_chain_untiled"] = {"seconds": dt, "iterations": it, "relres": rel,
                                           "ms_per_iteration": dt * 1e3 / max(1, it)}
     finally:
