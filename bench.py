@@ -552,6 +552,44 @@ def cpu_baseline(n_full, seconds=12.0):
     tt = time.perf_counter() - t0
     out["skewed_tiled_cpu"] = {"value": U * tsteps / tt / 1e9, "unit": "GB/s", "tile": [n + 4, rows],
                                "steps": tsteps, "speedup_vs_untiled_cpu": (t / nsteps) / (tt / tsteps)}
+    out["compiled_cpu"] = compiled_cpu_context(n)
+    return out
+
+
+def compiled_cpu_context(n, seconds=2.0, rows=(32, 64, 128, 256, 512)):
+    """Context beside the oracle: the paper's CPU scheme with compiled loop
+    bodies (oracle.cpu_compiled; C from the IR, gcc, OpenMP inside each
+    tile) on the same sample, untiled and with Algorithm 1 tiles of whole
+    rows, each timed over about `seconds`."""
+    import numpy as np
+    import oracle
+    from oracle import cpu_compiled
+    from synth import workloads as W
+    chain = W.cloverleaf2d(n=n, steps=1)
+    U, _ = workload_numbers(chain)
+    comp = cpu_compiled.CompiledChain(chain)
+    dats = [np.ascontiguousarray(d.init.astype(np.float64)) for d in chain.dats]
+    ident = [oracle.red_identity(op) for op in chain.reductions]
+
+    def timed(tile):
+        comp.run(dats, ident, 1.0, tile)
+        t0, k = time.perf_counter(), 0
+        while True:
+            comp.run(dats, ident, 1.0, tile)
+            k += 1
+            if time.perf_counter() - t0 > seconds:
+                break
+        return (time.perf_counter() - t0) / k
+
+    tu = timed(None)
+    out = {"sample": f"one step of the chain at {n}^2", "cores": comp.threads_used,
+           "untiled": {"value": U / tu / 1e9, "unit": "GB/s", "ms_per_step": tu * 1e3}, "tiled": {}}
+    for r in rows:
+        tt = timed((n + 4, r))
+        out["tiled"][str(r)] = {"value": U / tt / 1e9, "ms_per_step": tt * 1e3}
+    best = min(out["tiled"], key=lambda k: out["tiled"][k]["ms_per_step"])
+    out["best_tile_rows"] = int(best)
+    out["speedup_tiled_vs_untiled"] = tu * 1e3 / out["tiled"][best]["ms_per_step"]
     return out
 
 
