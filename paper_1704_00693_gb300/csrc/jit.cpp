@@ -1027,7 +1027,7 @@ int jit_compile_overlap_only(const DLoop* loops, int count, const OvLayout& lay,
 }
 
 int jit_grid_policy() {
-  static const int v = env_int("OPSTILE_JIT_GRID", 8, 0, 64);
+  static const int v = env_int("OPSTILE_JIT_GRID", 0, 0, 64);
   return v;
 }
 

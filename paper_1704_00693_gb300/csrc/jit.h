@@ -34,12 +34,11 @@ int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vecto
 
 // CTAs of kernel u<i> resident per SM (queried once per kernel).
 int jit_resident(JitSegment* s, int i);
-// Grid policy of the compiled per-loop kernels (OPSTILE_JIT_GRID): k > 0 =
-// up to k CTAs per SM (default 8: more than stay resident, so the block
-// scheduler balances units of unequal width); 0 = the kernel's resident
-// CTAs x SMs, one wave striding over the units (3.5% faster on the 2D FP32
-// chain, 20-25% slower on the 3D chains, where a fixed stride gives each CTA
-// the same one of a row's two unequal x-chunks every time).
+// Grid policy of the compiled per-loop kernels (OPSTILE_JIT_GRID): 0 (the
+// default) = one wave of the kernel's resident CTAs striding over the units,
+// with the stride kept coprime to the row's x-chunk count so that no CTA
+// always draws the same (possibly short) chunk; k > 0 = up to k CTAs per SM,
+// more than stay resident, balanced by the block scheduler instead.
 int jit_grid_policy();
 
 // One launch of loop i of the segment over box (grid-stride units, the

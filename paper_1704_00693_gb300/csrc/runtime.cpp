@@ -12,6 +12,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <numeric>
 #include <set>
 #include <string>
 #include <vector>
@@ -1066,14 +1067,24 @@ int run_wavefront(ops_ctx c, int first, int count, int dl_base, std::vector<DLoo
   return OPS_OK;
 }
 
-// Grid of a compiled per-loop kernel over a box: the box's enumeration
-// units, capped at OPSTILE_JIT_GRID CTAs per SM (default 8), or with
-// OPSTILE_JIT_GRID = 0 at one wave of the CTAs that stay resident.
+// Grid of a compiled per-loop kernel over a box: by default one wave of the
+// CTAs that stay resident (the kernel's occupancy x SMs), each striding over
+// the box's units, so no partly filled last wave of CTAs idles SMs;
+// OPSTILE_JIT_GRID = k caps the grid at k CTAs per SM instead.
 int compiled_grid(ops_ctx c, JitSegment* js, int i, const LaunchEnv& env, const int* box) {
   const int units = untiled_grid(env, box);  // enumeration units, capped at 8 CTAs per SM
   const int k = jit_grid_policy();
   const int cap = k > 0 ? k * c->num_sms : jit_resident(js, i) * c->num_sms;
-  return std::max(1, std::min(units, std::min(cap, c->part_stride)));
+  int g = std::max(1, std::min(units, std::min(cap, c->part_stride)));
+  const int64_t nx = box[1] - box[0];
+  if (k == 0 && g < units && nx >= 128) {
+    // a stride that shares a factor with the row's x-chunk count hands each
+    // CTA the same chunks of every row (unequal when nx is not a multiple of
+    // the chunk width): keep the stride coprime to it
+    const int xch = (int)((nx + kThreads - 1) / kThreads);
+    while (g > 1 && std::gcd(g, xch) != 1) --g;
+  }
+  return g;
 }
 
 // Execute a segment in a given mode; tile_in entries <= 0 are chosen automatically.
