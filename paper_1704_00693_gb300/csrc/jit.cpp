@@ -45,8 +45,10 @@ namespace opstile {
 namespace {
 
 // Shape of the compiled kernels: rows per unit (independent points per
-// thread) and the CTAs per SM the register budget is sized for.  Defaults
-// from measurement on GB300; OPSTILE_JIT_PTS / OPSTILE_JIT_MINB override.
+// thread; FP64 and FP32 loops) and the CTAs per SM the register budget is
+// sized for.  Defaults from measurement on GB300 (FP32 loops, with half the
+// registers per value, run 3.6% faster at 8 rows than at 4; FP64 loops do
+// not); OPSTILE_JIT_PTS / OPSTILE_JIT_PTS32 / OPSTILE_JIT_MINB override.
 int env_int(const char* name, int def, int lo, int hi) {
   const char* e = getenv(name);
   if (!e || !*e) return def;
@@ -54,6 +56,8 @@ int env_int(const char* name, int def, int lo, int hi) {
   return v < lo ? lo : (v > hi ? hi : v);
 }
 const int kJitPts = env_int("OPSTILE_JIT_PTS", 4, 1, 8);
+const int kJitPts32 = env_int("OPSTILE_JIT_PTS32", 8, 1, 8);
+int pts_for(int es) { return es == 4 ? kJitPts32 : kJitPts; }
 const int kJitMinCtas = env_int("OPSTILE_JIT_MINB", 2, 1, 8);
 // Overlapped tiles: one CTA per SM holds the footprints, so it takes twice
 // the threads of the untiled kernels; one point per thread at a time keeps
@@ -428,7 +432,7 @@ struct LoopGen {
     emit_points(1);
     os << "  };\n";
     // P consecutive rows
-    const int P = ov ? kOvPts : kJitPts;
+    const int P = ov ? kOvPts : (f32 ? kJitPts32 : kJitPts);
     os << "  auto full = [&](int x, int y, int z) {\n";
     for (int k = 0; k < (int)classes.size(); ++k) {
       os << "    const i64 i" << k << "_0 = (i64)x + (i64)y * " << classes[k].first << "ll + (i64)z * "
@@ -453,7 +457,7 @@ struct LoopGen {
 // Source of the kernels u<l0> .. u<l1-1> for loops[l0..l1) of a segment.
 std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::vector<char>>& ro, int es) {
   std::ostringstream os;
-  os << "// opstile compiled loop bodies: " << kJitPts << " rows per unit, " << kJitMinCtas << " CTAs per SM, "
+  os << "// opstile compiled loop bodies: " << pts_for(es) << " rows per unit, " << kJitMinCtas << " CTAs per SM, "
      << (es == 4 ? "fp32" : "fp64") << "\n";
   os << kPrelude << kDeviceCommon << kPreludeTail;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
@@ -608,7 +612,7 @@ __device__ __forceinline__ void red_release(int* p, int v) {
 std::string generate_wavefront(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es) {
   const int nt = jit_wave_threads();
   std::ostringstream os;
-  os << "// opstile wavefront kernel: " << kJitPts << " rows per unit, " << nt << " threads, "
+  os << "// opstile wavefront kernel: " << pts_for(es) << " rows per unit, " << nt << " threads, "
      << jit_wave_min_ctas() << " CTAs per SM, "
      << (es == 4 ? "fp32" : "fp64") << "\n";
   os << kPrelude << kDeviceCommon << kPreludeTail << kWfPrelude;
@@ -1055,7 +1059,7 @@ cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const D
 }
 
 
-int jit_rows_per_unit() { return kJitPts; }
+int jit_rows_per_unit(int es) { return pts_for(es); }
 
 int jit_wave_units_per_chunk() {
   static const int v = env_int("OPSTILE_WF_UNITS", 16, 1, 1 << 20);

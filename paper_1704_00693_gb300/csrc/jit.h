@@ -84,9 +84,9 @@ struct WfPhase {
   int box[6];
 };
 struct JitWave;
-// P of the compiled enumeration (rows per unit); enumeration units per
-// wavefront work unit (OPSTILE_WF_UNITS, default 16)
-int jit_rows_per_unit();
+// P of the compiled enumeration (rows per unit) for elements of es bytes;
+// enumeration units per wavefront work unit (OPSTILE_WF_UNITS, default 16)
+int jit_rows_per_unit(int es);
 int jit_wave_units_per_chunk();
 // threads per CTA of the wavefront kernel (OPSTILE_WF_THREADS, default 128)
 int jit_wave_threads();

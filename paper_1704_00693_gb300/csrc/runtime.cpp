@@ -950,7 +950,7 @@ int wave_plan(ops_ctx c, int first, int count, const int* tile_in, CachedPlan** 
   }
   tile[ndim - 1] =
       tile_in[ndim - 1] > 0 ? tile_in[ndim - 1] : (int)std::max<int64_t>(1, kWavePoints / std::max<int64_t>(1, inner));
-  const int P = jit_rows_per_unit(), upc = jit_wave_units_per_chunk(), slope = jit_wave_slope();
+  const int P = jit_rows_per_unit(c->es), upc = jit_wave_units_per_chunk(), slope = jit_wave_slope();
   std::vector<int> key = {-OPS_MODE_WAVEFRONT, ndim, tile[0], tile[1], tile[2], P, upc, slope, jit_wave_threads()};
   for (int i = 0; i < count; ++i) {
     const QLoop& q = c->queue[first + i];
@@ -1922,7 +1922,7 @@ int ops_plan_wavefront(ops_ctx c, const int* tile, int64_t* counts, int* out_pha
   build_skewed_ranges(pl, (int)c->dats.size(), ndim, t, P);
   build_phases(pl, P);
   WavePlan W;
-  build_wavefront(pl, (int)c->dats.size(), P, ndim - 1, jit_rows_per_unit(), jit_wave_threads(),
+  build_wavefront(pl, (int)c->dats.size(), P, ndim - 1, jit_rows_per_unit(c->es), jit_wave_threads(),
                   jit_wave_units_per_chunk(), jit_wave_slope(), W);
   const int64_t nph = (int64_t)P.phases.size();
   counts[0] = nph;
