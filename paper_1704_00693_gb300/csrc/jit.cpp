@@ -91,6 +91,7 @@ struct Api {
   CUresult (*occupancy)(int*, CUfunction, int, size_t);
   CUresult (*attribute)(int*, CUfunction_attribute, CUfunction);
   CUresult (*set_attribute)(CUfunction, CUfunction_attribute, int);
+  CUresult (*launch_ex)(const CUlaunchConfig*, CUfunction, void**, void**) = nullptr;  // optional
 };
 
 Api g_api;
@@ -143,6 +144,7 @@ bool api_ready(std::string* why, bool nvrtc_only = false) {
       g_api.why = "driver module entry points unavailable";
     } else {
       g_api.ok = true;
+      if (!drv("cuLaunchKernelEx", &g_api.launch_ex)) g_api.launch_ex = nullptr;
     }
   }
   if (!g_api.ok && why) *why = g_api.why;
@@ -467,7 +469,9 @@ std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::
     g.emit(i);
     os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas << ") u" << i
        << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
-          "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n  body"
+          "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n"
+          "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
+          "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n  body"
        << i << "(L, x0, x1, y0, y1, z0, z1, blockIdx.x, gridDim.x, scal, part, stride, assign);\n}\n";
   }
   return os.str();
@@ -1030,6 +1034,11 @@ int jit_compile_overlap_only(const DLoop* loops, int count, const OvLayout& lay,
   return OPS_OK;
 }
 
+int jit_pdl() {
+  static const int v = env_int("OPSTILE_PDL", 1, 0, 1);
+  return v;
+}
+
 int jit_grid_policy() {
   static const int v = env_int("OPSTILE_JIT_GRID", 0, 0, 64);
   return v;
@@ -1055,6 +1064,22 @@ cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const D
   int st = env.part_stride;
   int as = assign;
   void* args[] = {&a0, &b0, &b1, &b2, &b3, &b4, &b5, &sc, &pt, &st, &as};
+  if (g_api.launch_ex && jit_pdl()) {
+    CUlaunchAttribute at[1];
+    std::memset(at, 0, sizeof at);
+    at[0].id = CU_LAUNCH_ATTRIBUTE_PROGRAMMATIC_STREAM_SERIALIZATION;
+    at[0].value.programmaticStreamSerializationAllowed = 1;
+    CUlaunchConfig cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDimX = (unsigned)grid;
+    cfg.gridDimY = cfg.gridDimZ = 1;
+    cfg.blockDimX = kThreads;
+    cfg.blockDimY = cfg.blockDimZ = 1;
+    cfg.hStream = (CUstream)env.stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return to_cuda(g_api.launch_ex(&cfg, s->u[i], args, nullptr));
+  }
   return to_cuda(g_api.launch(s->u[i], (unsigned)grid, 1, 1, kThreads, 1, 1, 0, (CUstream)env.stream, args, nullptr));
 }
 

@@ -32,6 +32,11 @@ int jit_segment(int device, const DLoop* loops, int count, const std::vector<std
 int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
                      std::string* src, std::string* why, double* compile_ms);
 
+// 1 (OPSTILE_PDL, default) launches the per-loop kernels with programmatic
+// stream serialisation: a kernel's CTAs may become resident while its
+// predecessor in the stream drains, and wait on the device
+// (griddepcontrol.wait) until the predecessor has completed.
+int jit_pdl();
 // CTAs of kernel u<i> resident per SM (queried once per kernel).
 int jit_resident(JitSegment* s, int i);
 // Grid policy of the compiled per-loop kernels (OPSTILE_JIT_GRID): 0 (the
