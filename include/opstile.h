@@ -78,6 +78,22 @@ extern "C" {
  * NVRTC, the segment runs in OPS_MODE_SKEWED.  Results are identical to every
  * other mode.  OPS_MODE_AUTO does not try this mode. */
 
+#define OPS_MODE_TILEWAVE 5  /* Algorithm 1 tiles cut in every dimension, each run whole by one CTA (the
+                                 inner loop of Algorithm 2), tiles concurrent as a wavefront */
+/* OPS_MODE_TILEWAVE cuts every dimension into tiles (tile[d] points; 0 =
+ * automatic: about 4096 points per tile, x the widest) and gives every
+ * (tile, loop) its Algorithm 1 range.  One persistent kernel holding every
+ * loop body of the segment (compiled at run time, so this mode needs NVRTC)
+ * hands whole tiles to CTAs in order of the sum of their tile coordinates;
+ * a CTA runs the tile's loops in order, and before loop l waits only until
+ * the tiles one step back in any subset of the dimensions have completed
+ * the loops l conflicts with.  A tile's intermediate values are re-read
+ * from the SM's L1 and from L2 while the CTA works through its loops.
+ * Tiles smaller than the chain's skew (a conflict two tiles back) are grown
+ * until they are not; a segment of one loop runs untiled; with check = 1 or
+ * interpret = 1, or without NVRTC, the segment runs in OPS_MODE_SKEWED.
+ * Results are identical to every other mode. */
+
 /* ---- argument kinds, access modes, reduction operators ---- */
 #define OPS_ARG_DAT 0    /* a dat accessed through a stencil */
 #define OPS_ARG_SCALAR 1 /* read the current value of a reduction handle */
@@ -282,6 +298,18 @@ int ops_plan_overlapped(ops_ctx ctx, const int owned[6], int* out_boxes, int* ou
  * indices of earlier phases.  Call with NULL arrays to learn the sizes. */
 int ops_plan_wavefront(ops_ctx ctx, const int* tile, int64_t* counts, int* out_phases, int64_t phase_cap,
                        int* out_deps, int64_t dep_cap);
+/* Build the tile-wavefront plan (OPS_MODE_TILEWAVE) of the currently queued
+ * loops for the given tile sizes (all >= 1), without executing them.
+ * OPS_ERR_INVALID_ARG, with the reason in ops_last_error, when the tiles are
+ * smaller than the chain's skew.  counts[0..3] receive the number of tiles,
+ * of tile classes, of predecessor directions (2^dims - 1; direction k steps
+ * back one tile in dimension d when bit d of k + 1 is set) and of loops.
+ * Optional outputs (NULL to skip): out_need (classes x directions x loops
+ * ints): the loops of each predecessor tile that must be complete before a
+ * tile of that class runs each loop; out_class (tiles ints, x fastest): the
+ * class of each tile; out_order (tiles ints): the tile of each ticket. */
+int ops_plan_tilewave(ops_ctx ctx, const int* tile, int64_t* counts, int* out_need, int64_t need_cap, int* out_class,
+                      int* out_order, int64_t tile_cap);
 /* Generate the CUDA source of the compiled loop bodies for the currently
  * queued loops (as one segment) and compile it for sm_103a with NVRTC,
  * without loading it: no device is needed.  src_out (cap bytes, may be NULL)
@@ -293,6 +321,9 @@ int ops_compile_queued(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len
 /* The same for the wavefront kernel of the queued loops (OPS_MODE_WAVEFRONT:
  * every loop body in one kernel). */
 int ops_compile_queued_wavefront(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
+
+/* The same for the tile-wavefront kernel of the queued loops (OPS_MODE_TILEWAVE). */
+int ops_compile_queued_tilewave(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
 
 /* ---- heat-conduction solves (TeaLeaf-shaped, Sec. 5 and Sec. 6.D) ----
  * Solve A x = b on an n x n cell grid for the implicit heat-conduction

@@ -28,7 +28,8 @@ OPS_ERR_CUDA = -7
 OPS_ERR_STATE = -8
 OPS_ERR_NO_DEVICE = -9
 
-OPS_MODE_UNTILED, OPS_MODE_SKEWED, OPS_MODE_OVERLAPPED, OPS_MODE_AUTO, OPS_MODE_WAVEFRONT = 0, 1, 2, 3, 4
+(OPS_MODE_UNTILED, OPS_MODE_SKEWED, OPS_MODE_OVERLAPPED, OPS_MODE_AUTO, OPS_MODE_WAVEFRONT,
+ OPS_MODE_TILEWAVE) = 0, 1, 2, 3, 4, 5
 OPS_ARG_DAT, OPS_ARG_SCALAR, OPS_ARG_RED = 0, 1, 2
 OPS_READ, OPS_WRITE, OPS_RW, OPS_INC = 0, 1, 2, 3
 OPS_RED_SUM, OPS_RED_MIN, OPS_RED_MAX = 0, 1, 2
@@ -39,7 +40,7 @@ OPS_REAL_F64, OPS_REAL_F32 = 0, 1
  OPS_IR_SGT, OPS_IR_WSUM, OPS_IR_WACC, OPS_IR_POLY, OPS_IR_ST, OPS_IR_RED) = range(1, 16)
 
 MODES = {"untiled": OPS_MODE_UNTILED, "skewed": OPS_MODE_SKEWED, "overlapped": OPS_MODE_OVERLAPPED,
-         "auto": OPS_MODE_AUTO, "wavefront": OPS_MODE_WAVEFRONT}
+         "auto": OPS_MODE_AUTO, "wavefront": OPS_MODE_WAVEFRONT, "tilewave": OPS_MODE_TILEWAVE}
 
 
 class OpsError(RuntimeError):
@@ -294,12 +295,32 @@ def ops_plan_wavefront(ctx, tile):
     return ph[:nph].copy(), dp[:ndep].copy(), int(counts[2]), int(counts[3])
 
 
-def ops_compile_queued(ctx, want_source: bool = False, wavefront: bool = False):
+def ops_plan_tilewave(ctx, tile):
+    """Tile-wavefront plan of the queued loops for the given tile sizes:
+    (need, tile_class, order), need an int32 array [classes, directions,
+    loops], tile_class the class of each tile (x fastest) and order the tile
+    of each ticket."""
+    counts = (C.c_int64 * 4)()
+    t = _i3(list(tile) + [1] * (3 - len(tile)))
+    _check(ctx, load().ops_plan_tilewave(ctx, t, counts, None, C.c_int64(0), None, None, C.c_int64(0)))
+    ntiles, ncl, ndirs, nloops = (int(v) for v in counts)
+    need = np.zeros(max(1, ncl * ndirs * nloops), dtype=np.int32)
+    cls = np.zeros(max(1, ntiles), dtype=np.int32)
+    order = np.zeros(max(1, ntiles), dtype=np.int32)
+    ip = C.POINTER(C.c_int)
+    _check(ctx, load().ops_plan_tilewave(ctx, t, counts, need.ctypes.data_as(ip), C.c_int64(need.size),
+                                         cls.ctypes.data_as(ip), order.ctypes.data_as(ip), C.c_int64(ntiles)))
+    return need[:ncl * ndirs * nloops].reshape(ncl, ndirs, nloops).copy(), cls[:ntiles].copy(), order[:ntiles].copy()
+
+
+def ops_compile_queued(ctx, want_source: bool = False, wavefront: bool = False, tilewave: bool = False):
     """Generate and compile (NVRTC, sm_103a, no device) the loop bodies of the
     queued loops -- the per-loop and overlapped-tile kernels, or with
-    wavefront=True the wavefront kernel; returns (source or None, source
-    length, compile ms)."""
-    f = load().ops_compile_queued_wavefront if wavefront else load().ops_compile_queued
+    wavefront=True the wavefront kernel, with tilewave=True the
+    tile-wavefront kernel; returns (source or None, source length, compile
+    ms)."""
+    f = (load().ops_compile_queued_tilewave if tilewave else
+         load().ops_compile_queued_wavefront if wavefront else load().ops_compile_queued)
     n = C.c_int64(0)
     ms = C.c_double(0.0)
     buf = None

@@ -448,12 +448,12 @@ cudaError_t launch_part_init(const LaunchEnv& env, int row0, int nrows) {
 // Each row's partials are combined in a fixed order (strided per thread, then
 // a fixed tree), so results depend only on the launch shape, never on timing.
 __global__ void __launch_bounds__(kThreads) k_fold(const DD* __restrict__ part, int stride, const FoldRow* rows,
-                                                   int row0, int nused, double* scal) {
+                                                   int row0, int nused, double* scal, int rbase) {
   __shared__ DD sh[32];
   const int r = row0 + blockIdx.x;
   const int op = rows[r].op;
   DD v{red_identity(op), 0.0};
-  for (int i = threadIdx.x; i < nused; i += blockDim.x) v = red_combine(op, v, part[(size_t)r * stride + i]);
+  for (int i = threadIdx.x; i < nused; i += blockDim.x) v = red_combine(op, v, part[(size_t)(r - rbase) * stride + i]);
   v = block_combine(op, v, sh);
   if (threadIdx.x == 0) {
     const int s = rows[r].slot;
@@ -471,7 +471,13 @@ __global__ void __launch_bounds__(kThreads) k_fold(const DD* __restrict__ part, 
 
 cudaError_t launch_fold(const LaunchEnv& env, int row0, int nrows, int grid_used) {
   if (nrows <= 0) return cudaSuccess;
-  k_fold<<<nrows, kThreads, 0, env.stream>>>(env.part, env.part_stride, env.rows, row0, grid_used, env.scal);
+  k_fold<<<nrows, kThreads, 0, env.stream>>>(env.part, env.part_stride, env.rows, row0, grid_used, env.scal, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_rows(const LaunchEnv& env, const DD* part, int stride, int row0, int nrows, int nused) {
+  if (nrows <= 0) return cudaSuccess;
+  k_fold<<<nrows, kThreads, 0, env.stream>>>(part, stride, env.rows, row0, nused, env.scal, row0);
   return cudaGetLastError();
 }
 

@@ -145,6 +145,8 @@ int untiled_grid(const LaunchEnv& env, const int* box);
 cudaError_t launch_untiled(const LaunchEnv& env, const DLoop* d_loop, const int* box, int grid);
 cudaError_t launch_part_init(const LaunchEnv& env, int row0, int nrows);
 cudaError_t launch_fold(const LaunchEnv& env, int row0, int nrows, int grid_used);
+// the same for partials held elsewhere: row r of the fold at part + (r - row0) * stride, nused columns
+cudaError_t launch_fold_rows(const LaunchEnv& env, const DD* part, int stride, int row0, int nrows, int nused);
 int skewed_max_grid(int num_sms, int blocks_per_sm);
 cudaError_t launch_skewed(const LaunchEnv& env, const DLoop* d_loops, const Phase* d_phases, int nphases,
                           int grid);

@@ -382,20 +382,8 @@ struct LoopGen {
     }
   }
 
-  // lay: shared-memory layout of an overlapped run (footprint of dat slot k
-  // at area + smem_off[k], strides spitch[k] / splane[k], corner ft[6k..])
-  void emit(int i, const OvLayout* lay = nullptr) const {
-    if (ov) {
-      os << "\n__device__ __forceinline__ void ovb" << i
-         << "(const DLoop* __restrict__ L, const int* bx, double* area, const int* ft,\n"
-            "    const double* __restrict__ scal, const int* ob, DD* part, int stride) {\n"
-            "  const int x0 = bx[0], x1 = bx[1], y0 = bx[2], y1 = bx[3], z0 = bx[4], z1 = bx[5];\n";
-    } else {
-      os << "\n__device__ __forceinline__ void body" << i
-         << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1, int ck, int nck,\n"
-            "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n";
-    }
-    // hoisted: dat pointers, scalars, constants
+  // hoisted per call: dat pointers, scalars, constants, reduction accumulators
+  void emit_hoist(const OvLayout* lay) const {
     std::vector<char> kused(OPS_MAX_CONSTS, 0);
     std::vector<char> sused(L.nargs, 0);
     for (int pc = 0; pc < L.nins; ++pc) {
@@ -426,6 +414,22 @@ struct LoopGen {
     for (int k = 0; k < OPS_MAX_CONSTS; ++k)
       if (kused[k]) os << "  const " << T << " K" << k << " = (" << T << ")L->K[" << k << "];\n";
     for (int k = 0; k < L.nreds; ++k) os << "  DD acc" << k << " = dd_of(red_identity(" << L.red_op[k] << "));\n";
+  }
+
+  // lay: shared-memory layout of an overlapped run (footprint of dat slot k
+  // at area + smem_off[k], strides spitch[k] / splane[k], corner ft[6k..])
+  void emit(int i, const OvLayout* lay = nullptr) const {
+    if (ov) {
+      os << "\n__device__ __forceinline__ void ovb" << i
+         << "(const DLoop* __restrict__ L, const int* bx, double* area, const int* ft,\n"
+            "    const double* __restrict__ scal, const int* ob, DD* part, int stride) {\n"
+            "  const int x0 = bx[0], x1 = bx[1], y0 = bx[2], y1 = bx[3], z0 = bx[4], z1 = bx[5];\n";
+    } else {
+      os << "\n__device__ __forceinline__ void body" << i
+         << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1, int ck, int nck,\n"
+            "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n";
+    }
+    emit_hoist(lay);
     // one point
     os << "  auto one = [&](int x, int y, int z) {\n";
     for (int k = 0; k < (int)classes.size(); ++k)
@@ -452,6 +456,56 @@ struct LoopGen {
     for (int k = 0; k < L.nreds; ++k)
       os << "  flush_red(" << L.red_op[k] << ", acc" << k << ", part, stride, L->part_row + " << k << ", "
          << (ov ? "0" : "assign") << ");\n";
+    os << "}\n";
+  }
+
+  // Tile wavefront: the whole CTA (NT threads) enumerates one box, flat in
+  // x-fastest order (point j of the box is x0 + j % nx, ...), each thread
+  // taking P points NT apart at a time as independent dependency chains;
+  // reductions go to the tile's column `col` of the partial rows (row =
+  // the loop's partial row - row0), assigned.
+  void emit_tile(int i, int NT, int P) const {
+    os << "\n__device__ __forceinline__ void tb" << i
+       << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
+          "    const double* __restrict__ scal, DD* part, int stride, int row0, int col) {\n";
+    emit_hoist(nullptr);
+    os << "  auto one = [&](int x, int y, int z) {\n";
+    for (int k = 0; k < (int)classes.size(); ++k)
+      os << "    const i64 i" << k << "_0 = (i64)x + (i64)y * " << classes[k].first << "ll + (i64)z * "
+         << classes[k].second << "ll;\n";
+    emit_points(1);
+    os << "  };\n";
+    os << "  auto multi = [&](const int* xs, const int* ys, const int* zs) {\n";
+    for (int k = 0; k < (int)classes.size(); ++k)
+      for (int p = 0; p < P; ++p)
+        os << "    const i64 i" << k << "_" << p << " = (i64)xs[" << p << "] + (i64)ys[" << p << "] * "
+           << classes[k].first << "ll + (i64)zs[" << p << "] * " << classes[k].second << "ll;\n";
+    emit_points(P);
+    os << "  };\n";
+    os << "  const int nx = x1 - x0, ny = y1 - y0, nz = z1 - z0;\n"
+          "  if (nx > 0 && ny > 0 && nz > 0) {\n"
+          "    const int n = nx * ny * nz;\n"
+          "    const int sr = " << NT << " / nx, sx = " << NT << " - sr * nx;\n"
+          "    int j = (int)threadIdx.x;\n"
+          "    int r = j / nx, x = j - r * nx, y = r, z = 0;\n"
+          "    while (y >= ny) { y -= ny; ++z; }\n"
+          "    auto adv = [&]() {\n"
+          "      x += sx;\n"
+          "      y += sr;\n"
+          "      if (x >= nx) { x -= nx; ++y; }\n"
+          "      while (y >= ny) { y -= ny; ++z; }\n"
+          "    };\n"
+          "    for (; j + " << (P - 1) * NT << " < n; j += " << P * NT << ") {\n"
+          "      int xs[" << P << "], ys[" << P << "], zs[" << P << "];\n"
+          "#pragma unroll\n"
+          "      for (int p = 0; p < " << P << "; ++p) { xs[p] = x0 + x; ys[p] = y0 + y; zs[p] = z0 + z; adv(); }\n"
+          "      multi(xs, ys, zs);\n"
+          "    }\n"
+          "    for (; j < n; j += " << NT << ") { one(x0 + x, y0 + y, z0 + z); adv(); }\n"
+          "  }\n";
+    for (int k = 0; k < L.nreds; ++k)
+      os << "  flush_red_col(" << L.red_op[k] << ", acc" << k << ", part + (size_t)(L->part_row + " << k
+         << " - row0) * stride + col);\n";
     os << "}\n";
   }
 };
@@ -685,6 +739,143 @@ std::string generate_wavefront(const DLoop* loops, int count, const std::vector<
   os << "      default: break;\n"
         "    }\n"
         "    __syncthreads();\n"
+        "  }\n"
+        "}\n";
+  return os.str();
+}
+
+// Source of the tile-wavefront kernel "tw" for the loops of a segment (see
+// build_tile_wave).  A persistent grid draws tiles from a ticket counter in
+// the plan's order; a CTA runs every loop of its tile in order over the
+// tile's box of that loop, with a block barrier between loops, and after
+// loop l publishes l + 1 as the tile's progress (release).  Before loop l
+// it makes sure that each predecessor tile (one step back in a subset of
+// the dimensions) has completed the loops that l conflicts with; the last
+// progress value it saw of each predecessor is kept in shared memory, so a
+// counter is polled (relaxed loads, then one acquire fence) only when that
+// value falls short.  The earliest unfinished ticket always belongs to a
+// running CTA whose predecessors have smaller tickets and are done, so the
+// waits end; each is still bounded in wall-clock time, after which the CTA
+// sets the error word and leaves, as does every CTA that finds it set.  The
+// next ticket is drawn while the current tile runs.
+const char* kTwPrelude = R"TWP(
+struct TwArgs {
+  const DLoop* loops; const int* rng; const int* order; const int* cls; const unsigned short* need;
+  int* prog; int* ticket; const double* scal; DD* part; int* err; long long timeout_ns;
+  int nt[3]; int ncls[3]; int roff[3]; int coff[3];
+  int ntiles, stride, row0, skip_tile;
+};
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void flush_red_col(int op, DD v, DD* dst) {
+  v = block_combine(op, v, g_sh);
+  if (threadIdx.x == 0) *dst = v;
+  __syncthreads();
+}
+)TWP";
+
+std::string generate_tilewave(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                              int ndim) {
+  const int nt = jit_tile_threads(), P = jit_tile_pts(es), ndirs = (1 << ndim) - 1;
+  std::ostringstream os;
+  os << "// opstile tile wavefront kernel: " << nt << " threads, " << P << " points per thread at a time, "
+     << jit_tile_min_ctas() << " CTAs per SM, " << ndim << "D, " << (es == 4 ? "fp32" : "fp64") << "\n";
+  os << kPrelude << kDeviceCommon << kPreludeTail << kTwPrelude;
+  os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
+  os << "static_assert(sizeof(TwArgs) == " << sizeof(TwArgs) << ", \"TwArgs layout\");\n";
+  for (int i = 0; i < count; ++i) {
+    LoopGen g(loops[i], ro[i], os, false, es == 4);
+    g.emit_tile(i, nt, P);
+  }
+  os << "extern \"C\" __global__ void __launch_bounds__(" << nt << ", " << jit_tile_min_ctas()
+     << ") tw(const TwArgs A) {\n"
+        "  constexpr int NL = " << count << ", ND = " << ndirs << ";\n"
+        "  __shared__ unsigned short s_need[ND * NL];\n"
+        "  __shared__ int s_have[ND], s_pred[ND], s_tk, s_stop;\n"
+        "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
+        "  const int tid = threadIdx.x;\n"
+        "  int nxt = 0;\n"
+        "  if (tid == 0) {\n"
+        "    s_tk = atomicAdd(A.ticket, 1);\n"
+        "    s_stop = 0;\n"
+        "  }\n"
+        "  for (;;) {\n"
+        "    __syncthreads();\n"
+        "    const int tk = s_tk;\n"
+        "    if (tk >= A.ntiles || s_stop) return;\n"
+        "    const int tile = A.order[tk];\n"
+        "    const int tc[3] = {tile % A.nt[0], (tile / A.nt[0]) % A.nt[1], tile / (A.nt[0] * A.nt[1])};\n"
+        "    const int cl = (A.cls[A.coff[2] + tc[2]] * A.ncls[1] + A.cls[A.coff[1] + tc[1]]) * A.ncls[0] +\n"
+        "                   A.cls[A.coff[0] + tc[0]];\n"
+        "    for (int j = tid; j < ND * NL; j += blockDim.x) s_need[j] = A.need[(size_t)cl * (ND * NL) + j];\n"
+        "    if (tid < ND) {\n"
+        "      const int m = tid + 1;\n"
+        "      const int px = tc[0] - (m & 1), py = tc[1] - ((m >> 1) & 1), pz = tc[2] - ((m >> 2) & 1);\n"
+        "      const bool has = px >= 0 && py >= 0 && pz >= 0;\n"
+        "      s_pred[tid] = has ? (pz * A.nt[1] + py) * A.nt[0] + px : -1;\n"
+        "      s_have[tid] = has ? 0 : 0x7fffffff;\n"
+        "    }\n"
+        "    if (tid == 0) nxt = atomicAdd(A.ticket, 1);\n"
+        "    __syncthreads();\n"
+        "    for (int l = 0; l < NL; ++l) {\n"
+        "      bool ready = true;\n"
+        "#pragma unroll\n"
+        "      for (int d = 0; d < ND; ++d) ready = ready && (int)s_need[d * NL + l] <= s_have[d];\n"
+        "      if (!ready) {\n"
+        "        if (tid < ND) {\n"
+        "          const int want = s_need[tid * NL + l];\n"
+        "          if (s_have[tid] < want) {\n"
+        "            const int* pp = A.prog + s_pred[tid];\n"
+        "            int v = ld_relaxed(pp);\n"
+        "            unsigned spins = 0;\n"
+        "            unsigned long long t0 = 0;\n"
+        "            while (v < want) {\n"
+        "              if ((++spins & 63u) == 0) {\n"
+        "                if (t0 == 0) {\n"
+        "                  t0 = now_ns();\n"
+        "                } else if (*(volatile int*)A.err || (long long)(now_ns() - t0) > A.timeout_ns) {\n"
+        "                  atomicCAS(A.err, 0, 1);\n"
+        "                  s_stop = 1;\n"
+        "                  break;\n"
+        "                }\n"
+        "              }\n"
+        "              v = ld_relaxed(pp);\n"
+        "            }\n"
+        "            fence_acq_rel();\n"
+        "            s_have[tid] = v;\n"
+        "          }\n"
+        "        }\n"
+        "        __syncthreads();\n"
+        "        if (s_stop) return;\n"
+        "      }\n"
+        "      const int* rx = A.rng + A.roff[0] + 2 * (tc[0] * NL + l);\n"
+        "      const int* ry = A.rng + A.roff[1] + 2 * (tc[1] * NL + l);\n"
+        "      const int* rz = A.rng + A.roff[2] + 2 * (tc[2] * NL + l);\n"
+        "      const int x0 = rx[0], x1 = rx[1], y0 = ry[0], y1 = ry[1], z0 = rz[0], z1 = rz[1];\n"
+        "      const bool live = x1 > x0 && y1 > y0 && z1 > z0;\n"
+        "      switch (l) {\n";
+  for (int i = 0; i < count; ++i) {
+    // a loop with reductions always writes its tile's partials (the identity when its box is empty)
+    if (loops[i].nreds)
+      os << "        case " << i << ": tb" << i << "(A.loops + " << i
+         << ", x0, x1, y0, y1, z0, z1, A.scal, A.part, A.stride, A.row0, tile); break;\n";
+    else
+      os << "        case " << i << ": if (live) tb" << i << "(A.loops + " << i
+         << ", x0, x1, y0, y1, z0, z1, A.scal, A.part, A.stride, A.row0, tile); break;\n";
+  }
+  os << "        default: break;\n"
+        "      }\n"
+        "      __syncthreads();\n"
+        "      if (tid == 0 && tile != A.skip_tile) st_release(A.prog + tile, l + 1);\n"
+        "    }\n"
+        "    if (tid == 0) s_tk = nxt;\n"
         "  }\n"
         "}\n";
   return os.str();
@@ -1203,6 +1394,96 @@ cudaError_t jit_launch_wavefront(const JitWave* w, const LaunchEnv& env, const D
   void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9, &a10, &a11, &a12};
   return to_cuda(
       g_api.launch(w->f, (unsigned)grid, 1, 1, jit_wave_threads(), 1, 1, 0, (CUstream)env.stream, args, nullptr));
+}
+
+
+int jit_tile_threads() {
+  static const int v = [] {
+    int t = env_int("OPSTILE_TW_THREADS", 256, 128, 512), p = 128;
+    while (p * 2 <= t) p *= 2;
+    return p;
+  }();
+  return v;
+}
+
+int jit_tile_min_ctas() {
+  static const int v = env_int("OPSTILE_TW_MINB", 2, 1, 16);
+  return v;
+}
+
+int jit_tile_pts(int es) {
+  static const int v32 = env_int("OPSTILE_TW_PTS32", 4, 1, 8), v64 = env_int("OPSTILE_TW_PTS", 2, 1, 8);
+  return es == 4 ? v32 : v64;
+}
+
+struct JitTile {
+  CUfunction f = nullptr;
+};
+
+namespace {
+std::map<std::pair<int, std::string>, std::unique_ptr<JitTile>> g_tiles;
+}  // namespace
+
+int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es, int ndim,
+                 JitTile** out, std::string* why, double* compile_ms) {
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!api_ready(why)) return OPS_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  const std::string src = generate_tilewave(loops, count, ro, es, ndim);
+  auto key = std::make_pair(device, src);
+  auto it = g_tiles.find(key);
+  if (it != g_tiles.end()) {
+    *out = it->second.get();
+    return OPS_OK;
+  }
+  std::string cubin;
+  if (!cubin_for(src, &cubin, why)) return OPS_ERR_CUDA;
+  CUmodule mod;
+  if (g_api.load(&mod, cubin.data()) != CUDA_SUCCESS) {
+    *why = "cuModuleLoadData failed";
+    return OPS_ERR_CUDA;
+  }
+  std::unique_ptr<JitTile> t(new JitTile);
+  if (g_api.get_function(&t->f, mod, "tw") != CUDA_SUCCESS) {
+    *why = "cuModuleGetFunction failed";
+    return OPS_ERR_CUDA;
+  }
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = t.get();
+  g_tiles[key] = std::move(t);
+  return OPS_OK;
+}
+
+int jit_compile_tilewave_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                              int ndim, std::string* src, std::string* why, double* compile_ms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  *src = generate_tilewave(loops, count, ro, es, ndim);
+  if (!api_ready(why, true)) {
+    if (why->empty()) *why = g_api.why;
+    return OPS_ERR_NO_DEVICE;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  std::string cubin;
+  const bool ok = compile(*src, &cubin, why);
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return ok ? OPS_OK : OPS_ERR_CUDA;
+}
+
+int jit_tilewave_max_grid(JitTile* t, int num_sms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  int per_sm = 0;
+  if (g_api.occupancy(&per_sm, t->f, jit_tile_threads(), 0) != CUDA_SUCCESS) return 0;
+  return per_sm * num_sms;
+}
+
+cudaError_t jit_launch_tilewave(const JitTile* t, const TwArgs& args, cudaStream_t stream, int grid) {
+  TwArgs a = args;
+  void* params[] = {&a};
+  return to_cuda(g_api.launch(t->f, (unsigned)grid, 1, 1, (unsigned)jit_tile_threads(), 1, 1, 0, (CUstream)stream,
+                              params, nullptr));
 }
 
 }  // namespace opstile

@@ -114,4 +114,37 @@ cudaError_t jit_launch_wavefront(const JitWave* w, const LaunchEnv& env, const D
                                  const WfPhase* d_phases, const int* d_deps, const int* d_uphase, int nunits,
                                  int* d_done, int* d_ticket, int grid);
 
+// Tile wavefront (OPS_MODE_TILEWAVE, see build_tile_wave): one persistent
+// kernel with every loop body of the segment; each CTA runs all the loops of
+// one tile at a time.  Its arguments travel by value in one struct.
+struct TwArgs {
+  const DLoop* loops;        // the segment's descriptors
+  const int* rng;            // per dimension d at roff[d]: (start, end) of tile t, loop l at 2 (t L + l)
+  const int* order;          // ticket -> linear tile index (x fastest)
+  const int* cls;            // per dimension d at coff[d]: class of each tile index
+  const unsigned short* need;  // per class: ndirs x L loop counts of the predecessor tiles
+  int* prog;                 // per tile: loops completed (zero before the launch)
+  int* ticket;               // zero before the launch
+  const double* scal;
+  DD* part;                  // reduction partials: (row - row0) * stride + tile
+  int* err;
+  long long timeout_ns;
+  int nt[3], ncls[3], roff[3], coff[3];
+  int ntiles, stride, row0, skip_tile;  // skip_tile >= 0 (test hook): that tile never reports progress
+};
+struct JitTile;
+// threads per CTA (OPSTILE_TW_THREADS: 128, 256 (default) or 512), CTAs per
+// SM the registers are sized for (OPSTILE_TW_MINB, default 2) and points a
+// thread evaluates at a time (OPSTILE_TW_PTS; default 4 in FP32, 2 in FP64)
+int jit_tile_threads();
+int jit_tile_min_ctas();
+int jit_tile_pts(int es);
+int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es, int ndim,
+                 JitTile** out, std::string* why, double* compile_ms);
+int jit_compile_tilewave_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                              int ndim, std::string* src, std::string* why, double* compile_ms);
+// CTAs of the kernel resident on the device at once
+int jit_tilewave_max_grid(JitTile* t, int num_sms);
+cudaError_t jit_launch_tilewave(const JitTile* t, const TwArgs& args, cudaStream_t stream, int grid);
+
 }  // namespace opstile

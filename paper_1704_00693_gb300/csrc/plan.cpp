@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <array>
 #include <climits>
+#include <map>
 
 namespace opstile {
 
@@ -338,6 +339,206 @@ void build_overlap_tile(const std::vector<PLoop>& loops, int ndats, int ndim, co
     }
   }
   out.foot = rb;
+}
+
+// ---------------------------------------------------------------------------
+// Tile wavefront (see plan.h)
+// ---------------------------------------------------------------------------
+namespace {
+// One conflicting pair of accesses: argument `a` of loop `l` (the later loop)
+// and argument `b` of loop `lp` < l on the same dat, at least one writing it.
+struct APair {
+  int l, a, lp, b;
+};
+// The interval of dimension d an argument touches in tile t (reads widened
+// by the stencil); empty (lo >= hi) when the loop's range there is empty.
+inline void touched(const SkewedPlan& P, int L, int d, int t, int l, const PArg& a, int* lo, int* hi) {
+  const std::vector<int>& R = P.ranges[d];
+  const int s = R[2 * (t * L + l)], e = R[2 * (t * L + l) + 1];
+  if (e <= s) {
+    *lo = 0;
+    *hi = 0;
+    return;
+  }
+  *lo = s + (a.reads ? a.slo[d] : 0);
+  *hi = e + (a.reads ? a.shi[d] : 0);
+}
+inline bool meet(int alo, int ahi, int blo, int bhi) { return alo < ahi && blo < bhi && alo < bhi && blo < ahi; }
+}  // namespace
+
+bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& P, TileWavePlan& out, std::string* why) {
+  const int L = (int)loops.size();
+  const int nd = P.ndim;
+  out = TileWavePlan();
+  out.ndim = nd;
+  out.nloops = L;
+  if (L >= 65535) {
+    *why = "too many loops in one segment";
+    return false;
+  }
+  // conflicting argument pairs (later loop first)
+  std::vector<APair> pairs;
+  for (int l = 0; l < L; ++l)
+    for (int a = 0; a < (int)loops[l].args.size(); ++a) {
+      const PArg& A = loops[l].args[a];
+      if (A.kind != OPS_ARG_DAT) continue;
+      for (int lp = 0; lp < l; ++lp)
+        for (int b = 0; b < (int)loops[lp].args.size(); ++b) {
+          const PArg& B = loops[lp].args[b];
+          if (B.kind != OPS_ARG_DAT || B.dat != A.dat || !(A.writes || B.writes)) continue;
+          pairs.push_back(APair{l, a, lp, b});
+        }
+    }
+  out.pairs = (int64_t)pairs.size();
+  // Per dimension, for every pair and tile t: the later access in tile t
+  // must not touch what the earlier one touches in tiles after t (the order
+  // of Algorithm 2 would then run them the wrong way round), nor what it
+  // touches two or more tiles back (no wait covers that distance).  The
+  // tiles of one loop partition its range in order, so the union of its
+  // touched intervals over a run of consecutive tiles is one interval.
+  for (int d = 0; d < nd; ++d) {
+    const int T = P.ntiles[d];
+    const std::vector<int>& R = P.ranges[d];
+    for (const APair& q : pairs) {
+      const PArg& A = loops[q.l].args[q.a];
+      const PArg& B = loops[q.lp].args[q.b];
+      const int blo0 = R[2 * (0 * L + q.lp)], bhi_all = R[2 * ((T - 1) * L + q.lp) + 1];
+      const int bs = B.reads ? B.slo[d] : 0, be = B.reads ? B.shi[d] : 0;
+      for (int t = 0; t < T; ++t) {
+        int alo, ahi;
+        touched(P, L, d, t, q.l, A, &alo, &ahi);
+        if (alo >= ahi) continue;
+        if (t + 1 < T) {
+          const int e = R[2 * (t * L + q.lp) + 1];  // the earlier loop's later tiles: [e, end)
+          if (e < bhi_all && meet(alo, ahi, e + bs, bhi_all + be)) {
+            *why = "an access of a later loop falls in an earlier tile than a conflicting access of an earlier loop";
+            return false;
+          }
+        }
+        if (t >= 2) {
+          const int e2 = R[2 * ((t - 2) * L + q.lp) + 1];  // the earlier loop's tiles up to t - 2: [start, e2)
+          if (e2 > blo0 && meet(alo, ahi, blo0 + bs, e2 + be)) {
+            *why = "the skew reaches two tiles back: tiles are too small for this chain";
+            out.bad_dim = d;
+            return false;
+          }
+        }
+        // the same two checks with the roles of the tiles exchanged: the
+        // earlier loop's access in tile t against the later loop's in tiles
+        // two or more back (a conflict the other way round)
+        int blo, bhi;
+        touched(P, L, d, t, q.lp, B, &blo, &bhi);
+        if (blo < bhi && t >= 2) {
+          const int e2 = R[2 * ((t - 2) * L + q.l) + 1];
+          const int a0 = R[2 * (0 * L + q.l)];
+          const int as = A.reads ? A.slo[d] : 0, ae = A.reads ? A.shi[d] : 0;
+          if (e2 > a0 && meet(blo, bhi, a0 + as, e2 + ae)) {
+            *why = "an access of an earlier loop falls two or more tiles after a conflicting access of a later loop";
+            out.bad_dim = d;
+            return false;
+          }
+        }
+      }
+    }
+  }
+  // predecessor directions
+  out.ndirs = (1 << nd) - 1;
+  for (int m = 1; m <= out.ndirs; ++m)
+    for (int d = 0; d < 3; ++d) out.dirs[m - 1][d] = d < nd ? (m >> d) & 1 : 0;
+  // classes per dimension: tiles whose own ranges and the previous tile's,
+  // relative to the tile's default start, are the same
+  int Tn[3] = {1, 1, 1};
+  std::vector<int> rep[3];
+  for (int d = 0; d < 3; ++d) {
+    Tn[d] = d < nd ? P.ntiles[d] : 1;
+    out.cls[d].assign(Tn[d], 0);
+    if (d >= nd) {
+      rep[d].push_back(0);
+      continue;
+    }
+    std::map<std::vector<int>, int> ids;
+    const std::vector<int>& R = P.ranges[d];
+    for (int t = 0; t < Tn[d]; ++t) {
+      std::vector<int> key;
+      key.reserve(4 * L + 1);
+      const int base = t * P.tile[d];
+      key.push_back(t == 0 ? 1 : 0);
+      for (int u = t - 1; u <= t; ++u)
+        for (int l = 0; l < L; ++l) {
+          const int s0 = u < 0 ? 0 : R[2 * (u * L + l)], e0 = u < 0 ? 0 : R[2 * (u * L + l) + 1];
+          if (e0 <= s0) {  // no tile, or an empty range: where it sits does not matter
+            key.push_back(INT_MIN);
+            key.push_back(u < 0 ? INT_MIN : INT_MIN + 1);
+          } else {
+            key.push_back(s0 - base);
+            key.push_back(e0 - base);
+          }
+        }
+      auto it = ids.find(key);
+      if (it == ids.end()) {
+        const int id = (int)ids.size();
+        ids.emplace(std::move(key), id);
+        rep[d].push_back(t);
+        out.cls[d][t] = id;
+      } else {
+        out.cls[d][t] = it->second;
+      }
+    }
+    out.ncls[d] = (int)ids.size();
+  }
+  // per dimension, class and step back (0 or 1): which pairs meet
+  const size_t np = pairs.size();
+  std::vector<std::vector<char>> meets[3];
+  for (int d = 0; d < 3; ++d) {
+    meets[d].assign((size_t)out.ncls[d] * 2, std::vector<char>(np, 0));
+    for (int c = 0; c < out.ncls[d]; ++c) {
+      const int t = rep[d][c];
+      for (int s = 0; s < 2; ++s) {
+        std::vector<char>& m = meets[d][(size_t)c * 2 + s];
+        if (d >= nd) {
+          std::fill(m.begin(), m.end(), s == 0 ? 1 : 0);
+          continue;
+        }
+        if (t - s < 0) continue;
+        for (size_t k = 0; k < np; ++k) {
+          const APair& q = pairs[k];
+          int alo, ahi, blo, bhi;
+          touched(P, L, d, t, q.l, loops[q.l].args[q.a], &alo, &ahi);
+          touched(P, L, d, t - s, q.lp, loops[q.lp].args[q.b], &blo, &bhi);
+          m[k] = meet(alo, ahi, blo, bhi) ? 1 : 0;
+        }
+      }
+    }
+  }
+  const int ncl = out.ncls[0] * out.ncls[1] * out.ncls[2];
+  out.need.assign((size_t)ncl * out.ndirs * L, 0);
+  for (int cz = 0; cz < out.ncls[2]; ++cz)
+    for (int cy = 0; cy < out.ncls[1]; ++cy)
+      for (int cx = 0; cx < out.ncls[0]; ++cx) {
+        const int cc[3] = {cx, cy, cz};
+        const int cl = (cz * out.ncls[1] + cy) * out.ncls[0] + cx;
+        for (int di = 0; di < out.ndirs; ++di) {
+          const char* m[3];
+          for (int d = 0; d < 3; ++d) m[d] = meets[d][(size_t)cc[d] * 2 + out.dirs[di][d]].data();
+          uint16_t* nv = &out.need[((size_t)cl * out.ndirs + di) * L];
+          for (size_t k = 0; k < np; ++k)
+            if (m[0][k] && m[1][k] && m[2][k]) {
+              const APair& q = pairs[k];
+              nv[q.l] = (uint16_t)std::max<int>(nv[q.l], q.lp + 1);
+            }
+        }
+      }
+  // tickets: by coordinate sum, then z, y, x
+  out.order.clear();
+  out.order.reserve((size_t)Tn[0] * Tn[1] * Tn[2]);
+  for (int s = 0; s <= Tn[0] + Tn[1] + Tn[2] - 3; ++s)
+    for (int tz = 0; tz < Tn[2]; ++tz)
+      for (int ty = 0; ty < Tn[1]; ++ty) {
+        const int tx = s - tz - ty;
+        if (tx < 0 || tx >= Tn[0]) continue;
+        out.order.push_back((tz * Tn[1] + ty) * Tn[0] + tx);
+      }
+  return true;
 }
 
 }  // namespace opstile

@@ -3,6 +3,7 @@
 
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -83,5 +84,35 @@ struct OverlapTile {
   std::vector<int> foot;     // 6 ints per dat: live-in box (lo > hi if unread)
 };
 void build_overlap_tile(const std::vector<PLoop>& loops, int ndats, int ndim, const int owned[6], OverlapTile& out);
+
+// Tile wavefront (OPS_MODE_TILEWAVE): the tiles of Algorithm 1 cut in every
+// dimension; one CTA runs all the loops of a tile in order (the inner loop
+// of Algorithm 2), and tiles run concurrently.  Algorithm 1 orders every
+// conflicting pair of accesses the same way in each dimension on its own (an
+// earlier loop's access never falls in a later tile than a later loop's
+// access to the same data), so program order only needs tile T's loop l to
+// run after the phases of the tiles one step back in any subset of
+// dimensions (T - delta, delta in {0,1}^ndim, delta != 0) that conflict with
+// it: those are earlier loops l' < l.  need[(class, delta, l)] = 1 + the
+// latest such l' (0: none), a count of completed loops of tile T - delta.
+// build_tile_wave checks both premises on the plan, per dimension: that the
+// order holds for every pair of accesses (monotonicity) and that no access
+// reaches data an access two or more tiles back touches.  Tiles whose
+// per-dimension neighbourhoods have identical relative ranges share a class.
+// Tickets hand out tiles by the sum of their tile coordinates (then z, y,
+// x): every predecessor has a smaller sum, so the earliest unfinished tile
+// never waits on a later one.
+struct TileWavePlan {
+  int ndim = 0, ndirs = 0;
+  int dirs[7][3] = {};
+  int ncls[3] = {1, 1, 1};
+  std::vector<int> cls[3];        // per dimension: class of each tile index
+  std::vector<uint16_t> need;     // [(class * ndirs + dir) * nloops + l]
+  std::vector<int> order;         // ticket -> linear tile index (x fastest)
+  int nloops = 0;
+  int64_t pairs = 0;              // conflicting argument pairs examined
+  int bad_dim = -1;               // on failure: the dimension whose tiles are too small
+};
+bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& plan, TileWavePlan& out, std::string* why);
 
 }  // namespace opstile

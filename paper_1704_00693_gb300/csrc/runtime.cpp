@@ -70,6 +70,17 @@ struct CachedPlan {
   void* d_wave = nullptr;
   size_t wave_bytes = 0;
   int* d_wdone = nullptr;
+  // tile-wavefront form: ranges | ticket order | tile classes | need table
+  // (one allocation), per-tile progress + ticket, per-tile reduction partials
+  TileWavePlan tw;
+  void* d_tw = nullptr;
+  size_t tw_bytes = 0;
+  size_t tw_order = 0, tw_cls = 0, tw_need = 0;  // byte offsets inside d_tw
+  int tw_roff[3] = {0, 0, 0}, tw_coff[3] = {0, 0, 0};
+  int* d_twprog = nullptr;
+  int tw_ntiles = 0;
+  DD* d_twpart = nullptr;
+  int tw_rows = 0;
 };
 
 // An overlapped-tile plan of one segment (Sec. 4.D per CTA tile).
@@ -139,6 +150,7 @@ struct ops_ctx_s {
   // compiled loop bodies per segment (by signature and IR); nullptr: interpret
   std::map<std::vector<int>, JitSegment*> jit;
   std::map<std::vector<int>, JitWave*> jitw;  // wavefront kernels, same keys
+  std::map<std::vector<int>, JitTile*> jitt;  // tile-wavefront kernels, same keys
   std::string jit_why;
   int64_t allocated = 0;
   std::string err;
@@ -1067,6 +1079,265 @@ int run_wavefront(ops_ctx c, int first, int count, int dl_base, std::vector<DLoo
   return OPS_OK;
 }
 
+// Tile-wavefront kernel of a segment (every loop body in one module),
+// compiled at the segment's first such flush; nullptr when run-time
+// compilation is unavailable (reason in jit_why).
+int tile_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitTile** out) {
+  *out = nullptr;
+  std::vector<int> key = code_key(c, first, count);
+  auto it = c->jitt.find(key);
+  if (it != c->jitt.end()) {
+    *out = it->second;
+    return OPS_OK;
+  }
+  std::vector<std::vector<char>> ro = read_only_args(c, first, count);
+  JitTile* t = nullptr;
+  std::string why;
+  double ms = 0.0;
+  const int rc = jit_tilewave(c->cfg.device, hl.data() + first, count, ro, c->es, c->queue[first].dims, &t, &why, &ms);
+  c->stats.compile_ms += ms;
+  if (rc) return fail(c, rc, "compiling the tile-wavefront kernel: %s", why.c_str());
+  if (!t) c->jit_why = why;
+  c->jitt[key] = t;
+  *out = t;
+  return OPS_OK;
+}
+
+// Automatic tile of the tile wavefront: the tiles the resident CTAs hold
+// at once should fit about half the cache budget (bytes per point = element
+// size x the distinct dats of the segment), with 512 to 8192 points per
+// tile; x takes up to 128 points, the other dimensions share the rest.
+void auto_tile_wave(ops_ctx c, const std::vector<PLoop>& pl, int ndim, int tile[3]) {
+  std::vector<char> used(c->dats.size(), 0);
+  int ndat = 0;
+  int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
+  for (const PLoop& p : pl) {
+    for (const PArg& a : p.args)
+      if (a.kind == OPS_ARG_DAT && !used[a.dat]) {
+        used[a.dat] = 1;
+        ++ndat;
+      }
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], p.rng[2 * d]);
+      hi[d] = std::max(hi[d], p.rng[2 * d + 1]);
+    }
+  }
+  const int64_t budget = c->cfg.l2_bytes > 0 ? c->cfg.l2_bytes : (c->l2_size > 0 ? c->l2_size * 3 / 4 : 96ll << 20);
+  const int64_t bpp = (int64_t)c->es * std::max(1, ndat);
+  const int64_t ctas = (int64_t)std::max(1, c->num_sms) * jit_tile_min_ctas();
+  const int64_t pts = std::min<int64_t>(8192, std::max<int64_t>(512, budget / 2 / (ctas * bpp)));
+  int ext[3];
+  for (int d = 0; d < 3; ++d) {
+    ext[d] = std::max(1, hi[d] - lo[d]);
+    tile[d] = 1;
+  }
+  tile[0] = (int)std::min<int64_t>(ext[0], ndim == 1 ? pts : 128);
+  const int64_t rest = std::max<int64_t>(1, pts / tile[0]);
+  if (ndim == 2) tile[1] = (int)std::min<int64_t>(ext[1], rest);
+  if (ndim == 3) {
+    int s = 1;
+    while ((int64_t)(s + 1) * (s + 1) <= rest) ++s;
+    tile[1] = std::min(ext[1], s);
+    tile[2] = std::min(ext[2], (int)std::max<int64_t>(1, rest / s));
+  }
+}
+
+// The tile-wavefront plan of a segment (cached like the other plans).  A
+// tile size the chain's skew reaches across is doubled in that dimension
+// until the plan is valid; *out = nullptr (and jit_why says why) if no size
+// up to the whole extent is.
+int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int dl_base, const int* tile_in,
+              CachedPlan** out) {
+  *out = nullptr;
+  const int ndim = c->queue[first].dims;
+  std::vector<PLoop> pl;
+  pl.reserve(count);
+  for (int i = 0; i < count; ++i) pl.push_back(plan_loop(c, c->queue[first + i]));
+  int tile[3] = {tile_in[0], tile_in[1], tile_in[2]};
+  bool autod = false;
+  for (int d = 0; d < ndim; ++d) autod = autod || tile[d] <= 0;
+  if (autod) {
+    int at[3];
+    auto_tile_wave(c, pl, ndim, at);
+    for (int d = 0; d < 3; ++d)
+      if (tile[d] <= 0) tile[d] = at[d];
+  }
+  for (int d = ndim; d < 3; ++d) tile[d] = 1;
+  std::vector<int> key = {-OPS_MODE_TILEWAVE, ndim, tile[0], tile[1], tile[2]};
+  for (int i = 0; i < count; ++i) {
+    const QLoop& q = c->queue[first + i];
+    for (int k = 0; k < 6; ++k) key.push_back(q.rng[k]);
+    key.push_back((int)q.args.size());
+    for (const ops_arg& a : q.args) {
+      key.push_back(a.kind);
+      key.push_back(a.handle);
+      key.push_back(a.kind == OPS_ARG_DAT ? a.stencil : -1);
+      key.push_back(a.access);
+    }
+  }
+  auto it = c->plans.find(key);
+  if (it != c->plans.end()) {
+    ++c->stats.plan_cache_hits;
+    *out = it->second.get();
+    return OPS_OK;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  std::unique_ptr<CachedPlan> np(new CachedPlan);
+  np->key = key;
+  std::string why;
+  bool ok = false;
+  for (int attempt = 0; attempt < 24; ++attempt) {
+    build_skewed_ranges(pl, (int)c->dats.size(), ndim, tile, np->plan);
+    if (build_tile_wave(pl, np->plan, np->tw, &why)) {
+      ok = true;
+      break;
+    }
+    const int d = np->tw.bad_dim;
+    if (d < 0 || d >= ndim || np->plan.ntiles[d] <= 1) break;
+    tile[d] *= 2;
+  }
+  c->stats.plan_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (!ok) {
+    c->jit_why = "no tile size gives a valid tile wavefront: " + why;
+    c->plans[key] = nullptr;
+    return OPS_OK;
+  }
+  const SkewedPlan& P = np->plan;
+  const TileWavePlan& W = np->tw;
+  const int ntiles = P.ntiles[0] * P.ntiles[1] * P.ntiles[2];
+  // ranges of every dimension (dimensions beyond the loops': each loop's (0, 1))
+  std::vector<int> rng;
+  for (int d = 0; d < 3; ++d) {
+    np->tw_roff[d] = (int)rng.size();
+    if (d < ndim) {
+      rng.insert(rng.end(), P.ranges[d].begin(), P.ranges[d].end());
+    } else {
+      for (int l = 0; l < count; ++l) {
+        rng.push_back(pl[l].rng[2 * d]);
+        rng.push_back(pl[l].rng[2 * d + 1]);
+      }
+    }
+  }
+  std::vector<int> cls;
+  for (int d = 0; d < 3; ++d) {
+    np->tw_coff[d] = (int)cls.size();
+    cls.insert(cls.end(), W.cls[d].begin(), W.cls[d].end());
+  }
+  const size_t b_rng = sizeof(int) * rng.size(), b_order = sizeof(int) * W.order.size(),
+               b_cls = sizeof(int) * cls.size(), b_need = sizeof(uint16_t) * W.need.size();
+  np->tw_order = (b_rng + 15) / 16 * 16;
+  np->tw_cls = np->tw_order + (b_order + 15) / 16 * 16;
+  np->tw_need = np->tw_cls + (b_cls + 15) / 16 * 16;
+  np->tw_bytes = np->tw_need + b_need + 16;
+  np->tw_ntiles = ntiles;
+  int rows = 0;
+  {
+    int row0 = -1;
+    for (int i = 0; i < count; ++i) {
+      const DLoop& L = hl[dl_base + i];
+      if (L.nreds) {
+        if (row0 < 0) row0 = L.part_row;
+        rows = L.part_row + L.nreds - row0;
+      }
+    }
+  }
+  np->tw_rows = rows;
+  int rc = dev_alloc(c, &np->d_tw, np->tw_bytes);
+  if (!rc) rc = dev_alloc(c, (void**)&np->d_twprog, sizeof(int) * (ntiles + 1));
+  if (!rc && rows) rc = dev_alloc(c, (void**)&np->d_twpart, sizeof(DD) * (size_t)rows * ntiles);
+  if (rc) return rc;
+  char* d = (char*)np->d_tw;
+  CUDA_TRY(c, cudaMemcpyAsync(d, rng.data(), b_rng, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_order, W.order.data(), b_order, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_cls, cls.data(), b_cls, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_need, W.need.data(), b_need, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host tables are temporaries
+  *out = np.get();
+  c->plans[key] = std::move(np);
+  return OPS_OK;
+}
+
+// Tile-wavefront execution of a segment (OPS_MODE_TILEWAVE).  *ran = false
+// when no valid plan exists (the caller then runs the segment skewed).
+int run_tilewave(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl, const int* tile_in,
+                 JitTile* t, bool* ran) {
+  *ran = false;
+  CachedPlan* cp = nullptr;
+  int rc = tile_plan(c, first, count, hl, dl_base, tile_in, &cp);
+  if (rc) return rc;
+  if (!cp) return OPS_OK;
+  *ran = true;
+  const SkewedPlan& P = cp->plan;
+  LaunchEnv env = make_env(c);
+  c->stats.mode = OPS_MODE_TILEWAVE;
+  c->stats.compiled = 1;
+  ++c->stats.segments;
+  c->stats.loops += count;
+  for (int d = 0; d < 3; ++d) {
+    c->stats.tile[d] = P.tile[d];
+    c->stats.skew[d] = P.skew[d];
+  }
+  c->stats.tiles = cp->tw_ntiles;
+  int64_t pts = 0;
+  for (int l = 0; l < count; ++l) {
+    int64_t n = 1;
+    for (int d = 0; d < 3; ++d) {
+      const QLoop& q = c->queue[first + l];
+      const int a = d < q.dims ? q.rng[2 * d] : 0, b = d < q.dims ? q.rng[2 * d + 1] : 1;
+      n *= std::max(0, b - a);
+    }
+    pts += n;
+  }
+  c->stats.points += pts;
+  int row0 = -1, nrows = 0;
+  for (int i = 0; i < count; ++i) {
+    const DLoop& L = hl[dl_base + i];
+    if (L.nreds) {
+      if (row0 < 0) row0 = L.part_row;
+      nrows = L.part_row + L.nreds - row0;
+    }
+  }
+  if (nrows > cp->tw_rows) return fail(c, OPS_ERR_STATE, "tile-wavefront partial rows changed under a cached plan");
+  const int grid = std::max(1, std::min(cp->tw_ntiles, jit_tilewave_max_grid(t, c->num_sms)));
+  CUDA_TRY(c, cudaMemsetAsync(cp->d_twprog, 0, sizeof(int) * (cp->tw_ntiles + 1), c->stream));
+  rc = record_event(c);
+  if (rc) return rc;
+  const char* d = (const char*)cp->d_tw;
+  TwArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.loops = c->d_loops + dl_base;
+  a.rng = (const int*)d;
+  a.order = (const int*)(d + cp->tw_order);
+  a.cls = (const int*)(d + cp->tw_cls);
+  a.need = (const unsigned short*)(d + cp->tw_need);
+  a.prog = cp->d_twprog;
+  a.ticket = cp->d_twprog + cp->tw_ntiles;
+  a.scal = env.scal;
+  a.part = cp->d_twpart;
+  a.err = env.err;
+  a.timeout_ns = env.timeout_ns;
+  for (int k = 0; k < 3; ++k) {
+    a.nt[k] = P.ntiles[k];
+    a.ncls[k] = cp->tw.ncls[k];
+    a.roff[k] = cp->tw_roff[k];
+    a.coff[k] = cp->tw_coff[k];
+  }
+  a.ntiles = cp->tw_ntiles;
+  a.stride = cp->tw_ntiles;
+  a.row0 = row0 < 0 ? 0 : row0;
+  a.skip_tile = env.skip_block;
+  CUDA_TRY(c, jit_launch_tilewave(t, a, c->stream, grid));
+  ++c->stats.launches;
+  ++c->stats.kernel_launches;
+  rc = record_event(c);
+  if (rc) return rc;
+  if (nrows) {
+    CUDA_TRY(c, launch_fold_rows(env, cp->d_twpart, cp->tw_ntiles, row0, nrows, cp->tw_ntiles));
+    ++c->stats.launches;
+  }
+  return OPS_OK;
+}
+
 // Grid of a compiled per-loop kernel over a box: by default one wave of the
 // CTAs that stay resident (the kernel's occupancy x SMs), each striding over
 // the box's units, so no partly filled last wave of CTAs idles SMs;
@@ -1136,6 +1407,23 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
     }
     mode = OPS_MODE_SKEWED;
     tile_in = c->cfg.tile;
+  }
+  if (mode == OPS_MODE_TILEWAVE) {
+    // one loop has no dependencies to schedule; checked and interpreted runs,
+    // runs without run-time compilation and chains no tile size suits go
+    // through the skewed path
+    if (count > 1 && !c->cfg.interpret && !c->cfg.check) {
+      JitTile* t = nullptr;
+      int rc = tile_code(c, first, count, hl, &t);
+      if (rc) return rc;
+      if (t) {
+        bool ran = false;
+        rc = run_tilewave(c, first, count, dl_base, hl, tile_in, t, &ran);
+        if (rc || ran) return rc;
+        tile_in = c->cfg.tile;
+      }
+    }
+    mode = count > 1 ? OPS_MODE_SKEWED : OPS_MODE_UNTILED;
   }
   if (mode == OPS_MODE_WAVEFRONT) {
     // one loop has no dependencies to schedule; checked and interpreted
@@ -1576,9 +1864,14 @@ int ops_finalize(ops_ctx c) {
       dev_free(c, d.alt, d.bytes);
     }
     for (auto& kv : c->plans) {
+      if (!kv.second) continue;  // a tile-wavefront plan no tile size suits
       if (kv.second->d_phases) dev_free(c, kv.second->d_phases, sizeof(Phase) * kv.second->plan.phases.size());
       if (kv.second->d_wave) dev_free(c, kv.second->d_wave, kv.second->wave_bytes);
       if (kv.second->d_wdone) dev_free(c, kv.second->d_wdone, sizeof(int) * (kv.second->plan.phases.size() + 1));
+      if (kv.second->d_tw) dev_free(c, kv.second->d_tw, kv.second->tw_bytes);
+      if (kv.second->d_twprog) dev_free(c, kv.second->d_twprog, sizeof(int) * (kv.second->tw_ntiles + 1));
+      if (kv.second->d_twpart)
+        dev_free(c, kv.second->d_twpart, sizeof(DD) * (size_t)kv.second->tw_rows * kv.second->tw_ntiles);
     }
     for (auto& kv : c->oplans)
       if (kv.second && kv.second->d_tab) dev_free(c, kv.second->d_tab, sizeof(int) * kv.second->tab_ints);
@@ -1611,7 +1904,7 @@ int ops_set_timing(ops_ctx c, int timing) {
 
 int ops_set_mode(ops_ctx c, int mode, const int* tile, int segment) {
   if (!c) return OPS_ERR_INVALID_ARG;
-  if (mode < OPS_MODE_UNTILED || mode > OPS_MODE_WAVEFRONT) return fail(c, OPS_ERR_INVALID_ARG, "bad mode %d", mode);
+  if (mode < OPS_MODE_UNTILED || mode > OPS_MODE_TILEWAVE) return fail(c, OPS_ERR_INVALID_ARG, "bad mode %d", mode);
   c->cfg.mode = mode;
   if (tile)
     for (int d = 0; d < 3; ++d) c->cfg.tile[d] = tile[d];
@@ -1900,6 +2193,71 @@ int ops_compile_queued_wavefront(ops_ctx c, char* src_out, int64_t cap, int64_t*
   }
   if (compile_ms) *compile_ms = ms;
   if (rc) return fail(c, rc, "%s", why.c_str());
+  return OPS_OK;
+}
+
+int ops_compile_queued_tilewave(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
+  const int n = (int)c->queue.size();
+  std::vector<DLoop> hl(n);
+  std::vector<FoldRow> rows;
+  for (int i = 0; i < n; ++i) fill_dloop(c, c->queue[i], hl[i], (int)rows.size(), rows);
+  std::string src, why;
+  double ms = 0.0;
+  const int rc = jit_compile_tilewave_only(hl.data(), n, read_only_args(c, 0, n), c->es, c->queue[0].dims, &src,
+                                           &why, &ms);
+  if (src_len) *src_len = (int64_t)src.size();
+  if (src_out && cap > 0) {
+    const size_t k = std::min<size_t>(src.size(), (size_t)cap - 1);
+    std::memcpy(src_out, src.data(), k);
+    src_out[k] = '\0';
+  }
+  if (compile_ms) *compile_ms = ms;
+  if (rc) return fail(c, rc, "%s", why.c_str());
+  return OPS_OK;
+}
+
+int ops_plan_tilewave(ops_ctx c, const int* tile, int64_t* counts, int* out_need, int64_t need_cap, int* out_class,
+                      int* out_order, int64_t tile_cap) {
+  if (!c || !tile || !counts) return OPS_ERR_INVALID_ARG;
+  if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
+  const int ndim = c->queue[0].dims;
+  std::vector<PLoop> pl;
+  for (const QLoop& q : c->queue) {
+    if (q.dims != ndim) return fail(c, OPS_ERR_INVALID_ARG, "queued loops of different dimensionality");
+    pl.push_back(plan_loop(c, q));
+  }
+  int t[3] = {1, 1, 1};
+  for (int d = 0; d < ndim; ++d) {
+    if (tile[d] < 1) return fail(c, OPS_ERR_INVALID_ARG, "tile sizes must be >= 1");
+    t[d] = tile[d];
+  }
+  SkewedPlan P;
+  build_skewed_ranges(pl, (int)c->dats.size(), ndim, t, P);
+  TileWavePlan W;
+  std::string why;
+  if (!build_tile_wave(pl, P, W, &why)) return fail(c, OPS_ERR_INVALID_ARG, "%s", why.c_str());
+  const int64_t ntiles = (int64_t)P.ntiles[0] * P.ntiles[1] * P.ntiles[2];
+  const int64_t ncl = (int64_t)W.ncls[0] * W.ncls[1] * W.ncls[2];
+  counts[0] = ntiles;
+  counts[1] = ncl;
+  counts[2] = W.ndirs;
+  counts[3] = W.nloops;
+  if (out_need) {
+    if ((int64_t)W.need.size() > need_cap)
+      return fail(c, OPS_ERR_INVALID_ARG, "out_need needs %lld ints", (long long)W.need.size());
+    for (size_t k = 0; k < W.need.size(); ++k) out_need[k] = W.need[k];
+  }
+  if ((out_class || out_order) && ntiles > tile_cap)
+    return fail(c, OPS_ERR_INVALID_ARG, "tile outputs need %lld ints", (long long)ntiles);
+  if (out_class)
+    for (int tz = 0; tz < P.ntiles[2]; ++tz)
+      for (int ty = 0; ty < P.ntiles[1]; ++ty)
+        for (int tx = 0; tx < P.ntiles[0]; ++tx)
+          out_class[((int64_t)tz * P.ntiles[1] + ty) * P.ntiles[0] + tx] =
+              (W.cls[2][tz] * W.ncls[1] + W.cls[1][ty]) * W.ncls[0] + W.cls[0][tx];
+  if (out_order) std::memcpy(out_order, W.order.data(), sizeof(int) * W.order.size());
   return OPS_OK;
 }
 

@@ -399,7 +399,7 @@ def test_full_size_opensbli_one_step():
 
 
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 16, 0)), ("overlapped", None),
-                                       ("auto", None), ("wavefront", (0, 8, 0))])
+                                       ("auto", None), ("wavefront", (0, 8, 0)), ("tilewave", (0, 0, 0))])
 def test_borrowed_device_dats(mode, tile):
     """Dats declared on caller-owned device memory (torch tensors with a pitch
     of their own): the chain reads and writes them in place in every mode
@@ -434,6 +434,8 @@ def test_borrowed_device_dats(mode, tile):
         assert st["mode"] == ops.OPS_MODE_SKEWED
     if mode == "wavefront":
         assert st["mode"] == ops.OPS_MODE_WAVEFRONT
+    if mode == "tilewave":
+        assert st["mode"] == ops.OPS_MODE_TILEWAVE
 
 
 @pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 17, 0)), ("skewed", (0, 0, 0)),
