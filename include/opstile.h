@@ -415,10 +415,12 @@ int ops_serve_close(ops_server srv);
  * must not grow its footprint behind that allocator's back.  Such callers
  * run a loop here instead of through a context.
  *
- * ops_loop_noalloc runs one parallel loop (same IR, same access rules, same
- * kernel and bit-identical results as a single queued loop run by
- * ops_par_loop + ops_execute) over caller-owned dats, and returns its
- * reductions.  Its only scratch (loop descriptor, reduction partials and
+ * ops_loop_noalloc runs one parallel loop over caller-owned dats and returns
+ * its reductions.  The IR and the access rules are those of ops_par_loop;
+ * the written dats come out identical to a single queued loop run by
+ * ops_par_loop + ops_execute, and reduction sums agree with it within 1e-12
+ * relative (min and max exactly): the partial sums are combined over a
+ * launch shape of this entry point's own.  Its only scratch (loop descriptor, reduction partials and
  * slots) is a fixed array of OPS_NOALLOC_SCRATCH_BYTES inside the library's
  * device image: every GPU that loads the library holds it until the process
  * exits.  No call allocates: no cudaMalloc, cudaFree or allocating library
@@ -438,7 +440,10 @@ int ops_serve_close(ops_server srv);
  *   dims, range: as ops_par_loop; args[i].handle is ignored;
  *   views[i]: for DAT args, the dat (address of grid point (0,0,0), strides,
  *     allocation box [lo, hi) in grid coordinates; every access must lie
- *     inside it, else OPS_ERR_BOUNDS);
+ *     inside it, else OPS_ERR_BOUNDS).  OPS_ERR_INVALID_ARG when a pitch is
+ *     smaller than the box's x extent (or, in 3D, a plane smaller than
+ *     pitch x y extent), or when the memory of two views overlaps and the
+ *     loop writes one of them;
  *   stencil_npts[i], stencil_offsets: for DAT args, the number of stencil
  *     points and their offsets (3 ints each), concatenated in argument order;
  *   scalar_values[i]: the value a SCALAR arg reads;

@@ -260,6 +260,16 @@ struct LoopGen {
   std::ostringstream& os;
   bool ov = false;                    // overlapped tile: dats in shared footprints, owned-point reductions
   bool f32 = false;                   // FP32 dats and arithmetic
+  // every dat pointer __restrict__: a dat appears at most once in a loop
+  // (checked at enqueue), so a loop's stores never alias its other
+  // arguments' loads and the compiler may overlap consecutive points
+  mutable bool restrict_all = false;
+  // tile bodies read their dat pointers from the step's shared-memory slot
+  // (ptrs[a]), which the control warp fills, instead of the descriptor
+  mutable bool staged_ptrs = false;
+  std::string ptr_src(int a) const {
+    return staged_ptrs ? "ptrs[" + std::to_string(a) + "]" : "L->args[" + std::to_string(a) + "].ptr0";
+  }
   int nt = kThreads;                  // threads per CTA of the enumeration (not overlapped)
   const char* T = "double";
   const char *fadd = "__dadd_rn", *fsub = "__dsub_rn", *fmul = "__dmul_rn", *fdiv = "__ddiv_rn", *ffma = "__fma_rn";
@@ -405,7 +415,9 @@ struct LoopGen {
              << ");\n";
         }
         else if (ro[a])
-          os << "  const " << T << "* __restrict__ p" << a << " = (const " << T << "*)L->args[" << a << "].ptr0;\n";
+          os << "  const " << T << "* __restrict__ p" << a << " = (const " << T << "*)" << ptr_src(a) << ";\n";
+        else if (restrict_all)
+          os << "  " << T << "* __restrict__ p" << a << " = (" << T << "*)" << ptr_src(a) << ";\n";
         else
           os << "  " << T << "* p" << a << " = (" << T << "*)L->args[" << a << "].ptr0;\n";
       }
@@ -465,8 +477,10 @@ struct LoopGen {
   // reductions go to the tile's column `col` of the partial rows (row =
   // the loop's partial row - row0), assigned.
   void emit_tile(int i, int NT, int P) const {
+    restrict_all = true;
+    staged_ptrs = true;
     os << "\n__device__ __forceinline__ void tb" << i
-       << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
+       << "(const DLoop* __restrict__ L, void* const* ptrs, int x0, int x1, int y0, int y1, int z0, int z1,\n"
           "    const double* __restrict__ scal, DD* part, int stride, int row0, int col) {\n";
     emit_hoist(nullptr);
     os << "  auto one = [&](int x, int y, int z) {\n";
@@ -746,25 +760,73 @@ std::string generate_wavefront(const DLoop* loops, int count, const std::vector<
 
 // Source of the tile-wavefront kernel "tw" for the loops of a segment (see
 // build_tile_wave).  A persistent grid draws tiles from a ticket counter in
-// the plan's order; a CTA runs every loop of its tile in order over the
-// tile's box of that loop, with a block barrier between loops, and after
-// loop l publishes l + 1 as the tile's progress (release).  Before loop l
-// it makes sure that each predecessor tile (one step back in a subset of
-// the dimensions) has completed the loops that l conflicts with; the last
-// progress value it saw of each predecessor is kept in shared memory, so a
-// counter is polled (relaxed loads, then one acquire fence) only when that
-// value falls short.  The earliest unfinished ticket always belongs to a
-// running CTA whose predecessors have smaller tickets and are done, so the
-// waits end; each is still bounded in wall-clock time, after which the CTA
-// sets the error word and leaves, as does every CTA that finds it set.  The
-// next ticket is drawn while the current tile runs.
+// the plan's order; each CTA runs every loop of its tile in order.  Its
+// warps are specialised: NT compute threads evaluate the loop bodies over
+// the (tile, loop) boxes, and one control warp runs a step ahead of them.
+// Between two steps all threads meet at one named barrier; while the compute
+// warps run step s, the control warp
+//   - publishes the progress of step s - 1 (a release store of the number
+//     of loops the tile has completed),
+//   - makes sure step s + 1 may run: each predecessor tile (one step back in
+//     a subset of the dimensions) must have completed the loops that loop
+//     conflicts with; the last progress value seen of each predecessor is
+//     kept, so a counter is polled (relaxed loads, then one acquire fence)
+//     only when that value falls short,
+//   - writes step s + 1's loop and box into a double-buffered slot.
+// At the end of a tile the control warp inserts an empty step, publishes
+// the tile's completion before it looks at the next tile's predecessors (a
+// tile can precede the next one the same CTA draws), and reads the next
+// tile's wait table.  The release and the polls thus stay off the compute
+// warps' path, and the compute warps never touch the counters.  The
+// earliest unfinished ticket always belongs to a running CTA whose
+// predecessors have smaller tickets and are done, so the waits end; each is
+// still bounded in wall-clock time, after which the CTA sets the error word
+// and leaves, as does every CTA that finds it set.  Reductions combine over
+// the compute warps only (a second named barrier).
 const char* kTwPrelude = R"TWP(
 struct TwArgs {
   const DLoop* loops; const int* rng; const int* order; const int* cls; const unsigned short* need;
   int* prog; int* ticket; const double* scal; DD* part; int* err; long long timeout_ns;
   int nt[3]; int ncls[3]; int roff[3]; int coff[3];
   int ntiles, stride, row0, skip_tile;
+  const unsigned char* pf; int ahead, pad;
 };
+// Ask L2 to fetch the rows of the arguments of loop l that the mask pf[l]
+// selects, over the tile's box of that loop widened by each argument's
+// stencil and clipped to the dat's allocation (16-byte aligned inward:
+// bulk prefetches take aligned addresses and sizes).  The whole control
+// warp takes part, one row per lane.
+template <int ES>
+__device__ __forceinline__ void tw_prefetch(const TwArgs& A, int NL, int l, const int* tc, int lane) {
+  const unsigned m = A.pf[l];
+  if (!m) return;
+  int b[6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const int* r = A.rng + A.roff[d] + 2 * (tc[d] * NL + l);
+    b[2 * d] = r[0];
+    b[2 * d + 1] = r[1];
+  }
+  if (b[1] <= b[0] || b[3] <= b[2] || b[5] <= b[4]) return;
+  const DLoop* L = A.loops + l;
+  for (int a = 0; a < 8; ++a) {
+    if (!((m >> a) & 1u)) continue;
+    const DArg& g = L->args[a];
+    const int x0 = max(b[0] + g.slo[0], g.alo[0]), x1 = min(b[1] + g.shi[0], g.ahi[0]);
+    const int y0 = max(b[2] + g.slo[1], g.alo[1]), y1 = min(b[3] + g.shi[1], g.ahi[1]);
+    const int z0 = max(b[4] + g.slo[2], g.alo[2]), z1 = min(b[5] + g.shi[2], g.ahi[2]);
+    if (x1 <= x0 || y1 <= y0 || z1 <= z0) continue;
+    const int ny = y1 - y0, rows = ny * (z1 - z0);
+    for (int r = lane; r < rows; r += 32) {
+      const long long y = y0 + r % ny, z = z0 + r / ny;
+      const char* base = (const char*)g.ptr0 + (y * g.pitch + z * g.plane) * ES;
+      const unsigned long long a0 = ((unsigned long long)(base + (long long)x0 * ES) + 15) & ~15ull;
+      const unsigned long long a1 = ((unsigned long long)(base + (long long)x1 * ES)) & ~15ull;
+      if (a1 > a0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(a0), "r"((unsigned)(a1 - a0)) : "memory");
+    }
+  }
+}
 __device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -774,10 +836,21 @@ __device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gp
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
 }
+// the compute warps' own barrier (named barrier 2; the step barrier is 1)
+__device__ __forceinline__ void bar_compute() { asm volatile("bar.sync 2, %0;" :: "n"(kTwNtc) : "memory"); }
+__device__ __forceinline__ void bar_step() { asm volatile("bar.sync 1, %0;" :: "n"(kTwNtc + 32) : "memory"); }
 __device__ __forceinline__ void flush_red_col(int op, DD v, DD* dst) {
-  v = block_combine(op, v, g_sh);
-  if (threadIdx.x == 0) *dst = v;
-  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) v = red_combine(op, v, shfl_down_dd(v, o));
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bar_compute();
+  if (lane == 0) g_sh[w] = v;
+  bar_compute();
+  if (w == 0) {
+    v = lane < kTwNtc / 32 ? g_sh[lane] : dd_of(red_identity(op));
+    for (int o = 16; o > 0; o >>= 1) v = red_combine(op, v, shfl_down_dd(v, o));
+    if (lane == 0) *dst = v;
+  }
+  bar_compute();
 }
 )TWP";
 
@@ -785,98 +858,143 @@ std::string generate_tilewave(const DLoop* loops, int count, const std::vector<s
                               int ndim) {
   const int nt = jit_tile_threads(), P = jit_tile_pts(es), ndirs = (1 << ndim) - 1;
   std::ostringstream os;
-  os << "// opstile tile wavefront kernel: " << nt << " threads, " << P << " points per thread at a time, "
-     << jit_tile_min_ctas() << " CTAs per SM, " << ndim << "D, " << (es == 4 ? "fp32" : "fp64") << "\n";
-  os << kPrelude << kDeviceCommon << kPreludeTail << kTwPrelude;
+  os << "// opstile tile wavefront kernel: " << nt << " compute threads + 1 control warp, " << P
+     << " points per thread at a time, " << jit_tile_min_ctas() << " CTAs per SM, " << ndim << "D, "
+     << (es == 4 ? "fp32" : "fp64") << "\n";
+  os << kPrelude << kDeviceCommon << kPreludeTail;
+  os << "constexpr int kTwNtc = " << nt << ";\n" << kTwPrelude;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
   os << "static_assert(sizeof(TwArgs) == " << sizeof(TwArgs) << ", \"TwArgs layout\");\n";
   for (int i = 0; i < count; ++i) {
     LoopGen g(loops[i], ro[i], os, false, es == 4);
     g.emit_tile(i, nt, P);
   }
-  os << "extern \"C\" __global__ void __launch_bounds__(" << nt << ", " << jit_tile_min_ctas()
+  // s_step[k]: loop of the step in slot k (-1: stop, -2: an empty step),
+  // its tile, and its box
+  os << "extern \"C\" __global__ void __launch_bounds__(" << nt + 32 << ", " << jit_tile_min_ctas()
      << ") tw(const TwArgs A) {\n"
-        "  constexpr int NL = " << count << ", ND = " << ndirs << ";\n"
+        "  constexpr int NL = " << count << ", ND = " << ndirs << ", ES = " << es << ";\n"
         "  __shared__ unsigned short s_need[ND * NL];\n"
-        "  __shared__ int s_have[ND], s_pred[ND], s_tk, s_stop;\n"
+        "  __shared__ int s_step[2][8];\n"
+        "  __shared__ void* s_ptr[2][8];\n"
         "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
         "  const int tid = threadIdx.x;\n"
-        "  int nxt = 0;\n"
-        "  if (tid == 0) {\n"
-        "    s_tk = atomicAdd(A.ticket, 1);\n"
-        "    s_stop = 0;\n"
+        "  if (tid < kTwNtc) {\n"
+        "    // compute warps: run the step of each slot in turn\n"
+        "    for (int k = 0;; k ^= 1) {\n"
+        "      bar_step();\n"
+        "      const int l = s_step[k][0];\n"
+        "      if (l == -1) return;\n"
+        "      if (l < 0) continue;\n"
+        "      const int tile = s_step[k][1];\n"
+        "      const int x0 = s_step[k][2], x1 = s_step[k][3], y0 = s_step[k][4], y1 = s_step[k][5];\n"
+        "      const int z0 = s_step[k][6], z1 = s_step[k][7];\n"
+        "      switch (l) {\n";
+  for (int i = 0; i < count; ++i)
+    os << "        case " << i << ": tb" << i
+       << "(A.loops + " << i << ", s_ptr[k], x0, x1, y0, y1, z0, z1, A.scal, A.part, A.stride, A.row0, tile); break;\n";
+  os << "        default: break;\n"
+        "      }\n"
+        "    }\n"
         "  }\n"
-        "  for (;;) {\n"
-        "    __syncthreads();\n"
-        "    const int tk = s_tk;\n"
-        "    if (tk >= A.ntiles || s_stop) return;\n"
+        "  // control warp\n"
+        "  const int lane = tid - kTwNtc;\n"
+        "  int k = 0;              // slot of the next step\n"
+        "  int prev_tile = -1, prev_l = 0;  // the step the compute warps run now\n"
+        "  bool stop = false;\n"
+        "  int tk = 0, nxt = 0;\n"
+        "  if (lane == 0) tk = atomicAdd(A.ticket, 1);\n"
+        "  tk = __shfl_sync(0xffffffffu, tk, 0);\n"
+        "  // publish the progress of the step the compute warps just finished\n"
+        "  auto publish = [&]() {\n"
+        "    if (lane == 0 && prev_tile >= 0 && prev_tile != A.skip_tile) st_release(A.prog + prev_tile, prev_l + 1);\n"
+        "  };\n"
+        "  // hand a slot to the compute warps and meet them at the step barrier\n"
+        "  auto post = [&](int l, int tile, const int* box) {\n"
+        "    if (lane == 0) {\n"
+        "      s_step[k][0] = l;\n"
+        "      s_step[k][1] = tile;\n"
+        "    }\n"
+        "    if (lane < 6 && box) s_step[k][2 + lane] = box[lane];\n"
+        "    if (l >= 0 && lane < A.loops[l].nargs) s_ptr[k][lane] = A.loops[l].args[lane].ptr0;\n"
+        "    __syncwarp();\n"
+        "    bar_step();\n"
+        "    k ^= 1;\n"
+        "  };\n"
+        "  while (!stop && tk < A.ntiles) {\n"
         "    const int tile = A.order[tk];\n"
         "    const int tc[3] = {tile % A.nt[0], (tile / A.nt[0]) % A.nt[1], tile / (A.nt[0] * A.nt[1])};\n"
         "    const int cl = (A.cls[A.coff[2] + tc[2]] * A.ncls[1] + A.cls[A.coff[1] + tc[1]]) * A.ncls[0] +\n"
         "                   A.cls[A.coff[0] + tc[0]];\n"
-        "    for (int j = tid; j < ND * NL; j += blockDim.x) s_need[j] = A.need[(size_t)cl * (ND * NL) + j];\n"
-        "    if (tid < ND) {\n"
-        "      const int m = tid + 1;\n"
+        "    for (int j = lane; j < ND * NL; j += 32) s_need[j] = A.need[(size_t)cl * (ND * NL) + j];\n"
+        "    __syncwarp();\n"
+        "    int pred = -1, have = 0x7fffffff;\n"
+        "    if (lane < ND) {\n"
+        "      const int m = lane + 1;\n"
         "      const int px = tc[0] - (m & 1), py = tc[1] - ((m >> 1) & 1), pz = tc[2] - ((m >> 2) & 1);\n"
-        "      const bool has = px >= 0 && py >= 0 && pz >= 0;\n"
-        "      s_pred[tid] = has ? (pz * A.nt[1] + py) * A.nt[0] + px : -1;\n"
-        "      s_have[tid] = has ? 0 : 0x7fffffff;\n"
+        "      if (px >= 0 && py >= 0 && pz >= 0) {\n"
+        "        pred = (pz * A.nt[1] + py) * A.nt[0] + px;\n"
+        "        have = 0;\n"
+        "      }\n"
         "    }\n"
-        "    if (tid == 0) nxt = atomicAdd(A.ticket, 1);\n"
-        "    __syncthreads();\n"
+        "    if (lane == 0) nxt = atomicAdd(A.ticket, 1);\n"
+        "    for (int l = 0; l < A.ahead && l < NL; ++l) tw_prefetch<ES>(A, NL, l, tc, lane);\n"
         "    for (int l = 0; l < NL; ++l) {\n"
-        "      bool ready = true;\n"
-        "#pragma unroll\n"
-        "      for (int d = 0; d < ND; ++d) ready = ready && (int)s_need[d * NL + l] <= s_have[d];\n"
-        "      if (!ready) {\n"
-        "        if (tid < ND) {\n"
-        "          const int want = s_need[tid * NL + l];\n"
-        "          if (s_have[tid] < want) {\n"
-        "            const int* pp = A.prog + s_pred[tid];\n"
-        "            int v = ld_relaxed(pp);\n"
-        "            unsigned spins = 0;\n"
-        "            unsigned long long t0 = 0;\n"
-        "            while (v < want) {\n"
-        "              if ((++spins & 63u) == 0) {\n"
-        "                if (t0 == 0) {\n"
-        "                  t0 = now_ns();\n"
-        "                } else if (*(volatile int*)A.err || (long long)(now_ns() - t0) > A.timeout_ns) {\n"
-        "                  atomicCAS(A.err, 0, 1);\n"
-        "                  s_stop = 1;\n"
-        "                  break;\n"
-        "                }\n"
+        "      if (l + A.ahead < NL) tw_prefetch<ES>(A, NL, l + A.ahead, tc, lane);\n"
+        "      // may loop l of this tile run?\n"
+        "      bool ok = true;\n"
+        "      if (lane < ND) {\n"
+        "        const int want = s_need[lane * NL + l];\n"
+        "        if (have < want) {\n"
+        "          const int* pp = A.prog + pred;\n"
+        "          int v = ld_relaxed(pp);\n"
+        "          unsigned spins = 0;\n"
+        "          unsigned long long t0 = 0;\n"
+        "          while (v < want) {\n"
+        "            if ((++spins & 63u) == 0) {\n"
+        "              if (t0 == 0) {\n"
+        "                t0 = now_ns();\n"
+        "              } else if (*(volatile int*)A.err || (long long)(now_ns() - t0) > A.timeout_ns) {\n"
+        "                ok = false;\n"
+        "                break;\n"
         "              }\n"
-        "              v = ld_relaxed(pp);\n"
         "            }\n"
-        "            fence_acq_rel();\n"
-        "            s_have[tid] = v;\n"
+        "            v = ld_relaxed(pp);\n"
         "          }\n"
+        "          fence_acq_rel();  // what the predecessor wrote is visible to the compute warps after the barrier\n"
+        "          have = v;\n"
         "        }\n"
-        "        __syncthreads();\n"
-        "        if (s_stop) return;\n"
         "      }\n"
-        "      const int* rx = A.rng + A.roff[0] + 2 * (tc[0] * NL + l);\n"
-        "      const int* ry = A.rng + A.roff[1] + 2 * (tc[1] * NL + l);\n"
-        "      const int* rz = A.rng + A.roff[2] + 2 * (tc[2] * NL + l);\n"
-        "      const int x0 = rx[0], x1 = rx[1], y0 = ry[0], y1 = ry[1], z0 = rz[0], z1 = rz[1];\n"
-        "      const bool live = x1 > x0 && y1 > y0 && z1 > z0;\n"
-        "      switch (l) {\n";
-  for (int i = 0; i < count; ++i) {
-    // a loop with reductions always writes its tile's partials (the identity when its box is empty)
-    if (loops[i].nreds)
-      os << "        case " << i << ": tb" << i << "(A.loops + " << i
-         << ", x0, x1, y0, y1, z0, z1, A.scal, A.part, A.stride, A.row0, tile); break;\n";
-    else
-      os << "        case " << i << ": if (live) tb" << i << "(A.loops + " << i
-         << ", x0, x1, y0, y1, z0, z1, A.scal, A.part, A.stride, A.row0, tile); break;\n";
-  }
-  os << "        default: break;\n"
+        "      if (!__all_sync(0xffffffffu, ok)) {\n"
+        "        if (lane == 0) atomicCAS(A.err, 0, 1);\n"
+        "        stop = true;\n"
+        "        break;\n"
         "      }\n"
-        "      __syncthreads();\n"
-        "      if (tid == 0 && tile != A.skip_tile) st_release(A.prog + tile, l + 1);\n"
+        "      int box[6];\n"
+        "#pragma unroll\n"
+        "      for (int d = 0; d < 3; ++d) {\n"
+        "        const int* r = A.rng + A.roff[d] + 2 * (tc[d] * NL + l);\n"
+        "        box[2 * d] = r[0];\n"
+        "        box[2 * d + 1] = r[1];\n"
+        "      }\n"
+        "      const bool live = box[1] > box[0] && box[3] > box[2] && box[5] > box[4];\n"
+        "      // a loop with reductions always runs: it writes its tile's partials (the identity when empty)\n"
+        "      const int runs = live || A.loops[l].nreds;\n"
+        "      post(runs ? l : -2, tile, box);\n"
+        "      publish();\n"
+        "      prev_tile = tile;\n"
+        "      prev_l = l;\n"
         "    }\n"
-        "    if (tid == 0) s_tk = nxt;\n"
+        "    if (stop) break;\n"
+        "    // an empty step: the tile's last loop completes, then its progress is published\n"
+        "    post(-2, tile, nullptr);\n"
+        "    publish();\n"
+        "    prev_tile = -1;\n"
+        "    tk = __shfl_sync(0xffffffffu, nxt, 0);\n"
+        "    if (*(volatile int*)A.err) stop = true;\n"
         "  }\n"
+        "  post(-1, -1, nullptr);\n"
+        "  publish();\n"
         "}\n";
   return os.str();
 }
@@ -1416,6 +1534,16 @@ int jit_tile_pts(int es) {
   return es == 4 ? v32 : v64;
 }
 
+int jit_tile_prefetch() {
+  static const int v = env_int("OPSTILE_TW_PREFETCH", 1, 0, 2);
+  return v;
+}
+
+int jit_tile_ahead() {
+  static const int v = env_int("OPSTILE_TW_AHEAD", 3, 0, 64);
+  return v;
+}
+
 struct JitTile {
   CUfunction f = nullptr;
 };
@@ -1475,15 +1603,15 @@ int jit_compile_tilewave_only(const DLoop* loops, int count, const std::vector<s
 int jit_tilewave_max_grid(JitTile* t, int num_sms) {
   std::lock_guard<std::mutex> lk(g_mu);
   int per_sm = 0;
-  if (g_api.occupancy(&per_sm, t->f, jit_tile_threads(), 0) != CUDA_SUCCESS) return 0;
+  if (g_api.occupancy(&per_sm, t->f, jit_tile_threads() + 32, 0) != CUDA_SUCCESS) return 0;
   return per_sm * num_sms;
 }
 
 cudaError_t jit_launch_tilewave(const JitTile* t, const TwArgs& args, cudaStream_t stream, int grid) {
   TwArgs a = args;
   void* params[] = {&a};
-  return to_cuda(g_api.launch(t->f, (unsigned)grid, 1, 1, (unsigned)jit_tile_threads(), 1, 1, 0, (CUstream)stream,
-                              params, nullptr));
+  return to_cuda(g_api.launch(t->f, (unsigned)grid, 1, 1, (unsigned)(jit_tile_threads() + 32), 1, 1, 0,
+                              (CUstream)stream, params, nullptr));
 }
 
 }  // namespace opstile

@@ -11,6 +11,7 @@
 // library holds until the process exits.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -68,6 +69,35 @@ cudaError_t scratch_for_current_device(unsigned char** out, int* num_sms) {
 }
 
 bool reg_ok(int r) { return r >= 0 && r < kNReg; }
+
+// What one call stages into the scratch array: it travels as a kernel
+// parameter (copied when the launch is issued), so no host buffer has to
+// outlive the call and no host-to-device copy is queued.
+struct Staged {
+  DLoop L;
+  double scal[64];
+  FoldRow rows[8];
+};
+static_assert(sizeof(Staged) <= 32000, "kernel parameters are limited to 32 KB");
+static_assert(kOffScal >= sizeof(DLoop) && kOffRows == kOffScal + sizeof(double) * 64, "scratch layout");
+
+__global__ void k_stage(const Staged in, unsigned char* S) {
+  const int n0 = (int)(sizeof(DLoop) / sizeof(int)), n1 = 64, n2 = (int)(sizeof(FoldRow) * 8 / sizeof(int));
+  const int* L = (const int*)&in.L;
+  const int* R = (const int*)in.rows;
+  for (int i = threadIdx.x; i < n0; i += blockDim.x) ((int*)(S + kOffLoop))[i] = L[i];
+  for (int i = threadIdx.x; i < n1; i += blockDim.x) ((double*)(S + kOffScal))[i] = in.scal[i];
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) ((int*)(S + kOffRows))[i] = R[i];
+  if (threadIdx.x == 0) *(int*)(S + kOffErr) = 0;
+}
+
+// bytes [first, last) a view's allocation box spans
+void view_span(const ops_dat_view& V, uintptr_t* first, uintptr_t* last) {
+  const int64_t lo = (int64_t)V.lo[0] + (int64_t)V.lo[1] * V.pitch + (int64_t)V.lo[2] * V.plane;
+  const int64_t hi = (int64_t)(V.hi[0] - 1) + (int64_t)(V.hi[1] - 1) * V.pitch + (int64_t)(V.hi[2] - 1) * V.plane;
+  *first = (uintptr_t)(V.ptr0 + lo);
+  *last = (uintptr_t)(V.ptr0 + hi + 1);
+}
 }  // namespace
 
 }  // namespace opstile
@@ -110,6 +140,11 @@ extern "C" int ops_loop_noalloc(int dims, const int* range, int nargs, const ops
       if (np < 1) return OPS_ERR_INVALID_ARG;
       if (a.access < OPS_READ || a.access > OPS_INC) return OPS_ERR_INVALID_ARG;
       const ops_dat_view& V = views[i];
+      // a view's rows (and planes) must not overlap one another
+      for (int d = 0; d < 3; ++d)
+        if (V.hi[d] <= V.lo[d] || (d >= dims && (V.lo[d] != 0 || V.hi[d] != 1))) return OPS_ERR_INVALID_ARG;
+      if (V.pitch < V.hi[0] - V.lo[0] || (dims > 2 && V.plane < V.pitch * (V.hi[1] - V.lo[1])))
+        return OPS_ERR_INVALID_ARG;
       A.ptr0 = V.ptr0;
       A.pitch = V.pitch;
       A.plane = V.plane;
@@ -156,6 +191,18 @@ extern "C" int ops_loop_noalloc(int dims, const int* range, int nargs, const ops
   }
   L.nreds = nreds;
   L.part_row = 0;
+  // as in ops_par_loop, a loop's dats are distinct: two views whose memory
+  // overlaps, one of them written, would make the result depend on the
+  // order of the points
+  for (int i = 0; i < nargs; ++i)
+    for (int j = i + 1; j < nargs; ++j) {
+      if (args[i].kind != OPS_ARG_DAT || args[j].kind != OPS_ARG_DAT) continue;
+      if (args[i].access == OPS_READ && args[j].access == OPS_READ) continue;
+      uintptr_t a0, a1, b0, b1;
+      view_span(views[i], &a0, &a1);
+      view_span(views[j], &b0, &b1);
+      if (a0 < b1 && b0 < a1) return OPS_ERR_INVALID_ARG;
+    }
   // ---- IR well-formedness (same rules as ops_par_loop) ----
   std::memcpy(L.ins, code, sizeof(int32_t) * 6 * (size_t)nins);
   if (nconsts) std::memcpy(L.K, consts, sizeof(double) * (size_t)nconsts);
@@ -215,12 +262,12 @@ extern "C" int ops_loop_noalloc(int dims, const int* range, int nargs, const ops
   int grid = empty ? 1 : untiled_grid(env, box);
   if (grid > kNoallocMaxGrid) grid = kNoallocMaxGrid;
   // ---- stage descriptor, slots, rows and a cleared error word ----
-  int zero = 0;
-  if (cudaMemcpyAsync(S + kOffLoop, &L, sizeof L, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(S + kOffScal, scal, sizeof scal, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(S + kOffRows, rows, sizeof rows, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(S + kOffErr, &zero, sizeof zero, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return OPS_ERR_CUDA;
+  Staged in;
+  std::memcpy(&in.L, &L, sizeof L);
+  std::memcpy(in.scal, scal, sizeof scal);
+  std::memcpy(in.rows, rows, sizeof rows);
+  k_stage<<<1, 256, 0, st>>>(in, S);
+  if (cudaGetLastError() != cudaSuccess) return OPS_ERR_CUDA;
   if (!empty) {
     if (launch_untiled(env, (const DLoop*)(S + kOffLoop), box, grid) != cudaSuccess) return OPS_ERR_CUDA;
     if (nreds && launch_fold(env, 0, nreds, grid) != cudaSuccess) return OPS_ERR_CUDA;

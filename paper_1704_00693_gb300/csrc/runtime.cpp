@@ -75,7 +75,7 @@ struct CachedPlan {
   TileWavePlan tw;
   void* d_tw = nullptr;
   size_t tw_bytes = 0;
-  size_t tw_order = 0, tw_cls = 0, tw_need = 0;  // byte offsets inside d_tw
+  size_t tw_order = 0, tw_cls = 0, tw_need = 0, tw_pf = 0;  // byte offsets inside d_tw
   int tw_roff[3] = {0, 0, 0}, tw_coff[3] = {0, 0, 0};
   int* d_twprog = nullptr;
   int tw_ntiles = 0;
@@ -1223,12 +1223,30 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
     np->tw_coff[d] = (int)cls.size();
     cls.insert(cls.end(), W.cls[d].begin(), W.cls[d].end());
   }
+  // L2 prefetch masks per loop: its reading arguments whose dat no earlier
+  // loop of the segment touched (mode 1), or all its reading arguments (2)
+  std::vector<unsigned char> pf(count, 0);
+  {
+    const int pmode = jit_tile_prefetch();
+    std::vector<char> seen(c->dats.size(), 0);
+    for (int l = 0; l < count; ++l) {
+      const QLoop& q = c->queue[first + l];
+      for (size_t a = 0; a < q.args.size(); ++a) {
+        const ops_arg& g = q.args[a];
+        if (g.kind != OPS_ARG_DAT) continue;
+        if (g.access != OPS_WRITE && (pmode == 2 || (pmode == 1 && !seen[g.handle]))) pf[l] |= (unsigned char)(1u << a);
+      }
+      for (const ops_arg& g : q.args)
+        if (g.kind == OPS_ARG_DAT) seen[g.handle] = 1;
+    }
+  }
   const size_t b_rng = sizeof(int) * rng.size(), b_order = sizeof(int) * W.order.size(),
-               b_cls = sizeof(int) * cls.size(), b_need = sizeof(uint16_t) * W.need.size();
+               b_cls = sizeof(int) * cls.size(), b_need = sizeof(uint16_t) * W.need.size(), b_pf = pf.size();
   np->tw_order = (b_rng + 15) / 16 * 16;
   np->tw_cls = np->tw_order + (b_order + 15) / 16 * 16;
   np->tw_need = np->tw_cls + (b_cls + 15) / 16 * 16;
-  np->tw_bytes = np->tw_need + b_need + 16;
+  np->tw_pf = np->tw_need + (b_need + 15) / 16 * 16;
+  np->tw_bytes = np->tw_pf + b_pf + 16;
   np->tw_ntiles = ntiles;
   int rows = 0;
   {
@@ -1251,6 +1269,7 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
   CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_order, W.order.data(), b_order, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_cls, cls.data(), b_cls, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_need, W.need.data(), b_need, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_pf, pf.data(), b_pf, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host tables are temporaries
   *out = np.get();
   c->plans[key] = std::move(np);
@@ -1326,6 +1345,8 @@ int run_tilewave(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop
   a.stride = cp->tw_ntiles;
   a.row0 = row0 < 0 ? 0 : row0;
   a.skip_tile = env.skip_block;
+  a.pf = (const unsigned char*)(d + cp->tw_pf);
+  a.ahead = jit_tile_ahead();
   CUDA_TRY(c, jit_launch_tilewave(t, a, c->stream, grid));
   ++c->stats.launches;
   ++c->stats.kernel_launches;

@@ -343,3 +343,38 @@ def test_generated_wavefront_kernel_compiles(lib, name, fp32):
     assert ("fp32" in src) == fp32
     ops.ops_queue_clear(ctx)
     ops.ops_finalize(ctx)
+
+
+def test_noalloc_rejects_overlapping_views_and_short_pitches(lib):
+    """ops_loop_noalloc checks its views on the host before any device work
+    (so fake device addresses do here): two views of overlapping memory
+    with one of them written, and a pitch shorter than the view's rows, are
+    OPS_ERR_INVALID_ARG; overlapping views that are only read are allowed
+    up to the first device call."""
+    from synth.program import BodyBuilder, DAT, READ, WRITE
+    n = 16
+
+    def view(addr, pitch=n + 2):
+        v = ops.ops_dat_view()
+        v.ptr0 = addr
+        v.pitch, v.plane = pitch, pitch * (n + 2)
+        v.lo[:] = [-1, -1, 0]
+        v.hi[:] = [n + 1, n + 1, 1]
+        return v
+
+    code, K = BodyBuilder().wsum(0, 0, [0.2] * 5).st(1, 0).build()
+    s5 = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0)]
+    base = 1 << 20
+    rng = ((0, n), (0, n))
+    with pytest.raises(ops.OpsError) as e:  # the same memory read through a stencil and written
+        ops.ops_loop_noalloc(2, rng, [(DAT, READ), (DAT, WRITE)], [view(base), view(base)], [s5, [(0, 0, 0)]],
+                             code, K)
+    assert e.value.code == ops.OPS_ERR_INVALID_ARG
+    with pytest.raises(ops.OpsError) as e:  # overlapping by one row
+        ops.ops_loop_noalloc(2, rng, [(DAT, READ), (DAT, WRITE)],
+                             [view(base), view(base + 8 * (n + 2) * (n + 1))], [s5, [(0, 0, 0)]], code, K)
+    assert e.value.code == ops.OPS_ERR_INVALID_ARG
+    with pytest.raises(ops.OpsError) as e:  # rows shorter than the view's x extent
+        ops.ops_loop_noalloc(2, rng, [(DAT, READ), (DAT, WRITE)],
+                             [view(base, pitch=n), view(base + (1 << 20))], [s5, [(0, 0, 0)]], code, K)
+    assert e.value.code == ops.OPS_ERR_INVALID_ARG
