@@ -336,7 +336,7 @@ def bench_serving(nreq=512, seq_sample=None, tol=1e-8, budget=48 << 30):
     # solve at a time, with CG written as a loop chain run untiled (three
     # loops per iteration, both reductions read by the host, Sec. 4.A);
     # compiled code and contexts per grid size are set up before the clock.
-    from paper_1704_00693_gb300.cgchain import ChainCG
+    from cg_loopchain import ChainCG
     sizes = sorted({n for _, n, _ in reqs})
     chains = {n: ChainCG(n, mode="untiled") for n in sizes}
     try:
@@ -435,7 +435,7 @@ def bench_cg(n=4000, tol=1e-10):
     finally:
         ops.ops_finalize(ctx)
     # the same solve as a loop chain (three loops per iteration, host-read reductions)
-    from paper_1704_00693_gb300.cgchain import ChainCG
+    from cg_loopchain import ChainCG
     cg = ChainCG(n, mode="untiled")
     try:
         cg.solve(kappa, b, tol, maxit=2)  # compiled code and plans

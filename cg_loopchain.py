@@ -11,10 +11,13 @@ every CG iteration is three loops,
     p = r + b p
 
 where the host reads both reductions (the flush points of Sec. 4.A) to form
-a and b and to test convergence.  All arithmetic is FP64.  This is the plain
-OPS-style solver the batched engine (ops_cg_solve_batch) and the served
-solves are measured against; run with mode "untiled" it is one kernel per
-loop.
+a and b and to test convergence, and hands them to the loops as
+device-resident scalars (ops_decl_scalar / ops_scalar_set).  All arithmetic
+is FP64.  This is the application code of the plain OPS-style solver that
+the batched engine (ops_cg_solve_batch) and the served solves are measured
+against; run with mode "untiled" it is one kernel per loop.  It sits beside
+the benchmark, outside the library package: the library only runs the loops
+it is given.
 """
 from __future__ import annotations
 
@@ -23,11 +26,12 @@ from typing import Optional, Tuple
 
 import numpy as np
 
-from . import (OPS_ARG_DAT, OPS_ARG_RED, MODES, OPS_READ, OPS_RED_SUM, OPS_RW, OPS_WRITE,
-               OPS_IR_ADD, OPS_IR_CST, OPS_IR_DIV, OPS_IR_FMA, OPS_IR_LD, OPS_IR_MUL, OPS_IR_RED, OPS_IR_ST,
-               OPS_IR_SUB, _check, load, ops_arg, ops_config_default, ops_dat_fetch, ops_dat_upload,
-               ops_decl_block, ops_decl_dat, ops_decl_reduction, ops_decl_stencil, ops_finalize, ops_init,
-               ops_reduction_result)
+from paper_1704_00693_gb300 import (OPS_ARG_DAT, OPS_ARG_RED, OPS_ARG_SCALAR, MODES, OPS_READ, OPS_RED_SUM, OPS_RW,
+                                    OPS_WRITE, OPS_IR_ADD, OPS_IR_CST, OPS_IR_DIV, OPS_IR_FMA, OPS_IR_LD, OPS_IR_MUL,
+                                    OPS_IR_RED, OPS_IR_ST, OPS_IR_SUB, _check, load, ops_arg, ops_config_default,
+                                    ops_dat_fetch, ops_dat_upload, ops_decl_block, ops_decl_dat, ops_decl_reduction,
+                                    ops_decl_scalar, ops_decl_stencil, ops_finalize, ops_init, ops_reduction_result,
+                                    ops_scalar_set)
 
 
 def _ins(*rows):
@@ -62,6 +66,10 @@ class ChainCG:
         self.s = {k: ops_decl_stencil(ctx, 2, v) for k, v in st.items()}
         self.pw = ops_decl_reduction(ctx, OPS_RED_SUM)
         self.rr = ops_decl_reduction(ctx, OPS_RED_SUM)
+        # the step lengths a, -a and b live on the device; the loops read them as SCALAR arguments
+        self.sa = ops_decl_scalar(ctx, 0.0)
+        self.sna = ops_decl_scalar(ctx, 0.0)
+        self.sb = ops_decl_scalar(ctx, 0.0)
         self.blk = blk
         self._ext = (n + 2, n + 2)
         self._host = np.zeros(self._ext, dtype=np.float64)
@@ -84,7 +92,7 @@ class ChainCG:
 
     def _build_loops(self):
         n, d, s = self.n, self.d, self.s
-        D, RD = OPS_ARG_DAT, OPS_ARG_RED
+        D, RD, SC = OPS_ARG_DAT, OPS_ARG_RED, OPS_ARG_SCALAR
         LD, CST, ADD, SUB, MUL, DIV, FMA, ST, RED = (OPS_IR_LD, OPS_IR_CST, OPS_IR_ADD, OPS_IR_SUB, OPS_IR_MUL,
                                                      OPS_IR_DIV, OPS_IR_FMA, OPS_IR_ST, OPS_IR_RED)
         cells = ((0, n), (0, n))
@@ -128,17 +136,18 @@ class ChainCG:
                  (LD, 0, 3, 0), (LD, 1, 0, 3), (FMA, 2, 0, 1, 2),
                  (LD, 0, 3, 1), (LD, 1, 0, 4), (FMA, 2, 0, 1, 2),
                  (ST, 4, 2), (LD, 1, 0, 0), (MUL, 3, 1, 2), (RED, 5, 3)), [0.0])
-        # x += a p; r -= a w; r.r   (K0 = a, K1 = -a)
+        # x += a p; r -= a w; r.r   (scalars a and -a)
         self.update = self._loop(
             cells, [(D, d["p"], s["P"], OPS_READ), (D, d["w"], s["P"], OPS_READ), (D, d["x"], s["P"], OPS_RW),
-                    (D, d["r"], s["P"], OPS_RW), (RD, self.rr, -1, OPS_READ)],
-            _ins((CST, 0, 0), (LD, 1, 0, 0), (LD, 2, 2, 0), (FMA, 3, 0, 1, 2), (ST, 2, 3),
-                 (CST, 0, 1), (LD, 1, 1, 0), (LD, 2, 3, 0), (FMA, 3, 0, 1, 2), (ST, 3, 3),
-                 (MUL, 4, 3, 3), (RED, 4, 4)), [0.0, 0.0])
-        # p = r + b p   (K0 = b)
+                    (D, d["r"], s["P"], OPS_RW), (RD, self.rr, -1, OPS_READ), (SC, self.sa, -1, OPS_READ),
+                    (SC, self.sna, -1, OPS_READ)],
+            _ins((LD, 0, 5, 0), (LD, 1, 0, 0), (LD, 2, 2, 0), (FMA, 3, 0, 1, 2), (ST, 2, 3),
+                 (LD, 0, 6, 0), (LD, 1, 1, 0), (LD, 2, 3, 0), (FMA, 3, 0, 1, 2), (ST, 3, 3),
+                 (MUL, 4, 3, 3), (RED, 4, 4)), [0.0])
+        # p = r + b p   (scalar b)
         self.direction = self._loop(
-            cells, [(D, d["r"], s["P"], OPS_READ), (D, d["p"], s["P"], OPS_RW)],
-            _ins((CST, 0, 0), (LD, 1, 1, 0), (LD, 2, 0, 0), (FMA, 3, 0, 1, 2), (ST, 1, 3)), [0.0])
+            cells, [(D, d["r"], s["P"], OPS_READ), (D, d["p"], s["P"], OPS_RW), (SC, self.sb, -1, OPS_READ)],
+            _ins((LD, 0, 2, 0), (LD, 1, 1, 0), (LD, 2, 0, 0), (FMA, 3, 0, 1, 2), (ST, 1, 3)), [0.0])
 
     def _enqueue(self, loop):
         rc = load().ops_par_loop(self.ctx, *loop[4])
@@ -172,14 +181,15 @@ class ChainCG:
             self._enqueue(self.matvec)
             pw = self._red(self.pw)
             a = rr / pw
-            self.update[3][0], self.update[3][1] = a, -a
+            ops_scalar_set(self.ctx, self.sa, a)
+            ops_scalar_set(self.ctx, self.sna, -a)
             self._enqueue(self.update)
             rr_new = self._red(self.rr)
             it += 1
             relres = float(np.sqrt(rr_new)) / nb
             if relres <= tol:
                 break
-            self.direction[3][0] = rr_new / rr
+            ops_scalar_set(self.ctx, self.sb, rr_new / rr)
             self._enqueue(self.direction)
             rr = rr_new
         x = ops_dat_fetch(self.ctx, self.d["x"]).reshape(n + 2, n + 2)[1:n + 1, 1:n + 1].copy()

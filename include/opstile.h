@@ -96,7 +96,7 @@ extern "C" {
 
 /* ---- argument kinds, access modes, reduction operators ---- */
 #define OPS_ARG_DAT 0    /* a dat accessed through a stencil */
-#define OPS_ARG_SCALAR 1 /* read the current value of a reduction handle */
+#define OPS_ARG_SCALAR 1 /* read the current value of a reduction or scalar handle */
 #define OPS_ARG_RED 2    /* contribute to a reduction handle */
 #define OPS_READ 0
 #define OPS_WRITE 1
@@ -198,6 +198,16 @@ int ops_decl_stencil(ops_ctx ctx, int dims, int npts, const int* offsets, const 
  * the operator's identity, accumulates the contributions of every loop that
  * reduces into it, and is read (and reset) by ops_reduction_result. */
 int ops_decl_reduction(ops_ctx ctx, int op, int* out);
+
+/* A device-resident scalar (OPS's global constants; a CG coefficient):
+ * SCALAR arguments read its value, which stays on the device.  It starts
+ * at init; ops_scalar_set changes it after every loop queued before the
+ * call (those read the old value), ops_scalar_get flushes and reads it.
+ * Scalars and reductions share one handle space; a scalar cannot be the
+ * target of a RED argument, nor be read by ops_reduction_result. */
+int ops_decl_scalar(ops_ctx ctx, double init, int* out);
+int ops_scalar_set(ops_ctx ctx, int scalar, double value);
+int ops_scalar_get(ops_ctx ctx, int scalar, double* host_out);
 
 /* ---- parallel loops (Sec. 3, Sec. 4.A) ---- */
 typedef struct {
@@ -301,15 +311,18 @@ int ops_plan_wavefront(ops_ctx ctx, const int* tile, int64_t* counts, int* out_p
 /* Build the tile-wavefront plan (OPS_MODE_TILEWAVE) of the currently queued
  * loops for the given tile sizes (all >= 1), without executing them.
  * OPS_ERR_INVALID_ARG, with the reason in ops_last_error, when the tiles are
- * smaller than the chain's skew.  counts[0..3] receive the number of tiles,
+ * smaller than the chain's skew.  counts[0..4] receive the number of tiles,
  * of tile classes, of predecessor directions (2^dims - 1; direction k steps
- * back one tile in dimension d when bit d of k + 1 is set) and of loops.
- * Optional outputs (NULL to skip): out_need (classes x directions x loops
- * ints): the loops of each predecessor tile that must be complete before a
- * tile of that class runs each loop; out_class (tiles ints, x fastest): the
- * class of each tile; out_order (tiles ints): the tile of each ticket. */
+ * back one tile in dimension d when bit d of k + 1 is set), of loops and of
+ * steps (runs of consecutive loops a CTA runs without a barrier between
+ * them).  Optional outputs (NULL to skip): out_need (classes x directions x
+ * loops ints): the loops of each predecessor tile that must be complete
+ * before a tile of that class runs each loop; out_class (tiles ints, x
+ * fastest): the class of each tile; out_order (tiles ints): the tile of
+ * each ticket; out_steps (loops + 1 ints): the first loop of each step,
+ * then the number of loops. */
 int ops_plan_tilewave(ops_ctx ctx, const int* tile, int64_t* counts, int* out_need, int64_t need_cap, int* out_class,
-                      int* out_order, int64_t tile_cap);
+                      int* out_order, int64_t tile_cap, int* out_steps);
 /* Generate the CUDA source of the compiled loop bodies for the currently
  * queued loops (as one segment) and compile it for sm_103a with NVRTC,
  * without loading it: no device is needed.  src_out (cap bytes, may be NULL)
@@ -379,7 +392,9 @@ int ops_cg_solve_batch(ops_ctx ctx, int count, const int* n, const double* const
  * iterations at a time in one batch, and retires finished ones, so requests
  * arriving while others run join the batch as memory frees up.  Each
  * request's result is the same alone and in any mix (see ops_cg_solve_batch).
- * The serving loop itself makes no device allocation. */
+ * The pool and the batch's device tables are allocated by ops_serve_open;
+ * the serving loop itself makes no device allocation, and the captured
+ * graph of a batch iteration is replayed whatever requests come and go. */
 typedef struct ops_server_s* ops_server;
 typedef struct {
   int device;
@@ -397,14 +412,43 @@ typedef struct {
   double submit_ms, done_ms;  /* host steady-clock stamps (ms) */
 } ops_solve_stats;
 int ops_serve_open(ops_server* out, const ops_serve_config* cfg);
-/* Queue a solve (arrays of n*n doubles are copied); *id identifies it.
- * OPS_ERR_NOMEM if it could never fit the pool. */
-int ops_serve_submit(ops_server srv, int n, const double* host_kappa, const double* host_rhs, uint64_t* id);
+/* Queue a solve (arrays of n*n doubles are copied) to relative residual
+ * tol in precision OPS_PREC_FP64 or OPS_PREC_MIXED (tol <= 0 or precision
+ * < 0: the server's params); *id identifies it.  OPS_ERR_NOMEM if it could
+ * never fit the pool. */
+int ops_serve_submit(ops_server srv, int n, const double* host_kappa, const double* host_rhs, double tol, int precision,
+                     uint64_t* id);
 /* OPS_OK and x (n*n doubles) + stats once the solve is done (the request is
  * then forgotten); OPS_ERR_STATE while pending (wait = 0); wait = 1 blocks. */
 int ops_serve_poll(ops_server srv, uint64_t id, int wait, double* host_x, ops_solve_stats* stats);
 /* Finish running solves, drop queued ones, free the pool and the context. */
 int ops_serve_close(ops_server srv);
+
+/* ---- hardware probes behind the reported roofline ----
+ * The paper sets its roofline from STREAM, the L3 bandwidth and DGEMM on
+ * its CPUs (Sec. 6); these are the GB300 counterparts the bench needs:
+ * the FP64 and FP32 arithmetic rates (every SM busy, independent chains),
+ * the read bandwidth of a buffer resident in L2, the copy bandwidth of
+ * HBM, and the cost of the two synchronisations the tiled schedules use (a
+ * grid-wide barrier with one CTA per SM; a release store answered through
+ * another CTA's acquire poll).  ops_probe_device runs them on `device`
+ * (allocating about 2 GiB for a moment) and fills *out; OPS_ERR_TIMEOUT if
+ * a synchronisation probe's bounded wait ran out, OPS_ERR_CUDA or
+ * OPS_ERR_NO_DEVICE otherwise on failure. */
+typedef struct {
+  double fp64_fma_tflops;   /* 2 flops per DFMA */
+  double fp64_add_tops;     /* DADD per second / 1e12 */
+  double fp32_fma_tflops;   /* 2 flops per FFMA */
+  double l2_read_gbs;       /* reads of a buffer of a third of L2 */
+  double hbm_copy_gbs;      /* read + write bytes of 1 GiB copies */
+  double grid_barrier_us;   /* one grid-wide barrier */
+  double flag_roundtrip_us; /* release store -> acquire poll -> answer -> acquire poll */
+  int64_t l2_bytes;
+  int64_t persisting_l2_max_bytes;  /* cudaDevAttrMaxPersistingL2CacheSize */
+  int num_sms;
+  int sm_clock_khz_max;
+} ops_probe_result;
+int ops_probe_device(int device, ops_probe_result* out);
 
 /* ---- one loop without any device allocation ----
  * The paper has no counterpart: this is a service for callers that must not

@@ -166,6 +166,22 @@ def ops_decl_reduction(ctx, op: int) -> int:
 
 
 # -------------------------------------------------------------------- loops
+def ops_decl_scalar(ctx, init: float = 0.0) -> int:
+    out = C.c_int()
+    _check(ctx, load().ops_decl_scalar(ctx, C.c_double(init), C.byref(out)))
+    return out.value
+
+
+def ops_scalar_set(ctx, h: int, value: float):
+    _check(ctx, load().ops_scalar_set(ctx, C.c_int(h), C.c_double(value)))
+
+
+def ops_scalar_get(ctx, h: int) -> float:
+    v = C.c_double()
+    _check(ctx, load().ops_scalar_get(ctx, C.c_int(h), C.byref(v)))
+    return v.value
+
+
 def ops_par_loop(ctx, block: int, dims: int, rng, args, code, consts, name: str = ""):
     r = np.zeros(6, dtype=np.int32)
     for d in range(dims):
@@ -297,20 +313,24 @@ def ops_plan_wavefront(ctx, tile):
 
 def ops_plan_tilewave(ctx, tile):
     """Tile-wavefront plan of the queued loops for the given tile sizes:
-    (need, tile_class, order), need an int32 array [classes, directions,
-    loops], tile_class the class of each tile (x fastest) and order the tile
-    of each ticket."""
-    counts = (C.c_int64 * 4)()
+    (need, tile_class, order, steps), need an int32 array [classes,
+    directions, loops], tile_class the class of each tile (x fastest), order
+    the tile of each ticket and steps the first loop of each step of a tile
+    followed by the number of loops."""
+    counts = (C.c_int64 * 5)()
     t = _i3(list(tile) + [1] * (3 - len(tile)))
-    _check(ctx, load().ops_plan_tilewave(ctx, t, counts, None, C.c_int64(0), None, None, C.c_int64(0)))
-    ntiles, ncl, ndirs, nloops = (int(v) for v in counts)
+    _check(ctx, load().ops_plan_tilewave(ctx, t, counts, None, C.c_int64(0), None, None, C.c_int64(0), None))
+    ntiles, ncl, ndirs, nloops, nsteps = (int(v) for v in counts)
     need = np.zeros(max(1, ncl * ndirs * nloops), dtype=np.int32)
     cls = np.zeros(max(1, ntiles), dtype=np.int32)
     order = np.zeros(max(1, ntiles), dtype=np.int32)
+    steps = np.zeros(nsteps + 1, dtype=np.int32)
     ip = C.POINTER(C.c_int)
     _check(ctx, load().ops_plan_tilewave(ctx, t, counts, need.ctypes.data_as(ip), C.c_int64(need.size),
-                                         cls.ctypes.data_as(ip), order.ctypes.data_as(ip), C.c_int64(ntiles)))
-    return need[:ncl * ndirs * nloops].reshape(ncl, ndirs, nloops).copy(), cls[:ntiles].copy(), order[:ntiles].copy()
+                                         cls.ctypes.data_as(ip), order.ctypes.data_as(ip), C.c_int64(ntiles),
+                                         steps.ctypes.data_as(ip)))
+    return (need[:ncl * ndirs * nloops].reshape(ncl, ndirs, nloops).copy(), cls[:ntiles].copy(), order[:ntiles].copy(),
+            steps)
 
 
 def ops_compile_queued(ctx, want_source: bool = False, wavefront: bool = False, tilewave: bool = False):
@@ -329,6 +349,26 @@ def ops_compile_queued(ctx, want_source: bool = False, wavefront: bool = False, 
         buf = C.create_string_buffer(n.value + 1)
     _check(ctx, f(ctx, buf, C.c_int64(n.value + 1 if buf is not None else 0), C.byref(n), C.byref(ms)))
     return (buf.value.decode() if buf is not None else None), n.value, ms.value
+
+
+# ------------------------------------------------------------ hardware probes
+class ops_probe_result(C.Structure):
+    _fields_ = [("fp64_fma_tflops", C.c_double), ("fp64_add_tops", C.c_double), ("fp32_fma_tflops", C.c_double),
+                ("l2_read_gbs", C.c_double), ("hbm_copy_gbs", C.c_double), ("grid_barrier_us", C.c_double),
+                ("flag_roundtrip_us", C.c_double), ("l2_bytes", C.c_int64), ("persisting_l2_max_bytes", C.c_int64),
+                ("num_sms", C.c_int), ("sm_clock_khz_max", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def ops_probe_device(device: int = 0) -> dict:
+    """Measured FP64/FP32 rates, L2 and HBM bandwidth and synchronisation costs of `device`."""
+    out = ops_probe_result()
+    rc = load().ops_probe_device(C.c_int(device), C.byref(out))
+    if rc != OPS_OK:
+        raise OpsError(rc, "ops_probe_device failed")
+    return out.as_dict()
 
 
 # ------------------------------------------------ one loop, no device allocation
@@ -455,13 +495,15 @@ def ops_serve_open(tol: float, precision: int, hbm_budget: int, device: int = 0,
     return srv
 
 
-def ops_serve_submit(srv, kappa: np.ndarray, rhs: np.ndarray) -> int:
+def ops_serve_submit(srv, kappa: np.ndarray, rhs: np.ndarray, tol: float = 0.0, precision: int = -1) -> int:
+    """Queue a solve; tol <= 0 / precision < 0 take the server's parameters."""
     n = kappa.shape[0]
     k = np.ascontiguousarray(kappa, dtype=np.float64)
     b = np.ascontiguousarray(rhs, dtype=np.float64)
     rid = C.c_uint64()
     P = C.POINTER(C.c_double)
-    rc = load().ops_serve_submit(srv, C.c_int(n), k.ctypes.data_as(P), b.ctypes.data_as(P), C.byref(rid))
+    rc = load().ops_serve_submit(srv, C.c_int(n), k.ctypes.data_as(P), b.ctypes.data_as(P), C.c_double(tol),
+                                 C.c_int(precision), C.byref(rid))
     if rc != OPS_OK:
         raise OpsError(rc, "ops_serve_submit failed")
     return rid.value

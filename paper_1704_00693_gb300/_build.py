@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.environ.get("OPSTILE_BUILD_DIR") or os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libopstile.so")
 
-SOURCES = ["runtime.cpp", "plan.cpp", "chain_kernels.cu", "cg.cu", "serve.cpp", "noalloc.cu", "jit.cpp"]
+SOURCES = ["runtime.cpp", "plan.cpp", "chain_kernels.cu", "cg.cu", "serve.cpp", "noalloc.cu", "jit.cpp", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

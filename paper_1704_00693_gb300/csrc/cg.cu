@@ -24,6 +24,8 @@
 //     on what else is in the batch.
 #include <cuda_runtime.h>
 
+#include <array>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -289,8 +291,9 @@ __device__ __forceinline__ void a_cg64(const CgUnit& U, const OpView<double>& A,
 }
 
 // A: FP64 residual r = b - A x and |r|^2 (OUTER, FINISH); w = A p and p.w (INNER, CG64)
-__global__ void __launch_bounds__(kCgThreads) k_cg_a(CgProb* probs, const CgUnit* units, int nunits, DD* part) {
+__global__ void __launch_bounds__(kCgThreads) k_cg_a(CgProb* probs, const CgUnit* units, const int* cnt, DD* part) {
   __shared__ double sh[32];
+  const int nunits = cnt[0];
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const CgUnit U = units[u];
     const CgProb& P = probs[U.prob];
@@ -356,8 +359,9 @@ __device__ __forceinline__ void b_cg64(const CgUnit& U, double al, const double*
 }
 
 // B: INIT (scaled residual into the FP32 inner vectors), INNER / CG64 updates
-__global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit* units, int nunits, DD* part) {
+__global__ void __launch_bounds__(kCgThreads) k_cg_b(CgProb* probs, const CgUnit* units, const int* cnt, DD* part) {
   __shared__ double sh[32];
+  const int nunits = cnt[0];
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const CgUnit U = units[u];
     const CgProb& P = probs[U.prob];
@@ -395,7 +399,8 @@ __device__ __forceinline__ void c_finish(const CgUnit& U, double nr, const float
   });
 }
 
-__global__ void __launch_bounds__(kCgThreads) k_cg_c(CgProb* probs, const CgUnit* units, int nunits) {
+__global__ void __launch_bounds__(kCgThreads) k_cg_c(CgProb* probs, const CgUnit* units, const int* cnt) {
+  const int nunits = cnt[0];
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const CgUnit U = units[u];
     const CgProb& P = probs[U.prob];
@@ -437,10 +442,10 @@ __device__ __forceinline__ double block_partial_sum(const DD* part, int u0, int 
 }
 
 // Scalars after kernel A.
-__global__ void k_cg_s1(CgProb* probs, const int2* ranges, int nslots, const DD* part) {
+__global__ void k_cg_s1(CgProb* probs, const int2* ranges, const int* cnt, const DD* part) {
   __shared__ double sh[32];
   const int p = blockIdx.x;
-  if (p >= nslots) return;
+  if (p >= cnt[1]) return;
   CgProb& P = probs[p];
   const int st = P.state;  // uniform over the block
   if (st != CG_OUTER && st != CG_FINISH && st != CG_INNER && st != CG64) return;
@@ -468,10 +473,10 @@ __global__ void k_cg_s1(CgProb* probs, const int2* ranges, int nslots, const DD*
 }
 
 // Scalars after kernel B.
-__global__ void k_cg_s2(CgProb* probs, const int2* ranges, int nslots, const DD* part) {
+__global__ void k_cg_s2(CgProb* probs, const int2* ranges, const int* cnt, const DD* part) {
   __shared__ double sh[32];
   const int p = blockIdx.x;
-  if (p >= nslots) return;
+  if (p >= cnt[1]) return;
   CgProb& P = probs[p];
   const int st = P.state;  // uniform over the block
   if (st != CG_INIT && st != CG_INNER && st != CG64_INIT && st != CG64) return;
@@ -530,6 +535,24 @@ int64_t cg_problem_bytes(int n) {
 
 CgBatch::CgBatch(cudaStream_t stream, int num_sms) : stream_(stream), num_sms_(num_sms) {}
 
+CgBatch::CgBatch(cudaStream_t stream, int num_sms, int max_slots, int max_units)
+    : stream_(stream), num_sms_(num_sms), fixed_(true) {
+  // every table at its final size, once: adding and removing problems then
+  // never allocates, and the captured tick graph stays valid
+  dprob_cap_ = std::max(1, max_slots);
+  dranges_cap_ = dprob_cap_;
+  dunits_cap_ = std::max(1, max_units);
+  dpart_cap_ = dunits_cap_;
+  if (cudaMalloc(&dprob_, sizeof(CgProb) * dprob_cap_) != cudaSuccess ||
+      cudaMalloc(&dranges_, sizeof(int2) * dranges_cap_) != cudaSuccess ||
+      cudaMalloc(&dunits_, sizeof(CgUnit) * dunits_cap_) != cudaSuccess ||
+      cudaMalloc(&dpart_, sizeof(DD) * dpart_cap_) != cudaSuccess || cudaMalloc(&dcnt_, 2 * sizeof(int)) != cudaSuccess)
+    init_error_ = cudaErrorMemoryAllocation;
+  else if (cudaMemsetAsync(dprob_, 0, sizeof(CgProb) * dprob_cap_, stream_) != cudaSuccess ||
+           cudaMemsetAsync(dcnt_, 0, 2 * sizeof(int), stream_) != cudaSuccess)
+    init_error_ = cudaErrorUnknown;
+}
+
 CgBatch::~CgBatch() {
   cudaStreamSynchronize(stream_);
   if (gexec_) cudaGraphExecDestroy(gexec_);
@@ -537,6 +560,14 @@ CgBatch::~CgBatch() {
   cudaFree(dunits_);
   cudaFree(dranges_);
   cudaFree(dpart_);
+  cudaFree(dcnt_);
+}
+
+int cg_unit_count(int n) {
+  const int pts = cg_unit_pts();
+  if (n > pts) return n * ((n + pts - 1) / pts);
+  const int nr = std::max(1, pts / n);
+  return (n + nr - 1) / nr;
 }
 
 // Units of whole rows holding about cg_unit_pts() cells (rows wider than
@@ -622,6 +653,17 @@ cudaError_t CgBatch::rebuild_units() {
   // the device array of problems must hold every slot; slots keep their
   // device state across rebuilds (only new problems are uploaded)
   const int nslots = (int)hprob_.size();
+  if (fixed_) {
+    if (init_error_ != cudaSuccess) return init_error_;
+    int nu = 0;
+    for (int s = 0; s < nslots; ++s)
+      if (live_[s]) nu += cg_unit_count(hprob_[s].n);
+    if (nslots > dprob_cap_ || nu > dunits_cap_) return cudaErrorMemoryAllocation;
+  }
+  if (!dcnt_) {
+    cudaError_t e = cudaMalloc(&dcnt_, 2 * sizeof(int));
+    if (e != cudaSuccess) return e;
+  }
   if (nslots > dprob_cap_) {
     CgProb* nd = nullptr;
     const int cap = std::max(nslots, 2 * dprob_cap_);
@@ -694,11 +736,14 @@ cudaError_t CgBatch::rebuild_units() {
       hstate_[s] = hprob_[s].state;
     }
   }
+  // the kernels read the unit and slot counts from the device
+  hcnt_[0] = nunits_;
+  hcnt_[1] = nslots;
+  e = cudaMemcpyAsync(dcnt_, hcnt_, 2 * sizeof(int), cudaMemcpyHostToDevice, stream_);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(stream_);  // hcnt_ is host memory the copy reads
+  if (e != cudaSuccess) return e;
   units_dirty_ = false;
-  if (gexec_) {  // the captured ticks refer to the old unit table
-    cudaGraphExecDestroy(gexec_);
-    gexec_ = nullptr;
-  }
   return cudaSuccess;
 }
 
@@ -716,20 +761,24 @@ cudaError_t CgBatch::run(int ticks) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_a, kCgThreads, 0) != cudaSuccess || per_sm < 1)
       per_sm = 4;
   }
-  const int g = std::max(1, std::min(nunits_, num_sms_ * per_sm));
-  const int gs = nslots;  // scalar kernels: one block per problem slot
-  // the tick sequence is captured once per batch composition and replayed
-  if (!gexec_ || gticks_ != ticks) {
+  // fixed tables: one wave of resident CTAs whatever the batch holds, and a
+  // scalar block per possible slot, so the graph never has to change
+  const int g = fixed_ ? num_sms_ * per_sm : std::max(1, std::min(nunits_, num_sms_ * per_sm));
+  const int gs = fixed_ ? dprob_cap_ : nslots;  // scalar kernels: one block per problem slot
+  // the tick sequence is captured once and replayed; it is captured again
+  // only when a table moved or the launch shape changed
+  const std::array<const void*, 5> args = {dprob_, dunits_, dranges_, dpart_, dcnt_};
+  if (!gexec_ || gticks_ != ticks || gargs_ != args || gg_ != g || ggs_ != gs) {
     if (gexec_) cudaGraphExecDestroy(gexec_);
     gexec_ = nullptr;
     cudaError_t e = cudaStreamBeginCapture(stream_, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     for (int t = 0; t < ticks; ++t) {
-      k_cg_a<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_, dpart_);
-      k_cg_s1<<<gs, 256, 0, stream_>>>(dprob_, ranges, nslots, dpart_);
-      k_cg_b<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_, dpart_);
-      k_cg_s2<<<gs, 256, 0, stream_>>>(dprob_, ranges, nslots, dpart_);
-      k_cg_c<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, nunits_);
+      k_cg_a<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, dcnt_, dpart_);
+      k_cg_s1<<<gs, 256, 0, stream_>>>(dprob_, ranges, dcnt_, dpart_);
+      k_cg_b<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, dcnt_, dpart_);
+      k_cg_s2<<<gs, 256, 0, stream_>>>(dprob_, ranges, dcnt_, dpart_);
+      k_cg_c<<<g, kCgThreads, 0, stream_>>>(dprob_, dunits_, dcnt_);
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(stream_, &graph);
@@ -738,6 +787,9 @@ cudaError_t CgBatch::run(int ticks) {
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return e;
     gticks_ = ticks;
+    gargs_ = args;
+    gg_ = g;
+    ggs_ = gs;
   }
   return cudaGraphLaunch(gexec_, stream_);
 }

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <vector>
 
 #include "internal.h"
@@ -44,11 +45,19 @@ struct CgUnit {
 
 // Device bytes one problem of side n needs (all arrays above, 256-byte aligned).
 int64_t cg_problem_bytes(int n);
+// Work units of one problem of side n.
+int cg_unit_count(int n);
 
 // A set of problems advanced together one CG iteration per tick.
 class CgBatch {
  public:
   CgBatch(cudaStream_t stream, int num_sms);
+  // Fixed capacity: every device table is allocated here, at its final
+  // size, so adding and removing problems never allocates and the captured
+  // tick graph is reused for every batch composition.  Problems beyond
+  // max_slots slots or max_units work units in total fail at the next run
+  // (the caller admits only what fits).
+  CgBatch(cudaStream_t stream, int num_sms, int max_slots, int max_units);
   ~CgBatch();
   // Add a problem in `slab` (cg_problem_bytes(n) device bytes, owned by the
   // caller); kappa and rhs are host arrays of n*n.  Returns the slot.
@@ -64,6 +73,7 @@ class CgBatch {
   // rounded to / widened from float); host arrays of n*n doubles.
   cudaError_t apply(int slot, int prec, const double* host_u, double* host_w);
   int live() const { return nlive_; }
+  cudaError_t init_status() const { return init_error_; }
   cudaStream_t stream() const { return stream_; }
 
  private:
@@ -85,8 +95,13 @@ class CgBatch {
   int dpart_cap_ = 0;
   bool units_dirty_ = true;
   std::vector<int> hstate_;
-  cudaGraphExec_t gexec_ = nullptr;  // captured tick sequence for the current units
-  int gticks_ = 0;
+  cudaGraphExec_t gexec_ = nullptr;  // captured tick sequence
+  int gticks_ = 0, gg_ = 0, ggs_ = 0;
+  std::array<const void*, 5> gargs_{};  // the tables the captured kernels point at
+  bool fixed_ = false;
+  cudaError_t init_error_ = cudaSuccess;
+  int* dcnt_ = nullptr;   // device: unit count, slot count
+  int hcnt_[2] = {0, 0};
 };
 
 }  // namespace opstile

@@ -66,6 +66,9 @@ const int kJitMinCtas = env_int("OPSTILE_JIT_MINB", 2, 1, 8);
 constexpr int kOvThreads = 512;
 constexpr int kOvPts = 1;
 constexpr int kJitChunk = 6;  // loops per compiled module (modules compile in parallel)
+constexpr int kTwMaxGroup = 8;  // loops of one tile-wavefront step at most
+// FP64 MIN / MAX / SGT on the integer pipe (dlt); 0 = IEEE double compares
+const int kIntCmp = env_int("OPSTILE_JIT_INTCMP", 1, 0, 1);
 
 // ---------------------------------------------------------------------------
 // entry points reached at run time
@@ -189,6 +192,20 @@ __device__ __forceinline__ unsigned long long now_ns() {
   return t;
 }
 
+// b < a for doubles, decided on the integer pipe (the FP64 pipe is the
+// narrow one on GB300): the IEEE order of non-NaN doubles is the signed
+// integer order of their bit patterns once negative ones have their
+// magnitude bits flipped, except that -0 and +0 compare equal; a NaN
+// operand makes the comparison false.
+__device__ __forceinline__ bool dlt(double b, double a) {
+  const unsigned long long m = 0x7fffffffffffffffull, inf = 0x7ff0000000000000ull;
+  const long long A = __double_as_longlong(a), B = __double_as_longlong(b);
+  const bool nan = ((unsigned long long)A & m) > inf || ((unsigned long long)B & m) > inf;
+  const bool zeros = (((unsigned long long)A | (unsigned long long)B) << 1) == 0;
+  const long long ka = A >= 0 ? A : (A ^ (long long)m), kb = B >= 0 ? B : (B ^ (long long)m);
+  return !nan && !zeros && kb < ka;
+}
+
 __device__ __forceinline__ void flush_red(int op, DD v, DD* part, int stride, int row, int assign) {
   v = block_combine(op, v, g_sh);
   if (threadIdx.x == 0) {
@@ -198,16 +215,17 @@ __device__ __forceinline__ void flush_red(int op, DD v, DD* part, int stride, in
   __syncthreads();
 }
 
-// A CTA's share of a box: rows of >= 128 points in units of NT x by P rows
-// (u = part, part + nparts, ...), thinner boxes in flattened groups of P
-// points NT apart (NT = threads per CTA).  full(x, y, z) takes rows
+// A CTA's (or a warp's) share of a box: rows of >= 128 points in units of NT
+// x by P rows (u = part, part + nparts, ...), thinner boxes in flattened
+// groups of P points NT apart (NT = threads per part: a CTA's, or 32 when
+// the parts are warps; a thread's lane in its part is threadIdx.x % NT).  full(x, y, z) takes rows
 // y .. y+P-1 at x; one(x, y, z) a single point.
 template <int P, int NT, class F1, class FP>
 __device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0, int z1, int part, int nparts,
                                           F1& one, FP& full) {
   const int nx = x1 - x0, ny = y1 - y0, nz = z1 - z0;
   if (nx <= 0 || ny <= 0 || nz <= 0) return;
-  if (nx >= 128) {
+  if (nx >= (NT >= 128 ? 128 : NT)) {
     const int xch = (nx + NT - 1) / NT;
     const int nrg = (ny + P - 1) / P;
     const int nunits = xch * nrg * nz;
@@ -215,7 +233,7 @@ __device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0
     int xc = u % xch, rg = (u / xch) % nrg, z = u / (xch * nrg);
     const int dxc = nparts % xch, drg = (nparts / xch) % nrg, dz = nparts / (xch * nrg);
     while (u < nunits) {
-      const int x = x0 + xc * NT + (int)threadIdx.x;
+      const int x = x0 + xc * NT + (int)(threadIdx.x % NT);
       if (x < x1) {
         const int yb = rg * P;
         if (yb + P <= ny) {
@@ -231,7 +249,7 @@ __device__ __forceinline__ void run_units(int x0, int x1, int y0, int y1, int z0
   } else {
     const int npts = nx * ny * nz;
     const int step = nparts * NT * P;
-    for (int i = part * NT * P + (int)threadIdx.x; i < npts; i += step) {
+    for (int i = part * NT * P + (int)(threadIdx.x % NT); i < npts; i += step) {
       for (int p = 0; p < P; ++p) {
         const int j = i + p * NT;
         if (j >= npts) break;
@@ -336,14 +354,24 @@ struct LoopGen {
           case OPS_IR_FMA:
             os << "    " << R(d) << " = " << ffma << "(" << R(a) << ", " << R(b) << ", " << R(c) << ");\n";
             break;
+          // FP64 comparisons go through dlt (integer pipe) unless OPSTILE_JIT_INTCMP=0
           case OPS_IR_MIN:
-            os << "    " << R(d) << " = (" << R(b) << " < " << R(a) << ") ? " << R(b) << " : " << R(a) << ";\n";
+            if (!f32 && kIntCmp)
+              os << "    " << R(d) << " = dlt(" << R(b) << ", " << R(a) << ") ? " << R(b) << " : " << R(a) << ";\n";
+            else
+              os << "    " << R(d) << " = (" << R(b) << " < " << R(a) << ") ? " << R(b) << " : " << R(a) << ";\n";
             break;
           case OPS_IR_MAX:
-            os << "    " << R(d) << " = (" << R(b) << " > " << R(a) << ") ? " << R(b) << " : " << R(a) << ";\n";
+            if (!f32 && kIntCmp)
+              os << "    " << R(d) << " = dlt(" << R(a) << ", " << R(b) << ") ? " << R(b) << " : " << R(a) << ";\n";
+            else
+              os << "    " << R(d) << " = (" << R(b) << " > " << R(a) << ") ? " << R(b) << " : " << R(a) << ";\n";
             break;
           case OPS_IR_SGT:
-            os << "    " << R(d) << " = (" << R(a) << " > " << R(b) << ") ? " << R(c) << " : " << R(e) << ";\n";
+            if (!f32 && kIntCmp)
+              os << "    " << R(d) << " = dlt(" << R(b) << ", " << R(a) << ") ? " << R(c) << " : " << R(e) << ";\n";
+            else
+              os << "    " << R(d) << " = (" << R(a) << " > " << R(b) << ") ? " << R(c) << " : " << R(e) << ";\n";
             break;
           case OPS_IR_WSUM:
           case OPS_IR_WACC: {
@@ -471,11 +499,13 @@ struct LoopGen {
     os << "}\n";
   }
 
-  // Tile wavefront: the whole CTA (NT threads) enumerates one box, flat in
-  // x-fastest order (point j of the box is x0 + j % nx, ...), each thread
-  // taking P points NT apart at a time as independent dependency chains;
-  // reductions go to the tile's column `col` of the partial rows (row =
-  // the loop's partial row - row0), assigned.
+  // Tile wavefront: the compute warps share one box in units of 32 x by P
+  // rows (a unit per warp at a time, round robin over the warps; boxes
+  // narrower than 128 in flattened groups), as the per-loop kernels do with
+  // CTAs: a unit's rows sit a compile-time pitch apart, so every stencil
+  // load of a point is an immediate offset from one address.  Reductions go
+  // to the tile's column `col` of the partial rows (row = the loop's partial
+  // row - row0), assigned.
   void emit_tile(int i, int NT, int P) const {
     restrict_all = true;
     staged_ptrs = true;
@@ -489,34 +519,18 @@ struct LoopGen {
          << classes[k].second << "ll;\n";
     emit_points(1);
     os << "  };\n";
-    os << "  auto multi = [&](const int* xs, const int* ys, const int* zs) {\n";
-    for (int k = 0; k < (int)classes.size(); ++k)
-      for (int p = 0; p < P; ++p)
-        os << "    const i64 i" << k << "_" << p << " = (i64)xs[" << p << "] + (i64)ys[" << p << "] * "
-           << classes[k].first << "ll + (i64)zs[" << p << "] * " << classes[k].second << "ll;\n";
+    os << "  auto full = [&](int x, int y, int z) {\n";
+    for (int k = 0; k < (int)classes.size(); ++k) {
+      os << "    const i64 i" << k << "_0 = (i64)x + (i64)y * " << classes[k].first << "ll + (i64)z * "
+         << classes[k].second << "ll;\n";
+      for (int p = 1; p < P; ++p)
+        os << "    const i64 i" << k << "_" << p << " = i" << k << "_0 + " << (int64_t)p * classes[k].first
+           << "ll;\n";
+    }
     emit_points(P);
     os << "  };\n";
-    os << "  const int nx = x1 - x0, ny = y1 - y0, nz = z1 - z0;\n"
-          "  if (nx > 0 && ny > 0 && nz > 0) {\n"
-          "    const int n = nx * ny * nz;\n"
-          "    const int sr = " << NT << " / nx, sx = " << NT << " - sr * nx;\n"
-          "    int j = (int)threadIdx.x;\n"
-          "    int r = j / nx, x = j - r * nx, y = r, z = 0;\n"
-          "    while (y >= ny) { y -= ny; ++z; }\n"
-          "    auto adv = [&]() {\n"
-          "      x += sx;\n"
-          "      y += sr;\n"
-          "      if (x >= nx) { x -= nx; ++y; }\n"
-          "      while (y >= ny) { y -= ny; ++z; }\n"
-          "    };\n"
-          "    for (; j + " << (P - 1) * NT << " < n; j += " << P * NT << ") {\n"
-          "      int xs[" << P << "], ys[" << P << "], zs[" << P << "];\n"
-          "#pragma unroll\n"
-          "      for (int p = 0; p < " << P << "; ++p) { xs[p] = x0 + x; ys[p] = y0 + y; zs[p] = z0 + z; adv(); }\n"
-          "      multi(xs, ys, zs);\n"
-          "    }\n"
-          "    for (; j < n; j += " << NT << ") { one(x0 + x, y0 + y, z0 + z); adv(); }\n"
-          "  }\n";
+    os << "  run_units<" << P << ", 32>(x0, x1, y0, y1, z0, z1, (int)(threadIdx.x >> 5), " << NT / 32
+       << ", one, full);\n";
     for (int k = 0; k < L.nreds; ++k)
       os << "  flush_red_col(" << L.red_op[k] << ", acc" << k << ", part + (size_t)(L->part_row + " << k
          << " - row0) * stride + col);\n";
@@ -789,7 +803,8 @@ struct TwArgs {
   int* prog; int* ticket; const double* scal; DD* part; int* err; long long timeout_ns;
   int nt[3]; int ncls[3]; int roff[3]; int coff[3];
   int ntiles, stride, row0, skip_tile;
-  const unsigned char* pf; int ahead, pad;
+  const unsigned char* pf; int ahead, ngroups;
+  const int* groups;
 };
 // Ask L2 to fetch the rows of the arguments of loop l that the mask pf[l]
 // selects, over the tile's box of that loop widened by each argument's
@@ -869,54 +884,60 @@ std::string generate_tilewave(const DLoop* loops, int count, const std::vector<s
     LoopGen g(loops[i], ro[i], os, false, es == 4);
     g.emit_tile(i, nt, P);
   }
-  // s_step[k]: loop of the step in slot k (-1: stop, -2: an empty step),
-  // its tile, and its box
+  // Shared state: every loop's dat pointers and argument counts (loaded
+  // once per launch), the current tile's box of every loop and its wait
+  // table (loaded once per tile), and two slots of the step hand-over:
+  // s_n[k] loops (-1: stop), their tile and their loop indices.
   os << "extern \"C\" __global__ void __launch_bounds__(" << nt + 32 << ", " << jit_tile_min_ctas()
      << ") tw(const TwArgs A) {\n"
-        "  constexpr int NL = " << count << ", ND = " << ndirs << ", ES = " << es << ";\n"
+        "  constexpr int NL = " << count << ", ND = " << ndirs << ", ES = " << es << ", MG = " << kTwMaxGroup << ";\n"
         "  __shared__ unsigned short s_need[ND * NL];\n"
-        "  __shared__ int s_step[2][8];\n"
-        "  __shared__ void* s_ptr[2][8];\n"
+        "  __shared__ int s_box[NL][6];\n"
+        "  __shared__ void* s_lptr[NL][8];\n"
+        "  __shared__ unsigned char s_live[NL];\n"
+        "  __shared__ int s_n[2], s_tile[2], s_ent[2][MG];\n"
         "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
         "  const int tid = threadIdx.x;\n"
         "  if (tid < kTwNtc) {\n"
-        "    // compute warps: run the step of each slot in turn\n"
+        "    // compute warps: run the loops of each slot in turn\n"
         "    for (int k = 0;; k ^= 1) {\n"
         "      bar_step();\n"
-        "      const int l = s_step[k][0];\n"
-        "      if (l == -1) return;\n"
-        "      if (l < 0) continue;\n"
-        "      const int tile = s_step[k][1];\n"
-        "      const int x0 = s_step[k][2], x1 = s_step[k][3], y0 = s_step[k][4], y1 = s_step[k][5];\n"
-        "      const int z0 = s_step[k][6], z1 = s_step[k][7];\n"
-        "      switch (l) {\n";
+        "      const int ne = s_n[k];\n"
+        "      if (ne < 0) return;\n"
+        "      const int tile = s_tile[k];\n"
+        "      for (int e = 0; e < ne; ++e) {\n"
+        "        const int l = s_ent[k][e];\n"
+        "        const int* B = s_box[l];\n"
+        "        switch (l) {\n";
   for (int i = 0; i < count; ++i)
-    os << "        case " << i << ": tb" << i
-       << "(A.loops + " << i << ", s_ptr[k], x0, x1, y0, y1, z0, z1, A.scal, A.part, A.stride, A.row0, tile); break;\n";
-  os << "        default: break;\n"
+    os << "          case " << i << ": tb" << i << "(A.loops + " << i
+       << ", s_lptr[" << i << "], B[0], B[1], B[2], B[3], B[4], B[5], A.scal, A.part, A.stride, A.row0, tile); break;\n";
+  os << "          default: break;\n"
+        "        }\n"
         "      }\n"
         "    }\n"
         "  }\n"
         "  // control warp\n"
         "  const int lane = tid - kTwNtc;\n"
-        "  int k = 0;              // slot of the next step\n"
-        "  int prev_tile = -1, prev_l = 0;  // the step the compute warps run now\n"
+        "  for (int j = lane; j < NL * 8; j += 32) {\n"
+        "    const int l = j >> 3, a = j & 7;\n"
+        "    s_lptr[l][a] = a < A.loops[l].nargs ? (void*)A.loops[l].args[a].ptr0 : nullptr;\n"
+        "  }\n"
+        "  int k = 0;                         // slot of the next step\n"
+        "  int pub_tile = -1, pub_val = 0;    // progress owed once the running step completes\n"
         "  bool stop = false;\n"
         "  int tk = 0, nxt = 0;\n"
         "  if (lane == 0) tk = atomicAdd(A.ticket, 1);\n"
         "  tk = __shfl_sync(0xffffffffu, tk, 0);\n"
-        "  // publish the progress of the step the compute warps just finished\n"
         "  auto publish = [&]() {\n"
-        "    if (lane == 0 && prev_tile >= 0 && prev_tile != A.skip_tile) st_release(A.prog + prev_tile, prev_l + 1);\n"
+        "    if (lane == 0 && pub_tile >= 0 && pub_tile != A.skip_tile) st_release(A.prog + pub_tile, pub_val);\n"
         "  };\n"
-        "  // hand a slot to the compute warps and meet them at the step barrier\n"
-        "  auto post = [&](int l, int tile, const int* box) {\n"
+        "  // hand slot k to the compute warps and meet them at the step barrier\n"
+        "  auto post = [&](int ne, int tile) {\n"
         "    if (lane == 0) {\n"
-        "      s_step[k][0] = l;\n"
-        "      s_step[k][1] = tile;\n"
+        "      s_n[k] = ne;\n"
+        "      s_tile[k] = tile;\n"
         "    }\n"
-        "    if (lane < 6 && box) s_step[k][2 + lane] = box[lane];\n"
-        "    if (l >= 0 && lane < A.loops[l].nargs) s_ptr[k][lane] = A.loops[l].args[lane].ptr0;\n"
         "    __syncwarp();\n"
         "    bar_step();\n"
         "    k ^= 1;\n"
@@ -926,8 +947,19 @@ std::string generate_tilewave(const DLoop* loops, int count, const std::vector<s
         "    const int tc[3] = {tile % A.nt[0], (tile / A.nt[0]) % A.nt[1], tile / (A.nt[0] * A.nt[1])};\n"
         "    const int cl = (A.cls[A.coff[2] + tc[2]] * A.ncls[1] + A.cls[A.coff[1] + tc[1]]) * A.ncls[0] +\n"
         "                   A.cls[A.coff[0] + tc[0]];\n"
+        "    if (lane == 0) nxt = atomicAdd(A.ticket, 1);\n"
+        "    // the compute warps are past the previous tile: its boxes can be replaced\n"
         "    for (int j = lane; j < ND * NL; j += 32) s_need[j] = A.need[(size_t)cl * (ND * NL) + j];\n"
+        "    for (int j = lane; j < 6 * NL; j += 32) {\n"
+        "      const int l = j / 6, q = j - 6 * l, d = q >> 1;\n"
+        "      s_box[l][q] = A.rng[A.roff[d] + 2 * (tc[d] * NL + l) + (q & 1)];\n"
+        "    }\n"
         "    __syncwarp();\n"
+        "    // a loop with reductions always runs: it writes its tile's partials (the identity when its box is empty)\n"
+        "    for (int l = lane; l < NL; l += 32) {\n"
+        "      const int* b = s_box[l];\n"
+        "      s_live[l] = (b[1] > b[0] && b[3] > b[2] && b[5] > b[4]) || A.loops[l].nreds;\n"
+        "    }\n"
         "    int pred = -1, have = 0x7fffffff;\n"
         "    if (lane < ND) {\n"
         "      const int m = lane + 1;\n"
@@ -937,14 +969,27 @@ std::string generate_tilewave(const DLoop* loops, int count, const std::vector<s
         "        have = 0;\n"
         "      }\n"
         "    }\n"
-        "    if (lane == 0) nxt = atomicAdd(A.ticket, 1);\n"
+        "    __syncwarp();\n"
         "    for (int l = 0; l < A.ahead && l < NL; ++l) tw_prefetch<ES>(A, NL, l, tc, lane);\n"
-        "    for (int l = 0; l < NL; ++l) {\n"
-        "      if (l + A.ahead < NL) tw_prefetch<ES>(A, NL, l + A.ahead, tc, lane);\n"
-        "      // may loop l of this tile run?\n"
+        "    for (int g = 0; g < A.ngroups; ++g) {\n"
+        "      const int l0 = A.groups[g], l1 = A.groups[g + 1];\n"
+        "      for (int l = l0 + A.ahead; l < l1 + A.ahead && l < NL; ++l) tw_prefetch<ES>(A, NL, l, tc, lane);\n"
+        "      int ne = 0;\n"
+        "      for (int l = l0; l < l1; ++l)\n"
+        "        if (s_live[l]) {\n"
+        "          if (lane == 0) s_ent[k][ne] = l;\n"
+        "          ++ne;\n"
+        "        }\n"
+        "      if (ne == 0) {  // nothing to run: these loops count as done with the running step\n"
+        "        pub_tile = tile;\n"
+        "        pub_val = l1;\n"
+        "        continue;\n"
+        "      }\n"
+        "      // may the step run?  each predecessor must have completed what its loops conflict with\n"
         "      bool ok = true;\n"
         "      if (lane < ND) {\n"
-        "        const int want = s_need[lane * NL + l];\n"
+        "        int want = 0;\n"
+        "        for (int l = l0; l < l1; ++l) want = max(want, (int)s_need[lane * NL + l]);\n"
         "        if (have < want) {\n"
         "          const int* pp = A.prog + pred;\n"
         "          int v = ld_relaxed(pp);\n"
@@ -970,30 +1015,20 @@ std::string generate_tilewave(const DLoop* loops, int count, const std::vector<s
         "        stop = true;\n"
         "        break;\n"
         "      }\n"
-        "      int box[6];\n"
-        "#pragma unroll\n"
-        "      for (int d = 0; d < 3; ++d) {\n"
-        "        const int* r = A.rng + A.roff[d] + 2 * (tc[d] * NL + l);\n"
-        "        box[2 * d] = r[0];\n"
-        "        box[2 * d + 1] = r[1];\n"
-        "      }\n"
-        "      const bool live = box[1] > box[0] && box[3] > box[2] && box[5] > box[4];\n"
-        "      // a loop with reductions always runs: it writes its tile's partials (the identity when empty)\n"
-        "      const int runs = live || A.loops[l].nreds;\n"
-        "      post(runs ? l : -2, tile, box);\n"
+        "      post(ne, tile);\n"
         "      publish();\n"
-        "      prev_tile = tile;\n"
-        "      prev_l = l;\n"
+        "      pub_tile = tile;\n"
+        "      pub_val = l1;\n"
         "    }\n"
         "    if (stop) break;\n"
-        "    // an empty step: the tile's last loop completes, then its progress is published\n"
-        "    post(-2, tile, nullptr);\n"
+        "    // an empty step: the tile's last loops complete, then its progress is published\n"
+        "    post(0, tile);\n"
         "    publish();\n"
-        "    prev_tile = -1;\n"
+        "    pub_tile = -1;\n"
         "    tk = __shfl_sync(0xffffffffu, nxt, 0);\n"
         "    if (*(volatile int*)A.err) stop = true;\n"
         "  }\n"
-        "  post(-1, -1, nullptr);\n"
+        "  post(-1, -1);\n"
         "  publish();\n"
         "}\n";
   return os.str();
@@ -1535,7 +1570,12 @@ int jit_tile_pts(int es) {
 }
 
 int jit_tile_prefetch() {
-  static const int v = env_int("OPSTILE_TW_PREFETCH", 1, 0, 2);
+  static const int v = env_int("OPSTILE_TW_PREFETCH", 0, 0, 2);
+  return v;
+}
+
+int jit_tile_group() {
+  static const int v = env_int("OPSTILE_TW_GROUP", kTwMaxGroup, 1, kTwMaxGroup);
   return v;
 }
 

@@ -132,7 +132,8 @@ struct TwArgs {
   int nt[3], ncls[3], roff[3], coff[3];
   int ntiles, stride, row0, skip_tile;  // skip_tile >= 0 (test hook): that tile never reports progress
   const unsigned char* pf;   // per loop: arguments whose rows are prefetched into L2 `ahead` loops early
-  int ahead, pad;
+  int ahead, ngroups;
+  const int* groups;         // the loops of step g: groups[g] .. groups[g + 1]
 };
 struct JitTile;
 // threads per CTA (OPSTILE_TW_THREADS: 128, 256 (default) or 512), CTAs per
@@ -141,12 +142,15 @@ struct JitTile;
 int jit_tile_threads();
 int jit_tile_min_ctas();
 int jit_tile_pts(int es);
-// L2 prefetch of the tile wavefront (OPSTILE_TW_PREFETCH): 0 none, 1 (the
-// default) the rows a loop reads from dats no earlier loop of the segment
-// touched (first reads of the segment's inputs), 2 every row a loop reads;
-// issued OPSTILE_TW_AHEAD (default 3) loops ahead
+// L2 prefetch of the tile wavefront (OPSTILE_TW_PREFETCH): 0 (the default:
+// measured no faster on GB300) none, 1 the rows a loop reads from dats no
+// earlier loop of the segment touched (first reads of the segment's
+// inputs), 2 every row a loop reads; issued OPSTILE_TW_AHEAD (default 3)
+// loops ahead
 int jit_tile_prefetch();
 int jit_tile_ahead();
+// loops of one tile step at most (OPSTILE_TW_GROUP, 1..8, default 8)
+int jit_tile_group();
 int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es, int ndim,
                  JitTile** out, std::string* why, double* compile_ms);
 int jit_compile_tilewave_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,

@@ -366,7 +366,8 @@ inline void touched(const SkewedPlan& P, int L, int d, int t, int l, const PArg&
 inline bool meet(int alo, int ahi, int blo, int bhi) { return alo < ahi && blo < bhi && alo < bhi && blo < ahi; }
 }  // namespace
 
-bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& P, TileWavePlan& out, std::string* why) {
+bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& P, TileWavePlan& out, std::string* why,
+                     int max_group) {
   const int L = (int)loops.size();
   const int nd = P.ndim;
   out = TileWavePlan();
@@ -528,6 +529,29 @@ bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& P, TileW
             }
         }
       }
+  // steps: consecutive loops that share no dat with a write among them
+  out.groups.clear();
+  {
+    auto clash = [&](const PLoop& a, const PLoop& b) {
+      for (const PArg& x : a.args) {
+        if (x.kind != OPS_ARG_DAT) continue;
+        for (const PArg& y : b.args)
+          if (y.kind == OPS_ARG_DAT && y.dat == x.dat && (x.writes || y.writes)) return true;
+      }
+      return false;
+    };
+    int g0 = 0;
+    out.groups.push_back(0);
+    for (int l = 1; l < L; ++l) {
+      bool cut = l - g0 >= std::max(1, max_group);
+      for (int m = g0; m < l && !cut; ++m) cut = clash(loops[m], loops[l]);
+      if (cut) {
+        out.groups.push_back(l);
+        g0 = l;
+      }
+    }
+    out.groups.push_back(L);
+  }
   // tickets: by coordinate sum, then z, y, x
   out.order.clear();
   out.order.reserve((size_t)Tn[0] * Tn[1] * Tn[2]);

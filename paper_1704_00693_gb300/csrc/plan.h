@@ -112,7 +112,14 @@ struct TileWavePlan {
   int nloops = 0;
   int64_t pairs = 0;              // conflicting argument pairs examined
   int bad_dim = -1;               // on failure: the dimension whose tiles are too small
+  // Steps of a tile: runs of consecutive loops, none of which shares a dat
+  // with an earlier loop of its run where either writes it, so a run's
+  // loops need no barrier between them; groups[g] .. groups[g + 1] are the
+  // loops of step g (groups.back() = nloops)
+  std::vector<int> groups;
 };
-bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& plan, TileWavePlan& out, std::string* why);
+// max_group caps the loops of one step (1: a step per loop)
+bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& plan, TileWavePlan& out, std::string* why,
+                     int max_group = 8);
 
 }  // namespace opstile

@@ -75,7 +75,7 @@ struct CachedPlan {
   TileWavePlan tw;
   void* d_tw = nullptr;
   size_t tw_bytes = 0;
-  size_t tw_order = 0, tw_cls = 0, tw_need = 0, tw_pf = 0;  // byte offsets inside d_tw
+  size_t tw_order = 0, tw_cls = 0, tw_need = 0, tw_grp = 0, tw_pf = 0;  // byte offsets inside d_tw
   int tw_roff[3] = {0, 0, 0}, tw_coff[3] = {0, 0, 0};
   int* d_twprog = nullptr;
   int tw_ntiles = 0;
@@ -161,6 +161,10 @@ struct ops_ctx_s {
 };
 
 namespace {
+
+// red_ops entry of a handle made by ops_decl_scalar: a value SCALAR
+// arguments read, which no loop reduces into
+constexpr int kScalarHandle = 100;
 
 int fail(ops_ctx c, int code, const char* fmt, ...) {
   if (c) {
@@ -290,6 +294,9 @@ int validate_loop(ops_ctx c, const QLoop& q) {
       if (a.handle < 0 || a.handle >= (int)c->red_ops.size())
         return fail(c, OPS_ERR_INVALID_ARG, "loop '%s' arg %d: bad reduction handle %d", q.name.c_str(), i, a.handle);
       if (a.kind == OPS_ARG_RED) {
+        if (c->red_ops[a.handle] == kScalarHandle)
+          return fail(c, OPS_ERR_INVALID_ARG, "loop '%s' arg %d: handle %d is a scalar, not a reduction", q.name.c_str(),
+                      i, a.handle);
         if (std::find(seen_red.begin(), seen_red.end(), a.handle) != seen_red.end())
           return fail(c, OPS_ERR_INVALID_ARG, "loop '%s': reduction %d appears twice", q.name.c_str(), a.handle);
         seen_red.push_back(a.handle);
@@ -1163,7 +1170,7 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
       if (tile[d] <= 0) tile[d] = at[d];
   }
   for (int d = ndim; d < 3; ++d) tile[d] = 1;
-  std::vector<int> key = {-OPS_MODE_TILEWAVE, ndim, tile[0], tile[1], tile[2]};
+  std::vector<int> key = {-OPS_MODE_TILEWAVE, ndim, tile[0], tile[1], tile[2], jit_tile_group(), jit_tile_prefetch()};
   for (int i = 0; i < count; ++i) {
     const QLoop& q = c->queue[first + i];
     for (int k = 0; k < 6; ++k) key.push_back(q.rng[k]);
@@ -1188,7 +1195,7 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
   bool ok = false;
   for (int attempt = 0; attempt < 24; ++attempt) {
     build_skewed_ranges(pl, (int)c->dats.size(), ndim, tile, np->plan);
-    if (build_tile_wave(pl, np->plan, np->tw, &why)) {
+    if (build_tile_wave(pl, np->plan, np->tw, &why, jit_tile_group())) {
       ok = true;
       break;
     }
@@ -1241,11 +1248,13 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
     }
   }
   const size_t b_rng = sizeof(int) * rng.size(), b_order = sizeof(int) * W.order.size(),
-               b_cls = sizeof(int) * cls.size(), b_need = sizeof(uint16_t) * W.need.size(), b_pf = pf.size();
+               b_cls = sizeof(int) * cls.size(), b_need = sizeof(uint16_t) * W.need.size(), b_pf = pf.size(),
+               b_grp = sizeof(int) * W.groups.size();
   np->tw_order = (b_rng + 15) / 16 * 16;
   np->tw_cls = np->tw_order + (b_order + 15) / 16 * 16;
   np->tw_need = np->tw_cls + (b_cls + 15) / 16 * 16;
-  np->tw_pf = np->tw_need + (b_need + 15) / 16 * 16;
+  np->tw_grp = np->tw_need + (b_need + 15) / 16 * 16;
+  np->tw_pf = np->tw_grp + (b_grp + 15) / 16 * 16;
   np->tw_bytes = np->tw_pf + b_pf + 16;
   np->tw_ntiles = ntiles;
   int rows = 0;
@@ -1270,6 +1279,7 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
   CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_cls, cls.data(), b_cls, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_need, W.need.data(), b_need, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_pf, pf.data(), b_pf, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(d + np->tw_grp, W.groups.data(), b_grp, cudaMemcpyHostToDevice, c->stream));
   CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // the host tables are temporaries
   *out = np.get();
   c->plans[key] = std::move(np);
@@ -1347,6 +1357,8 @@ int run_tilewave(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop
   a.skip_tile = env.skip_block;
   a.pf = (const unsigned char*)(d + cp->tw_pf);
   a.ahead = jit_tile_ahead();
+  a.groups = (const int*)(d + cp->tw_grp);
+  a.ngroups = (int)cp->tw.groups.size() - 1;
   CUDA_TRY(c, jit_launch_tilewave(t, a, c->stream, grid));
   ++c->stats.launches;
   ++c->stats.kernel_launches;
@@ -2007,9 +2019,47 @@ int ops_decl_stencil(ops_ctx c, int dims, int npts, const int* offsets, const ch
   return OPS_OK;
 }
 
+namespace {
+// a new slot of the device scalar array, holding init (reductions: their identity)
+int new_slot(ops_ctx c, int op, double init, int* out);
+}  // namespace
+
 int ops_decl_reduction(ops_ctx c, int op, int* out) {
   if (!c || !out) return OPS_ERR_INVALID_ARG;
   if (op < OPS_RED_SUM || op > OPS_RED_MAX) return fail(c, OPS_ERR_INVALID_ARG, "bad reduction op %d", op);
+  return new_slot(c, op, red_identity(op), out);
+}
+
+int ops_decl_scalar(ops_ctx c, double init, int* out) {
+  if (!c || !out) return OPS_ERR_INVALID_ARG;
+  return new_slot(c, kScalarHandle, init, out);
+}
+
+int ops_scalar_set(ops_ctx c, int h, double value) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  if (h < 0 || h >= (int)c->red_ops.size() || c->red_ops[h] != kScalarHandle)
+    return fail(c, OPS_ERR_INVALID_ARG, "bad scalar %d", h);
+  if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
+  int rc = flush(c);  // loops queued before the call read the old value
+  if (rc) return rc;
+  LaunchEnv env = make_env(c);
+  CUDA_TRY(c, launch_set_scalar(env, h, value));
+  return OPS_OK;
+}
+
+int ops_scalar_get(ops_ctx c, int h, double* host_out) {
+  if (!c || !host_out) return OPS_ERR_INVALID_ARG;
+  if (h < 0 || h >= (int)c->red_ops.size() || c->red_ops[h] != kScalarHandle)
+    return fail(c, OPS_ERR_INVALID_ARG, "bad scalar %d", h);
+  if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
+  int rc = flush(c);
+  if (rc) return rc;
+  CUDA_TRY(c, cudaMemcpyAsync(host_out, c->d_scal + h, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  return check_device_error(c);  // synchronises the stream
+}
+
+namespace {
+int new_slot(ops_ctx c, int op, double init, int* out) {
   const int h = (int)c->red_ops.size();
   if (!c->host_only) {
     int rc = flush(c);  // the slot array may be reallocated
@@ -2028,12 +2078,13 @@ int ops_decl_reduction(ops_ctx c, int op, int* out) {
       c->scal_cap = nc;
     }
     LaunchEnv env = make_env(c);
-    CUDA_TRY(c, launch_set_scalar(env, h, red_identity(op)));
+    CUDA_TRY(c, launch_set_scalar(env, h, init));
   }
   c->red_ops.push_back(op);
   *out = h;
   return OPS_OK;
 }
+}  // namespace
 
 int ops_par_loop(ops_ctx c, int block, int dims, const int* range, int nargs, const ops_arg* args, int nins,
                  const int32_t* code, int nconsts, const double* consts, const char* name) {
@@ -2084,7 +2135,8 @@ int ops_sync(ops_ctx c) {
 
 int ops_reduction_result(ops_ctx c, int red, double* host_out) {
   if (!c || !host_out) return OPS_ERR_INVALID_ARG;
-  if (red < 0 || red >= (int)c->red_ops.size()) return fail(c, OPS_ERR_INVALID_ARG, "bad reduction %d", red);
+  if (red < 0 || red >= (int)c->red_ops.size() || c->red_ops[red] == kScalarHandle)
+    return fail(c, OPS_ERR_INVALID_ARG, "bad reduction %d", red);
   int rc = flush(c);
   if (rc) return rc;
   if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
@@ -2240,7 +2292,7 @@ int ops_compile_queued_tilewave(ops_ctx c, char* src_out, int64_t cap, int64_t* 
 }
 
 int ops_plan_tilewave(ops_ctx c, const int* tile, int64_t* counts, int* out_need, int64_t need_cap, int* out_class,
-                      int* out_order, int64_t tile_cap) {
+                      int* out_order, int64_t tile_cap, int* out_steps) {
   if (!c || !tile || !counts) return OPS_ERR_INVALID_ARG;
   if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
   const int ndim = c->queue[0].dims;
@@ -2258,13 +2310,15 @@ int ops_plan_tilewave(ops_ctx c, const int* tile, int64_t* counts, int* out_need
   build_skewed_ranges(pl, (int)c->dats.size(), ndim, t, P);
   TileWavePlan W;
   std::string why;
-  if (!build_tile_wave(pl, P, W, &why)) return fail(c, OPS_ERR_INVALID_ARG, "%s", why.c_str());
+  if (!build_tile_wave(pl, P, W, &why, jit_tile_group())) return fail(c, OPS_ERR_INVALID_ARG, "%s", why.c_str());
   const int64_t ntiles = (int64_t)P.ntiles[0] * P.ntiles[1] * P.ntiles[2];
   const int64_t ncl = (int64_t)W.ncls[0] * W.ncls[1] * W.ncls[2];
   counts[0] = ntiles;
   counts[1] = ncl;
   counts[2] = W.ndirs;
   counts[3] = W.nloops;
+  counts[4] = (int64_t)W.groups.size() - 1;
+  if (out_steps) std::memcpy(out_steps, W.groups.data(), sizeof(int) * W.groups.size());
   if (out_need) {
     if ((int64_t)W.need.size() > need_cap)
       return fail(c, OPS_ERR_INVALID_ARG, "out_need needs %lld ints", (long long)W.need.size());

@@ -7,9 +7,12 @@
 // every admitted solve by a few CG iterations per round, and retires the
 // finished ones -- so requests that arrive while others run join the batch
 // as soon as memory frees up, and their work overlaps on the GPU.  The pool
-// is one allocation made at open; the serving loop never calls cudaMalloc.
+// and the batch's device tables are allocated at open; the serving loop
+// never calls cudaMalloc, and the batch's captured tick graph is reused
+// whatever requests come and go.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -79,7 +82,9 @@ enum ReqState { RQ_QUEUED, RQ_RUNNING, RQ_DONE, RQ_FAILED };
 
 struct Request {
   uint64_t id;
-  int n;
+  int n, units = 0;
+  double tol = 0.0;
+  int prec = 0;
   std::vector<double> kappa, rhs, x;
   int state = RQ_QUEUED;
   int slot = -1;
@@ -102,6 +107,7 @@ struct ops_server_s {
   std::deque<Request*> queue;
   std::map<uint64_t, std::unique_ptr<Request>> reqs;
   std::map<int, Request*> by_slot;
+  int max_units = 0, live_units = 0;  // work units the batch's fixed tables hold / the admitted solves use
   uint64_t next_id = 1;
   bool stop = false;
   int error = OPS_OK;
@@ -112,29 +118,41 @@ namespace {
 
 void worker_loop(ops_server s) {
   std::vector<int> done;
+  std::vector<Request*> admit;
   for (;;) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
-      // admit the oldest requests while a slot and pool memory are free
-      while (!s->queue.empty() && s->batch->live() < s->cfg.max_batch) {
+      // admit the oldest requests while a slot, pool memory and unit-table
+      // room are free
+      admit.clear();
+      while (!s->queue.empty() && s->batch->live() + (int)admit.size() < s->cfg.max_batch) {
         Request* r = s->queue.front();
+        if (s->live_units + r->units > s->max_units) break;
         const size_t off = s->pool.take(r->bytes);
         if (off == (size_t)-1) break;
         s->queue.pop_front();
         r->off = off;
-        const ops_cg_params& P = s->cfg.params;
-        r->slot = s->batch->add(r->n, r->kappa.data(), r->rhs.data(), P.tol, P.precision,
-                                P.inner_tol > 0 ? P.inner_tol : 1e-4, P.maxit, P.maxouter > 0 ? P.maxouter : 100,
-                                s->pool.base() + off);
-        r->state = RQ_RUNNING;
-        r->t_admit = now_ms();
-        s->by_slot[r->slot] = r;
+        s->live_units += r->units;
+        admit.push_back(r);
       }
-      if (s->batch->live() == 0) {
+      if (admit.empty() && s->batch->live() == 0) {
         if (s->stop) return;
         s->cv_work.wait_for(lk, std::chrono::milliseconds(1));
         continue;
       }
+    }
+    // uploads happen outside the lock, so submitters never wait on them
+    // (only this thread touches the batch)
+    const ops_cg_params& P = s->cfg.params;
+    for (Request* r : admit) {
+      const int slot = s->batch->add(r->n, r->kappa.data(), r->rhs.data(), r->tol, r->prec,
+                                     P.inner_tol > 0 ? P.inner_tol : 1e-4, P.maxit, P.maxouter > 0 ? P.maxouter : 100,
+                                     s->pool.base() + r->off);
+      std::lock_guard<std::mutex> lk(s->mu);
+      r->slot = slot;
+      r->state = RQ_RUNNING;
+      r->t_admit = now_ms();
+      s->by_slot[slot] = r;
     }
     cudaError_t e = s->batch->run(s->cfg.ticks_per_poll);
     if (e == cudaSuccess) e = s->batch->poll(done);
@@ -161,6 +179,7 @@ void worker_loop(ops_server s) {
       r->t_done = now_ms();
       s->batch->remove(slot);
       s->pool.give(r->off, r->bytes);
+      s->live_units -= r->units;
       s->by_slot.erase(slot);
       std::vector<double>().swap(r->kappa);
       std::vector<double>().swap(r->rhs);
@@ -195,19 +214,35 @@ int ops_serve_open(ops_server* out, const ops_serve_config* cfg) {
     return rc;
   }
   s->pool.init((char*)s->region, s->region_bytes);
-  s->batch.reset(new CgBatch(ctx_stream(s->ctx), ctx_num_sms(s->ctx)));
+  // the batch's tables, sized once for the most work units the pool can
+  // hold: problems hold at least min_bpu pool bytes per unit
+  double min_bpu = 1e30;
+  for (int n = 1; n <= 4096; ++n) min_bpu = std::min(min_bpu, (double)cg_problem_bytes(n) / cg_unit_count(n));
+  s->max_units = (int)std::min<double>(1 << 30, (double)s->region_bytes / min_bpu + s->cfg.max_batch);
+  s->batch.reset(new CgBatch(ctx_stream(s->ctx), ctx_num_sms(s->ctx), s->cfg.max_batch, s->max_units));
+  if (s->batch->init_status() != cudaSuccess) {
+    s->batch.reset();
+    ctx_free(s->ctx, s->region, s->region_bytes);
+    ops_finalize(s->ctx);
+    return OPS_ERR_NOMEM;
+  }
   ops_server raw = s.get();
   s->worker = std::thread(worker_loop, raw);
   *out = s.release();
   return OPS_OK;
 }
 
-int ops_serve_submit(ops_server s, int n, const double* host_kappa, const double* host_rhs, uint64_t* id) {
+int ops_serve_submit(ops_server s, int n, const double* host_kappa, const double* host_rhs, double tol, int precision,
+                     uint64_t* id) {
   if (!s || !host_kappa || !host_rhs || !id || n < 1 || n > 46000) return OPS_ERR_INVALID_ARG;
+  if (precision >= 0 && precision != OPS_PREC_FP64 && precision != OPS_PREC_MIXED) return OPS_ERR_INVALID_ARG;
   const size_t bytes = (size_t)cg_problem_bytes(n);
-  if (bytes > s->region_bytes) return OPS_ERR_NOMEM;  // could never be admitted
+  if (bytes > s->region_bytes || cg_unit_count(n) > s->max_units) return OPS_ERR_NOMEM;  // could never be admitted
   std::unique_ptr<Request> r(new Request);
   r->n = n;
+  r->units = cg_unit_count(n);
+  r->tol = tol > 0.0 ? tol : s->cfg.params.tol;
+  r->prec = precision >= 0 ? precision : s->cfg.params.precision;
   r->bytes = bytes;
   r->kappa.assign(host_kappa, host_kappa + (size_t)n * n);
   r->rhs.assign(host_rhs, host_rhs + (size_t)n * n);

@@ -378,3 +378,32 @@ def test_noalloc_rejects_overlapping_views_and_short_pitches(lib):
         ops.ops_loop_noalloc(2, rng, [(DAT, READ), (DAT, WRITE)],
                              [view(base, pitch=n), view(base + (1 << 20))], [s5, [(0, 0, 0)]], code, K)
     assert e.value.code == ops.OPS_ERR_INVALID_ARG
+
+
+def test_scalars_share_the_handle_space_but_not_reductions(lib):
+    """A scalar handle can be read by SCALAR arguments but is not a
+    reduction: a RED argument targeting it is rejected at enqueue, and
+    ops_reduction_result refuses it."""
+    from synth.program import BodyBuilder, DAT, SCALAR, REDARG, READ, WRITE
+    ctx = host_ctx()
+    try:
+        b = ops.ops_decl_block(ctx, 2)
+        d0 = ops.ops_decl_dat(ctx, b, (8, 8, 1), (1, 1, 0), (1, 1, 0))
+        d1 = ops.ops_decl_dat(ctx, b, (8, 8, 1), (1, 1, 0), (1, 1, 0))
+        p0 = ops.ops_decl_stencil(ctx, 2, [(0, 0, 0)])
+        red = ops.ops_decl_reduction(ctx, ops.OPS_RED_SUM)
+        sc = ops.ops_decl_scalar(ctx, 0.5)
+        assert sc == red + 1
+        code, K = BodyBuilder().ld(0, 0, 0).ld(1, 1, 0).emit(5, 2, 0, 1).st(2, 2).build()
+        ops.ops_par_loop(ctx, b, 2, ((0, 8), (0, 8)), [(DAT, d0, p0, READ), (SCALAR, sc, -1, READ),
+                                                        (DAT, d1, p0, WRITE)], code, K, "reads a scalar")
+        code, K = BodyBuilder().ld(0, 0, 0).red(1, 0).build()
+        with pytest.raises(ops.OpsError) as e:
+            ops.ops_par_loop(ctx, b, 2, ((0, 8), (0, 8)), [(DAT, d0, p0, READ), (REDARG, sc, -1, READ)], code, K,
+                             "reduces into a scalar")
+        assert e.value.code == ops.OPS_ERR_INVALID_ARG and "scalar" in str(e.value)
+        with pytest.raises(ops.OpsError):
+            ops.ops_reduction_result(ctx, sc)
+        ops.ops_queue_clear(ctx)
+    finally:
+        ops.ops_finalize(ctx)

@@ -115,7 +115,7 @@ def test_chain_cg_matches_oracle(n):
     three loops per iteration, host-read reductions) converges like the
     oracle's FP64 CG, and its operator is the engine's bit for bit (one
     iteration from x = 0 gives w = A b)."""
-    from paper_1704_00693_gb300.cgchain import ChainCG
+    from cg_loopchain import ChainCG
     kappa, b = W.cg_problem(n, 1e-2, 1e2)
     x_ref, it_ref, _ = oracle.cg64(kappa, b, tol=1e-10)
     for mode in ("untiled", "skewed"):

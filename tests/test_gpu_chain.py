@@ -463,3 +463,38 @@ def test_fp32_refuses_interpreted_and_checked_modes():
                 r.step()
         finally:
             r.close()
+
+
+def test_compare_select_on_signed_zeros_and_nan():
+    """MIN, MAX and SGT bodies over data full of ties, signed zeros, NaN and
+    infinities: the compiled kernels (whose FP64 compares run on the
+    integer pipe) and the interpreter give the oracle's bit patterns in
+    every mode, FP64 and FP32."""
+    import math
+    from synth.program import MIN as IMIN, MAX as IMAX, SGT as ISGT
+    n = 40
+    shp = (1, n + 2, n + 2)
+    special = np.array([0.0, -0.0, 1.0, -1.0, math.nan, math.inf, -math.inf, 1.0, 5e-324, -5e-324])
+    rnd = np.random.default_rng(21)
+    dats = [DatSpec(f"s{k}", special[rnd.integers(0, len(special), shp)]) for k in range(3)]
+    dats.append(DatSpec("o", np.zeros(shp)))
+    st = [[(0, 0, 0)], [(0, 0, 0), (1, 0, 0)]]
+    loops = []
+    for k, op in enumerate((IMIN, IMAX)):
+        code, K = BodyBuilder().ld(0, 0, 0).ld(1, 1, 1).emit(op, 2, 0, 1).st(2, 2).build()
+        loops.append(Loop(f"mm{k}", ((0, n), (0, n)), [Arg(DAT, k, 0, READ), Arg(DAT, 2, 1, READ),
+                                                       Arg(DAT, 3, 0, WRITE)], code, K))
+    code, K = BodyBuilder().ld(0, 0, 0).ld(1, 1, 0).ld(2, 2, 0).ld(3, 3, 0).emit(ISGT, 4, 0, 1, 2, 3).st(3, 4).build()
+    loops.append(Loop("sgt", ((0, n), (0, n)), [Arg(DAT, 0, 0, READ), Arg(DAT, 1, 0, READ), Arg(DAT, 2, 0, READ),
+                                                Arg(DAT, 3, 0, RW)], code, K))
+    c = Chain("special", 2, (n, n, 1), (1, 1, 0), (1, 1, 0), dats, st, [], loops, steps=2)
+    for fp32 in (False, True):
+        ref, _ = oracle.run_chain(c, fp32=fp32)
+        ut = np.uint32 if fp32 else np.uint64
+        for mode, tile, interp in (("untiled", None, False), ("untiled", None, True), ("tilewave", (16, 16, 0), False),
+                                   ("wavefront", (0, 8, 0), False), ("skewed", (0, 8, 0), False)):
+            if fp32 and interp:
+                continue
+            got, _, _ = run_gpu(c, mode, tile, interpret=interp, fp32=fp32)
+            for k, (a, b) in enumerate(zip(got, ref)):
+                assert np.array_equal(a.view(ut), b.view(ut)), f"{mode} interpret={interp} fp32={fp32} dat {k}"

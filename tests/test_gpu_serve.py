@@ -111,3 +111,43 @@ def test_oversized_request_is_refused():
         assert e.value.code == ops.OPS_ERR_NOMEM
     finally:
         ops.ops_serve_close(srv)
+
+
+def test_per_request_tolerance_and_precision():
+    """Requests carry their own tolerance and precision: an FP64 request and
+    a mixed one at a tighter tolerance share the batch, each meets its own
+    tolerance and equals the same request solved alone."""
+    probs = problems([128, 192, 96], "perreq")
+    want = [(1e-6, ops.OPS_PREC_FP64), (1e-10, ops.OPS_PREC_MIXED), (0.0, -1)]
+    srv = ops.ops_serve_open(TOL, ops.OPS_PREC_MIXED, hbm_budget=1 << 30)
+    try:
+        ids = [ops.ops_serve_submit(srv, k, b, tol, prec) for (k, b), (tol, prec) in zip(probs, want)]
+        res = [ops.ops_serve_poll(srv, i, k.shape[0]) for i, (k, b) in zip(ids, probs)]
+    finally:
+        ops.ops_serve_close(srv)
+    ctx = ops.ops_init()
+    try:
+        for (k, b), (tol, prec), (x, st) in zip(probs, want, res):
+            t, p = (tol, prec) if tol > 0 else (TOL, ops.OPS_PREC_MIXED)
+            assert st["converged"] == 1 and oracle.relres(k, b, x) <= t
+            xa, sta = ops.ops_cg_solve(ctx, k, b, t, p)
+            assert np.array_equal(x, xa)
+    finally:
+        ops.ops_finalize(ctx)
+
+
+def test_many_requests_reuse_fixed_tables():
+    """A stream of 40 small requests of mixed sizes through a server whose
+    batch can hold 8: every result meets the tolerance (admission keeps the
+    fixed tables within their capacity while solves come and go)."""
+    sizes = [64 + 32 * (i % 9) for i in range(40)]
+    probs = problems(sizes, "stream")
+    srv = ops.ops_serve_open(TOL, ops.OPS_PREC_MIXED, hbm_budget=1 << 30, max_batch=8)
+    try:
+        ids = [ops.ops_serve_submit(srv, k, b) for k, b in probs]
+        res = [ops.ops_serve_poll(srv, i, n) for i, n in zip(ids, sizes)]
+    finally:
+        ops.ops_serve_close(srv)
+    assert max_concurrency([s for _, s in res]) <= 8
+    for (k, b), (x, st) in zip(probs, res):
+        assert st["converged"] == 1 and oracle.relres(k, b, x) <= TOL

@@ -98,7 +98,7 @@ def _check(loops, st, ndim, tile, rnd, schedules=3):
     got = _plan(loops, st, ndim, tile)
     if got is None:
         return False
-    need, cls, order = got
+    need, cls, order, steps = got
     nt, rg, _ = oplan.skewed_plan(loops, st, ndim, tile)
     ntiles = int(np.prod(nt))
     assert len(cls) == ntiles and sorted(order.tolist()) == list(range(ntiles))
@@ -125,21 +125,34 @@ def _check(loops, st, ndim, tile, rnd, schedules=3):
             assert lp_ < l
             assert need[cls[_lin(t, nt)], _dir_index(delta), l] >= lp_ + 1, \
                 f"tile {t} loop {l} does not wait for loop {lp_} of tile {tp}"
-    # random interleavings that obey the plan give the program-order versions
+    # steps: consecutive loops that share no dat with a write among them
+    steps = [int(v) for v in steps]
+    assert steps[0] == 0 and steps[-1] == len(loops) and all(a < b for a, b in zip(steps, steps[1:]))
+    for a, b in zip(steps, steps[1:]):
+        for l in range(a, b):
+            for m in range(a, l):
+                for x in loops[l].args:
+                    for y in loops[m].args:
+                        assert not (x.kind == DAT and y.kind == DAT and x.handle == y.handle and
+                                    (x.access != READ or y.access != READ)), f"loops {m} and {l} share a step"
+    # random interleavings that obey the plan give the program-order versions:
+    # a tile runs its steps in order, the loops of a step in any order,
+    # once every predecessor has completed what the step's loops need
     idx = {(t, l): q for q, (t, l, _) in enumerate(ph)}
     for _ in range(schedules):
-        prog = {t: 0 for t in tiles}
+        prog = {t: 0 for t in tiles}     # loops completed (a step's end once it ran)
         seq = []
         while True:
             ready = []
             for t in tiles:
-                l = prog[t]
-                if l == len(loops):
+                l0 = prog[t]
+                if l0 == len(loops):
                     continue
+                l1 = steps[steps.index(l0) + 1]
                 ok = True
                 for m in range(1, 1 << ndim):
                     p = tuple(t[d] - ((m >> d) & 1) for d in range(ndim))
-                    if min(p) >= 0 and prog[p] < need[cls[_lin(t, nt)], m - 1, l]:
+                    if min(p) >= 0 and prog[p] < max(need[cls[_lin(t, nt)], m - 1, l0:l1]):
                         ok = False
                         break
                 if ok:
@@ -147,10 +160,12 @@ def _check(loops, st, ndim, tile, rnd, schedules=3):
             if not ready:
                 break
             t = rnd.choice(ready)
-            q = idx.get((t, prog[t]))
-            if q is not None:
-                seq.append(q)
-            prog[t] += 1
+            l0 = prog[t]
+            l1 = steps[steps.index(l0) + 1]
+            members = list(range(l0, l1))
+            rnd.shuffle(members)
+            seq.extend(idx[(t, l)] for l in members if (t, l) in idx)
+            prog[t] = l1
         assert all(v == len(loops) for v in prog.values()), "the plan's waits deadlock"
         check_phase_order(loops, st, ndim, [(l, box) for _, l, box in ph], seq)
     return True
@@ -159,7 +174,7 @@ def _check(loops, st, ndim, tile, rnd, schedules=3):
 def test_worked_example_tilewave(lib):
     g = json.load(open(os.path.join(ROOT, "tests", "golden", "worked_example_1d_tilewave.json")))
     c = W.worked_example_1d()
-    need, cls, order = _plan(c.loops, c.stencils, 1, g["tile"])
+    need, cls, order, steps = _plan(c.loops, c.stencils, 1, g["tile"])
     assert len(cls) == g["tiles"]
     assert need[cls[1], 0].tolist() == g["need_tile1"]
     assert need[cls[0], 0].tolist() == g["need_tile0"]  # no predecessor: nothing to wait for
@@ -200,7 +215,7 @@ def test_tilewave_check_catches_a_weakened_plan(lib):
     plan shortened by one loop (planted on the CPU, in the test's copy of the
     table), the exact-conflict coverage fails on the CloverLeaf shape."""
     c = W.cloverleaf2d(n=64, steps=1)
-    need, cls, order = _plan(c.loops, c.stencils, 2, [32, 32])
+    need, cls, order, steps = _plan(c.loops, c.stencils, 2, [32, 32])
     nt, rg, _ = oplan.skewed_plan(c.loops, c.stencils, 2, [32, 32])
     ph = _tile_phases(c.loops, 2, nt, rg)
     exact = oplan.phase_conflicts(c.loops, c.stencils, 2, [(l, box) for _, l, box in ph])
