@@ -36,9 +36,10 @@ def workload(n: int) -> str:
             "reduction per step")
 PROFILE = os.path.join(ROOT, "profiles", "chain_cloverleaf2d_3840.md")
 KERNEL_SRC = [os.path.join(ROOT, "paper_1704_00693_gb300", "csrc", f) for f in ("jit.cpp", "chain_kernels.cu", "device_common.cuh")]
-# FP64: 2 DFMA per clock per SM on GB300 (measured 1.97 at 1995 MHz), fma = 2 flops
+# FP64 fallback when the probe is skipped: 2 DFMA per clock per SM on GB300, fma = 2 flops
 FP64_DFMA_PER_CLK_SM = 2
 NUM_SMS = 152
+SCHEDULES = {0: "untiled", 1: "skewed", 2: "overlapped", 3: "auto", 4: "wavefront", 5: "tilewave"}
 
 
 def parse():
@@ -48,7 +49,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--mode", default="auto", choices=["skewed", "untiled", "overlapped", "wavefront", "auto"])
+    p.add_argument("--mode", default="auto", choices=["skewed", "untiled", "overlapped", "wavefront", "tilewave", "auto"])
+    p.add_argument("--no-probe", action="store_true", help="skip the hardware probes (FP64 rate, L2, barriers)")
     p.add_argument("--tile", default="", help="x,y tile (0 = automatic)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
@@ -178,8 +180,10 @@ def time_mode(chain, mode, tile, steps, warmup, stream, torch, fp32=False):
     from paper_1704_00693_gb300.chain import ChainRunner
     r = ChainRunner(chain, mode=mode, tile=tile, stream=stream.cuda_stream, timing=False, fp32=fp32)
     try:
-        for _ in range(warmup):
+        for w in range(warmup):
             r.step()
+            if w == 0:
+                time_mode.first = r.stats()  # plan building and run-time compilation happen here
         # in auto mode, keep warming up until the autotuner has timed every candidate
         extra = 0
         while mode == "auto" and r.stats()["tuning"] and extra < 40:
@@ -454,19 +458,27 @@ def bench_cg(n=4000, tol=1e-10):
     return out
 
 
-def bench_chain(chain, stream, torch, steps=5):
-    """Autotuned schedule against the untiled form on one chain, effective GB/s of each."""
-    n = chain.size[0]
+def compare_schedules(chain, stream, torch, schedules, steps=5, fp32=False, bytes_per_elem=8):
+    """Effective GB/s of each (mode, tile) schedule of one chain, with the
+    speedup of each over the untiled form (the first entry)."""
     U, flops = workload_numbers(chain)
-    out = {"n": n, "untiled_bytes_per_step": U, "flops_per_step": flops}
-    for mode in ("auto", "untiled"):
-        ms, kms, kl, launches, st = time_mode(chain, mode, None, steps, 3, stream, torch)
-        out[mode] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
-                     "kernel_ms_per_step": kms / steps,
-                     "schedule": {0: "untiled", 1: "skewed", 2: "overlapped", 4: "wavefront"}.get(st["mode"]),
-                     "tile": st["tile"], "compiled": st["compiled"]}
-    out["speedup_auto_vs_untiled"] = out["untiled"]["ms_per_step"] / out["auto"]["ms_per_step"]
+    U = U * bytes_per_elem // 8
+    out = {"n": chain.size[0], "untiled_bytes_per_step": U, "flops_per_step": flops, "dtype": "f32" if fp32 else "f64"}
+    for mode, tile, key in schedules:
+        ms, kms, kl, launches, st = time_mode(chain, mode, tile, steps, 3, stream, torch, fp32=fp32)
+        first = getattr(time_mode, "first", None) or {}
+        out[key] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
+                    "kernel_ms_per_step": kms / steps, "schedule": SCHEDULES.get(st["mode"]), "tile": st["tile"],
+                    "tiles": st["tiles"], "plan_ms": first.get("plan_ms"), "compile_ms": first.get("compile_ms")}
+    for key in [k for k in out if isinstance(out[k], dict) and k != "untiled"]:
+        out[f"speedup_{key}_vs_untiled"] = out["untiled"]["ms_per_step"] / out[key]["ms_per_step"]
     return out
+
+
+def bench_chain(chain, stream, torch, steps=5):
+    """Autotuned schedule and the tile wavefront against the untiled form on one chain."""
+    return compare_schedules(chain, stream, torch, [("untiled", None, "untiled"), ("tilewave", None, "tilewave"),
+                                                    ("auto", None, "auto")], steps)
 
 
 def bench_opensbli3d(stream, torch, n=320, steps=5):
@@ -477,41 +489,28 @@ def bench_opensbli3d(stream, torch, n=320, steps=5):
 
 def bench_ppcg(stream, torch, n=4000, inner=10, steps=5):
     """The TeaLeaf-PPCG-shaped chain (one preconditioner application: 7
-    setup loops, 10 Chebyshev iterations of three loops, z.r): every
-    schedule, effective GB/s of each."""
+    setup loops, 10 Chebyshev iterations of three loops, z.r), the paper's
+    best tiling case: every schedule against untiled."""
     from synth import workloads as W
     chain = W.ppcg2d(n=n, inner=inner)
-    U, flops = workload_numbers(chain)
-    out = {"n": n, "inner": inner, "untiled_bytes_per_step": U, "flops_per_step": flops}
-    for mode in ("untiled", "skewed", "overlapped", "wavefront", "auto"):
-        ms, kms, kl, launches, st = time_mode(chain, mode, None, steps, 3, stream, torch)
-        out[mode] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
-                     "schedule": {0: "untiled", 1: "skewed", 2: "overlapped", 4: "wavefront"}.get(st["mode"]),
-                     "tile": st["tile"], "tiles": st["tiles"]}
-    for mode in ("skewed", "overlapped", "wavefront", "auto"):
-        out[f"speedup_{mode}_vs_untiled"] = out["untiled"]["ms_per_step"] / out[mode]["ms_per_step"]
+    out = compare_schedules(chain, stream, torch, [("untiled", None, "untiled"), ("tilewave", None, "tilewave"),
+                                                   ("skewed", None, "skewed"), ("wavefront", None, "wavefront"),
+                                                   ("overlapped", None, "overlapped"), ("auto", None, "auto")], steps)
+    out["inner"] = inner
     return out
 
 
 def bench_fp32(stream, torch, n=3840, steps=5):
     """The CloverLeaf-shaped chain in an OPS_REAL_F32 context (float dats and
     arithmetic): every schedule, effective GB/s at 4 bytes per element.  With
-    single-precision arithmetic the chain is bound by HBM, not by the FP64
-    pipe, which is where tiling pays."""
+    single-precision arithmetic the chain is bound by memory, not by the
+    FP64 pipe, which is where tiling pays."""
     from synth import workloads as W
     chain = W.cloverleaf2d(n=n, steps=1)
-    U, flops = workload_numbers(chain)
-    U = U // 2  # 4-byte elements
-    out = {"n": n, "untiled_bytes_per_step": U, "dtype": "f32"}
-    for mode, tile in (("untiled", None), ("skewed", None), ("skewed", [0, 1024, 0]), ("overlapped", None),
-                       ("wavefront", None), ("auto", None)):
-        ms, kms, kl, launches, st = time_mode(chain, mode, tile, steps, 3, stream, torch, fp32=True)
-        key = mode if tile is None else f"{mode}_{tile[1]}"
-        out[key] = {"value": U * steps / (ms * 1e-3) / 1e9, "unit": "GB/s", "ms_per_step": ms / steps,
-                    "schedule": {0: "untiled", 1: "skewed", 2: "overlapped", 4: "wavefront"}.get(st["mode"]), "tile": st["tile"]}
-    for key in [k for k in out if isinstance(out[k], dict) and k != "untiled"]:
-        out[f"speedup_{key}_vs_untiled"] = out["untiled"]["ms_per_step"] / out[key]["ms_per_step"]
-    return out
+    return compare_schedules(chain, stream, torch,
+                             [("untiled", None, "untiled"), ("tilewave", None, "tilewave"),
+                              ("skewed", [0, 1024, 0], "skewed_1024"), ("wavefront", None, "wavefront"),
+                              ("auto", None, "auto")], steps, fp32=True, bytes_per_elem=4)
 
 
 def bench_cloverleaf3d(stream, torch, n=330, steps=3):
@@ -638,7 +637,15 @@ def main():
         dist.init_process_group("nccl")
     from paper_1704_00693_gb300 import _build
     _build.build()
+    import paper_1704_00693_gb300 as ops
     from synth import workloads as W
+
+    probe = None
+    if not args.no_probe:
+        try:
+            probe = ops.ops_probe_device(local)
+        except ops.OpsError as e:
+            probe = {"error": str(e)}
 
     chain = W.cloverleaf2d(n=args.n, steps=1)
     U, flops = workload_numbers(chain)
@@ -660,21 +667,25 @@ def main():
     ms = max_over_ranks(ms)
     value = whole_job_gbs(U, args.steps, world, ms)
 
+    first = getattr(time_mode, "first", None) or {}
     untiled = None
     if not args.no_untiled and args.mode != "untiled":
         ums, ukms, ukl, _, _ = time_mode(chain, "untiled", None, args.steps, args.warmup, stream, torch)
         untiled = {"value": U * args.steps / (ums * 1e-3) / 1e9, "ms_per_step": ums / args.steps,
                    "kernel_ms_per_step": ukms / args.steps, "kernel_launches_per_step": ukl / args.steps}
-    wavefront = None
-    if not args.no_untiled and args.mode != "wavefront":
-        wms, wkms, wkl, _, wst = time_mode(chain, "wavefront", None, args.steps, args.warmup, stream, torch)
-        wavefront = {"value": U * args.steps / (wms * 1e-3) / 1e9, "ms_per_step": wms / args.steps,
-                     "kernel_ms_per_step": wkms / args.steps, "tile": wst["tile"], "phases": wst["phases"],
-                     "how": "OPS_MODE_WAVEFRONT: Algorithm 1 tiles of about 64 rows, one persistent kernel that "
-                            "runs (tile, loop) phases as their dependencies complete"}
+    tilewave = None
+    if not args.no_untiled and args.mode != "tilewave":
+        tms, tkms, tkl, _, tst = time_mode(chain, "tilewave", None, args.steps, args.warmup, stream, torch)
+        tfirst = getattr(time_mode, "first", None) or {}
+        tilewave = {"value": U * args.steps / (tms * 1e-3) / 1e9, "ms_per_step": tms / args.steps,
+                    "kernel_ms_per_step": tkms / args.steps, "tile": tst["tile"], "tiles": tst["tiles"],
+                    "plan": {"plan_ms": tfirst.get("plan_ms"), "compile_ms": tfirst.get("compile_ms"),
+                             "phases": tst["phases"], "steps": tst["barriers"], "skew": tst["skew"]},
+                    "how": "OPS_MODE_TILEWAVE: Algorithm 1 tiles cut in x and y, each run whole by one CTA, "
+                           "tiles concurrent with per-tile progress counters"}
 
     # the schedule the timed steps ran (the autotuner's pick in auto mode)
-    chosen_mode = {0: "untiled", 1: "skewed", 2: "overlapped", 4: "wavefront"}.get(st["mode"], "skewed") if st else args.mode
+    chosen_mode = SCHEDULES.get(st["mode"], "skewed") if st else args.mode
     chosen_tile = list(st["tile"]) if st and chosen_mode != "untiled" else None
     e2e = None
     if not args.no_e2e:
@@ -688,32 +699,42 @@ def main():
                       "contexts so copies overlap compute",
                "sequential_one_context": {"value": U * 3 / (sms * 1e-3) / 1e9, "ms_per_step": sms / 3}}
 
-    # roofline of the dominant kernel (one persistent launch per step in tiled mode)
-    kernel_ms_per_launch = kms / max(1, kl)
+    # roofline of the dominant kernel: the step's kernels (one per loop
+    # untiled, one persistent launch tiled), per launch.  Per-kernel events
+    # serialise launches that otherwise overlap (programmatic dependent
+    # launch), so the kernel time is capped by the step's own time.
+    step_ms = ms / args.steps
+    kernel_ms_step = min(kms / max(1, args.steps), step_ms)
     launches_per_step = kl / max(1, args.steps)
+    kernel_ms_per_launch = kernel_ms_step / max(1.0, launches_per_step)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except OSError:
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = NUM_SMS * FP64_DFMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12
-    flops_per_launch = flops / launches_per_step
+    if probe and probe.get("fp64_fma_tflops"):
+        peak_tflops = probe["fp64_fma_tflops"]
+        peak_source = ("FP64: measured by ops_probe_device on this GPU (every SM issuing independent DFMA "
+                       "chains, 2 flop each)")
+    else:
+        peak_tflops = NUM_SMS * FP64_DFMA_PER_CLK_SM * 2 * sm_max * 1e6 / 1e12
+        peak_source = f"FP64: {NUM_SMS} SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 flop x {sm_max:.0f} MHz (no probe)"
+    flops_per_launch = flops / max(1.0, launches_per_step)
     achieved = flops_per_launch / (kernel_ms_per_launch * 1e-3) / 1e12
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     traffic = profile_traffic(chosen_mode, chosen_tile) if args.n == N_DEFAULT else None
+    kernel_name = {"wavefront": "wf: the wavefront kernel, one launch per step",
+                   "tilewave": "tw: the tile-wavefront kernel, one launch per step"}.get(
+        chosen_mode, "u<i>: the loop bodies compiled from the IR, one kernel per loop, averaged over the step's "
+                     "launches" if st and st.get("compiled") else "k_untiled")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": achieved / peak_tflops, "traffic": traffic,
-                "kernel": "wf: the wavefront kernel, one launch per step" if chosen_mode == "wavefront" else
-                          ("u<i>: the loop bodies compiled from the IR, one kernel per loop, averaged over the "
-                           "step's launches") if st and st.get("compiled") else
-                          {"skewed": "k_skewed", "overlapped": "k_overlap"}.get(chosen_mode, "k_untiled"),
-                "peak_source": f"FP64: {NUM_SMS} SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 flop x {sm_max:.0f} MHz "
-                               "(unit count from a GB300 probe; MEASURED_PEAKS.json has no FP64 figure)",
-                "kernel_ms_per_launch": kernel_ms_per_launch,
+                "frac": achieved / peak_tflops, "traffic": traffic, "kernel": kernel_name,
+                "peak_source": peak_source, "kernel_ms_per_launch": kernel_ms_per_launch,
+                "kernel_time": "per-kernel CUDA events on the launching stream, capped by the step time",
                 "algorithmic_flops_per_launch": flops_per_launch,
-                "algorithmic_bytes_per_launch": U / launches_per_step,
-                "effective_hbm_frac": (U / launches_per_step) / (kernel_ms_per_launch * 1e-3) / 1e9 / hbm_peak,
+                "algorithmic_bytes_per_launch": U / max(1.0, launches_per_step),
+                "effective_hbm_frac": (U / max(1.0, launches_per_step)) / (kernel_ms_per_launch * 1e-3) / 1e9 / hbm_peak,
                 "hbm_peak_gbs": hbm_peak}
     if traffic is not None:
         roofline["dram_gbs"] = traffic / (kernel_ms_per_launch * 1e-3) / 1e9
@@ -737,11 +758,13 @@ def main():
                        "parallelism": "replicas" if world > 1 else "1 GPU",
                        "untiled_bytes_per_step": U, "flops_per_step": flops},
             "speedup_vs_untiled": (untiled["ms_per_step"] / (ms / args.steps)) if untiled else None,
-            "untiled": untiled, "wavefront": wavefront, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "untiled": untiled, "tilewave": tilewave, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
             "cg_4000": cg, "serving": serving, "opensbli3d_320": chain3d, "cloverleaf3d_330": hydro3d, "ppcg_4000": ppcg, "cloverleaf2d_3840_fp32": fp32,
             "plan": {"phases": st["phases"], "barriers": st["barriers"], "skew": st["skew"],
-                     "plan_cache_hits": st["plan_cache_hits"]} if st else None}
+                     "plan_ms_first_flush": first.get("plan_ms"), "compile_ms_first_flush": first.get("compile_ms"),
+                     "plan_cache_hits": st["plan_cache_hits"]} if st else None,
+            "probe": probe}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -262,7 +262,8 @@ typedef struct {
   int loops;             /* loops executed */
   int tiles;             /* tiles in the last skewed / overlapped segment */
   int phases;            /* non-empty (tile, loop) pieces executed */
-  int barriers;          /* grid barriers executed by persistent kernels */
+  int barriers;          /* grid barriers executed by persistent kernels; OPS_MODE_TILEWAVE: the
+                            CTA-wide steps (groups of loops) over all tiles */
   int launches;          /* kernel launches issued by the flush */
   int plan_cache_hits;   /* segments whose plan came from the cache */
   int mode;              /* OPS_MODE_* of the last segment */

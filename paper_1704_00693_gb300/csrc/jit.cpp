@@ -1378,6 +1378,11 @@ int jit_compile_overlap_only(const DLoop* loops, int count, const OvLayout& lay,
   return OPS_OK;
 }
 
+bool jit_available() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return api_ready(nullptr);
+}
+
 int jit_pdl() {
   static const int v = env_int("OPSTILE_PDL", 1, 0, 1);
   return v;
@@ -1576,6 +1581,11 @@ int jit_tile_prefetch() {
 
 int jit_tile_group() {
   static const int v = env_int("OPSTILE_TW_GROUP", kTwMaxGroup, 1, kTwMaxGroup);
+  return v;
+}
+
+int jit_tile_band() {
+  static const int v = env_int("OPSTILE_TW_BAND", 16, 0, 1 << 20);
   return v;
 }
 

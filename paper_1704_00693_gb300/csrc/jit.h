@@ -37,6 +37,8 @@ int jit_compile_only(const DLoop* loops, int count, const std::vector<std::vecto
 // predecessor in the stream drains, and wait on the device
 // (griddepcontrol.wait) until the predecessor has completed.
 int jit_pdl();
+// true when NVRTC and the driver's module calls can be reached
+bool jit_available();
 // CTAs of kernel u<i> resident per SM (queried once per kernel).
 int jit_resident(JitSegment* s, int i);
 // Grid policy of the compiled per-loop kernels (OPSTILE_JIT_GRID): 0 (the
@@ -151,6 +153,8 @@ int jit_tile_prefetch();
 int jit_tile_ahead();
 // loops of one tile step at most (OPSTILE_TW_GROUP, 1..8, default 8)
 int jit_tile_group();
+// tiles along x per strip of the ticket order (OPSTILE_TW_BAND; 0 = one strip)
+int jit_tile_band();
 int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es, int ndim,
                  JitTile** out, std::string* why, double* compile_ms);
 int jit_compile_tilewave_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,

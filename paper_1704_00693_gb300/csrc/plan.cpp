@@ -367,7 +367,7 @@ inline bool meet(int alo, int ahi, int blo, int bhi) { return alo < ahi && blo <
 }  // namespace
 
 bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& P, TileWavePlan& out, std::string* why,
-                     int max_group) {
+                     int max_group, int band) {
   const int L = (int)loops.size();
   const int nd = P.ndim;
   out = TileWavePlan();
@@ -552,16 +552,21 @@ bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& P, TileW
     }
     out.groups.push_back(L);
   }
-  // tickets: by coordinate sum, then z, y, x
+  // tickets: strip by strip of `band` tiles along x, and inside a strip by
+  // coordinate sum, then z, y, x
   out.order.clear();
   out.order.reserve((size_t)Tn[0] * Tn[1] * Tn[2]);
-  for (int s = 0; s <= Tn[0] + Tn[1] + Tn[2] - 3; ++s)
-    for (int tz = 0; tz < Tn[2]; ++tz)
-      for (int ty = 0; ty < Tn[1]; ++ty) {
-        const int tx = s - tz - ty;
-        if (tx < 0 || tx >= Tn[0]) continue;
-        out.order.push_back((tz * Tn[1] + ty) * Tn[0] + tx);
-      }
+  const int bw = band > 0 ? std::min(band, Tn[0]) : Tn[0];
+  for (int b0 = 0; b0 < Tn[0]; b0 += bw) {
+    const int w = std::min(bw, Tn[0] - b0);
+    for (int s = 0; s <= w + Tn[1] + Tn[2] - 3; ++s)
+      for (int tz = 0; tz < Tn[2]; ++tz)
+        for (int ty = 0; ty < Tn[1]; ++ty) {
+          const int tl = s - tz - ty;
+          if (tl < 0 || tl >= w) continue;
+          out.order.push_back((tz * Tn[1] + ty) * Tn[0] + b0 + tl);
+        }
+  }
   return true;
 }
 

@@ -99,9 +99,13 @@ void build_overlap_tile(const std::vector<PLoop>& loops, int ndats, int ndim, co
 // order holds for every pair of accesses (monotonicity) and that no access
 // reaches data an access two or more tiles back touches.  Tiles whose
 // per-dimension neighbourhoods have identical relative ranges share a class.
-// Tickets hand out tiles by the sum of their tile coordinates (then z, y,
-// x): every predecessor has a smaller sum, so the earliest unfinished tile
-// never waits on a later one.
+// Tickets hand out tiles strip by strip (strips of `band` tiles along x; 0:
+// one strip), and inside a strip by the sum of their tile coordinates
+// (then z, y, x): every predecessor is in the same or an earlier strip and
+// has a smaller sum, so the earliest unfinished tile never waits on a later
+// one.  Narrow strips keep the tiles in flight together in one compact
+// region, whose data (the tiles' and their skew halos, shared between
+// neighbours) then fits L2.
 struct TileWavePlan {
   int ndim = 0, ndirs = 0;
   int dirs[7][3] = {};
@@ -120,6 +124,6 @@ struct TileWavePlan {
 };
 // max_group caps the loops of one step (1: a step per loop)
 bool build_tile_wave(const std::vector<PLoop>& loops, const SkewedPlan& plan, TileWavePlan& out, std::string* why,
-                     int max_group = 8);
+                     int max_group = 8, int band = 0);
 
 }  // namespace opstile

@@ -79,6 +79,8 @@ struct CachedPlan {
   int tw_roff[3] = {0, 0, 0}, tw_coff[3] = {0, 0, 0};
   int* d_twprog = nullptr;
   int tw_ntiles = 0;
+  int tw_phases = 0;  // non-empty (tile, loop) pieces
+  int tw_steps = 0;   // CTA-wide steps (block barriers between loop groups) over all tiles
   DD* d_twpart = nullptr;
   int tw_rows = 0;
 };
@@ -1111,9 +1113,11 @@ int tile_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, Jit
 }
 
 // Automatic tile of the tile wavefront: the tiles the resident CTAs hold
-// at once should fit about half the cache budget (bytes per point = element
-// size x the distinct dats of the segment), with 512 to 8192 points per
-// tile; x takes up to 128 points, the other dimensions share the rest.
+// at once (with the banded ticket order they sit together in one region)
+// should fit about 70% of the cache budget, at element size x the distinct
+// dats of the segment bytes per point, with 512 to 8192 points per tile;
+// x takes up to 64 points (two warp-wide chunks), the other dimensions share
+// the rest.  Tiles the chain's skew reaches across are grown by the planner.
 void auto_tile_wave(ops_ctx c, const std::vector<PLoop>& pl, int ndim, int tile[3]) {
   std::vector<char> used(c->dats.size(), 0);
   int ndat = 0;
@@ -1132,13 +1136,13 @@ void auto_tile_wave(ops_ctx c, const std::vector<PLoop>& pl, int ndim, int tile[
   const int64_t budget = c->cfg.l2_bytes > 0 ? c->cfg.l2_bytes : (c->l2_size > 0 ? c->l2_size * 3 / 4 : 96ll << 20);
   const int64_t bpp = (int64_t)c->es * std::max(1, ndat);
   const int64_t ctas = (int64_t)std::max(1, c->num_sms) * jit_tile_min_ctas();
-  const int64_t pts = std::min<int64_t>(8192, std::max<int64_t>(512, budget / 2 / (ctas * bpp)));
+  const int64_t pts = std::min<int64_t>(8192, std::max<int64_t>(512, budget * 7 / 10 / (ctas * bpp)));
   int ext[3];
   for (int d = 0; d < 3; ++d) {
     ext[d] = std::max(1, hi[d] - lo[d]);
     tile[d] = 1;
   }
-  tile[0] = (int)std::min<int64_t>(ext[0], ndim == 1 ? pts : 128);
+  tile[0] = (int)std::min<int64_t>(ext[0], ndim == 1 ? pts : 64);
   const int64_t rest = std::max<int64_t>(1, pts / tile[0]);
   if (ndim == 2) tile[1] = (int)std::min<int64_t>(ext[1], rest);
   if (ndim == 3) {
@@ -1170,7 +1174,8 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
       if (tile[d] <= 0) tile[d] = at[d];
   }
   for (int d = ndim; d < 3; ++d) tile[d] = 1;
-  std::vector<int> key = {-OPS_MODE_TILEWAVE, ndim, tile[0], tile[1], tile[2], jit_tile_group(), jit_tile_prefetch()};
+  std::vector<int> key = {-OPS_MODE_TILEWAVE, ndim, tile[0], tile[1], tile[2],
+                          jit_tile_group(), jit_tile_prefetch(), jit_tile_band()};
   for (int i = 0; i < count; ++i) {
     const QLoop& q = c->queue[first + i];
     for (int k = 0; k < 6; ++k) key.push_back(q.rng[k]);
@@ -1195,7 +1200,7 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
   bool ok = false;
   for (int attempt = 0; attempt < 24; ++attempt) {
     build_skewed_ranges(pl, (int)c->dats.size(), ndim, tile, np->plan);
-    if (build_tile_wave(pl, np->plan, np->tw, &why, jit_tile_group())) {
+    if (build_tile_wave(pl, np->plan, np->tw, &why, jit_tile_group(), jit_tile_band())) {
       ok = true;
       break;
     }
@@ -1269,6 +1274,24 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
     }
   }
   np->tw_rows = rows;
+  {
+    // phases: per loop, the product over dimensions of the tiles its range meets;
+    // steps: per tile, the loop groups with at least one non-empty loop
+    int64_t ph = 0, st = 0;
+    for (int l = 0; l < count; ++l) {
+      int64_t k = 1;
+      for (int d = 0; d < ndim; ++d) {
+        int m = 0;
+        for (int t = 0; t < P.ntiles[d]; ++t)
+          m += P.ranges[d][2 * (t * count + l) + 1] > P.ranges[d][2 * (t * count + l)];
+        k *= m;
+      }
+      ph += k;
+    }
+    st = (int64_t)ntiles * ((int64_t)W.groups.size() - 1);
+    np->tw_phases = (int)std::min<int64_t>(ph, 1 << 30);
+    np->tw_steps = (int)std::min<int64_t>(st, 1 << 30);
+  }
   int rc = dev_alloc(c, &np->d_tw, np->tw_bytes);
   if (!rc) rc = dev_alloc(c, (void**)&np->d_twprog, sizeof(int) * (ntiles + 1));
   if (!rc && rows) rc = dev_alloc(c, (void**)&np->d_twpart, sizeof(DD) * (size_t)rows * ntiles);
@@ -1307,6 +1330,8 @@ int run_tilewave(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop
     c->stats.skew[d] = P.skew[d];
   }
   c->stats.tiles = cp->tw_ntiles;
+  c->stats.phases += cp->tw_phases;
+  c->stats.barriers += cp->tw_steps;
   int64_t pts = 0;
   for (int l = 0; l < count; ++l) {
     int64_t n = 1;
@@ -1664,16 +1689,27 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<D
         break;
       }
     T.cand.push_back({OPS_MODE_UNTILED, 0, 0, 0, 0});
-    for (int f = 1; f <= 16; f *= 2) {
+    // the tile wavefront with its automatic tiles and two larger shapes
+    // (run-time compiled, so only where NVRTC is there)
+    if (count > 1 && !c->cfg.interpret && !c->cfg.check && jit_available()) {
+      T.cand.push_back({OPS_MODE_TILEWAVE, 0, 0, 0, 0});
+      if (ndim == 2) {
+        T.cand.push_back({OPS_MODE_TILEWAVE, 128, 64, 0, 0});
+        T.cand.push_back({OPS_MODE_TILEWAVE, 256, 32, 0, 0});
+      } else if (ndim == 3) {
+        T.cand.push_back({OPS_MODE_TILEWAVE, 64, 32, 32, 0});
+      }
+    }
+    // Algorithm 2 with every CTA on one L2-sized tile, at the seed tile and 4x taller
+    for (int f = 1; f <= 4; f *= 4) {
       std::array<int, 5> cd = {OPS_MODE_SKEWED, at[0], at[1], at[2], 0};
       cd[1 + od] = (int)std::min<int64_t>((int64_t)at[od] * f, ext[od]);
       T.cand.push_back(cd);
       if (cd[1 + od] >= ext[od]) break;
     }
-    // shorter segments: less skew, so the automatic tile of each part is larger
-    for (int parts = 2; parts <= 4 && count / parts >= 4; parts *= 2)
-      T.cand.push_back({OPS_MODE_SKEWED, 0, 0, 0, (count + parts - 1) / parts});
-    if (count > 1) T.cand.push_back({OPS_MODE_OVERLAPPED, 0, 0, 0, 0});
+    // Overlapped tiles are not a candidate: on GB300 their redundant halo
+    // work and one-CTA-per-SM footprints made them 4-10x slower than
+    // untiled on every chain measured; OPS_MODE_OVERLAPPED still runs them.
     T.ms.assign(T.cand.size(), -1.0);
     T.runs.assign(T.cand.size(), 0);
     CUDA_TRY(c, cudaEventCreate(&T.e0));
@@ -2310,7 +2346,8 @@ int ops_plan_tilewave(ops_ctx c, const int* tile, int64_t* counts, int* out_need
   build_skewed_ranges(pl, (int)c->dats.size(), ndim, t, P);
   TileWavePlan W;
   std::string why;
-  if (!build_tile_wave(pl, P, W, &why, jit_tile_group())) return fail(c, OPS_ERR_INVALID_ARG, "%s", why.c_str());
+  if (!build_tile_wave(pl, P, W, &why, jit_tile_group(), jit_tile_band()))
+    return fail(c, OPS_ERR_INVALID_ARG, "%s", why.c_str());
   const int64_t ntiles = (int64_t)P.ntiles[0] * P.ntiles[1] * P.ntiles[2];
   const int64_t ncl = (int64_t)W.ncls[0] * W.ncls[1] * W.ncls[2];
   counts[0] = ntiles;

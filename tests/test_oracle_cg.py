@@ -91,3 +91,19 @@ def test_refinement_reaches_tolerance_and_matches_fp64():
     assert rel <= 1e-10 and outer >= 2
     assert oracle.relres(kappa, b, xr) <= 1e-10
     assert np.abs(xr - x64).max() <= 1e-8 * np.abs(x64).max()
+
+
+def test_refinement_inner_cg_eigenmode_one_iteration():
+    """The FP32 inner CG on an eigenvector right-hand side: its Krylov space
+    has one dimension, so with the right step length the first inner solve
+    ends after one iteration with an FP32-rounding-level residual (about
+    1e-7 relative), and one correction already meets a 1e-6 tolerance.  A
+    wrong step length (or a wrong dot product in it) leaves a residual near
+    the right-hand side's size and needs many more iterations."""
+    n, kap, p, q = 31, 0.7, 2, 3
+    b = _eigvec(n, p, q)
+    xr, it, rel, outer = oracle.cg_refine(np.full((n, n), kap), b, tol=1e-6, inner_tol=1e-4)
+    assert it == 1 and outer == 1
+    assert 1e-9 < rel <= 1e-6  # an FP32 solve: rounding level, not an FP64 one
+    mu = 1 + kap * (4 * math.sin(math.pi * p / (2 * (n + 1))) ** 2 + 4 * math.sin(math.pi * q / (2 * (n + 1))) ** 2)
+    assert np.abs(xr - b / mu).max() <= 1e-6 * np.abs(b / mu).max()
