@@ -1556,11 +1556,8 @@ cudaError_t jit_launch_wavefront(const JitWave* w, const LaunchEnv& env, const D
 
 
 int jit_tile_threads() {
-  static const int v = [] {
-    int t = env_int("OPSTILE_TW_THREADS", 256, 128, 512), p = 128;
-    while (p * 2 <= t) p *= 2;
-    return p;
-  }();
+  // whole warps, with room for the control warp in a 1024-thread CTA
+  static const int v = env_int("OPSTILE_TW_THREADS", 256, 128, 992) / 32 * 32;
   return v;
 }
 
@@ -1570,7 +1567,7 @@ int jit_tile_min_ctas() {
 }
 
 int jit_tile_pts(int es) {
-  static const int v32 = env_int("OPSTILE_TW_PTS32", 4, 1, 8), v64 = env_int("OPSTILE_TW_PTS", 2, 1, 8);
+  static const int v32 = env_int("OPSTILE_TW_PTS32", 8, 1, 8), v64 = env_int("OPSTILE_TW_PTS", 4, 1, 8);
   return es == 4 ? v32 : v64;
 }
 

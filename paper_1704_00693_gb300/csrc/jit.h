@@ -138,9 +138,10 @@ struct TwArgs {
   const int* groups;         // the loops of step g: groups[g] .. groups[g + 1]
 };
 struct JitTile;
-// threads per CTA (OPSTILE_TW_THREADS: 128, 256 (default) or 512), CTAs per
-// SM the registers are sized for (OPSTILE_TW_MINB, default 2) and points a
-// thread evaluates at a time (OPSTILE_TW_PTS; default 4 in FP32, 2 in FP64)
+// compute threads per CTA (OPSTILE_TW_THREADS: whole warps, 128..992, default 256), CTAs per
+// SM the registers are sized for (OPSTILE_TW_MINB, default 2) and rows a
+// thread evaluates at a time (OPSTILE_TW_PTS32 / OPSTILE_TW_PTS; default 8 in
+// FP32, 4 in FP64: the fastest measured on GB300)
 int jit_tile_threads();
 int jit_tile_min_ctas();
 int jit_tile_pts(int es);

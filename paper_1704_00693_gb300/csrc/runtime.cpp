@@ -1112,44 +1112,24 @@ int tile_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, Jit
   return OPS_OK;
 }
 
-// Automatic tile of the tile wavefront: the tiles the resident CTAs hold
-// at once (with the banded ticket order they sit together in one region)
-// should fit about 70% of the cache budget, at element size x the distinct
-// dats of the segment bytes per point, with 512 to 8192 points per tile;
-// x takes up to 64 points (two warp-wide chunks), the other dimensions share
-// the rest.  Tiles the chain's skew reaches across are grown by the planner.
+// Automatic tile of the tile wavefront: 128 x 64 points in FP32 and 64 x 64
+// in FP64 (2D), 64 x 16 x 16 (3D) -- the fastest shapes measured on GB300
+// for the CloverLeaf- and PPCG-shaped chains; smaller, L2-sized tiles made
+// more, shorter steps and ran slower.  Dimensions are capped by the extent,
+// and tiles the chain's skew reaches across are grown by the planner.
 void auto_tile_wave(ops_ctx c, const std::vector<PLoop>& pl, int ndim, int tile[3]) {
-  std::vector<char> used(c->dats.size(), 0);
-  int ndat = 0;
   int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
-  for (const PLoop& p : pl) {
-    for (const PArg& a : p.args)
-      if (a.kind == OPS_ARG_DAT && !used[a.dat]) {
-        used[a.dat] = 1;
-        ++ndat;
-      }
+  for (const PLoop& p : pl)
     for (int d = 0; d < 3; ++d) {
       lo[d] = std::min(lo[d], p.rng[2 * d]);
       hi[d] = std::max(hi[d], p.rng[2 * d + 1]);
     }
-  }
-  const int64_t budget = c->cfg.l2_bytes > 0 ? c->cfg.l2_bytes : (c->l2_size > 0 ? c->l2_size * 3 / 4 : 96ll << 20);
-  const int64_t bpp = (int64_t)c->es * std::max(1, ndat);
-  const int64_t ctas = (int64_t)std::max(1, c->num_sms) * jit_tile_min_ctas();
-  const int64_t pts = std::min<int64_t>(8192, std::max<int64_t>(512, budget * 7 / 10 / (ctas * bpp)));
-  int ext[3];
+  const int shape2[2] = {c->es == 4 ? 128 : 64, 64}, shape3[3] = {64, 16, 16};
   for (int d = 0; d < 3; ++d) {
-    ext[d] = std::max(1, hi[d] - lo[d]);
-    tile[d] = 1;
-  }
-  tile[0] = (int)std::min<int64_t>(ext[0], ndim == 1 ? pts : 64);
-  const int64_t rest = std::max<int64_t>(1, pts / tile[0]);
-  if (ndim == 2) tile[1] = (int)std::min<int64_t>(ext[1], rest);
-  if (ndim == 3) {
-    int s = 1;
-    while ((int64_t)(s + 1) * (s + 1) <= rest) ++s;
-    tile[1] = std::min(ext[1], s);
-    tile[2] = std::min(ext[2], (int)std::max<int64_t>(1, rest / s));
+    const int ext = std::max(1, hi[d] - lo[d]);
+    int want = 1;
+    if (d < ndim) want = ndim == 1 ? 8192 : (ndim == 2 ? shape2[d] : shape3[d]);
+    tile[d] = std::min(ext, want);
   }
 }
 
@@ -1689,13 +1669,13 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<D
         break;
       }
     T.cand.push_back({OPS_MODE_UNTILED, 0, 0, 0, 0});
-    // the tile wavefront with its automatic tiles and two larger shapes
+    // the tile wavefront with its automatic tiles and two other shapes
     // (run-time compiled, so only where NVRTC is there)
     if (count > 1 && !c->cfg.interpret && !c->cfg.check && jit_available()) {
       T.cand.push_back({OPS_MODE_TILEWAVE, 0, 0, 0, 0});
       if (ndim == 2) {
-        T.cand.push_back({OPS_MODE_TILEWAVE, 128, 64, 0, 0});
         T.cand.push_back({OPS_MODE_TILEWAVE, 256, 32, 0, 0});
+        T.cand.push_back({OPS_MODE_TILEWAVE, 128, 32, 0, 0});
       } else if (ndim == 3) {
         T.cand.push_back({OPS_MODE_TILEWAVE, 64, 32, 32, 0});
       }
