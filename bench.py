@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--no-cg", action="store_true", help="skip the 4000^2 CG measurement")
     p.add_argument("--no-3d", action="store_true", help="skip the other chains (OpenSBLI 3D, CloverLeaf 3D, PPCG)")
     p.add_argument("--serve-requests", type=int, default=512)
+    p.add_argument("--no-batch", action="store_true", help="skip the batched small-grid chains")
     return p.parse_args()
 
 
@@ -519,6 +520,70 @@ def bench_cloverleaf3d(stream, torch, n=330, steps=3):
     return bench_chain(W.cloverleaf3d(n=n, steps=1), stream, torch, steps)
 
 
+def bench_batch(torch, chain, count=64, steps=5, warmup=3):
+    """Many small grids' chains: `count` instances of `chain` (same loops,
+    own field values) stepped together.  Batched: per step every context
+    queues its chain and one ops_execute_batch runs each segment of all of
+    them: untiled with one launch per loop for all grids, the tile
+    wavefront in one launch (automatic tiles), or as the batch autotuner
+    picks (auto); sequential: every context flushes on its own (ops_execute,
+    each on its own stream, so their kernels may overlap).
+    Either way every reduction of every grid is read each step (the
+    CloverLeaf time step feeds the next step).  Host wall clock over the
+    timed steps, device idle on both sides."""
+    from paper_1704_00693_gb300 import ops_execute, ops_reduction_result
+    from paper_1704_00693_gb300.chain import ChainRunner, run_batch
+    from synth import workloads as W
+    chains = W.instances(chain, count)
+    out = {"workload": f"{count} x {chain.name}", "count": count, "loops_per_chain": len(chain.loops),
+           "unit": "chains/s", "how": "host wall clock, synchronize on both sides; a chain = one step of one grid"}
+
+    def seq_step(runners):
+        for r in runners:
+            r.enqueue_step()
+            ops_execute(r.ctx)
+        for r in runners:
+            vals = [ops_reduction_result(r.ctx, h) for h in r.reds]
+            if r.chain.dt_red >= 0:
+                r.dt = vals[r.chain.dt_red]
+
+    shared = torch.cuda.Stream()
+    for key, mode, batched in (("sequential_untiled", "untiled", False), ("sequential_auto", "auto", False),
+                               ("batched_untiled", "untiled", True), ("batched_tilewave", "tilewave", True),
+                               ("batched_auto", "auto", True)):
+        # a batch's contexts share one stream (no cross-stream joins); the
+        # sequential contexts each have their own, so their kernels may overlap
+        runners = [ChainRunner(c, mode=mode, stream=shared.cuda_stream if batched else 0) for c in chains]
+        try:
+            def one():
+                if batched:
+                    run_batch(runners, 1, sync=False)
+                else:
+                    seq_step(runners)
+            for _ in range(warmup):
+                one()
+            extra = 0
+            while mode == "auto" and any(r.stats()["tuning"] for r in runners[:1]) and extra < 40:
+                one()
+                extra += 1
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(steps):
+                one()
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            st = runners[0].stats()
+            out[key] = {"value": count * steps / sec, "ms_per_step": sec * 1e3 / steps,
+                        "schedule": SCHEDULES.get(st["mode"]), "tile": st["tile"], "tiles_per_grid": st["tiles"],
+                        "batched": st["batched"]}
+        finally:
+            for r in runners:
+                r.close()
+    best_seq = max(out["sequential_untiled"]["value"], out["sequential_auto"]["value"])
+    out["speedup_batched_auto_vs_best_sequential"] = out["batched_auto"]["value"] / best_seq
+    return out
+
+
 def cpu_baseline(n_full, seconds=12.0):
     """The oracle (untiled, program order, FP64, all host cores) on a bounded
     sample: one step of the same chain on a grid with 1/4 of the points."""
@@ -748,6 +813,10 @@ def main():
     ppcg = bench_ppcg(stream, torch) if rank == 0 and not args.no_3d else None
     fp32 = bench_fp32(stream, torch) if rank == 0 and not args.no_3d else None
     serving = bench_serving(args.serve_requests) if rank == 0 and not args.no_serve else None
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = {"cloverleaf2d_256": bench_batch(torch, W.cloverleaf2d(n=256, steps=1)),
+                 "small2d_256": bench_batch(torch, W.small2d(n=256, reps=10))}
 
     line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -760,7 +829,7 @@ def main():
             "speedup_vs_untiled": (untiled["ms_per_step"] / (ms / args.steps)) if untiled else None,
             "untiled": untiled, "tilewave": tilewave, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
-            "cg_4000": cg, "serving": serving, "opensbli3d_320": chain3d, "cloverleaf3d_330": hydro3d, "ppcg_4000": ppcg, "cloverleaf2d_3840_fp32": fp32,
+            "cg_4000": cg, "serving": serving, "batch": batch, "opensbli3d_320": chain3d, "cloverleaf3d_330": hydro3d, "ppcg_4000": ppcg, "cloverleaf2d_3840_fp32": fp32,
             "plan": {"phases": st["phases"], "barriers": st["barriers"], "skew": st["skew"],
                      "plan_ms_first_flush": first.get("plan_ms"), "compile_ms_first_flush": first.get("compile_ms"),
                      "plan_cache_hits": st["plan_cache_hits"]} if st else None,

@@ -228,6 +228,31 @@ int ops_par_loop(ops_ctx ctx, int block, int dims, const int* range, int nargs, 
 /* Run every queued loop (Sec. 4.A flush).  Returns after the work is
  * queued on the stream; device errors surface at the next ops_sync. */
 int ops_execute(ops_ctx ctx);
+/* Batched flush of several grids' chains (not in the paper, whose chains run
+ * one grid per process; the chain and its tiling are those of Sec. 4):
+ * ctxs[0 .. count) each hold a queued chain that matches the first
+ * context's loop for loop in everything but the dats' addresses and the
+ * loops' constants -- the same loop bodies, ranges, stencils, reductions,
+ * scalars and dat shapes, declared in the same order (typically the same
+ * program run on count grids of one size).  Each segment of the chains
+ * runs for every context at once, in ctxs[0]'s mode and tile:
+ * OPS_MODE_UNTILED as one launch per loop for all contexts (one CTA row per
+ * context); OPS_MODE_TILEWAVE as one launch of the tile wavefront whose
+ * tickets interleave every context's tiles (one plan for all; progress
+ * counters, reductions and scalars per context); OPS_MODE_AUTO as the batch
+ * autotuner picks among those two (the wavefront at its automatic tiles,
+ * with the whole grid as one tile, and with half-height tiles), timed per
+ * segment signature and batch size; any other mode runs each context's
+ * segment on its own.  Every dat and reduction ends exactly as if each
+ * context had called ops_execute alone.  The work goes on ctxs[0]'s stream;
+ * every other context's stream waits for it, so later calls on any of the
+ * contexts follow the batch.  Device-side errors of a batched launch
+ * (OPS_ERR_TIMEOUT) surface at ops_sync of ctxs[0].  Errors:
+ * OPS_ERR_INVALID_ARG (NULL, count < 1, a context twice, another device or
+ * precision, or chains that differ; nothing runs and every queue is kept),
+ * any error of ops_execute.  ops_last_stats of each context reports
+ * batched = count for segments that ran in one launch. */
+int ops_execute_batch(ops_ctx* ctxs, int count);
 /* Drop every queued loop without running it. */
 int ops_queue_clear(ops_ctx ctx);
 /* Flush, wait, copy the reduction's value to *host_out and reset it. */
@@ -277,6 +302,8 @@ typedef struct {
   int tuning;            /* OPS_MODE_AUTO: 1 while the autotuner is still timing candidates */
   int compiled;          /* 1: the last untiled / skewed segment ran compiled loop bodies */
   double compile_ms;     /* host time spent generating and compiling loop bodies in this flush */
+  int batched;           /* ops_execute_batch: contexts whose segments ran in the same launch as
+                            this one's (0: not batched) */
 } ops_flush_stats;
 /* Statistics of the most recent flush; with timing=1 this waits for that
  * flush's kernels to finish. */
@@ -338,6 +365,9 @@ int ops_compile_queued_wavefront(ops_ctx ctx, char* src_out, int64_t cap, int64_
 
 /* The same for the tile-wavefront kernel of the queued loops (OPS_MODE_TILEWAVE). */
 int ops_compile_queued_tilewave(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
+/* The same for the batch form of the tile-wavefront kernel (ops_execute_batch). */
+int ops_compile_queued_tilewave_batch(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len,
+                                      double* compile_ms);
 
 /* ---- heat-conduction solves (TeaLeaf-shaped, Sec. 5 and Sec. 6.D) ----
  * Solve A x = b on an n x n cell grid for the implicit heat-conduction

@@ -65,7 +65,7 @@ class ops_flush_stats(C.Structure):
                 ("phases", C.c_int), ("barriers", C.c_int), ("launches", C.c_int), ("plan_cache_hits", C.c_int),
                 ("mode", C.c_int), ("tile", C.c_int * 3), ("redundant_points", C.c_int64), ("points", C.c_int64),
                 ("skew", C.c_int * 3), ("kernel_ms", C.c_double), ("kernel_launches", C.c_int),
-                ("tuning", C.c_int), ("compiled", C.c_int), ("compile_ms", C.c_double)]
+                ("tuning", C.c_int), ("compiled", C.c_int), ("compile_ms", C.c_double), ("batched", C.c_int)]
 
     def as_dict(self):
         return {k: (list(getattr(self, k)) if k in ("tile", "skew") else getattr(self, k))
@@ -197,6 +197,12 @@ def ops_par_loop(ctx, block: int, dims: int, rng, args, code, consts, name: str 
 
 def ops_execute(ctx):
     _check(ctx, load().ops_execute(ctx))
+
+
+def ops_execute_batch(ctxs):
+    """Flush the matching chains queued on every context of ctxs as one batch."""
+    arr = (C.c_void_p * len(ctxs))(*[c.value if isinstance(c, C.c_void_p) else c for c in ctxs])
+    _check(ctxs[0] if len(ctxs) else None, load().ops_execute_batch(arr, C.c_int(len(ctxs))))
 
 
 def ops_sync(ctx):
@@ -333,13 +339,15 @@ def ops_plan_tilewave(ctx, tile):
             steps)
 
 
-def ops_compile_queued(ctx, want_source: bool = False, wavefront: bool = False, tilewave: bool = False):
+def ops_compile_queued(ctx, want_source: bool = False, wavefront: bool = False, tilewave: bool = False,
+                       batch: bool = False):
     """Generate and compile (NVRTC, sm_103a, no device) the loop bodies of the
     queued loops -- the per-loop and overlapped-tile kernels, or with
     wavefront=True the wavefront kernel, with tilewave=True the
-    tile-wavefront kernel; returns (source or None, source length, compile
-    ms)."""
-    f = (load().ops_compile_queued_tilewave if tilewave else
+    tile-wavefront kernel (batch=True: its batch form); returns (source or
+    None, source length, compile ms)."""
+    f = (load().ops_compile_queued_tilewave_batch if tilewave and batch else
+         load().ops_compile_queued_tilewave if tilewave else
          load().ops_compile_queued_wavefront if wavefront else load().ops_compile_queued)
     n = C.c_int64(0)
     ms = C.c_double(0.0)

@@ -14,8 +14,8 @@ from typing import List, Optional
 import numpy as np
 
 from . import (OPS_ARG_DAT, OPS_MODE_AUTO, MODES, ops_config_default, ops_dat_fetch, ops_dat_upload,
-               ops_decl_block, ops_decl_dat, ops_decl_reduction, ops_decl_stencil, ops_execute, ops_finalize,
-               ops_init, ops_last_stats, ops_par_loop, ops_reduction_result, ops_set_mode, ops_sync)
+               ops_decl_block, ops_decl_dat, ops_decl_reduction, ops_decl_stencil, ops_execute, ops_execute_batch,
+               ops_finalize, ops_init, ops_last_stats, ops_par_loop, ops_reduction_result, ops_set_mode, ops_sync)
 
 
 class ChainRunner:
@@ -139,3 +139,24 @@ class ChainRunner:
         if self.own_ctx and self.ctx is not None:
             ops_finalize(self.ctx)
             self.ctx = None
+
+
+def run_batch(runners: List[ChainRunner], steps: Optional[int] = None, sync: bool = True):
+    """Step the runners' chains together: per step every chain is queued,
+    all are flushed by one ops_execute_batch, then every reduction of every
+    runner is read (each runner's next dt comes from its own)."""
+    n = runners[0].chain.steps if steps is None else steps
+    ctxs = [r.ctx for r in runners]
+    for _ in range(n):
+        for r in runners:
+            r.enqueue_step()
+        ops_execute_batch(ctxs)
+        for r in runners:
+            vals = [ops_reduction_result(r.ctx, h) for h in r.reds]
+            r.history.append(vals)
+            if r.chain.dt_red >= 0:
+                r.dt = vals[r.chain.dt_red]
+    if sync:
+        for r in runners:
+            ops_sync(r.ctx)
+    return [r.history for r in runners]

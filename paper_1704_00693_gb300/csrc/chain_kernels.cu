@@ -447,10 +447,10 @@ cudaError_t launch_part_init(const LaunchEnv& env, int row0, int nrows) {
 
 // Each row's partials are combined in a fixed order (strided per thread, then
 // a fixed tree), so results depend only on the launch shape, never on timing.
-__global__ void __launch_bounds__(kThreads) k_fold(const DD* __restrict__ part, int stride, const FoldRow* rows,
-                                                   int row0, int nused, double* scal, int rbase) {
+// Fold row r of the partials (stored at row r - rbase) into its slot.
+__device__ __forceinline__ void fold_row(const DD* __restrict__ part, int stride, const FoldRow* rows, int r,
+                                         int rbase, int nused, double* scal) {
   __shared__ DD sh[32];
-  const int r = row0 + blockIdx.x;
   const int op = rows[r].op;
   DD v{red_identity(op), 0.0};
   for (int i = threadIdx.x; i < nused; i += blockDim.x) v = red_combine(op, v, part[(size_t)(r - rbase) * stride + i]);
@@ -469,6 +469,18 @@ __global__ void __launch_bounds__(kThreads) k_fold(const DD* __restrict__ part, 
   }
 }
 
+__global__ void __launch_bounds__(kThreads) k_fold(const DD* __restrict__ part, int stride, const FoldRow* rows,
+                                                   int row0, int nused, double* scal, int rbase) {
+  fold_row(part, stride, rows, row0 + blockIdx.x, rbase, nused, scal);
+}
+
+// One launch folds the same rows of several instances (blockIdx.y).
+__global__ void __launch_bounds__(kThreads) k_fold_batch(const FoldInst* __restrict__ fi, int row0, int rbase,
+                                                         int nused) {
+  const FoldInst& F = fi[blockIdx.y];
+  fold_row(F.part, F.stride, F.rows, row0 + blockIdx.x, rbase, nused > 0 ? nused : F.nused, F.scal);
+}
+
 cudaError_t launch_fold(const LaunchEnv& env, int row0, int nrows, int grid_used) {
   if (nrows <= 0) return cudaSuccess;
   k_fold<<<nrows, kThreads, 0, env.stream>>>(env.part, env.part_stride, env.rows, row0, grid_used, env.scal, 0);
@@ -478,6 +490,13 @@ cudaError_t launch_fold(const LaunchEnv& env, int row0, int nrows, int grid_used
 cudaError_t launch_fold_rows(const LaunchEnv& env, const DD* part, int stride, int row0, int nrows, int nused) {
   if (nrows <= 0) return cudaSuccess;
   k_fold<<<nrows, kThreads, 0, env.stream>>>(part, stride, env.rows, row0, nused, env.scal, row0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fold_batch(cudaStream_t stream, const FoldInst* d_fi, int ninst, int row0, int nrows, int rbase,
+                              int nused) {
+  if (nrows <= 0 || ninst <= 0) return cudaSuccess;
+  k_fold_batch<<<dim3(nrows, ninst), kThreads, 0, stream>>>(d_fi, row0, rbase, nused);
   return cudaGetLastError();
 }
 

@@ -147,6 +147,24 @@ cudaError_t launch_part_init(const LaunchEnv& env, int row0, int nrows);
 cudaError_t launch_fold(const LaunchEnv& env, int row0, int nrows, int grid_used);
 // the same for partials held elsewhere: row r of the fold at part + (r - row0) * stride, nused columns
 cudaError_t launch_fold_rows(const LaunchEnv& env, const DD* part, int stride, int row0, int nrows, int nused);
+// One instance of a batched fold: its partials (row r at part + (r - row0) * stride, nused columns),
+// fold rows and scalar slots.
+struct FoldInst {
+  const DD* part;
+  const FoldRow* rows;
+  double* scal;
+  int stride, nused;
+};
+// rows row0 .. row0 + nrows of every instance of d_fi[0 .. ninst) in one launch; row r of an
+// instance's partials at part + (r - rbase) * stride; nused > 0 overrides the instances' nused
+cudaError_t launch_fold_batch(cudaStream_t stream, const FoldInst* d_fi, int ninst, int row0, int nrows, int rbase,
+                              int nused);
+// One instance of a batched per-loop launch: its segment's descriptors, scalar slots and partials.
+struct BatchInst {
+  const DLoop* loops;
+  const double* scal;
+  DD* part;
+};
 int skewed_max_grid(int num_sms, int blocks_per_sm);
 cudaError_t launch_skewed(const LaunchEnv& env, const DLoop* d_loops, const Phase* d_phases, int nphases,
                           int grid);

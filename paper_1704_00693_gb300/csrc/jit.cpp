@@ -539,22 +539,40 @@ struct LoopGen {
 };
 
 // Source of the kernels u<l0> .. u<l1-1> for loops[l0..l1) of a segment.
-std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::vector<char>>& ro, int es) {
+// batch = true: kernels ub<i> instead, one launch of loop i over several
+// instances of the segment (blockIdx.y = instance; each instance's
+// descriptors, scalars and reduction partials from its BatchInst).
+std::string generate(const DLoop* loops, int l0, int l1, const std::vector<std::vector<char>>& ro, int es,
+                     bool batch = false) {
   std::ostringstream os;
   os << "// opstile compiled loop bodies: " << pts_for(es) << " rows per unit, " << kJitMinCtas << " CTAs per SM, "
-     << (es == 4 ? "fp32" : "fp64") << "\n";
+     << (es == 4 ? "fp32" : "fp64") << (batch ? ", batch of instances" : "") << "\n";
   os << kPrelude << kDeviceCommon << kPreludeTail;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
   os << "static_assert(sizeof(DArg) == " << sizeof(DArg) << ", \"DArg layout\");\n";
+  if (batch)
+    os << "struct BatchInst { const DLoop* loops; const double* scal; DD* part; };\n"
+          "static_assert(sizeof(BatchInst) == " << sizeof(BatchInst) << ", \"BatchInst layout\");\n";
   for (int i = l0; i < l1; ++i) {
     LoopGen g(loops[i], ro[i], os, false, es == 4);
     g.emit(i);
-    os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas << ") u" << i
-       << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
-          "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n"
-          "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
-          "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n  body"
-       << i << "(L, x0, x1, y0, y1, z0, z1, blockIdx.x, gridDim.x, scal, part, stride, assign);\n}\n";
+    if (batch) {
+      os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas << ") ub" << i
+         << "(const BatchInst* __restrict__ B, int x0, int x1, int y0, int y1, int z0, int z1, int stride,\n"
+            "    int assign) {\n"
+            "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
+            "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n"
+            "  const BatchInst& b = B[blockIdx.y];\n  body"
+         << i << "(b.loops + " << i << ", x0, x1, y0, y1, z0, z1, blockIdx.x, gridDim.x, b.scal, b.part, stride, "
+         << "assign);\n}\n";
+    } else {
+      os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas << ") u" << i
+         << "(const DLoop* __restrict__ L, int x0, int x1, int y0, int y1, int z0, int z1,\n"
+            "    const double* __restrict__ scal, DD* part, int stride, int assign) {\n"
+            "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
+            "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n  body"
+         << i << "(L, x0, x1, y0, y1, z0, z1, blockIdx.x, gridDim.x, scal, part, stride, assign);\n}\n";
+    }
   }
   return os.str();
 }
@@ -870,12 +888,12 @@ __device__ __forceinline__ void flush_red_col(int op, DD v, DD* dst) {
 )TWP";
 
 std::string generate_tilewave(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
-                              int ndim) {
+                              int ndim, bool batch) {
   const int nt = jit_tile_threads(), P = jit_tile_pts(es), ndirs = (1 << ndim) - 1;
   std::ostringstream os;
   os << "// opstile tile wavefront kernel: " << nt << " compute threads + 1 control warp, " << P
      << " points per thread at a time, " << jit_tile_min_ctas() << " CTAs per SM, " << ndim << "D, "
-     << (es == 4 ? "fp32" : "fp64") << "\n";
+     << (es == 4 ? "fp32" : "fp64") << (batch ? ", batch of instances" : "") << "\n";
   os << kPrelude << kDeviceCommon << kPreludeTail;
   os << "constexpr int kTwNtc = " << nt << ";\n" << kTwPrelude;
   os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
@@ -888,9 +906,17 @@ std::string generate_tilewave(const DLoop* loops, int count, const std::vector<s
   // once per launch), the current tile's box of every loop and its wait
   // table (loaded once per tile), and two slots of the step hand-over:
   // s_n[k] loops (-1: stop), their tile and their loop indices.
-  os << "extern \"C\" __global__ void __launch_bounds__(" << nt + 32 << ", " << jit_tile_min_ctas()
-     << ") tw(const TwArgs A) {\n"
-        "  constexpr int NL = " << count << ", ND = " << ndirs << ", ES = " << es << ", MG = " << kTwMaxGroup << ";\n"
+  // The batch kernel "twb" runs the segment for several instances (same
+  // code, own dats, plans, progress counters and partials): tickets count
+  // over every instance's tiles, tmap[ticket] = (instance, tile), and the
+  // control warp copies an instance's arguments into shared memory when its
+  // next tile belongs to another instance than the last one.
+  os << "extern \"C\" __global__ void __launch_bounds__(" << nt + 32 << ", " << jit_tile_min_ctas() << ") "
+     << (batch ? "twb(const TwArgs* __restrict__ AA, const int2* __restrict__ tmap, int total, int* ticket) {\n"
+               "  __shared__ TwArgs s_A;\n"
+               "  const TwArgs& A = s_A;\n"
+               : "tw(const TwArgs A) {\n")
+     << "  constexpr int NL = " << count << ", ND = " << ndirs << ", ES = " << es << ", MG = " << kTwMaxGroup << ";\n"
         "  __shared__ unsigned short s_need[ND * NL];\n"
         "  __shared__ int s_box[NL][6];\n"
         "  __shared__ void* s_lptr[NL][8];\n"
@@ -919,15 +945,23 @@ std::string generate_tilewave(const DLoop* loops, int count, const std::vector<s
         "  }\n"
         "  // control warp\n"
         "  const int lane = tid - kTwNtc;\n"
-        "  for (int j = lane; j < NL * 8; j += 32) {\n"
-        "    const int l = j >> 3, a = j & 7;\n"
-        "    s_lptr[l][a] = a < A.loops[l].nargs ? (void*)A.loops[l].args[a].ptr0 : nullptr;\n"
-        "  }\n"
-        "  int k = 0;                         // slot of the next step\n"
+        "  auto load_ptrs = [&]() {\n"
+        "    for (int j = lane; j < NL * 8; j += 32) {\n"
+        "      const int l = j >> 3, a = j & 7;\n"
+        "      s_lptr[l][a] = a < A.loops[l].nargs ? (void*)A.loops[l].args[a].ptr0 : nullptr;\n"
+        "    }\n"
+        "  };\n"
+     << (batch ? "  int* const tkt = ticket;\n"
+                 "  const int ntk = total;\n"
+                 "  int inst = -1;\n"
+               : "  load_ptrs();\n"
+                 "  int* const tkt = A.ticket;\n"
+                 "  const int ntk = A.ntiles;\n")
+     << "  int k = 0;                         // slot of the next step\n"
         "  int pub_tile = -1, pub_val = 0;    // progress owed once the running step completes\n"
         "  bool stop = false;\n"
         "  int tk = 0, nxt = 0;\n"
-        "  if (lane == 0) tk = atomicAdd(A.ticket, 1);\n"
+        "  if (lane == 0) tk = atomicAdd(tkt, 1);\n"
         "  tk = __shfl_sync(0xffffffffu, tk, 0);\n"
         "  auto publish = [&]() {\n"
         "    if (lane == 0 && pub_tile >= 0 && pub_tile != A.skip_tile) st_release(A.prog + pub_tile, pub_val);\n"
@@ -942,12 +976,21 @@ std::string generate_tilewave(const DLoop* loops, int count, const std::vector<s
         "    bar_step();\n"
         "    k ^= 1;\n"
         "  };\n"
-        "  while (!stop && tk < A.ntiles) {\n"
-        "    const int tile = A.order[tk];\n"
-        "    const int tc[3] = {tile % A.nt[0], (tile / A.nt[0]) % A.nt[1], tile / (A.nt[0] * A.nt[1])};\n"
+        "  while (!stop && tk < ntk) {\n"
+     << (batch ? "    const int2 tm = tmap[tk];\n"
+                 "    if (tm.x != inst) {\n"
+                 "      // the compute warps wait at the step barrier: the instance can change\n"
+                 "      inst = tm.x;\n"
+                 "      if (lane == 0) s_A = AA[inst];\n"
+                 "      __syncwarp();\n"
+                 "      load_ptrs();\n"
+                 "    }\n"
+                 "    const int tile = tm.y;\n"
+               : "    const int tile = A.order[tk];\n")
+     << "    const int tc[3] = {tile % A.nt[0], (tile / A.nt[0]) % A.nt[1], tile / (A.nt[0] * A.nt[1])};\n"
         "    const int cl = (A.cls[A.coff[2] + tc[2]] * A.ncls[1] + A.cls[A.coff[1] + tc[1]]) * A.ncls[0] +\n"
         "                   A.cls[A.coff[0] + tc[0]];\n"
-        "    if (lane == 0) nxt = atomicAdd(A.ticket, 1);\n"
+        "    if (lane == 0) nxt = atomicAdd(tkt, 1);\n"
         "    // the compute warps are past the previous tile: its boxes can be replaced\n"
         "    for (int j = lane; j < ND * NL; j += 32) s_need[j] = A.need[(size_t)cl * (ND * NL) + j];\n"
         "    for (int j = lane; j < 6 * NL; j += 32) {\n"
@@ -1130,7 +1173,7 @@ std::string cache_base(const std::string& src) {
 }  // namespace
 
 int jit_segment(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
-                JitSegment** out, std::string* why, double* compile_ms) {
+                JitSegment** out, std::string* why, double* compile_ms, bool batch) {
   *out = nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!api_ready(why)) return OPS_OK;
@@ -1138,7 +1181,7 @@ int jit_segment(int device, const DLoop* loops, int count, const std::vector<std
   std::vector<std::string> srcs;
   std::string all;
   for (int l0 = 0; l0 < count; l0 += kJitChunk) {
-    srcs.push_back(generate(loops, l0, std::min(count, l0 + kJitChunk), ro, es));
+    srcs.push_back(generate(loops, l0, std::min(count, l0 + kJitChunk), ro, es, batch));
     all += srcs.back();
   }
   auto skey = std::make_pair(device, all);
@@ -1195,7 +1238,7 @@ int jit_segment(int device, const DLoop* loops, int count, const std::vector<std
       g_modules[mk] = mod;
     }
     for (int i = m * kJitChunk; i < std::min(count, (m + 1) * kJitChunk); ++i) {
-      const std::string name = "u" + std::to_string(i);
+      const std::string name = (batch ? "ub" : "u") + std::to_string(i);
       if (g_api.get_function(&s->u[i], mod, name.c_str()) != CUDA_SUCCESS) {
         *why = "cuModuleGetFunction failed";
         return OPS_ERR_CUDA;
@@ -1432,6 +1475,33 @@ cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const D
   return to_cuda(g_api.launch(s->u[i], (unsigned)grid, 1, 1, kThreads, 1, 1, 0, (CUstream)env.stream, args, nullptr));
 }
 
+cudaError_t jit_launch_batch(const JitSegment* s, int i, cudaStream_t stream, const BatchInst* d_inst, int ninst,
+                             const int* box, int grid, int stride) {
+  const BatchInst* a0 = d_inst;
+  int b0 = box[0], b1 = box[1], b2 = box[2], b3 = box[3], b4 = box[4], b5 = box[5];
+  int st = stride, as = 1;
+  void* args[] = {&a0, &b0, &b1, &b2, &b3, &b4, &b5, &st, &as};
+  if (g_api.launch_ex && jit_pdl()) {
+    CUlaunchAttribute at[1];
+    std::memset(at, 0, sizeof at);
+    at[0].id = CU_LAUNCH_ATTRIBUTE_PROGRAMMATIC_STREAM_SERIALIZATION;
+    at[0].value.programmaticStreamSerializationAllowed = 1;
+    CUlaunchConfig cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cfg.gridDimX = (unsigned)grid;
+    cfg.gridDimY = (unsigned)ninst;
+    cfg.gridDimZ = 1;
+    cfg.blockDimX = kThreads;
+    cfg.blockDimY = cfg.blockDimZ = 1;
+    cfg.hStream = (CUstream)stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return to_cuda(g_api.launch_ex(&cfg, s->u[i], args, nullptr));
+  }
+  return to_cuda(g_api.launch(s->u[i], (unsigned)grid, (unsigned)ninst, 1, kThreads, 1, 1, 0, (CUstream)stream, args,
+                              nullptr));
+}
+
 
 int jit_rows_per_unit(int es) { return pts_for(es); }
 
@@ -1600,12 +1670,12 @@ std::map<std::pair<int, std::string>, std::unique_ptr<JitTile>> g_tiles;
 }  // namespace
 
 int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es, int ndim,
-                 JitTile** out, std::string* why, double* compile_ms) {
+                 JitTile** out, std::string* why, double* compile_ms, bool batch) {
   *out = nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!api_ready(why)) return OPS_OK;
   auto t0 = std::chrono::steady_clock::now();
-  const std::string src = generate_tilewave(loops, count, ro, es, ndim);
+  const std::string src = generate_tilewave(loops, count, ro, es, ndim, batch);
   auto key = std::make_pair(device, src);
   auto it = g_tiles.find(key);
   if (it != g_tiles.end()) {
@@ -1620,7 +1690,7 @@ int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<st
     return OPS_ERR_CUDA;
   }
   std::unique_ptr<JitTile> t(new JitTile);
-  if (g_api.get_function(&t->f, mod, "tw") != CUDA_SUCCESS) {
+  if (g_api.get_function(&t->f, mod, batch ? "twb" : "tw") != CUDA_SUCCESS) {
     *why = "cuModuleGetFunction failed";
     return OPS_ERR_CUDA;
   }
@@ -1632,9 +1702,9 @@ int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<st
 }
 
 int jit_compile_tilewave_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
-                              int ndim, std::string* src, std::string* why, double* compile_ms) {
+                              int ndim, std::string* src, std::string* why, double* compile_ms, bool batch) {
   std::lock_guard<std::mutex> lk(g_mu);
-  *src = generate_tilewave(loops, count, ro, es, ndim);
+  *src = generate_tilewave(loops, count, ro, es, ndim, batch);
   if (!api_ready(why, true)) {
     if (why->empty()) *why = g_api.why;
     return OPS_ERR_NO_DEVICE;
@@ -1657,6 +1727,17 @@ int jit_tilewave_max_grid(JitTile* t, int num_sms) {
 cudaError_t jit_launch_tilewave(const JitTile* t, const TwArgs& args, cudaStream_t stream, int grid) {
   TwArgs a = args;
   void* params[] = {&a};
+  return to_cuda(g_api.launch(t->f, (unsigned)grid, 1, 1, (unsigned)(jit_tile_threads() + 32), 1, 1, 0,
+                              (CUstream)stream, params, nullptr));
+}
+
+cudaError_t jit_launch_tilewave_batch(const JitTile* t, const TwArgs* d_args, const int* d_tmap, int total,
+                                      int* d_ticket, cudaStream_t stream, int grid) {
+  const TwArgs* aa = d_args;
+  const int* tm = d_tmap;
+  int tot = total;
+  int* tk = d_ticket;
+  void* params[] = {&aa, &tm, &tot, &tk};
   return to_cuda(g_api.launch(t->f, (unsigned)grid, 1, 1, (unsigned)(jit_tile_threads() + 32), 1, 1, 0,
                               (CUstream)stream, params, nullptr));
 }

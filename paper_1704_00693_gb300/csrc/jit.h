@@ -23,8 +23,9 @@ struct JitSegment;
 // On success *out is a module shared by every context of the process with
 // the same device and code.  Returns OPS_OK with *out == nullptr, and the
 // reason in *why, when run-time compilation is unavailable.
+// batch = true compiles the batch kernels ub<i> instead (jit_launch_batch).
 int jit_segment(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
-                JitSegment** out, std::string* why, double* compile_ms);
+                JitSegment** out, std::string* why, double* compile_ms, bool batch = false);
 
 // Host only: the generated source of the segment, compiled for sm_103a
 // without loading it (no device needed).  OPS_ERR_CUDA with the compiler's
@@ -53,6 +54,13 @@ int jit_grid_policy();
 // into the CTA's partial column.
 cudaError_t jit_launch(const JitSegment* s, int i, const LaunchEnv& env, const DLoop* d_loop, const int* box,
                        int grid, int assign);
+// One launch of loop i of a batch segment (jit_segment with batch = true)
+// for ninst instances: grid CTAs per instance (blockIdx.y = instance) over
+// the box; instance k reads its descriptors at d_inst[k].loops + i, its
+// scalars at d_inst[k].scal, and assigns its reductions' partials at
+// d_inst[k].part + row * stride + CTA.
+cudaError_t jit_launch_batch(const JitSegment* s, int i, cudaStream_t stream, const BatchInst* d_inst, int ninst,
+                             const int* box, int grid, int stride);
 
 // Overlapped tiles (Sec. 4.D per CTA): one kernel per run of loops, with
 // the run's shared-memory layout compiled in.  loops: the run's descriptors
@@ -156,12 +164,21 @@ int jit_tile_ahead();
 int jit_tile_group();
 // tiles along x per strip of the ticket order (OPSTILE_TW_BAND; 0 = one strip)
 int jit_tile_band();
+// batch = true compiles the batch kernel "twb" instead of "tw": one launch
+// runs the segment for several instances of the same code (see
+// jit_launch_tilewave_batch).
 int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es, int ndim,
-                 JitTile** out, std::string* why, double* compile_ms);
+                 JitTile** out, std::string* why, double* compile_ms, bool batch = false);
 int jit_compile_tilewave_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
-                              int ndim, std::string* src, std::string* why, double* compile_ms);
+                              int ndim, std::string* src, std::string* why, double* compile_ms, bool batch = false);
 // CTAs of the kernel resident on the device at once
 int jit_tilewave_max_grid(JitTile* t, int num_sms);
 cudaError_t jit_launch_tilewave(const JitTile* t, const TwArgs& args, cudaStream_t stream, int grid);
+// The batch kernel: d_args[i] are instance i's arguments (every instance's
+// ticket and err pointing at the same words; prog arrays disjoint);
+// d_tmap[2 k], d_tmap[2 k + 1] = instance and linear tile index of ticket k
+// (each instance's tiles in its plan's order); d_ticket zero before the launch.
+cudaError_t jit_launch_tilewave_batch(const JitTile* t, const TwArgs* d_args, const int* d_tmap, int total,
+                                      int* d_ticket, cudaStream_t stream, int grid);
 
 }  // namespace opstile

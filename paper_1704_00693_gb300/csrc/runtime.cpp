@@ -140,6 +140,14 @@ struct ops_ctx_s {
   // uploads only the descriptors that changed since the last one
   std::vector<DLoop> loops_mirror;
   DLoop* mirror_of = nullptr;
+  // descriptors of the last flush, kept with the loops they were filled
+  // from: a flush that queues the same loop at the same position (same
+  // block, range, arguments, body, partial row; constants may differ) at the
+  // same buffer generation reuses the descriptor instead of refilling it
+  std::vector<DLoop> hl_cache;
+  std::vector<QLoop> hl_src;
+  std::vector<char> hl_ok;
+  uint64_t hl_gen = 0;
   uint64_t swap_gen = 0;  // bumped whenever overlapped tiles move dats to their other buffer
   int skewed_grid = 0;
   std::map<std::vector<int>, std::unique_ptr<CachedPlan>> plans;
@@ -160,6 +168,26 @@ struct ops_ctx_s {
   // timing=1: event pairs around the chain kernels of the last flush
   std::vector<cudaEvent_t> ev_pool;
   int ev_used = 0;
+  // batches this context leads (ops_execute_batch): the batch kernel's
+  // tables, and the autotuning state per segment signature and batch size
+  void* d_batch = nullptr;
+  size_t batch_cap = 0;
+  std::map<std::vector<int>, TuneRec> btune;
+  // recorded on this context's stream when another stream must wait for it
+  cudaEvent_t ev_join = nullptr;
+  // pinned staging of the flush's host-to-device copies (descriptors, fold
+  // rows), so they queue without a synchronous pageable copy: two buffers
+  // used by alternate flushes, each reused once the copies of the flush
+  // before last have completed (ev_stage)
+  char* h_stage[2] = {nullptr, nullptr};
+  size_t stage_cap[2] = {0, 0};
+  cudaEvent_t ev_stage[2] = {nullptr, nullptr};
+  bool stage_live[2] = {false, false};
+  int stage_slot = 0;
+  size_t stage_used = 0;
+  std::vector<FoldRow> rows_mirror;  // fold rows d_rows holds
+  // pinned landing slots of ops_reduction_result: the value, the error word
+  struct { double value; int err; int pad; }* h_small = nullptr;
 };
 
 namespace {
@@ -475,6 +503,45 @@ int record_event(ops_ctx c) {
 
 std::vector<int> segment_signature(ops_ctx c, int first, int count);
 
+// Make room for `bytes` of staged copies in this flush: waits for the
+// previous flush's staged copies, then grows the pinned buffer if needed.
+int stage_begin(ops_ctx c, size_t bytes) {
+  const int k = c->stage_slot ^= 1;
+  if (c->stage_live[k]) {
+    CUDA_TRY(c, cudaEventSynchronize(c->ev_stage[k]));
+    c->stage_live[k] = false;
+  }
+  c->stage_used = 0;
+  if (bytes > c->stage_cap[k]) {
+    if (c->h_stage[k]) cudaFreeHost(c->h_stage[k]);
+    c->h_stage[k] = nullptr;
+    c->stage_cap[k] = 0;
+    // slack for the batch tables a batched flush stages after the descriptors
+    const size_t want = std::max<size_t>(bytes + (64 << 10), 128 << 10);
+    CUDA_TRY(c, cudaHostAlloc((void**)&c->h_stage[k], want, cudaHostAllocDefault));
+    c->stage_cap[k] = want;
+  }
+  if (!c->ev_stage[k]) CUDA_TRY(c, cudaEventCreateWithFlags(&c->ev_stage[k], cudaEventDisableTiming));
+  return OPS_OK;
+}
+
+// Host-to-device copy on the context's stream through the pinned staging
+// (a plain pageable copy when the staging is full).
+int stage_copy(ops_ctx c, void* dst, const void* src, size_t bytes) {
+  const int k = c->stage_slot;
+  const size_t at = (c->stage_used + 15) / 16 * 16;
+  if (!c->h_stage[k] || at + bytes > c->stage_cap[k]) {
+    CUDA_TRY(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return OPS_OK;
+  }
+  std::memcpy(c->h_stage[k] + at, src, bytes);
+  CUDA_TRY(c, cudaMemcpyAsync(dst, c->h_stage[k] + at, bytes, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(c, cudaEventRecord(c->ev_stage[k], c->stream));
+  c->stage_live[k] = true;
+  c->stage_used = at + bytes;
+  return OPS_OK;
+}
+
 // Bring d_loops[first, first + count) up to date with hl, copying only the
 // runs of descriptors that differ from what the device already holds.
 int upload_loops(ops_ctx c, const std::vector<DLoop>& hl, int first, int count) {
@@ -497,8 +564,8 @@ int upload_loops(ops_ctx c, const std::vector<DLoop>& hl, int first, int count) 
     }
     int j = i + 1;
     while (j < end && std::memcmp(&c->loops_mirror[j], &hl[j], sizeof(DLoop)) != 0) ++j;
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_loops + i, hl.data() + i, sizeof(DLoop) * (j - i), cudaMemcpyHostToDevice,
-                                c->stream));
+    int rc = stage_copy(c, c->d_loops + i, hl.data() + i, sizeof(DLoop) * (j - i));
+    if (rc) return rc;
     std::memcpy(&c->loops_mirror[i], &hl[i], sizeof(DLoop) * (j - i));
     i = j;
   }
@@ -1674,8 +1741,10 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<D
     if (count > 1 && !c->cfg.interpret && !c->cfg.check && jit_available()) {
       T.cand.push_back({OPS_MODE_TILEWAVE, 0, 0, 0, 0});
       if (ndim == 2) {
-        T.cand.push_back({OPS_MODE_TILEWAVE, 256, 32, 0, 0});
-        T.cand.push_back({OPS_MODE_TILEWAVE, 128, 32, 0, 0});
+        // square tiles suit chains of few dats (the heat equation's Jacobi steps
+        // ran fastest at 128 x 128 in FP32), wide ones chains of many
+        T.cand.push_back({OPS_MODE_TILEWAVE, 128, 128, 0, 0});
+        T.cand.push_back({OPS_MODE_TILEWAVE, 256, 64, 0, 0});
       } else if (ndim == 3) {
         T.cand.push_back({OPS_MODE_TILEWAVE, 64, 32, 32, 0});
       }
@@ -1739,29 +1808,76 @@ int run_segment(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>
   return run_segment_mode(c, first, count, dl_base, hl, mode, c->cfg.tile);
 }
 
-int flush(ops_ctx c) {
-  if (c->queue.empty()) return OPS_OK;
+// The first half of a flush: every queued loop's descriptor and partial
+// rows, the device buffers they need, and the cuts into segments.
+struct FlushPrep {
+  explicit FlushPrep(ops_ctx c) : hl(c->hl_cache) {}
+  std::vector<DLoop>& hl;  // the context's descriptor cache, filled for this flush
+  std::vector<int> prow;
+  std::vector<std::pair<int, int>> segs;  // (first loop, loop count)
+  uint64_t filled_gen = 0;
+};
+
+// Two queued loops give the same descriptor up to its constants.
+bool same_loop_shape(const QLoop& a, const QLoop& b) {
+  return a.block == b.block && a.dims == b.dims && std::memcmp(a.rng, b.rng, sizeof a.rng) == 0 &&
+         a.args.size() == b.args.size() &&
+         (a.args.empty() || std::memcmp(a.args.data(), b.args.data(), sizeof(ops_arg) * a.args.size()) == 0) &&
+         a.code == b.code && a.K.size() == b.K.size();
+}
+
+int flush_prepare(ops_ctx c, FlushPrep& F) {
   std::memset(&c->stats, 0, sizeof c->stats);
   c->ev_used = 0;
   if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context cannot execute loops");
   const int n = (int)c->queue.size();
-  std::vector<DLoop> hl(n);
-  std::vector<FoldRow> rows;
-  std::vector<int> prow(n);
-  for (int i = 0; i < n; ++i) {
-    prow[i] = (int)rows.size();
-    fill_dloop(c, c->queue[i], hl[i], prow[i], rows);
+  if ((int)F.hl.size() < n) {
+    F.hl.resize(n);
+    c->hl_src.resize(n);
+    c->hl_ok.resize(n, 0);
   }
-  const uint64_t filled_gen = c->swap_gen;
+  if (c->hl_gen != c->swap_gen) std::fill(c->hl_ok.begin(), c->hl_ok.end(), 0);
+  F.prow.assign(n, 0);
+  F.segs.clear();
+  std::vector<FoldRow> rows;
+  for (int i = 0; i < n; ++i) {
+    F.prow[i] = (int)rows.size();
+    const QLoop& q = c->queue[i];
+    QLoop& src = c->hl_src[i];
+    DLoop& L = F.hl[i];
+    if (c->hl_ok[i] && L.part_row == F.prow[i] && same_loop_shape(src, q)) {
+      if (src.K != q.K) {
+        std::memcpy(L.K, q.K.data(), sizeof(double) * q.K.size());
+        src.K = q.K;
+      }
+      for (const ops_arg& a : q.args)
+        if (a.kind == OPS_ARG_RED) rows.push_back(FoldRow{a.handle, c->red_ops[a.handle]});
+    } else {
+      fill_dloop(c, q, L, F.prow[i], rows);
+      src = q;
+      c->hl_ok[i] = 1;
+    }
+  }
+  c->hl_gen = c->swap_gen;
+  F.filled_gen = c->swap_gen;
   const int cap0 = c->loops_cap;
   int rc = ensure(c, &c->d_loops, &c->loops_cap, n);
   if (rc) return rc;
   if (c->loops_cap != cap0) c->loops_mirror.clear();  // new allocation: contents unknown
+  // every descriptor at most once per segment and the fold rows
+  rc = stage_begin(c, sizeof(DLoop) * (size_t)n + sizeof(FoldRow) * rows.size() + 64);
+  if (rc) return rc;
   if (!rows.empty()) {
+    const int rcap0 = c->rows_cap;
     rc = ensure(c, &c->d_rows, &c->rows_cap, (int)rows.size());
     if (rc) return rc;
-    CUDA_TRY(c, cudaMemcpyAsync(c->d_rows, rows.data(), sizeof(FoldRow) * rows.size(), cudaMemcpyHostToDevice,
-                                c->stream));
+    if (c->rows_cap != rcap0) c->rows_mirror.clear();
+    if (c->rows_mirror.size() < rows.size() ||
+        std::memcmp(c->rows_mirror.data(), rows.data(), sizeof(FoldRow) * rows.size()) != 0) {
+      rc = stage_copy(c, c->d_rows, rows.data(), sizeof(FoldRow) * rows.size());
+      if (rc) return rc;
+      c->rows_mirror = rows;
+    }
     int cap = c->part_rows_cap;
     if ((int)rows.size() > cap) {
       int want = std::max((int)rows.size(), 8);
@@ -1790,22 +1906,7 @@ int flush(ops_ctx c) {
       if (!cut && c->queue[i].block != c->queue[first].block) cut = true;
     }
     if (cut && i > first) {
-      // an earlier overlapped segment of this flush may have moved dats to
-      // their other buffers: refill this segment's descriptors then
-      if (c->swap_gen != filled_gen) {
-        std::vector<FoldRow> unused;
-        for (int k = first; k < i; ++k) fill_dloop(c, c->queue[k], hl[k], prow[k], unused);
-      }
-      rc = upload_loops(c, hl, first, i - first);
-      if (rc) {
-        c->queue.clear();
-        return rc;
-      }
-      rc = run_segment(c, first, i - first, first, hl);
-      if (rc) {
-        c->queue.clear();
-        return rc;
-      }
+      F.segs.emplace_back(first, i - first);
       first = i;
       reduced.clear();
     }
@@ -1813,8 +1914,504 @@ int flush(ops_ctx c) {
       for (const ops_arg& a : c->queue[i].args)
         if (a.kind == OPS_ARG_RED) reduced.push_back(a.handle);
   }
-  c->queue.clear();
   return OPS_OK;
+}
+
+// Descriptors of segment (first, count) on the device, refilled first if an
+// earlier overlapped segment of this flush moved dats to their other buffers.
+int segment_descriptors(ops_ctx c, FlushPrep& F, int first, int count) {
+  if (c->swap_gen != F.filled_gen) {
+    std::vector<FoldRow> unused;
+    for (int k = first; k < first + count; ++k) fill_dloop(c, c->queue[k], F.hl[k], F.prow[k], unused);
+  }
+  return upload_loops(c, F.hl, first, count);
+}
+
+// After a flush: descriptors refilled mid-flush (dats moved to their other
+// buffers) leave the cache at mixed generations, so none of it is reused.
+void flush_done(ops_ctx c, const FlushPrep& F) {
+  if (c->swap_gen != F.filled_gen) std::fill(c->hl_ok.begin(), c->hl_ok.end(), 0);
+  c->queue.clear();
+}
+
+int flush(ops_ctx c) {
+  if (c->queue.empty()) return OPS_OK;
+  FlushPrep F(c);
+  int rc = flush_prepare(c, F);
+  if (rc) return rc;
+  for (size_t s = 0; s < F.segs.size() && !rc; ++s) {
+    const int first = F.segs[s].first, count = F.segs[s].second;
+    rc = segment_descriptors(c, F, first, count);
+    if (!rc) rc = run_segment(c, first, count, first, F.hl);
+  }
+  flush_done(c, F);
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// batched execution: several contexts' chains, one launch per segment
+// ---------------------------------------------------------------------------
+
+// Make dst's stream wait for the work queued so far on src's stream.
+int stream_after(ops_ctx dst, ops_ctx src) {
+  if (dst->stream == src->stream) return OPS_OK;
+  if (!src->ev_join) CUDA_TRY(src, cudaEventCreateWithFlags(&src->ev_join, cudaEventDisableTiming));
+  CUDA_TRY(src, cudaEventRecord(src->ev_join, src->stream));
+  CUDA_TRY(dst, cudaStreamWaitEvent(dst->stream, src->ev_join, 0));
+  return OPS_OK;
+}
+
+// The batch kernel of a segment (compiled once per code, like tile_code).
+int tile_code_batch(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitTile** out) {
+  *out = nullptr;
+  std::vector<int> key = code_key(c, first, count);
+  key.push_back(-OPS_MODE_TILEWAVE);  // the batch form
+  auto it = c->jitt.find(key);
+  if (it != c->jitt.end()) {
+    *out = it->second;
+    return OPS_OK;
+  }
+  std::vector<std::vector<char>> ro = read_only_args(c, first, count);
+  JitTile* t = nullptr;
+  std::string why;
+  double ms = 0.0;
+  const int rc = jit_tilewave(c->cfg.device, hl.data() + first, count, ro, c->es, c->queue[first].dims, &t, &why,
+                              &ms, true);
+  c->stats.compile_ms += ms;
+  if (rc) return fail(c, rc, "compiling the batch tile-wavefront kernel: %s", why.c_str());
+  if (!t) c->jit_why = why;
+  c->jitt[key] = t;
+  *out = t;
+  return OPS_OK;
+}
+
+// Segment (first, count) of every context of the batch in one launch of the
+// tile-wavefront batch kernel, on cs[0]'s stream (which the caller has made
+// wait for the others).  Tickets interleave the instances: the k-th tile in
+// plan order of every instance comes before the (k+1)-th of any, so the
+// instances advance together and each instance's tiles keep its plan order
+// (what the waits of the tile wavefront rely on).  *ran = false when an
+// instance has no valid plan or run-time compilation is unavailable.
+int run_batch_tilewave(ops_ctx* cs, int n, std::vector<FlushPrep>& F, int first, int count, const int* tile_in,
+                       bool* ran) {
+  *ran = false;
+  ops_ctx c0 = cs[0];
+  // The instances' loops match in ranges, stencils, accesses and dats, so
+  // the first context's plan is every instance's plan; only the progress
+  // counters and the reduction partials are per instance.
+  CachedPlan* p = nullptr;
+  int rc = tile_plan(c0, first, count, F[0].hl, first, tile_in, &p);
+  if (rc) return rc;
+  if (!p) return OPS_OK;
+  JitTile* t = nullptr;
+  rc = tile_code_batch(c0, first, count, F[0].hl, &t);
+  if (rc) return rc;
+  if (!t) return OPS_OK;
+  *ran = true;
+  int row0 = -1, nrows = 0;
+  for (int l = 0; l < count; ++l) {
+    const DLoop& L = F[0].hl[first + l];
+    if (L.nreds) {
+      if (row0 < 0) row0 = L.part_row;
+      nrows = L.part_row + L.nreds - row0;
+    }
+  }
+  if (nrows > p->tw_rows) return fail(c0, OPS_ERR_STATE, "tile-wavefront partial rows changed under a cached plan");
+  const int nt = p->tw_ntiles;
+  const int64_t total64 = (int64_t)nt * n;
+  if (total64 >= (1 << 30)) return fail(c0, OPS_ERR_INVALID_ARG, "a batch of %lld tiles is too large", (long long)total64);
+  const int total = (int)total64;
+  // device tables: arguments | fold instances | ticket map | partials | progress + ticket
+  const size_t b_args = sizeof(TwArgs) * n, b_fold = sizeof(FoldInst) * n, b_map = sizeof(int) * 2 * (size_t)total,
+               b_part = sizeof(DD) * (size_t)nrows * total, b_prog = sizeof(int) * ((size_t)total + 1);
+  const size_t o_fold = (b_args + 15) / 16 * 16, o_map = o_fold + (b_fold + 15) / 16 * 16,
+               o_part = o_map + (b_map + 15) / 16 * 16, o_prog = o_part + (b_part + 15) / 16 * 16,
+               bytes = o_prog + b_prog;
+  if (bytes > c0->batch_cap) {
+    if (c0->d_batch) {
+      CUDA_TRY(c0, cudaStreamSynchronize(c0->stream));
+      dev_free(c0, c0->d_batch, c0->batch_cap);
+      c0->d_batch = nullptr;
+      c0->batch_cap = 0;
+    }
+    const size_t want = std::max<size_t>(bytes, 4096);
+    rc = dev_alloc(c0, &c0->d_batch, want);
+    if (rc) return rc;
+    c0->batch_cap = want;
+  }
+  char* d = (char*)c0->d_batch;
+  int* d_prog = (int*)(d + o_prog);
+  DD* d_part = (DD*)(d + o_part);
+  std::vector<char> host(o_part, 0);
+  TwArgs* ha = (TwArgs*)host.data();
+  FoldInst* hf = (FoldInst*)(host.data() + o_fold);
+  int* hm = (int*)(host.data() + o_map);
+  const LaunchEnv env0 = make_env(c0);
+  const char* dt = (const char*)p->d_tw;
+  for (int i = 0; i < n; ++i) {
+    ops_ctx c = cs[i];
+    TwArgs& a = ha[i];
+    std::memset(&a, 0, sizeof a);
+    a.loops = c->d_loops + first;
+    a.rng = (const int*)dt;
+    a.order = (const int*)(dt + p->tw_order);
+    a.cls = (const int*)(dt + p->tw_cls);
+    a.need = (const unsigned short*)(dt + p->tw_need);
+    a.prog = d_prog + (size_t)i * nt;
+    a.ticket = d_prog + total;
+    a.scal = c->d_scal;
+    a.part = d_part + (size_t)i * nrows * nt;
+    a.err = env0.err;
+    a.timeout_ns = env0.timeout_ns;
+    for (int k = 0; k < 3; ++k) {
+      a.nt[k] = p->plan.ntiles[k];
+      a.ncls[k] = p->tw.ncls[k];
+      a.roff[k] = p->tw_roff[k];
+      a.coff[k] = p->tw_coff[k];
+    }
+    a.ntiles = nt;
+    a.stride = nt;
+    a.row0 = row0 < 0 ? 0 : row0;
+    a.skip_tile = i == 0 ? env0.skip_block : -1;
+    a.pf = (const unsigned char*)(dt + p->tw_pf);
+    a.ahead = jit_tile_ahead();
+    a.groups = (const int*)(dt + p->tw_grp);
+    a.ngroups = (int)p->tw.groups.size() - 1;
+    hf[i] = FoldInst{a.part, c->d_rows, c->d_scal, nt, nt};
+  }
+  for (int k = 0, q = 0; k < nt; ++k)
+    for (int i = 0; i < n; ++i, ++q) {
+      hm[2 * q] = i;
+      hm[2 * q + 1] = p->tw.order[k];
+    }
+  rc = stage_copy(c0, d, host.data(), o_map + b_map);
+  if (rc) return rc;
+  CUDA_TRY(c0, cudaMemsetAsync(d_prog, 0, b_prog, c0->stream));
+  const int grid = std::max(1, std::min(total, jit_tilewave_max_grid(t, c0->num_sms)));
+  rc = record_event(c0);
+  if (rc) return rc;
+  CUDA_TRY(c0, jit_launch_tilewave_batch(t, (const TwArgs*)d, (const int*)(d + o_map), total, d_prog + total,
+                                         c0->stream, grid));
+  rc = record_event(c0);
+  if (rc) return rc;
+  if (nrows) CUDA_TRY(c0, launch_fold_batch(c0->stream, (const FoldInst*)(d + o_fold), n, row0, nrows, row0, 0));
+  for (int i = 0; i < n; ++i) {
+    ops_ctx c = cs[i];
+    c->stats.mode = OPS_MODE_TILEWAVE;
+    c->stats.compiled = 1;
+    c->stats.batched = n;
+    ++c->stats.segments;
+    c->stats.loops += count;
+    for (int k = 0; k < 3; ++k) {
+      c->stats.tile[k] = p->plan.tile[k];
+      c->stats.skew[k] = p->plan.skew[k];
+    }
+    c->stats.tiles = p->tw_ntiles;
+    c->stats.phases += p->tw_phases;
+    c->stats.barriers += p->tw_steps;
+  }
+  ++c0->stats.launches;
+  ++c0->stats.kernel_launches;
+  if (nrows) ++c0->stats.launches;
+  return OPS_OK;
+}
+
+// The batch form of a segment's per-loop kernels (compiled once per code).
+int segment_code_batch(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitSegment** out) {
+  *out = nullptr;
+  if (c->cfg.interpret || c->cfg.check) return OPS_OK;
+  std::vector<int> key = code_key(c, first, count);
+  key.push_back(-OPS_MODE_UNTILED - 100);  // the batch form
+  auto it = c->jit.find(key);
+  if (it != c->jit.end()) {
+    *out = it->second;
+    return OPS_OK;
+  }
+  std::vector<std::vector<char>> ro = read_only_args(c, first, count);
+  JitSegment* js = nullptr;
+  std::string why;
+  double ms = 0.0;
+  const int rc = jit_segment(c->cfg.device, hl.data() + first, count, ro, c->es, &js, &why, &ms, true);
+  c->stats.compile_ms += ms;
+  if (rc) return fail(c, rc, "compiling the batch loop kernels: %s", why.c_str());
+  if (!js) c->jit_why = why;
+  c->jit[key] = js;
+  *out = js;
+  return OPS_OK;
+}
+
+// Segment (first, count) of every context of the batch untiled, one launch
+// per loop for all instances (blockIdx.y = instance), on cs[0]'s stream:
+// the loops run in program order as in the untiled form, each instance's
+// reductions fold from its own partials, all instances' in one launch.
+// *ran = false without run-time compilation.
+int run_batch_untiled(ops_ctx* cs, int n, std::vector<FlushPrep>& F, int first, int count, bool* ran) {
+  *ran = false;
+  ops_ctx c0 = cs[0];
+  JitSegment* js = nullptr;
+  int rc = segment_code_batch(c0, first, count, F[0].hl, &js);
+  if (rc) return rc;
+  if (!js) return OPS_OK;
+  *ran = true;
+  const LaunchEnv env0 = make_env(c0);
+  // per loop: its box and the CTAs per instance (one wave of the resident
+  // CTAs shared by the instances, at most one CTA per enumeration unit)
+  std::vector<std::array<int, 6>> boxes(count);
+  std::vector<int> grid(count, 0);
+  int stride = 1, rows = 0;
+  for (int i = 0; i < count; ++i) {
+    const QLoop& q = c0->queue[first + i];
+    std::array<int, 6>& box = boxes[i];
+    for (int k = 0; k < 6; ++k) box[k] = q.rng[k];
+    for (int d = q.dims; d < 3; ++d) {
+      box[2 * d] = 0;
+      box[2 * d + 1] = 1;
+    }
+    bool empty = false;
+    for (int d = 0; d < 3; ++d) empty = empty || box[2 * d + 1] <= box[2 * d];
+    if (empty) continue;
+    const int units = untiled_grid(env0, box.data());
+    const int cap = std::max(1, jit_resident(js, i) * c0->num_sms / n);
+    grid[i] = std::max(1, std::min(units, cap));
+    stride = std::max(stride, grid[i]);
+    const DLoop& L = F[0].hl[first + i];
+    if (L.nreds) rows = std::max(rows, L.part_row + L.nreds);
+  }
+  // device tables: instances | fold instances | partials
+  const size_t b_inst = sizeof(BatchInst) * n, b_fold = sizeof(FoldInst) * n,
+               b_part = sizeof(DD) * (size_t)rows * stride * n;
+  const size_t o_fold = (b_inst + 15) / 16 * 16, o_part = o_fold + (b_fold + 15) / 16 * 16, bytes = o_part + b_part;
+  if (bytes > c0->batch_cap) {
+    if (c0->d_batch) {
+      CUDA_TRY(c0, cudaStreamSynchronize(c0->stream));
+      dev_free(c0, c0->d_batch, c0->batch_cap);
+      c0->d_batch = nullptr;
+      c0->batch_cap = 0;
+    }
+    const size_t want = std::max<size_t>(bytes, 4096);
+    rc = dev_alloc(c0, &c0->d_batch, want);
+    if (rc) return rc;
+    c0->batch_cap = want;
+  }
+  char* d = (char*)c0->d_batch;
+  DD* d_part = (DD*)(d + o_part);
+  std::vector<char> host(o_part, 0);
+  BatchInst* hb = (BatchInst*)host.data();
+  FoldInst* hf = (FoldInst*)(host.data() + o_fold);
+  for (int k = 0; k < n; ++k) {
+    DD* part = d_part + (size_t)k * rows * stride;
+    hb[k] = BatchInst{cs[k]->d_loops + first, cs[k]->d_scal, part};
+    hf[k] = FoldInst{part, cs[k]->d_rows, cs[k]->d_scal, stride, 0};
+  }
+  rc = stage_copy(c0, d, host.data(), host.size());
+  if (rc) return rc;
+  int launches = 0, kernels = 0;
+  int64_t pts = 0;
+  for (int i = 0; i < count; ++i) {
+    if (!grid[i]) continue;
+    const std::array<int, 6>& box = boxes[i];
+    pts += (int64_t)(box[1] - box[0]) * (box[3] - box[2]) * (box[5] - box[4]);
+    rc = record_event(c0);
+    if (rc) return rc;
+    CUDA_TRY(c0, jit_launch_batch(js, i, c0->stream, (const BatchInst*)d, n, box.data(), grid[i], stride));
+    rc = record_event(c0);
+    if (rc) return rc;
+    ++launches;
+    ++kernels;
+    const DLoop& L = F[0].hl[first + i];
+    if (L.nreds) {
+      CUDA_TRY(c0, launch_fold_batch(c0->stream, (const FoldInst*)(d + o_fold), n, L.part_row, L.nreds, 0,
+                                     grid[i]));
+      ++launches;
+    }
+  }
+  for (int k = 0; k < n; ++k) {
+    ops_ctx c = cs[k];
+    c->stats.mode = OPS_MODE_UNTILED;
+    c->stats.compiled = 1;
+    c->stats.batched = n;
+    c->stats.loops += count;
+    c->stats.points += pts;
+  }
+  c0->stats.launches += launches;
+  c0->stats.kernel_launches += kernels;
+  return OPS_OK;
+}
+
+// Run segment (first, count) of every context of the batch, in the batch
+// candidate cd (mode, tile): untiled or the tile wavefront in launches
+// shared by all instances, or each context on its own stream in any other
+// mode cd[0].  On return cs[0]'s stream has the whole segment queued.
+int run_batch_candidate(ops_ctx* cs, int n, std::vector<FlushPrep>& F, int first, int count,
+                        const std::array<int, 5>& cd) {
+  ops_ctx c0 = cs[0];
+  if (cd[0] == OPS_MODE_TILEWAVE && count > 1) {
+    bool ran = false;
+    int rc = run_batch_tilewave(cs, n, F, first, count, &cd[1], &ran);
+    if (rc || ran) return rc;
+  }
+  if (cd[0] == OPS_MODE_TILEWAVE || cd[0] == OPS_MODE_UNTILED || cd[0] == OPS_MODE_AUTO) {
+    bool ran = false;
+    int rc = run_batch_untiled(cs, n, F, first, count, &ran);
+    if (rc || ran) return rc;
+  }
+  const int mode = cd[0] == OPS_MODE_TILEWAVE || cd[0] == OPS_MODE_AUTO ? OPS_MODE_UNTILED : cd[0];
+  for (int i = 1; i < n; ++i) {
+    int rc = stream_after(cs[i], c0);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < n; ++i) {
+    int rc = run_segment_mode(cs[i], first, count, first, F[i].hl, mode, &cd[1]);
+    if (rc) return rc;
+  }
+  for (int i = 1; i < n; ++i) {
+    int rc = stream_after(c0, cs[i]);
+    if (rc) return rc;
+  }
+  return OPS_OK;
+}
+
+// Candidates of the batch autotuner: untiled with one launch per loop for
+// all instances; the tile wavefront with its automatic tiles, with the
+// whole grid as one tile (each CTA then runs a whole instance's chain, no
+// waits), and with tiles of half the automatic size in y (more tiles per
+// instance for few instances).
+std::vector<std::array<int, 5>> batch_candidates(ops_ctx c, int first, int count) {
+  std::vector<std::array<int, 5>> cand;
+  cand.push_back({OPS_MODE_UNTILED, 0, 0, 0, 0});
+  if (count < 2 || c->cfg.interpret || c->cfg.check || !jit_available()) return cand;
+  const int ndim = c->queue[first].dims;
+  std::vector<PLoop> pl;
+  for (int i = 0; i < count; ++i) pl.push_back(plan_loop(c, c->queue[first + i]));
+  int at[3];
+  auto_tile_wave(c, pl, ndim, at);
+  cand.push_back({OPS_MODE_TILEWAVE, 0, 0, 0, 0});
+  cand.push_back({OPS_MODE_TILEWAVE, 1 << 20, ndim > 1 ? 1 << 20 : 1, ndim > 2 ? 1 << 20 : 1, 0});
+  if (ndim >= 2 && at[1] >= 16) cand.push_back({OPS_MODE_TILEWAVE, at[0], at[1] / 2, ndim > 2 ? at[2] : 1, 0});
+  return cand;
+}
+
+// One segment of the batch: the candidate of the context's mode, or under
+// OPS_MODE_AUTO the autotuner's pick (each candidate timed on cs[0]'s
+// stream twice, then the fastest kept for this signature and batch size).
+int run_batch_segment(ops_ctx* cs, int n, std::vector<FlushPrep>& F, int first, int count) {
+  ops_ctx c0 = cs[0];
+  for (int i = 1; i < n; ++i) {
+    int rc = segment_descriptors(cs[i], F[i], first, count);
+    if (!rc) rc = stream_after(c0, cs[i]);
+    if (rc) return rc;
+  }
+  int rc = segment_descriptors(c0, F[0], first, count);
+  if (rc) return rc;
+  const int mode = c0->cfg.mode;
+  if (mode != OPS_MODE_AUTO) {
+    std::array<int, 5> cd = {mode, c0->cfg.tile[0], c0->cfg.tile[1], c0->cfg.tile[2], 0};
+    return run_batch_candidate(cs, n, F, first, count, cd);
+  }
+  std::vector<int> key = segment_signature(c0, first, count);
+  key.push_back(-1);
+  key.push_back(n);
+  TuneRec& T = c0->btune[key];
+  if (T.cand.empty()) {
+    T.cand = batch_candidates(c0, first, count);
+    T.ms.assign(T.cand.size(), -1.0);
+    T.runs.assign(T.cand.size(), 0);
+    CUDA_TRY(c0, cudaEventCreate(&T.e0));
+    CUDA_TRY(c0, cudaEventCreate(&T.e1));
+  }
+  if (T.pending >= 0) {
+    float t = 0.f;
+    CUDA_TRY(c0, cudaEventSynchronize(T.e1));
+    CUDA_TRY(c0, cudaEventElapsedTime(&t, T.e0, T.e1));
+    T.ms[T.pending] = T.ms[T.pending] < 0 ? t : std::min<double>(T.ms[T.pending], t);
+    ++T.runs[T.pending];
+    T.pending = -1;
+  }
+  int pick = T.best;
+  if (pick < 0) {
+    constexpr int kTuneSamples = 2;
+    for (size_t i = 0; i < T.cand.size(); ++i)
+      if (T.runs[i] < kTuneSamples && (pick < 0 || T.runs[i] < T.runs[pick])) pick = (int)i;
+    if (pick < 0) {
+      pick = 0;
+      for (size_t i = 1; i < T.cand.size(); ++i)
+        if (T.ms[i] < T.ms[pick]) pick = (int)i;
+      T.best = pick;
+    }
+  }
+  const bool tuning = T.best < 0;
+  if (tuning) CUDA_TRY(c0, cudaEventRecord(T.e0, c0->stream));
+  rc = run_batch_candidate(cs, n, F, first, count, T.cand[pick]);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) cs[i]->stats.tuning |= tuning ? 1 : 0;
+  if (tuning) {
+    CUDA_TRY(c0, cudaEventRecord(T.e1, c0->stream));
+    T.pending = pick;
+  }
+  return OPS_OK;
+}
+
+// Two descriptors agree in everything the generated code depends on: all
+// but the dats' addresses and the constants (which the kernels load).
+bool same_descriptor(const DLoop& a, const DLoop& b) {
+  if (std::memcmp(&a, &b, offsetof(DLoop, ins)) != 0) return false;
+  if (std::memcmp(a.ins, b.ins, sizeof(a.ins[0]) * a.nins) != 0) return false;
+  for (int k = 0; k < a.nargs; ++k) {
+    const DArg &x = a.args[k], &y = b.args[k];
+    const size_t from = offsetof(DArg, pitch), to = offsetof(DArg, off) + sizeof(int32_t) * x.npts;
+    if (x.npts != y.npts || std::memcmp((const char*)&x + from, (const char*)&y + from, to - from) != 0) return false;
+  }
+  return true;
+}
+
+int execute_batch(ops_ctx* cs, int n) {
+  ops_ctx c0 = cs[0];
+  const int nloops = (int)c0->queue.size();
+  for (int i = 0; i < n; ++i) {
+    ops_ctx c = cs[i];
+    if (c->host_only) return fail(c0, OPS_ERR_NO_DEVICE, "host-only context %d in the batch", i);
+    if (c->cfg.device != c0->cfg.device || c->es != c0->es)
+      return fail(c0, OPS_ERR_INVALID_ARG, "context %d of the batch has another device or precision", i);
+    if ((int)c->queue.size() != nloops)
+      return fail(c0, OPS_ERR_INVALID_ARG, "context %d queued %d loops, the first %d", i, (int)c->queue.size(),
+                  nloops);
+    for (int j = 0; j < i; ++j)
+      if (cs[j] == c) return fail(c0, OPS_ERR_INVALID_ARG, "context %d appears twice in the batch", i);
+  }
+  if (nloops == 0) return OPS_OK;
+  std::vector<FlushPrep> F;
+  F.reserve(n);
+  for (int i = 0; i < n; ++i) F.emplace_back(cs[i]);
+  for (int i = 0; i < n; ++i) {
+    int rc = flush_prepare(cs[i], F[i]);
+    if (rc) return i == 0 ? rc : fail(c0, rc, "context %d of the batch: %s", i, cs[i]->err.c_str());
+  }
+  // The chains must match loop for loop in everything but the dats'
+  // addresses: the same code then serves every instance.  Nothing has run
+  // yet when they do not, and every queue is kept.
+  for (int i = 1; i < n; ++i) {
+    if (F[i].segs != F[0].segs)
+      return fail(c0, OPS_ERR_INVALID_ARG, "context %d cuts its chain into other segments", i);
+    for (int l = 0; l < nloops; ++l) {
+      const QLoop &q0 = c0->queue[l], &qi = cs[i]->queue[l];
+      bool same = same_descriptor(F[0].hl[l], F[i].hl[l]) && q0.dims == qi.dims && q0.code == qi.code &&
+                  q0.args.size() == qi.args.size();
+      for (size_t k = 0; same && k < q0.args.size(); ++k)
+        same = q0.args[k].kind == qi.args[k].kind && q0.args[k].handle == qi.args[k].handle &&
+               q0.args[k].stencil == qi.args[k].stencil && q0.args[k].access == qi.args[k].access;
+      if (!same)
+        return fail(c0, OPS_ERR_INVALID_ARG,
+                    "loop %d of context %d differs from the first context's in more than its dats' addresses "
+                    "and constants", l, i);
+    }
+  }
+  int rc = OPS_OK;
+  for (size_t s = 0; s < F[0].segs.size() && !rc; ++s)
+    rc = run_batch_segment(cs, n, F, F[0].segs[s].first, F[0].segs[s].second);
+  // the other contexts' later work follows the batch
+  for (int i = 1; i < n && !rc; ++i) rc = stream_after(cs[i], c0);
+  for (int i = 0; i < n; ++i) flush_done(cs[i], F[i]);
+  return rc;
 }
 
 int check_device_error(ops_ctx c) {
@@ -1933,10 +2530,18 @@ int ops_finalize(ops_ctx c) {
     dev_free(c, c->d_err, sizeof(int));
     dev_free(c, c->d_bar, 4 * sizeof(unsigned));
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-    for (auto& kv : c->tune) {
-      if (kv.second.e0) cudaEventDestroy(kv.second.e0);
-      if (kv.second.e1) cudaEventDestroy(kv.second.e1);
+    for (auto* tm : {&c->tune, &c->btune})
+      for (auto& kv : *tm) {
+        if (kv.second.e0) cudaEventDestroy(kv.second.e0);
+        if (kv.second.e1) cudaEventDestroy(kv.second.e1);
+      }
+    dev_free(c, c->d_batch, c->batch_cap);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (int k = 0; k < 2; ++k) {
+      if (c->ev_stage[k]) cudaEventDestroy(c->ev_stage[k]);
+      if (c->h_stage[k]) cudaFreeHost(c->h_stage[k]);
     }
+    if (c->h_small) cudaFreeHost(c->h_small);
     if (c->own_stream) cudaStreamDestroy(c->stream);
   }
   delete c;
@@ -2135,6 +2740,13 @@ int ops_execute(ops_ctx c) {
   return flush(c);
 }
 
+int ops_execute_batch(ops_ctx* ctxs, int count) {
+  if (!ctxs || count < 1) return OPS_ERR_INVALID_ARG;
+  for (int i = 0; i < count; ++i)
+    if (!ctxs[i]) return OPS_ERR_INVALID_ARG;
+  return execute_batch(ctxs, count);
+}
+
 int ops_queue_clear(ops_ctx c) {
   if (!c) return OPS_ERR_INVALID_ARG;
   c->queue.clear();
@@ -2156,9 +2768,17 @@ int ops_reduction_result(ops_ctx c, int red, double* host_out) {
   int rc = flush(c);
   if (rc) return rc;
   if (c->host_only) return fail(c, OPS_ERR_NO_DEVICE, "host-only context");
-  CUDA_TRY(c, cudaMemcpyAsync(host_out, c->d_scal + red, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  rc = check_device_error(c);  // synchronises the stream
-  if (rc) return rc;
+  if (!c->h_small) CUDA_TRY(c, cudaHostAlloc((void**)&c->h_small, sizeof *c->h_small, cudaHostAllocDefault));
+  // the value and the error word land in pinned memory: one wait for both
+  CUDA_TRY(c, cudaMemcpyAsync(&c->h_small->value, c->d_scal + red, sizeof(double), cudaMemcpyDeviceToHost,
+                              c->stream));
+  CUDA_TRY(c, cudaMemcpyAsync(&c->h_small->err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (c->h_small->err) {
+    rc = check_device_error(c);  // resets the word and reports it
+    if (rc) return rc;
+  }
+  *host_out = c->h_small->value;
   LaunchEnv env = make_env(c);
   CUDA_TRY(c, launch_set_scalar(env, red, red_identity(c->red_ops[red])));
   ++c->stats.launches;
@@ -2285,7 +2905,20 @@ int ops_compile_queued_wavefront(ops_ctx c, char* src_out, int64_t cap, int64_t*
   return OPS_OK;
 }
 
+int compile_queued_tilewave(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms,
+                            bool batch);
+
 int ops_compile_queued_tilewave(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms) {
+  return compile_queued_tilewave(c, src_out, cap, src_len, compile_ms, false);
+}
+
+int ops_compile_queued_tilewave_batch(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len,
+                                      double* compile_ms) {
+  return compile_queued_tilewave(c, src_out, cap, src_len, compile_ms, true);
+}
+
+int compile_queued_tilewave(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms,
+                            bool batch) {
   if (!c) return OPS_ERR_INVALID_ARG;
   if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
   const int n = (int)c->queue.size();
@@ -2295,7 +2928,7 @@ int ops_compile_queued_tilewave(ops_ctx c, char* src_out, int64_t cap, int64_t* 
   std::string src, why;
   double ms = 0.0;
   const int rc = jit_compile_tilewave_only(hl.data(), n, read_only_args(c, 0, n), c->es, c->queue[0].dims, &src,
-                                           &why, &ms);
+                                           &why, &ms, batch);
   if (src_len) *src_len = (int64_t)src.size();
   if (src_out && cap > 0) {
     const size_t k = std::min<size_t>(src.size(), (size_t)cap - 1);

@@ -582,3 +582,30 @@ def serving_stream(nreq: int = 512, seed: int = None, sizes: Sequence[int] = Non
     t = np.cumsum(gaps) - gaps[0]
     pick = R.splitmix64(R.subseed(seed, "size"), np.arange(nreq)) % np.uint64(len(sizes))
     return [(float(t[i]), int(sizes[int(pick[i])]), R.subseed(seed, "req", i)) for i in range(nreq)]
+
+
+def instances(chain: Chain, count: int, seed: int = None) -> List[Chain]:
+    """count copies of chain with the same loops, stencils and reductions and
+    fresh field values (the grids of a batch): each dat is drawn U(lo, hi)
+    over the range of the original's non-zero values, keeping the original's
+    zeros (the halos some workloads zero) and keeping a dat that is constant.
+    Instance 0 is chain itself."""
+    import copy
+    seed = R.subseed(R.BASE_SEED, "instances", chain.name) if seed is None else seed
+    out = [chain]
+    for k in range(1, count):
+        c = copy.copy(chain)
+        dats = []
+        for j, d in enumerate(chain.dats):
+            a = d.init
+            nz = a != 0.0
+            if not nz.any() or a[nz].min() == a[nz].max():
+                dats.append(DatSpec(d.name, a.copy()))
+                continue
+            lo, hi = float(a[nz].min()), float(a[nz].max())
+            u = R.uniform(R.subseed(seed, "inst", k, j), a.shape)
+            dats.append(DatSpec(d.name, np.where(nz, lo + (hi - lo) * u, 0.0)))
+        c.dats = dats
+        c.meta = dict(chain.meta, instance=k)
+        out.append(c)
+    return out

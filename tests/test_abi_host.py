@@ -345,6 +345,43 @@ def test_generated_wavefront_kernel_compiles(lib, name, fp32):
     ops.ops_finalize(ctx)
 
 
+@pytest.mark.parametrize("name,fp32,batch", [("edge", True, False), ("edge", False, True),
+                                             ("opensbli3d", False, True)])
+def test_generated_tilewave_kernels_compile(lib, name, fp32, batch):
+    """The tile-wavefront kernel and its batch form (one launch over several
+    instances' tiles) compile for sm_103a, FP64 or FP32, 2D or 3D; the batch
+    form maps tickets through its (instance, tile) table and stages each
+    instance's arguments in shared memory."""
+    from paper_1704_00693_gb300.chain import ChainRunner
+    if name == "edge":
+        from test_gpu_chain import edge_chain
+        c = edge_chain()
+    elif name == "cloverleaf2d":
+        c = W.cloverleaf2d(n=40, steps=1)
+    else:
+        c = W.opensbli3d(n=12, steps=1)
+    cfg = ops.ops_config_default()
+    cfg.device = ops.OPS_DEVICE_NONE
+    cfg.real = ops.OPS_REAL_F32 if fp32 else ops.OPS_REAL_F64
+    ctx = ops.ops_init(cfg)
+    r = ChainRunner(c, ctx=ctx, upload=False, mode="tilewave")
+    r.enqueue_step()
+    try:
+        src, n, ms = ops.ops_compile_queued(ctx, want_source=True, tilewave=True, batch=batch)
+    except ops.OpsError as e:
+        if e.code == ops.OPS_ERR_NO_DEVICE:
+            pytest.skip("NVRTC is not installed")
+        raise
+    assert n == len(src)
+    if batch:
+        assert " twb(" in src and " tw(" not in src and "tmap[tk]" in src and "s_A = AA[inst]" in src
+    else:
+        assert " tw(" in src and " twb(" not in src
+    assert src.count("          case ") == len(c.loops)
+    ops.ops_queue_clear(ctx)
+    ops.ops_finalize(ctx)
+
+
 def test_noalloc_rejects_overlapping_views_and_short_pitches(lib):
     """ops_loop_noalloc checks its views on the host before any device work
     (so fake device addresses do here): two views of overlapping memory
@@ -407,3 +444,29 @@ def test_scalars_share_the_handle_space_but_not_reductions(lib):
         ops.ops_queue_clear(ctx)
     finally:
         ops.ops_finalize(ctx)
+
+
+def test_execute_batch_argument_checks(lib):
+    """ops_execute_batch: no contexts, a NULL entry -> OPS_ERR_INVALID_ARG;
+    host-only contexts cannot execute -> OPS_ERR_NO_DEVICE, queues kept."""
+    import ctypes as C
+    L = ops.load()
+    assert L.ops_execute_batch(None, 0) == ops.OPS_ERR_INVALID_ARG
+    arr = (C.c_void_p * 2)(None, None)
+    assert L.ops_execute_batch(arr, 2) == ops.OPS_ERR_INVALID_ARG
+    cfg = ops.ops_config_default()
+    cfg.device = ops.OPS_DEVICE_NONE
+    ctxs = [ops.ops_init(cfg) for _ in range(2)]
+    try:
+        from paper_1704_00693_gb300.chain import ChainRunner
+        for ctx in ctxs:
+            r = ChainRunner(W.small2d(n=16, reps=1), ctx=ctx, upload=False, mode="tilewave")
+            r.enqueue_step()
+        with pytest.raises(ops.OpsError) as e:
+            ops.ops_execute_batch(ctxs)
+        assert e.value.code == ops.OPS_ERR_NO_DEVICE
+        assert L.ops_execute_batch((C.c_void_p * 1)(ctxs[0].value), 0) == ops.OPS_ERR_INVALID_ARG
+    finally:
+        for ctx in ctxs:
+            ops.ops_queue_clear(ctx)
+            ops.ops_finalize(ctx)
