@@ -60,6 +60,11 @@ def parse():
     p.add_argument("--no-3d", action="store_true", help="skip the other chains (OpenSBLI 3D, CloverLeaf 3D, PPCG)")
     p.add_argument("--serve-requests", type=int, default=512)
     p.add_argument("--no-batch", action="store_true", help="skip the batched small-grid chains")
+    p.add_argument("--only", default="", choices=["", "chain", "fp32", "ppcg", "jacobi", "batch"],
+                   help="run one section alone on grids of --n points per side and print its JSON (for "
+                        "profiling and sweeps): chain = the CloverLeaf-shaped step in --mode (FP64), fp32 = the "
+                        "same in FP32, ppcg, jacobi (FP32 heat-equation steps), batch (64 grids)")
+    p.add_argument("--real", default="f64", choices=["f64", "f32"], help="element type of --only chain")
     return p.parse_args()
 
 
@@ -514,6 +519,20 @@ def bench_fp32(stream, torch, n=3840, steps=5):
                               ("auto", None, "auto")], steps, fp32=True, bytes_per_elem=4)
 
 
+def bench_jacobi(stream, torch, n=8192, iters=10, steps=5):
+    """The paper's heat-equation benchmark shape (Sec. 6.A): Jacobi steps of
+    the 2D heat equation, `iters` iterations (2 loops each: the 5-point
+    update into a second dat, the copy back) per flush, in an FP32 context
+    on an n^2 grid (two 256 MB dats at 8192^2): untiled against the tile
+    wavefront at its automatic tiles and at 128 x 128, and the autotuner."""
+    from synth import workloads as W
+    chain = W.jacobi2d(n, iters, init="rand")
+    return compare_schedules(chain, stream, torch,
+                             [("untiled", None, "untiled"), ("tilewave", None, "tilewave"),
+                              ("tilewave", [128, 128, 0], "tilewave_128x128"), ("auto", None, "auto")],
+                             steps, fp32=True, bytes_per_elem=4)
+
+
 def bench_cloverleaf3d(stream, torch, n=330, steps=3):
     """The CloverLeaf-3D-shaped chain (330^3 as in the paper, 30 dats, 141 loops per step)."""
     from synth import workloads as W
@@ -719,6 +738,26 @@ def main():
         tile = [int(x) for x in args.tile.split(",")] + [0]
     stream = torch.cuda.Stream()
 
+    if args.only:
+        n = args.n
+        if args.only == "chain":
+            f32 = args.real == "f32"
+            ms, kms, kl, launches, st = time_mode(chain, args.mode, tile, args.steps, args.warmup, stream, torch,
+                                                  fp32=f32)
+            out = {"ms_per_step": ms / args.steps, "kernel_ms_per_step": kms / args.steps, "mode": args.mode,
+                   "schedule": SCHEDULES.get(st["mode"]), "tile": st["tile"], "tiles": st["tiles"], "n": n,
+                   "real": args.real, "gpu_launches": launches}
+        elif args.only == "fp32":
+            out = bench_fp32(stream, torch, n=n, steps=args.steps)
+        elif args.only == "ppcg":
+            out = bench_ppcg(stream, torch, n=n, steps=args.steps)
+        elif args.only == "jacobi":
+            out = bench_jacobi(stream, torch, n=n, steps=args.steps)
+        else:
+            out = bench_batch(torch, W.cloverleaf2d(n=n, steps=1), steps=args.steps, warmup=args.warmup)
+        print(json.dumps({"only": args.only, "result": out}), flush=True)
+        return
+
     def barrier():
         torch.cuda.synchronize()
         if world > 1:
@@ -812,6 +851,7 @@ def main():
     hydro3d = bench_cloverleaf3d(stream, torch) if rank == 0 and not args.no_3d else None
     ppcg = bench_ppcg(stream, torch) if rank == 0 and not args.no_3d else None
     fp32 = bench_fp32(stream, torch) if rank == 0 and not args.no_3d else None
+    jacobi = bench_jacobi(stream, torch) if rank == 0 and not args.no_3d else None
     serving = bench_serving(args.serve_requests) if rank == 0 and not args.no_serve else None
     batch = None
     if rank == 0 and not args.no_batch:
@@ -829,7 +869,7 @@ def main():
             "speedup_vs_untiled": (untiled["ms_per_step"] / (ms / args.steps)) if untiled else None,
             "untiled": untiled, "tilewave": tilewave, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk.summary(),
-            "cg_4000": cg, "serving": serving, "batch": batch, "opensbli3d_320": chain3d, "cloverleaf3d_330": hydro3d, "ppcg_4000": ppcg, "cloverleaf2d_3840_fp32": fp32,
+            "cg_4000": cg, "serving": serving, "batch": batch, "opensbli3d_320": chain3d, "cloverleaf3d_330": hydro3d, "ppcg_4000": ppcg, "cloverleaf2d_3840_fp32": fp32, "jacobi2d_8192_fp32": jacobi,
             "plan": {"phases": st["phases"], "barriers": st["barriers"], "skew": st["skew"],
                      "plan_ms_first_flush": first.get("plan_ms"), "compile_ms_first_flush": first.get("compile_ms"),
                      "plan_cache_hits": st["plan_cache_hits"]} if st else None,

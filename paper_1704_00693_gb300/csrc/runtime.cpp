@@ -138,7 +138,8 @@ struct ops_ctx_s {
   int loops_cap = 0;
   // host copy of the descriptors d_loops holds (in stream order), so a flush
   // uploads only the descriptors that changed since the last one
-  std::vector<DLoop> loops_mirror;
+  // dev_ok[i]: d_loops[i] holds the descriptor cache's entry i (stream order)
+  std::vector<char> dev_ok;
   DLoop* mirror_of = nullptr;
   // descriptors of the last flush, kept with the loops they were filled
   // from: a flush that queues the same loop at the same position (same
@@ -542,31 +543,27 @@ int stage_copy(ops_ctx c, void* dst, const void* src, size_t bytes) {
   return OPS_OK;
 }
 
-// Bring d_loops[first, first + count) up to date with hl, copying only the
-// runs of descriptors that differ from what the device already holds.
+// Bring d_loops[first, first + count) up to date with hl (the context's
+// descriptor cache), copying the runs of entries changed since the device
+// last received them.
 int upload_loops(ops_ctx c, const std::vector<DLoop>& hl, int first, int count) {
   if (c->mirror_of != c->d_loops) {
-    c->loops_mirror.clear();
+    c->dev_ok.clear();
     c->mirror_of = c->d_loops;
   }
-  if ((int)c->loops_mirror.size() < first + count) {
-    const size_t old = c->loops_mirror.size();
-    c->loops_mirror.resize(first + count);
-    // mark new entries as unknown (a descriptor never has nargs < 0)
-    for (size_t i = old; i < c->loops_mirror.size(); ++i) c->loops_mirror[i].nargs = -1;
-  }
+  if ((int)c->dev_ok.size() < first + count) c->dev_ok.resize(first + count, 0);
   int i = first;
   const int end = first + count;
   while (i < end) {
-    if (std::memcmp(&c->loops_mirror[i], &hl[i], sizeof(DLoop)) == 0) {
+    if (c->dev_ok[i]) {
       ++i;
       continue;
     }
     int j = i + 1;
-    while (j < end && std::memcmp(&c->loops_mirror[j], &hl[j], sizeof(DLoop)) != 0) ++j;
+    while (j < end && !c->dev_ok[j]) ++j;
     int rc = stage_copy(c, c->d_loops + i, hl.data() + i, sizeof(DLoop) * (j - i));
     if (rc) return rc;
-    std::memcpy(&c->loops_mirror[i], &hl[i], sizeof(DLoop) * (j - i));
+    std::fill(c->dev_ok.begin() + i, c->dev_ok.begin() + j, 1);
     i = j;
   }
   return OPS_OK;
@@ -1506,7 +1503,10 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
     if (first != dl_first) {
       // earlier runs moved written dats to their other buffers
       std::vector<FoldRow> unused;
-      for (int k = first; k < first + count; ++k) fill_dloop(c, c->queue[k], hl[k], hl[k].part_row, unused);
+      for (int k = first; k < first + count; ++k) {
+        fill_dloop(c, c->queue[k], hl[k], hl[k].part_row, unused);
+        if (k < (int)c->dev_ok.size()) c->dev_ok[k] = 0;
+      }
       int rc = upload_loops(c, hl, first, count);
       if (rc) return rc;
     }
@@ -1849,6 +1849,7 @@ int flush_prepare(ops_ctx c, FlushPrep& F) {
       if (src.K != q.K) {
         std::memcpy(L.K, q.K.data(), sizeof(double) * q.K.size());
         src.K = q.K;
+        if (i < (int)c->dev_ok.size()) c->dev_ok[i] = 0;
       }
       for (const ops_arg& a : q.args)
         if (a.kind == OPS_ARG_RED) rows.push_back(FoldRow{a.handle, c->red_ops[a.handle]});
@@ -1856,6 +1857,7 @@ int flush_prepare(ops_ctx c, FlushPrep& F) {
       fill_dloop(c, q, L, F.prow[i], rows);
       src = q;
       c->hl_ok[i] = 1;
+      if (i < (int)c->dev_ok.size()) c->dev_ok[i] = 0;
     }
   }
   c->hl_gen = c->swap_gen;
@@ -1863,7 +1865,7 @@ int flush_prepare(ops_ctx c, FlushPrep& F) {
   const int cap0 = c->loops_cap;
   int rc = ensure(c, &c->d_loops, &c->loops_cap, n);
   if (rc) return rc;
-  if (c->loops_cap != cap0) c->loops_mirror.clear();  // new allocation: contents unknown
+  if (c->loops_cap != cap0) c->dev_ok.clear();  // new allocation: contents unknown
   // every descriptor at most once per segment and the fold rows
   rc = stage_begin(c, sizeof(DLoop) * (size_t)n + sizeof(FoldRow) * rows.size() + 64);
   if (rc) return rc;
@@ -1922,7 +1924,10 @@ int flush_prepare(ops_ctx c, FlushPrep& F) {
 int segment_descriptors(ops_ctx c, FlushPrep& F, int first, int count) {
   if (c->swap_gen != F.filled_gen) {
     std::vector<FoldRow> unused;
-    for (int k = first; k < first + count; ++k) fill_dloop(c, c->queue[k], F.hl[k], F.prow[k], unused);
+    for (int k = first; k < first + count; ++k) {
+      fill_dloop(c, c->queue[k], F.hl[k], F.prow[k], unused);
+      if (k < (int)c->dev_ok.size()) c->dev_ok[k] = 0;
+    }
   }
   return upload_loops(c, F.hl, first, count);
 }
