@@ -60,10 +60,11 @@ def parse():
     p.add_argument("--no-3d", action="store_true", help="skip the other chains (OpenSBLI 3D, CloverLeaf 3D, PPCG)")
     p.add_argument("--serve-requests", type=int, default=512)
     p.add_argument("--no-batch", action="store_true", help="skip the batched small-grid chains")
-    p.add_argument("--only", default="", choices=["", "chain", "fp32", "ppcg", "jacobi", "batch"],
+    p.add_argument("--only", default="", choices=["", "chain", "fp32", "ppcg", "jacobi", "batch", "probe"],
                    help="run one section alone on grids of --n points per side and print its JSON (for "
                         "profiling and sweeps): chain = the CloverLeaf-shaped step in --mode (FP64), fp32 = the "
-                        "same in FP32, ppcg, jacobi (FP32 heat-equation steps), batch (64 grids)")
+                        "same in FP32, ppcg, jacobi (FP32 heat-equation steps), batch (64 grids), probe (the "
+                        "hardware probes with the SM clocks sampled while they run)")
     p.add_argument("--real", default="f64", choices=["f64", "f32"], help="element type of --only chain")
     return p.parse_args()
 
@@ -724,6 +725,11 @@ def main():
     import paper_1704_00693_gb300 as ops
     from synth import workloads as W
 
+    if args.only == "probe":
+        with ClockSampler(local) as clk:
+            res = ops.ops_probe_device(local)
+        print(json.dumps({"only": "probe", "result": res, "clocks": clk.summary()}), flush=True)
+        return
     probe = None
     if not args.no_probe:
         try:
