@@ -501,8 +501,7 @@ int ops_probe_device(int device, ops_probe_result* out);
  * exits.  No call allocates: no cudaMalloc, cudaFree or allocating library
  * routine.
  *   - The first call on a device looks the array's device address up
- *     (cudaGetSymbolAddress, with that device current) and caches it; make
- *     that first call before any stream capture on the device.
+ *     (cudaGetSymbolAddress, with that device current) and caches it.
  *   - Every call on a device shares the one array and overwrites what the
  *     previous call left there; two calls whose work overlaps on the GPU
  *     (different streams, no ordering between them) race and give wrong
