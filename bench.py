@@ -60,7 +60,7 @@ def parse():
     p.add_argument("--no-3d", action="store_true", help="skip the other chains (OpenSBLI 3D, CloverLeaf 3D, PPCG)")
     p.add_argument("--serve-requests", type=int, default=512)
     p.add_argument("--no-batch", action="store_true", help="skip the batched small-grid chains")
-    p.add_argument("--only", default="", choices=["", "chain", "fp32", "ppcg", "jacobi", "batch", "probe"],
+    p.add_argument("--only", default="", choices=["", "chain", "fp32", "ppcg", "jacobi", "batch", "probe", "serve"],
                    help="run one section alone on grids of --n points per side and print its JSON (for "
                         "profiling and sweeps): chain = the CloverLeaf-shaped step in --mode (FP64), fp32 = the "
                         "same in FP32, ppcg, jacobi (FP32 heat-equation steps), batch (64 grids), probe (the "
@@ -390,12 +390,15 @@ def bench_serving(nreq=512, seq_sample=None, tol=1e-8, budget=48 << 30):
                 ids.append(ops.ops_serve_submit(srv, *probs[i]))
             res = [ops.ops_serve_poll(srv, rid, reqs[i][1]) for i, rid in enumerate(ids)]
             makespan = time.perf_counter() - t0
+            counters = ops.ops_serve_stats(srv)
         finally:
             ops.ops_serve_close(srv)
         lat = np.array([st["latency_ms"] for _, st in res])
         conv = sum(st["converged"] for _, st in res)
         return {"solves_per_s": nreq / makespan, "makespan_s": makespan, "p50_ms": float(np.percentile(lat, 50)),
-                "p99_ms": float(np.percentile(lat, 99)), "converged": conv}, res
+                "p99_ms": float(np.percentile(lat, 99)), "converged": conv,
+                "worker_ms": {k: round(counters[k], 1) for k in ("upload_ms", "run_ms", "fetch_ms", "idle_ms")},
+                "rounds": counters["rounds"]}, res
 
     sat, res = serve([0.0] * nreq)
     # check a few results against the oracle's FP64 residual
@@ -759,6 +762,8 @@ def main():
             out = bench_ppcg(stream, torch, n=n, steps=args.steps)
         elif args.only == "jacobi":
             out = bench_jacobi(stream, torch, n=n, steps=args.steps)
+        elif args.only == "serve":
+            out = bench_serving(args.serve_requests)
         else:
             out = bench_batch(torch, W.cloverleaf2d(n=n, steps=1), steps=args.steps, warmup=args.warmup)
         print(json.dumps({"only": args.only, "result": out}), flush=True)

@@ -454,6 +454,15 @@ int ops_serve_submit(ops_server srv, int n, const double* host_kappa, const doub
 int ops_serve_poll(ops_server srv, uint64_t id, int wait, double* host_x, ops_solve_stats* stats);
 /* Finish running solves, drop queued ones, free the pool and the context. */
 int ops_serve_close(ops_server srv);
+/* Where the server's worker thread has spent its time since open. */
+typedef struct {
+  int64_t admitted, completed, rounds;  /* requests admitted / retired; batch rounds run */
+  double upload_ms;  /* copying admitted requests' arrays to the device */
+  double run_ms;     /* queueing a round's iterations and waiting for them */
+  double fetch_ms;   /* copying finished solutions back to host memory */
+  double idle_ms;    /* waiting for requests with nothing admitted */
+} ops_serve_counters;
+int ops_serve_stats(ops_server srv, ops_serve_counters* out);
 
 /* ---- hardware probes behind the reported roofline ----
  * The paper sets its roofline from STREAM, the L3 bandwidth and DGEMM on

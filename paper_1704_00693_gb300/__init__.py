@@ -530,6 +530,19 @@ def ops_serve_poll(srv, rid: int, n: int, wait: bool = True):
     return x, st.as_dict()
 
 
+class ops_serve_counters(C.Structure):
+    _fields_ = [("admitted", C.c_int64), ("completed", C.c_int64), ("rounds", C.c_int64), ("upload_ms", C.c_double),
+                ("run_ms", C.c_double), ("fetch_ms", C.c_double), ("idle_ms", C.c_double)]
+
+
+def ops_serve_stats(srv) -> dict:
+    out = ops_serve_counters()
+    rc = load().ops_serve_stats(srv, C.byref(out))
+    if rc != OPS_OK:
+        raise OpsError(rc, "ops_serve_stats failed")
+    return {k: getattr(out, k) for k, _ in out._fields_}
+
+
 def ops_serve_close(srv):
     rc = load().ops_serve_close(srv)
     if rc != OPS_OK:

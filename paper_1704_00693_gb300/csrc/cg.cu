@@ -794,8 +794,9 @@ cudaError_t CgBatch::run(int ticks) {
   return cudaGraphLaunch(gexec_, stream_);
 }
 
-cudaError_t CgBatch::poll(std::vector<int>& done) {
+cudaError_t CgBatch::poll(std::vector<int>& done, std::vector<CgProb>* infos) {
   done.clear();
+  if (infos) infos->clear();
   const int nslots = (int)hprob_.size();
   if (!nslots || !dprob_) return cudaSuccess;
   std::vector<CgProb> tmp(nslots);
@@ -807,6 +808,7 @@ cudaError_t CgBatch::poll(std::vector<int>& done) {
     if (live_[s] && !reported_[s] && tmp[s].state == CG_DONE) {
       reported_[s] = 1;
       done.push_back(s);
+      if (infos) infos->push_back(tmp[s]);
     }
   return cudaSuccess;
 }

@@ -66,9 +66,15 @@ class CgBatch {
   void remove(int slot);
   // Run `ticks` lockstep iterations for every live problem.
   cudaError_t run(int ticks);
-  // Copy states back; fills done slots (state CG_DONE) not yet reported.
-  cudaError_t poll(std::vector<int>& done);
+  // Copy states back; fills done slots (state CG_DONE) not yet reported
+  // and, if infos is given, their final state (iterations, residual).
+  cudaError_t poll(std::vector<int>& done, std::vector<CgProb>* infos = nullptr);
   cudaError_t fetch(int slot, double* host_x, CgProb* info);
+  // Device address of a problem's solution and its side; a problem in
+  // state CG_DONE is no longer written by any kernel, so its solution may be
+  // copied on another stream while later iterations of the batch run.
+  const double* solution(int slot) const { return hprob_[slot].x; }
+  int side(int slot) const { return hprob_[slot].n; }
   // w = A u for one problem's operator (prec 0: FP64; 1: FP32 with u and w
   // rounded to / widened from float); host arrays of n*n doubles.
   cudaError_t apply(int slot, int prec, const double* host_u, double* host_w);

@@ -151,3 +151,4 @@ def test_many_requests_reuse_fixed_tables():
     assert max_concurrency([s for _, s in res]) <= 8
     for (k, b), (x, st) in zip(probs, res):
         assert st["converged"] == 1 and oracle.relres(k, b, x) <= TOL
+
