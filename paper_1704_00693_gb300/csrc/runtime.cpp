@@ -1709,9 +1709,10 @@ std::vector<int> segment_signature(ops_ctx c, int first, int count) {
 // Autotuner (the paper picks tile sizes by a cache heuristic, Sec. 4.C; here
 // the heuristic only seeds the search): every schedule of a segment gives
 // bit-identical dats, so successive flushes of the same segment each run one
-// candidate -- untiled, or skewed with the cache-fitting outer tile size h0
-// and 2, 4, 8, 16 times it -- timed with CUDA events; afterwards the fastest
-// candidate is used for that segment.
+// candidate -- untiled, the tile wavefront at three tile shapes, skewed at
+// the cache-fitting outer tile size and 4 times it, skewed on quarter-length
+// sub-segments -- timed with CUDA events; afterwards the fastest candidate
+// (mode, tile and segment length) is used for that segment.
 int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl) {
   const int ndim = c->queue[first].dims;
   TuneRec& T = c->tune[segment_signature(c, first, count)];
@@ -1756,6 +1757,9 @@ int run_segment_auto(ops_ctx c, int first, int count, int dl_base, std::vector<D
       T.cand.push_back(cd);
       if (cd[1 + od] >= ext[od]) break;
     }
+    // the segment length too: long segments cut into quarters (at least 8
+    // loops each), whose smaller skew keeps the seed tiles valid
+    if (count >= 16) T.cand.push_back({OPS_MODE_SKEWED, at[0], at[1], at[2], std::max(8, count / 4)});
     // Overlapped tiles are not a candidate: on GB300 their redundant halo
     // work and one-CTA-per-SM footprints made them 4-10x slower than
     // untiled on every chain measured; OPS_MODE_OVERLAPPED still runs them.
