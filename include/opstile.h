@@ -55,7 +55,8 @@ extern "C" {
 
 /* ---- execution modes of a flushed chain ---- */
 #define OPS_MODE_UNTILED 0    /* one kernel per loop over its full range (the comparator) */
-#define OPS_MODE_SKEWED 1     /* Algorithm 1 tiles, run by one persistent kernel (Algorithm 2) */
+#define OPS_MODE_SKEWED 1     /* Algorithm 1 tiles run tile by tile (Algorithm 2); see
+                                 ops_config.skewed_persistent for the two compiled forms */
 #define OPS_MODE_OVERLAPPED 2 /* independent shared-memory tiles with halo recomputation (Sec. 4.D) */
 /* OPS_MODE_OVERLAPPED applies to a segment whose dats are all library-owned
  * with one common size and halo, and whose tile footprints fit one CTA's
@@ -162,6 +163,10 @@ typedef struct {
                           run compiled bodies only (no checked or interpreted mode); constants
                           and scalar arguments are rounded to float on load; reductions take the
                           float values exactly and accumulate as in FP64 */
+  int skewed_persistent; /* OPS_MODE_SKEWED with compiled bodies: 1 runs a segment's phases in
+                            one cooperative launch of a kernel holding every body, with grid
+                            barriers only before the phases the plan marks; 0 (default, measured
+                            faster on GB300) launches each phase's loop kernel in plan order */
 } ops_config;
 #define OPS_REAL_F64 0
 #define OPS_REAL_F32 1
@@ -365,6 +370,9 @@ int ops_compile_queued_wavefront(ops_ctx ctx, char* src_out, int64_t cap, int64_
 
 /* The same for the tile-wavefront kernel of the queued loops (OPS_MODE_TILEWAVE). */
 int ops_compile_queued_tilewave(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
+/* The same for the persistent skewed kernel of the queued loops (OPS_MODE_SKEWED
+ * with compiled bodies: every loop body in one cooperative kernel). */
+int ops_compile_queued_skewed(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
 /* The same for the batch form of the tile-wavefront kernel (ops_execute_batch). */
 int ops_compile_queued_tilewave_batch(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len,
                                       double* compile_ms);

@@ -53,7 +53,7 @@ class ops_config(C.Structure):
     _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("mode", C.c_int), ("tile", C.c_int * 3),
                 ("segment", C.c_int), ("check", C.c_int), ("l2_bytes", C.c_int64), ("hbm_budget", C.c_int64),
                 ("timeout_ms", C.c_int), ("blocks_per_sm", C.c_int), ("test_skip_barrier_block", C.c_int),
-                ("timing", C.c_int), ("interpret", C.c_int), ("real", C.c_int)]
+                ("timing", C.c_int), ("interpret", C.c_int), ("real", C.c_int), ("skewed_persistent", C.c_int)]
 
 
 class ops_arg(C.Structure):
@@ -340,13 +340,15 @@ def ops_plan_tilewave(ctx, tile):
 
 
 def ops_compile_queued(ctx, want_source: bool = False, wavefront: bool = False, tilewave: bool = False,
-                       batch: bool = False):
+                       batch: bool = False, skewed: bool = False):
     """Generate and compile (NVRTC, sm_103a, no device) the loop bodies of the
     queued loops -- the per-loop and overlapped-tile kernels, or with
     wavefront=True the wavefront kernel, with tilewave=True the
-    tile-wavefront kernel (batch=True: its batch form); returns (source or
-    None, source length, compile ms)."""
-    f = (load().ops_compile_queued_tilewave_batch if tilewave and batch else
+    tile-wavefront kernel (batch=True: its batch form), with skewed=True the
+    persistent skewed kernel; returns (source or None, source length,
+    compile ms)."""
+    f = (load().ops_compile_queued_skewed if skewed else
+         load().ops_compile_queued_tilewave_batch if tilewave and batch else
          load().ops_compile_queued_tilewave if tilewave else
          load().ops_compile_queued_wavefront if wavefront else load().ops_compile_queued)
     n = C.c_int64(0)

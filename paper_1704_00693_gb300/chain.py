@@ -22,7 +22,7 @@ class ChainRunner:
     def __init__(self, chain, mode: str = "auto", tile=None, segment: int = 0, check: bool = False,
                  stream: int = 0, device: int = 0, ctx=None, blocks_per_sm: int = 0, timeout_ms: int = 0,
                  skip_barrier_block: int = -1, upload: bool = True, timing: bool = False,
-                 interpret: bool = False, fp32: bool = False):
+                 interpret: bool = False, fp32: bool = False, skewed_persistent: bool = False):
         self.chain = chain
         self.dtype = np.float32 if fp32 else np.float64
         self.own_ctx = ctx is None
@@ -43,6 +43,7 @@ class ChainRunner:
             cfg.timing = 1 if timing else 0
             cfg.interpret = 1 if interpret else 0
             cfg.real = 1 if fp32 else 0
+            cfg.skewed_persistent = 1 if skewed_persistent else 0
             ctx = ops_init(cfg)
         else:
             ops_set_mode(ctx, MODES[mode], tile, segment)

@@ -790,6 +790,81 @@ std::string generate_wavefront(const DLoop* loops, int count, const std::vector<
   return os.str();
 }
 
+// Source of the persistent skewed kernel "sk" (Algorithm 2 in one launch):
+// every loop body of the segment behind a switch; the CTAs of one
+// cooperative grid run the plan's (tile, loop) phases in order, each phase
+// as a grid-stride enumeration of its box, and meet at a grid barrier only
+// before the phases the plan marks (where the phase conflicts with one
+// since the last barrier).  The barrier counts arrivals and bumps a
+// generation word; waits are bounded in wall-clock time, after which the
+// CTA sets the error word and every CTA leaves at its next barrier.
+// Reductions combine into each CTA's partial column.
+const char* kSkPrelude = R"SKP(
+struct SkPhase { int loop, barrier; int box[6]; };
+__device__ bool sk_barrier(unsigned* bar, int* err, long long timeout_ns, bool skip) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = bar + 1;
+    const unsigned gen = *vgen;
+    __threadfence();
+    bool wait = true;
+    if (!skip) {
+      if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        atomicAdd(bar + 1, 1u);
+        wait = false;
+      }
+    }
+    if (wait) {
+      const unsigned long long t0 = now_ns();
+      unsigned spins = 0;
+      while (*vgen == gen) {
+        if (*(volatile int*)err) break;
+        if ((++spins & 31u) == 0 && (long long)(now_ns() - t0) > timeout_ns) {
+          atomicCAS(err, 0, 1);
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)err == 0;
+}
+)SKP";
+
+std::string generate_skewed(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es) {
+  std::ostringstream os;
+  os << "// opstile persistent skewed kernel: " << pts_for(es) << " rows per unit, " << kJitMinCtas
+     << " CTAs per SM, " << (es == 4 ? "fp32" : "fp64") << "\n";
+  os << kPrelude << kDeviceCommon << kPreludeTail << kSkPrelude;
+  os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
+  os << "static_assert(sizeof(SkPhase) == " << sizeof(Phase) << ", \"Phase layout\");\n";
+  for (int i = 0; i < count; ++i) {
+    LoopGen g(loops[i], ro[i], os, false, es == 4);
+    g.emit(i);
+  }
+  os << "extern \"C\" __global__ void __launch_bounds__(256, " << kJitMinCtas
+     << ") sk(const DLoop* __restrict__ L,\n"
+        "    const SkPhase* __restrict__ ph, int nph, const double* __restrict__ scal, DD* part, int stride,\n"
+        "    unsigned* bar, int* err, long long timeout_ns, int skip_block) {\n"
+        "  const bool skip = (int)blockIdx.x == skip_block;\n"
+        "  for (int p = 0; p < nph; ++p) {\n"
+        "    const SkPhase P = ph[p];\n"
+        "    if (P.barrier && !sk_barrier(bar, err, timeout_ns, skip)) return;\n"
+        "    switch (P.loop) {\n";
+  for (int i = 0; i < count; ++i)
+    os << "      case " << i << ": body" << i
+       << "(L + " << i << ", P.box[0], P.box[1], P.box[2], P.box[3], P.box[4], P.box[5], blockIdx.x, gridDim.x, "
+          "scal, part, stride, 0); break;\n";
+  os << "      default: break;\n"
+        "    }\n"
+        "  }\n"
+        "}\n";
+  return os.str();
+}
+
 // Source of the tile-wavefront kernel "tw" for the loops of a segment (see
 // build_tile_wave).  A persistent grid draws tiles from a ticket counter in
 // the plan's order; each CTA runs every loop of its tile in order.  Its
@@ -1580,6 +1655,87 @@ int jit_wavefront(int device, const DLoop* loops, int count, const std::vector<s
   *out = w.get();
   g_waves[key] = std::move(w);
   return OPS_OK;
+}
+
+struct JitSkew {
+  CUfunction f = nullptr;
+  int per_sm = 0;
+};
+
+namespace {
+std::map<std::pair<int, std::string>, std::unique_ptr<JitSkew>> g_skews;
+}  // namespace
+
+int jit_skewed(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+               JitSkew** out, std::string* why, double* compile_ms) {
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!api_ready(why)) return OPS_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  const std::string src = generate_skewed(loops, count, ro, es);
+  auto key = std::make_pair(device, src);
+  auto it = g_skews.find(key);
+  if (it != g_skews.end()) {
+    *out = it->second.get();
+    return OPS_OK;
+  }
+  std::string cubin;
+  if (!cubin_for(src, &cubin, why)) return OPS_ERR_CUDA;
+  CUmodule mod;
+  if (g_api.load(&mod, cubin.data()) != CUDA_SUCCESS) {
+    *why = "cuModuleLoadData failed";
+    return OPS_ERR_CUDA;
+  }
+  std::unique_ptr<JitSkew> k(new JitSkew);
+  if (g_api.get_function(&k->f, mod, "sk") != CUDA_SUCCESS) {
+    *why = "cuModuleGetFunction failed";
+    return OPS_ERR_CUDA;
+  }
+  if (g_api.occupancy(&k->per_sm, k->f, kThreads, 0) != CUDA_SUCCESS || k->per_sm < 1) {
+    *why = "the persistent skewed kernel does not fit an SM";
+    return OPS_ERR_CUDA;
+  }
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = k.get();
+  g_skews[key] = std::move(k);
+  return OPS_OK;
+}
+
+int jit_compile_skewed_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                            std::string* src, std::string* why, double* compile_ms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  *src = generate_skewed(loops, count, ro, es);
+  if (!api_ready(why, true)) {
+    if (why->empty()) *why = g_api.why;
+    return OPS_ERR_NO_DEVICE;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  std::string cubin;
+  const bool ok = compile(*src, &cubin, why);
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return ok ? OPS_OK : OPS_ERR_CUDA;
+}
+
+int jit_skewed_max_grid(JitSkew* k, int num_sms) { return k->per_sm * num_sms; }
+
+cudaError_t jit_launch_skewed(const JitSkew* k, const LaunchEnv& env, const DLoop* d_loops, const Phase* d_phases,
+                              int nphases, int grid) {
+  cudaError_t e = cudaMemsetAsync(env.bar, 0, 2 * sizeof(unsigned), env.stream);
+  if (e != cudaSuccess) return e;
+  const DLoop* a0 = d_loops;
+  const Phase* a1 = d_phases;
+  int a2 = nphases;
+  const double* a3 = env.scal;
+  DD* a4 = env.part;
+  int a5 = env.part_stride;
+  unsigned* a6 = env.bar;
+  int* a7 = env.err;
+  long long a8 = env.timeout_ns;
+  int a9 = env.skip_block;
+  void* args[] = {&a0, &a1, &a2, &a3, &a4, &a5, &a6, &a7, &a8, &a9};
+  return to_cuda(g_api.launch_coop(k->f, (unsigned)grid, 1, 1, kThreads, 1, 1, 0, (CUstream)env.stream, args));
 }
 
 int jit_compile_wavefront_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,

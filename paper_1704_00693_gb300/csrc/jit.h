@@ -124,6 +124,21 @@ cudaError_t jit_launch_wavefront(const JitWave* w, const LaunchEnv& env, const D
                                  const WfPhase* d_phases, const int* d_deps, const int* d_uphase, int nunits,
                                  int* d_done, int* d_ticket, int grid);
 
+// Persistent skewed execution (Algorithm 2 in one cooperative launch of
+// compiled bodies, ops_config.skewed_persistent = 1): the plan's phases in
+// order, a grid barrier before each phase whose `barrier` flag is set.
+struct JitSkew;
+int jit_skewed(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+               JitSkew** out, std::string* why, double* compile_ms);
+int jit_compile_skewed_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                            std::string* src, std::string* why, double* compile_ms);
+// CTAs co-resident on the device (the cooperative grid's limit)
+int jit_skewed_max_grid(JitSkew* k, int num_sms);
+// env.bar (2 words) is reset on the stream first; reductions combine into
+// env.part's columns (the caller initialises and folds them).
+cudaError_t jit_launch_skewed(const JitSkew* k, const LaunchEnv& env, const DLoop* d_loops, const Phase* d_phases,
+                              int nphases, int grid);
+
 // Tile wavefront (OPS_MODE_TILEWAVE, see build_tile_wave): one persistent
 // kernel with every loop body of the segment; each CTA runs all the loops of
 // one tile at a time.  Its arguments travel by value in one struct.

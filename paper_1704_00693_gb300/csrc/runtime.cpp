@@ -162,6 +162,7 @@ struct ops_ctx_s {
   std::map<std::vector<int>, JitSegment*> jit;
   std::map<std::vector<int>, JitWave*> jitw;  // wavefront kernels, same keys
   std::map<std::vector<int>, JitTile*> jitt;  // tile-wavefront kernels, same keys
+  std::map<std::vector<int>, JitSkew*> jitk;  // persistent skewed kernels, same keys
   std::string jit_why;
   int64_t allocated = 0;
   std::string err;
@@ -1176,6 +1177,28 @@ int tile_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, Jit
   return OPS_OK;
 }
 
+// The persistent skewed kernel of a segment (compiled once per code).
+int skew_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitSkew** out) {
+  *out = nullptr;
+  std::vector<int> key = code_key(c, first, count);
+  auto it = c->jitk.find(key);
+  if (it != c->jitk.end()) {
+    *out = it->second;
+    return OPS_OK;
+  }
+  std::vector<std::vector<char>> ro = read_only_args(c, first, count);
+  JitSkew* k = nullptr;
+  std::string why;
+  double ms = 0.0;
+  const int rc = jit_skewed(c->cfg.device, hl.data() + first, count, ro, c->es, &k, &why, &ms);
+  c->stats.compile_ms += ms;
+  if (rc) return fail(c, rc, "compiling the persistent skewed kernel: %s", why.c_str());
+  if (!k) c->jit_why = why;
+  c->jitk[key] = k;
+  *out = k;
+  return OPS_OK;
+}
+
 // Automatic tile of the tile wavefront: 128 x 64 points in FP32 and 64 x 64
 // in FP64 (2D), 64 x 16 x 16 (3D) -- the fastest shapes measured on GB300
 // for the CloverLeaf- and PPCG-shaped chains; smaller, L2-sized tiles made
@@ -1663,7 +1686,19 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
   int rc = record_event(c);
   if (rc) return rc;
   int sgrid = c->skewed_grid;
-  if (js) {
+  JitSkew* sk = nullptr;
+  if (js && count > 1 && c->cfg.skewed_persistent) {
+    rc = skew_code(c, first, count, hl, &sk);
+    if (rc) return rc;
+  }
+  if (sk) {
+    // compiled bodies in one cooperative launch: grid barriers only where
+    // the plan keeps them
+    sgrid = std::max(1, std::min(jit_skewed_max_grid(sk, c->num_sms), c->part_stride));
+    CUDA_TRY(c, jit_launch_skewed(sk, env, c->d_loops + dl_base, cp->d_phases, (int)P.phases.size(), sgrid));
+    ++c->stats.launches;
+    ++c->stats.kernel_launches;
+  } else if (js) {
     // compiled bodies: one launch per phase in plan order; the stream
     // orders the phases as the persistent kernel's barriers do
     sgrid = 1;
@@ -2916,6 +2951,27 @@ int ops_compile_queued_wavefront(ops_ctx c, char* src_out, int64_t cap, int64_t*
 
 int compile_queued_tilewave(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms,
                             bool batch);
+
+int ops_compile_queued_skewed(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
+  const int n = (int)c->queue.size();
+  std::vector<DLoop> hl(n);
+  std::vector<FoldRow> rows;
+  for (int i = 0; i < n; ++i) fill_dloop(c, c->queue[i], hl[i], (int)rows.size(), rows);
+  std::string src, why;
+  double ms = 0.0;
+  const int rc = jit_compile_skewed_only(hl.data(), n, read_only_args(c, 0, n), c->es, &src, &why, &ms);
+  if (src_len) *src_len = (int64_t)src.size();
+  if (src_out && cap > 0) {
+    const size_t k = std::min<size_t>(src.size(), (size_t)cap - 1);
+    std::memcpy(src_out, src.data(), k);
+    src_out[k] = '\0';
+  }
+  if (compile_ms) *compile_ms = ms;
+  if (rc) return fail(c, rc, "%s", why.c_str());
+  return OPS_OK;
+}
 
 int ops_compile_queued_tilewave(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms) {
   return compile_queued_tilewave(c, src_out, cap, src_len, compile_ms, false);

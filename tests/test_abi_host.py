@@ -446,6 +446,30 @@ def test_scalars_share_the_handle_space_but_not_reductions(lib):
         ops.ops_finalize(ctx)
 
 
+@pytest.mark.parametrize("fp32", [False, True])
+def test_generated_persistent_skewed_kernel_compiles(lib, fp32):
+    """The persistent skewed kernel (every body behind one switch, bounded
+    grid barriers at the plan's marked phases) compiles for sm_103a."""
+    from paper_1704_00693_gb300.chain import ChainRunner
+    from test_gpu_chain import edge_chain
+    c = edge_chain()
+    cfg = ops.ops_config_default()
+    cfg.device = ops.OPS_DEVICE_NONE
+    cfg.real = ops.OPS_REAL_F32 if fp32 else ops.OPS_REAL_F64
+    ctx = ops.ops_init(cfg)
+    r = ChainRunner(c, ctx=ctx, upload=False, mode="skewed")
+    r.enqueue_step()
+    try:
+        src, n, ms = ops.ops_compile_queued(ctx, want_source=True, skewed=True)
+    except ops.OpsError as e:
+        if e.code == ops.OPS_ERR_NO_DEVICE:
+            pytest.skip("NVRTC is not installed")
+        raise
+    assert " sk(" in src and "sk_barrier" in src and src.count("      case ") == len(c.loops)
+    ops.ops_queue_clear(ctx)
+    ops.ops_finalize(ctx)
+
+
 def test_execute_batch_argument_checks(lib):
     """ops_execute_batch: no contexts, a NULL entry -> OPS_ERR_INVALID_ARG;
     host-only contexts cannot execute -> OPS_ERR_NO_DEVICE, queues kept."""

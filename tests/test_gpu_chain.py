@@ -251,6 +251,40 @@ def test_barrier_timeout_reports_and_context_recovers():
     assert_same(c, got, ref, what="after timeout")
 
 
+def test_compiled_skewed_barrier_timeout_reports_and_context_recovers():
+    """The same with compiled bodies: the persistent skewed kernel's grid
+    barriers give up after the limit, every CTA leaves, OPS_ERR_TIMEOUT."""
+    c = W.small2d(n=64, reps=1)
+    r = ChainRunner(c, mode="skewed", tile=(0, 8, 0), timeout_ms=200, skip_barrier_block=0,
+                    skewed_persistent=True)
+    try:
+        r.enqueue_step()
+        with pytest.raises(ops.OpsError) as e:
+            ops.ops_sync(r.ctx)
+        assert e.value.code == ops.OPS_ERR_TIMEOUT
+        assert r.stats()["kernel_launches"] == 1  # one persistent launch, not one per phase
+    finally:
+        r.close()
+    ref, _ = oracle.run_chain(c)
+    got, _, st = run_gpu(c, "skewed", (0, 8, 0), skewed_persistent=True)
+    assert_same(c, got, ref, what="after timeout")
+    assert st["kernel_launches"] == st["segments"]
+
+
+@pytest.mark.parametrize("fp32", [False, True])
+@pytest.mark.parametrize("name,tile", [("cloverleaf2d", (0, 0, 0)), ("cloverleaf2d", (0, 40, 0)),
+                                       ("ppcg2d", (0, 24, 0)), ("cloverleaf3d", (0, 0, 8))])
+def test_persistent_skewed_kernel_bit_exact(name, tile, fp32):
+    """The persistent skewed kernel (one cooperative launch per segment, grid
+    barriers only at the plan's marked phases) against the oracle."""
+    c = {"cloverleaf2d": lambda: W.cloverleaf2d(n=130, steps=2), "ppcg2d": lambda: W.ppcg2d(n=100, inner=10, steps=2),
+         "cloverleaf3d": lambda: W.cloverleaf3d(n=24, steps=1)}[name]()
+    ref, ref_hist = oracle.run_chain(c, fp32=fp32)
+    got, hist, st = run_gpu(c, "skewed", tile, fp32=fp32, skewed_persistent=True)
+    assert_same(c, got, ref, hist, ref_hist, what=f"persistent skewed {name} {tile} fp32={fp32}")
+    assert st["mode"] == ops.OPS_MODE_SKEWED and 4 * st["kernel_launches"] <= st["phases"]
+
+
 def test_wavefront_timeout_reports_and_context_recovers():
     """The wavefront kernel's first work unit never reports completion: the
     phases waiting on it give up after the limit, every CTA leaves, the host
