@@ -39,7 +39,7 @@ KERNEL_SRC = [os.path.join(ROOT, "paper_1704_00693_gb300", "csrc", f) for f in (
 # FP64 fallback when the probe is skipped: 2 DFMA per clock per SM on GB300, fma = 2 flops
 FP64_DFMA_PER_CLK_SM = 2
 NUM_SMS = 152
-SCHEDULES = {0: "untiled", 1: "skewed", 2: "overlapped", 3: "auto", 4: "wavefront", 5: "tilewave"}
+SCHEDULES = {0: "untiled", 1: "skewed", 2: "overlapped", 3: "auto", 4: "wavefront", 5: "tilewave", 6: "tilewarp"}
 
 
 def parse():
@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N_DEFAULT)
-    p.add_argument("--mode", default="auto", choices=["skewed", "untiled", "overlapped", "wavefront", "tilewave", "auto"])
+    p.add_argument("--mode", default="auto", choices=["skewed", "untiled", "overlapped", "wavefront", "tilewave", "tilewarp", "auto"])
     p.add_argument("--no-probe", action="store_true", help="skip the hardware probes (FP64 rate, L2, barriers)")
     p.add_argument("--tile", default="", help="x,y tile (0 = automatic)")
     p.add_argument("--no-e2e", action="store_true")
@@ -533,7 +533,8 @@ def bench_jacobi(stream, torch, n=8192, iters=10, steps=5):
     chain = W.jacobi2d(n, iters, init="rand")
     return compare_schedules(chain, stream, torch,
                              [("untiled", None, "untiled"), ("tilewave", None, "tilewave"),
-                              ("tilewave", [128, 128, 0], "tilewave_128x128"), ("auto", None, "auto")],
+                              ("tilewave", [128, 128, 0], "tilewave_128x128"), ("tilewarp", None, "tilewarp"),
+                              ("auto", None, "auto")],
                              steps, fp32=True, bytes_per_elem=4)
 
 

@@ -94,6 +94,13 @@ extern "C" {
  * until they are not; a segment of one loop runs untiled; with check = 1 or
  * interpret = 1, or without NVRTC, the segment runs in OPS_MODE_SKEWED.
  * Results are identical to every other mode. */
+#define OPS_MODE_TILEWARP 6  /* the tile wavefront's plan with a tile per warp instead of per CTA */
+/* OPS_MODE_TILEWARP runs OPS_MODE_TILEWAVE's plan (automatic tiles smaller:
+ * 64 x 32 in FP32, 32 x 32 in FP64, 32 x 8 x 8 in 3D) with every warp a worker
+ * of its own: a warp runs a tile's loops with only warp-level ordering
+ * between them and waits on the predecessor tiles' progress counters alone,
+ * so the warps of an SM never wait for one another at a CTA barrier.
+ * Fallbacks and results as OPS_MODE_TILEWAVE. */
 
 /* ---- argument kinds, access modes, reduction operators ---- */
 #define OPS_ARG_DAT 0    /* a dat accessed through a stencil */
@@ -370,6 +377,8 @@ int ops_compile_queued_wavefront(ops_ctx ctx, char* src_out, int64_t cap, int64_
 
 /* The same for the tile-wavefront kernel of the queued loops (OPS_MODE_TILEWAVE). */
 int ops_compile_queued_tilewave(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
+/* The same for the tile-per-warp kernel of the queued loops (OPS_MODE_TILEWARP). */
+int ops_compile_queued_tilewarp(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);
 /* The same for the persistent skewed kernel of the queued loops (OPS_MODE_SKEWED
  * with compiled bodies: every loop body in one cooperative kernel). */
 int ops_compile_queued_skewed(ops_ctx ctx, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms);

@@ -29,7 +29,7 @@ OPS_ERR_STATE = -8
 OPS_ERR_NO_DEVICE = -9
 
 (OPS_MODE_UNTILED, OPS_MODE_SKEWED, OPS_MODE_OVERLAPPED, OPS_MODE_AUTO, OPS_MODE_WAVEFRONT,
- OPS_MODE_TILEWAVE) = 0, 1, 2, 3, 4, 5
+ OPS_MODE_TILEWAVE, OPS_MODE_TILEWARP) = 0, 1, 2, 3, 4, 5, 6
 OPS_ARG_DAT, OPS_ARG_SCALAR, OPS_ARG_RED = 0, 1, 2
 OPS_READ, OPS_WRITE, OPS_RW, OPS_INC = 0, 1, 2, 3
 OPS_RED_SUM, OPS_RED_MIN, OPS_RED_MAX = 0, 1, 2
@@ -40,7 +40,8 @@ OPS_REAL_F64, OPS_REAL_F32 = 0, 1
  OPS_IR_SGT, OPS_IR_WSUM, OPS_IR_WACC, OPS_IR_POLY, OPS_IR_ST, OPS_IR_RED) = range(1, 16)
 
 MODES = {"untiled": OPS_MODE_UNTILED, "skewed": OPS_MODE_SKEWED, "overlapped": OPS_MODE_OVERLAPPED,
-         "auto": OPS_MODE_AUTO, "wavefront": OPS_MODE_WAVEFRONT, "tilewave": OPS_MODE_TILEWAVE}
+         "auto": OPS_MODE_AUTO, "wavefront": OPS_MODE_WAVEFRONT, "tilewave": OPS_MODE_TILEWAVE,
+         "tilewarp": OPS_MODE_TILEWARP}
 
 
 class OpsError(RuntimeError):
@@ -340,14 +341,15 @@ def ops_plan_tilewave(ctx, tile):
 
 
 def ops_compile_queued(ctx, want_source: bool = False, wavefront: bool = False, tilewave: bool = False,
-                       batch: bool = False, skewed: bool = False):
+                       batch: bool = False, skewed: bool = False, tilewarp: bool = False):
     """Generate and compile (NVRTC, sm_103a, no device) the loop bodies of the
     queued loops -- the per-loop and overlapped-tile kernels, or with
     wavefront=True the wavefront kernel, with tilewave=True the
     tile-wavefront kernel (batch=True: its batch form), with skewed=True the
     persistent skewed kernel; returns (source or None, source length,
     compile ms)."""
-    f = (load().ops_compile_queued_skewed if skewed else
+    f = (load().ops_compile_queued_tilewarp if tilewarp else
+         load().ops_compile_queued_skewed if skewed else
          load().ops_compile_queued_tilewave_batch if tilewave and batch else
          load().ops_compile_queued_tilewave if tilewave else
          load().ops_compile_queued_wavefront if wavefront else load().ops_compile_queued)

@@ -506,7 +506,9 @@ struct LoopGen {
   // load of a point is an immediate offset from one address.  Reductions go
   // to the tile's column `col` of the partial rows (row = the loop's partial
   // row - row0), assigned.
-  void emit_tile(int i, int NT, int P) const {
+  // warp = true: the tile-per-warp form, one warp evaluates every unit of
+  // the box and reduces with shuffles alone.
+  void emit_tile(int i, int NT, int P, bool warp = false) const {
     restrict_all = true;
     staged_ptrs = true;
     os << "\n__device__ __forceinline__ void tb" << i
@@ -529,11 +531,14 @@ struct LoopGen {
     }
     emit_points(P);
     os << "  };\n";
-    os << "  run_units<" << P << ", 32>(x0, x1, y0, y1, z0, z1, (int)(threadIdx.x >> 5), " << NT / 32
-       << ", one, full);\n";
+    if (warp)
+      os << "  run_units<" << P << ", 32>(x0, x1, y0, y1, z0, z1, 0, 1, one, full);\n";
+    else
+      os << "  run_units<" << P << ", 32>(x0, x1, y0, y1, z0, z1, (int)(threadIdx.x >> 5), " << NT / 32
+         << ", one, full);\n";
     for (int k = 0; k < L.nreds; ++k)
-      os << "  flush_red_col(" << L.red_op[k] << ", acc" << k << ", part + (size_t)(L->part_row + " << k
-         << " - row0) * stride + col);\n";
+      os << (warp ? "  flush_red_warp(" : "  flush_red_col(") << L.red_op[k] << ", acc" << k
+         << ", part + (size_t)(L->part_row + " << k << " - row0) * stride + col);\n";
     os << "}\n";
   }
 };
@@ -947,6 +952,10 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // the compute warps' own barrier (named barrier 2; the step barrier is 1)
 __device__ __forceinline__ void bar_compute() { asm volatile("bar.sync 2, %0;" :: "n"(kTwNtc) : "memory"); }
 __device__ __forceinline__ void bar_step() { asm volatile("bar.sync 1, %0;" :: "n"(kTwNtc + 32) : "memory"); }
+__device__ __forceinline__ void flush_red_warp(int op, DD v, DD* dst) {
+  for (int o = 16; o > 0; o >>= 1) v = red_combine(op, v, shfl_down_dd(v, o));
+  if ((threadIdx.x & 31) == 0) *dst = v;
+}
 __device__ __forceinline__ void flush_red_col(int op, DD v, DD* dst) {
   for (int o = 16; o > 0; o >>= 1) v = red_combine(op, v, shfl_down_dd(v, o));
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -961,6 +970,140 @@ __device__ __forceinline__ void flush_red_col(int op, DD v, DD* dst) {
   bar_compute();
 }
 )TWP";
+
+// Source of the tile-per-warp kernel "tww": the tile wavefront's plan and
+// arguments, but every warp is a worker of its own.  A warp draws a tile
+// from the ticket counter, stages the tile's boxes and wait table in its
+// slice of shared memory, and runs the tile's steps: its lanes below the
+// number of predecessor directions poll the predecessors' progress
+// (relaxed loads, one acquire fence, bounded wait), the warp runs the
+// step's loops over the whole box in units of 32 x by P rows with a
+// __syncwarp between loops, and lane 0 publishes the completed loops
+// (release store).  Warps never wait for one another except through the
+// progress counters, so the SM's warps hide each other's L2 latency; the
+// ticket order gives the same progress guarantee as in the tile wavefront
+// (the earliest unfinished tile is held by a running warp whose
+// predecessors are done).  Dynamic shared memory: per warp NL boxes, the
+// wait table and live flags; per CTA every loop's dat pointers.
+std::string generate_tilewarp(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                              int ndim) {
+  const int wpb = jit_tilewarp_warps(), nt = 32 * wpb, P = jit_tile_pts(es), ndirs = (1 << ndim) - 1;
+  std::ostringstream os;
+  os << "// opstile tile-per-warp kernel: " << wpb << " warps per CTA, " << P << " rows per unit, " << ndim << "D, "
+     << (es == 4 ? "fp32" : "fp64") << "\n";
+  os << kPrelude << kDeviceCommon << kPreludeTail;
+  os << "constexpr int kTwNtc = " << nt << ";\n" << kTwPrelude;
+  os << "static_assert(sizeof(DLoop) == " << sizeof(DLoop) << ", \"DLoop layout\");\n";
+  os << "static_assert(sizeof(TwArgs) == " << sizeof(TwArgs) << ", \"TwArgs layout\");\n";
+  for (int i = 0; i < count; ++i) {
+    LoopGen g(loops[i], ro[i], os, false, es == 4);
+    g.emit_tile(i, 32, P, true);
+  }
+  os << "extern \"C\" __global__ void __launch_bounds__(" << nt << ", " << jit_tilewarp_min_ctas()
+     << ") tww(const TwArgs A) {\n"
+        "  constexpr int NL = " << count << ", ND = " << ndirs << ", WPB = " << wpb << ";\n"
+        "  extern __shared__ __align__(16) unsigned char tww_smem[];\n"
+        "  void** s_lptr = (void**)tww_smem;                                   // [NL][8]\n"
+        "  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;\n"
+        "  int* s_box = (int*)(tww_smem + sizeof(void*) * 8 * NL) + w * 6 * NL;  // [NL][6] of this warp\n"
+        "  unsigned short* s_need = (unsigned short*)((int*)(tww_smem + sizeof(void*) * 8 * NL) + WPB * 6 * NL)\n"
+        "                           + w * ND * NL;                              // [ND][NL] of this warp\n"
+        "  unsigned char* s_live = (unsigned char*)((unsigned short*)((int*)(tww_smem + sizeof(void*) * 8 * NL)\n"
+        "                           + WPB * 6 * NL) + WPB * ND * NL) + w * NL;   // [NL] of this warp\n"
+        "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
+        "  for (int j = threadIdx.x; j < NL * 8; j += blockDim.x) {\n"
+        "    const int l = j >> 3, a = j & 7;\n"
+        "    s_lptr[j] = a < A.loops[l].nargs ? (void*)A.loops[l].args[a].ptr0 : nullptr;\n"
+        "  }\n"
+        "  __syncthreads();\n"
+        "  int tk = 0;\n"
+        "  if (lane == 0) tk = atomicAdd(A.ticket, 1);\n"
+        "  tk = __shfl_sync(0xffffffffu, tk, 0);\n"
+        "  while (tk < A.ntiles) {\n"
+        "    const int tile = A.order[tk];\n"
+        "    const int tc[3] = {tile % A.nt[0], (tile / A.nt[0]) % A.nt[1], tile / (A.nt[0] * A.nt[1])};\n"
+        "    const int cl = (A.cls[A.coff[2] + tc[2]] * A.ncls[1] + A.cls[A.coff[1] + tc[1]]) * A.ncls[0] +\n"
+        "                   A.cls[A.coff[0] + tc[0]];\n"
+        "    int nxt = 0;\n"
+        "    if (lane == 0) nxt = atomicAdd(A.ticket, 1);\n"
+        "    for (int j = lane; j < ND * NL; j += 32) s_need[j] = A.need[(size_t)cl * (ND * NL) + j];\n"
+        "    for (int j = lane; j < 6 * NL; j += 32) {\n"
+        "      const int l = j / 6, q = j - 6 * l, d = q >> 1;\n"
+        "      s_box[j] = A.rng[A.roff[d] + 2 * (tc[d] * NL + l) + (q & 1)];\n"
+        "    }\n"
+        "    __syncwarp();\n"
+        "    for (int l = lane; l < NL; l += 32) {\n"
+        "      const int* b = s_box + 6 * l;\n"
+        "      s_live[l] = (b[1] > b[0] && b[3] > b[2] && b[5] > b[4]) || A.loops[l].nreds;\n"
+        "    }\n"
+        "    int pred = -1, have = 0x7fffffff;\n"
+        "    if (lane < ND) {\n"
+        "      const int m = lane + 1;\n"
+        "      const int px = tc[0] - (m & 1), py = tc[1] - ((m >> 1) & 1), pz = tc[2] - ((m >> 2) & 1);\n"
+        "      if (px >= 0 && py >= 0 && pz >= 0) {\n"
+        "        pred = (pz * A.nt[1] + py) * A.nt[0] + px;\n"
+        "        have = 0;\n"
+        "      }\n"
+        "    }\n"
+        "    __syncwarp();\n"
+        "    bool stop = false;\n"
+        "    for (int g = 0; g < A.ngroups && !stop; ++g) {\n"
+        "      const int l0 = A.groups[g], l1 = A.groups[g + 1];\n"
+        "      bool any = false;\n"
+        "      for (int l = l0; l < l1; ++l) any = any || s_live[l];\n"
+        "      if (any) {\n"
+        "        // may the step run?  each predecessor must have completed what its loops conflict with\n"
+        "        bool ok = true;\n"
+        "        if (lane < ND) {\n"
+        "          int want = 0;\n"
+        "          for (int l = l0; l < l1; ++l) want = max(want, (int)s_need[lane * NL + l]);\n"
+        "          if (have < want) {\n"
+        "            const int* pp = A.prog + pred;\n"
+        "            int v = ld_relaxed(pp);\n"
+        "            unsigned spins = 0;\n"
+        "            unsigned long long t0 = 0;\n"
+        "            while (v < want) {\n"
+        "              if ((++spins & 63u) == 0) {\n"
+        "                if (t0 == 0) {\n"
+        "                  t0 = now_ns();\n"
+        "                } else if (*(volatile int*)A.err || (long long)(now_ns() - t0) > A.timeout_ns) {\n"
+        "                  ok = false;\n"
+        "                  break;\n"
+        "                }\n"
+        "              }\n"
+        "              v = ld_relaxed(pp);\n"
+        "            }\n"
+        "            fence_acq_rel();\n"
+        "            have = v;\n"
+        "          }\n"
+        "        }\n"
+        "        if (!__all_sync(0xffffffffu, ok)) {\n"
+        "          if (lane == 0) atomicCAS(A.err, 0, 1);\n"
+        "          stop = true;\n"
+        "          break;\n"
+        "        }\n"
+        "        __syncwarp();  // the polling lanes' acquire orders the other lanes' loads\n"
+        "        for (int l = l0; l < l1; ++l) {\n"
+        "          if (!s_live[l]) continue;\n"
+        "          const int* B = s_box + 6 * l;\n"
+        "          switch (l) {\n";
+  for (int i = 0; i < count; ++i)
+    os << "            case " << i << ": tb" << i << "(A.loops + " << i << ", s_lptr + " << 8 * i
+       << ", B[0], B[1], B[2], B[3], B[4], B[5], A.scal, A.part, A.stride, A.row0, tile); break;\n";
+  os << "            default: break;\n"
+        "          }\n"
+        "          __syncwarp();\n"
+        "        }\n"
+        "      }\n"
+        "      // the step's writes are ordered before lane 0's release by the __syncwarp above\n"
+        "      if (lane == 0 && tile != A.skip_tile) st_release(A.prog + tile, l1);\n"
+        "    }\n"
+        "    tk = __shfl_sync(0xffffffffu, nxt, 0);\n"
+        "    if (stop || *(volatile int*)A.err) break;\n"
+        "  }\n"
+        "}\n";
+  return os.str();
+}
 
 std::string generate_tilewave(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
                               int ndim, bool batch) {
@@ -1819,6 +1962,8 @@ int jit_tile_ahead() {
 
 struct JitTile {
   CUfunction f = nullptr;
+  int threads = 0;   // block size
+  int smem = 0;      // dynamic shared memory bytes
 };
 
 namespace {
@@ -1850,6 +1995,7 @@ int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<st
     *why = "cuModuleGetFunction failed";
     return OPS_ERR_CUDA;
   }
+  t->threads = jit_tile_threads() + 32;
   if (compile_ms)
     *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
   *out = t.get();
@@ -1876,15 +2022,88 @@ int jit_compile_tilewave_only(const DLoop* loops, int count, const std::vector<s
 int jit_tilewave_max_grid(JitTile* t, int num_sms) {
   std::lock_guard<std::mutex> lk(g_mu);
   int per_sm = 0;
-  if (g_api.occupancy(&per_sm, t->f, jit_tile_threads() + 32, 0) != CUDA_SUCCESS) return 0;
+  if (g_api.occupancy(&per_sm, t->f, t->threads, (size_t)t->smem) != CUDA_SUCCESS) return 0;
   return per_sm * num_sms;
 }
 
 cudaError_t jit_launch_tilewave(const JitTile* t, const TwArgs& args, cudaStream_t stream, int grid) {
   TwArgs a = args;
   void* params[] = {&a};
-  return to_cuda(g_api.launch(t->f, (unsigned)grid, 1, 1, (unsigned)(jit_tile_threads() + 32), 1, 1, 0,
+  return to_cuda(g_api.launch(t->f, (unsigned)grid, 1, 1, (unsigned)t->threads, 1, 1, (unsigned)t->smem,
                               (CUstream)stream, params, nullptr));
+}
+
+int jit_tilewarp_warps() {
+  static const int v = env_int("OPSTILE_TWW_WARPS", 4, 1, 32);
+  return v;
+}
+
+int jit_tilewarp_min_ctas() {
+  static const int v = env_int("OPSTILE_TWW_MINB", 4, 1, 32);
+  return v;
+}
+
+int jit_tilewarp_smem(int count, int ndim) {
+  const int wpb = jit_tilewarp_warps(), nd = (1 << ndim) - 1;
+  return (int)(sizeof(void*) * 8 * count + sizeof(int) * wpb * 6 * count + sizeof(unsigned short) * wpb * nd * count +
+               (size_t)wpb * count + 16);
+}
+
+std::map<std::pair<int, std::string>, std::unique_ptr<JitTile>> g_warps;
+
+int jit_tilewarp(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es, int ndim,
+                 JitTile** out, std::string* why, double* compile_ms) {
+  *out = nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!api_ready(why)) return OPS_OK;
+  auto t0 = std::chrono::steady_clock::now();
+  const std::string src = generate_tilewarp(loops, count, ro, es, ndim);
+  auto key = std::make_pair(device, src);
+  auto it = g_warps.find(key);
+  if (it != g_warps.end()) {
+    *out = it->second.get();
+    return OPS_OK;
+  }
+  std::string cubin;
+  if (!cubin_for(src, &cubin, why)) return OPS_ERR_CUDA;
+  CUmodule mod;
+  if (g_api.load(&mod, cubin.data()) != CUDA_SUCCESS) {
+    *why = "cuModuleLoadData failed";
+    return OPS_ERR_CUDA;
+  }
+  std::unique_ptr<JitTile> t(new JitTile);
+  if (g_api.get_function(&t->f, mod, "tww") != CUDA_SUCCESS) {
+    *why = "cuModuleGetFunction failed";
+    return OPS_ERR_CUDA;
+  }
+  t->threads = 32 * jit_tilewarp_warps();
+  t->smem = jit_tilewarp_smem(count, ndim);
+  if (t->smem > 48 * 1024 &&
+      g_api.set_attribute(t->f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, t->smem) != CUDA_SUCCESS) {
+    *why = "the tile-per-warp kernel's shared memory does not fit";
+    return OPS_ERR_CUDA;
+  }
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  *out = t.get();
+  g_warps[key] = std::move(t);
+  return OPS_OK;
+}
+
+int jit_compile_tilewarp_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                              int ndim, std::string* src, std::string* why, double* compile_ms) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  *src = generate_tilewarp(loops, count, ro, es, ndim);
+  if (!api_ready(why, true)) {
+    if (why->empty()) *why = g_api.why;
+    return OPS_ERR_NO_DEVICE;
+  }
+  auto t0 = std::chrono::steady_clock::now();
+  std::string cubin;
+  const bool ok = compile(*src, &cubin, why);
+  if (compile_ms)
+    *compile_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  return ok ? OPS_OK : OPS_ERR_CUDA;
 }
 
 cudaError_t jit_launch_tilewave_batch(const JitTile* t, const TwArgs* d_args, const int* d_tmap, int total,
@@ -1894,8 +2113,8 @@ cudaError_t jit_launch_tilewave_batch(const JitTile* t, const TwArgs* d_args, co
   int tot = total;
   int* tk = d_ticket;
   void* params[] = {&aa, &tm, &tot, &tk};
-  return to_cuda(g_api.launch(t->f, (unsigned)grid, 1, 1, (unsigned)(jit_tile_threads() + 32), 1, 1, 0,
-                              (CUstream)stream, params, nullptr));
+  return to_cuda(g_api.launch(t->f, (unsigned)grid, 1, 1, (unsigned)t->threads, 1, 1, 0, (CUstream)stream, params,
+                              nullptr));
 }
 
 }  // namespace opstile

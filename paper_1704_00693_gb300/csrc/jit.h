@@ -186,7 +186,16 @@ int jit_tilewave(int device, const DLoop* loops, int count, const std::vector<st
                  JitTile** out, std::string* why, double* compile_ms, bool batch = false);
 int jit_compile_tilewave_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
                               int ndim, std::string* src, std::string* why, double* compile_ms, bool batch = false);
-// CTAs of the kernel resident on the device at once
+// The tile-per-warp form (OPS_MODE_TILEWARP): the same plan and arguments,
+// each warp a worker running whole tiles; OPSTILE_TWW_WARPS warps per CTA
+// (default 4), registers sized for OPSTILE_TWW_MINB CTAs per SM (default 4).
+int jit_tilewarp_warps();
+int jit_tilewarp_min_ctas();
+int jit_tilewarp(int device, const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es, int ndim,
+                 JitTile** out, std::string* why, double* compile_ms);
+int jit_compile_tilewarp_only(const DLoop* loops, int count, const std::vector<std::vector<char>>& ro, int es,
+                              int ndim, std::string* src, std::string* why, double* compile_ms);
+// CTAs of the kernel (either form) resident on the device at once
 int jit_tilewave_max_grid(JitTile* t, int num_sms);
 cudaError_t jit_launch_tilewave(const JitTile* t, const TwArgs& args, cudaStream_t stream, int grid);
 // The batch kernel: d_args[i] are instance i's arguments (every instance's

@@ -1156,9 +1156,10 @@ int run_wavefront(ops_ctx c, int first, int count, int dl_base, std::vector<DLoo
 // Tile-wavefront kernel of a segment (every loop body in one module),
 // compiled at the segment's first such flush; nullptr when run-time
 // compilation is unavailable (reason in jit_why).
-int tile_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitTile** out) {
+int tile_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitTile** out, bool warp = false) {
   *out = nullptr;
   std::vector<int> key = code_key(c, first, count);
+  if (warp) key.push_back(-OPS_MODE_TILEWARP);  // the tile-per-warp form
   auto it = c->jitt.find(key);
   if (it != c->jitt.end()) {
     *out = it->second;
@@ -1168,7 +1169,10 @@ int tile_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, Jit
   JitTile* t = nullptr;
   std::string why;
   double ms = 0.0;
-  const int rc = jit_tilewave(c->cfg.device, hl.data() + first, count, ro, c->es, c->queue[first].dims, &t, &why, &ms);
+  const int rc = warp ? jit_tilewarp(c->cfg.device, hl.data() + first, count, ro, c->es, c->queue[first].dims, &t,
+                                     &why, &ms)
+                      : jit_tilewave(c->cfg.device, hl.data() + first, count, ro, c->es, c->queue[first].dims, &t,
+                                     &why, &ms);
   c->stats.compile_ms += ms;
   if (rc) return fail(c, rc, "compiling the tile-wavefront kernel: %s", why.c_str());
   if (!t) c->jit_why = why;
@@ -1204,14 +1208,16 @@ int skew_code(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, Jit
 // for the CloverLeaf- and PPCG-shaped chains; smaller, L2-sized tiles made
 // more, shorter steps and ran slower.  Dimensions are capped by the extent,
 // and tiles the chain's skew reaches across are grown by the planner.
-void auto_tile_wave(ops_ctx c, const std::vector<PLoop>& pl, int ndim, int tile[3]) {
+void auto_tile_wave(ops_ctx c, const std::vector<PLoop>& pl, int ndim, int tile[3], bool warp = false) {
   int lo[3] = {1 << 30, 1 << 30, 1 << 30}, hi[3] = {-(1 << 30), -(1 << 30), -(1 << 30)};
   for (const PLoop& p : pl)
     for (int d = 0; d < 3; ++d) {
       lo[d] = std::min(lo[d], p.rng[2 * d]);
       hi[d] = std::max(hi[d], p.rng[2 * d + 1]);
     }
-  const int shape2[2] = {c->es == 4 ? 128 : 64, 64}, shape3[3] = {64, 16, 16};
+  // a warp's tile is a quarter to an eighth of a CTA's: 64 x 32 FP32, 32 x 32 FP64, 32 x 8 x 8 in 3D
+  const int shape2[2] = {warp ? (c->es == 4 ? 64 : 32) : (c->es == 4 ? 128 : 64), warp ? 32 : 64};
+  const int shape3[3] = {warp ? 32 : 64, warp ? 8 : 16, warp ? 8 : 16};
   for (int d = 0; d < 3; ++d) {
     const int ext = std::max(1, hi[d] - lo[d]);
     int want = 1;
@@ -1225,7 +1231,7 @@ void auto_tile_wave(ops_ctx c, const std::vector<PLoop>& pl, int ndim, int tile[
 // until the plan is valid; *out = nullptr (and jit_why says why) if no size
 // up to the whole extent is.
 int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int dl_base, const int* tile_in,
-              CachedPlan** out) {
+              CachedPlan** out, bool warp = false) {
   *out = nullptr;
   const int ndim = c->queue[first].dims;
   std::vector<PLoop> pl;
@@ -1236,7 +1242,7 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
   for (int d = 0; d < ndim; ++d) autod = autod || tile[d] <= 0;
   if (autod) {
     int at[3];
-    auto_tile_wave(c, pl, ndim, at);
+    auto_tile_wave(c, pl, ndim, at, warp);
     for (int d = 0; d < 3; ++d)
       if (tile[d] <= 0) tile[d] = at[d];
   }
@@ -1379,16 +1385,16 @@ int tile_plan(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, int
 // Tile-wavefront execution of a segment (OPS_MODE_TILEWAVE).  *ran = false
 // when no valid plan exists (the caller then runs the segment skewed).
 int run_tilewave(ops_ctx c, int first, int count, int dl_base, std::vector<DLoop>& hl, const int* tile_in,
-                 JitTile* t, bool* ran) {
+                 JitTile* t, bool* ran, bool warp = false) {
   *ran = false;
   CachedPlan* cp = nullptr;
-  int rc = tile_plan(c, first, count, hl, dl_base, tile_in, &cp);
+  int rc = tile_plan(c, first, count, hl, dl_base, tile_in, &cp, warp);
   if (rc) return rc;
   if (!cp) return OPS_OK;
   *ran = true;
   const SkewedPlan& P = cp->plan;
   LaunchEnv env = make_env(c);
-  c->stats.mode = OPS_MODE_TILEWAVE;
+  c->stats.mode = warp ? OPS_MODE_TILEWARP : OPS_MODE_TILEWAVE;
   c->stats.compiled = 1;
   ++c->stats.segments;
   c->stats.loops += count;
@@ -1536,17 +1542,18 @@ int run_segment_mode(ops_ctx c, int first, int count, int dl_base, std::vector<D
     mode = OPS_MODE_SKEWED;
     tile_in = c->cfg.tile;
   }
-  if (mode == OPS_MODE_TILEWAVE) {
+  if (mode == OPS_MODE_TILEWAVE || mode == OPS_MODE_TILEWARP) {
     // one loop has no dependencies to schedule; checked and interpreted runs,
     // runs without run-time compilation and chains no tile size suits go
     // through the skewed path
+    const bool warp = mode == OPS_MODE_TILEWARP;
     if (count > 1 && !c->cfg.interpret && !c->cfg.check) {
       JitTile* t = nullptr;
-      int rc = tile_code(c, first, count, hl, &t);
+      int rc = tile_code(c, first, count, hl, &t, warp);
       if (rc) return rc;
       if (t) {
         bool ran = false;
-        rc = run_tilewave(c, first, count, dl_base, hl, tile_in, t, &ran);
+        rc = run_tilewave(c, first, count, dl_base, hl, tile_in, t, &ran, warp);
         if (rc || ran) return rc;
         tile_in = c->cfg.tile;
       }
@@ -2602,7 +2609,7 @@ int ops_set_timing(ops_ctx c, int timing) {
 
 int ops_set_mode(ops_ctx c, int mode, const int* tile, int segment) {
   if (!c) return OPS_ERR_INVALID_ARG;
-  if (mode < OPS_MODE_UNTILED || mode > OPS_MODE_TILEWAVE) return fail(c, OPS_ERR_INVALID_ARG, "bad mode %d", mode);
+  if (mode < OPS_MODE_UNTILED || mode > OPS_MODE_TILEWARP) return fail(c, OPS_ERR_INVALID_ARG, "bad mode %d", mode);
   c->cfg.mode = mode;
   if (tile)
     for (int d = 0; d < 3; ++d) c->cfg.tile[d] = tile[d];
@@ -2951,6 +2958,28 @@ int ops_compile_queued_wavefront(ops_ctx c, char* src_out, int64_t cap, int64_t*
 
 int compile_queued_tilewave(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms,
                             bool batch);
+
+int ops_compile_queued_tilewarp(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms) {
+  if (!c) return OPS_ERR_INVALID_ARG;
+  if (c->queue.empty()) return fail(c, OPS_ERR_STATE, "no queued loops");
+  const int n = (int)c->queue.size();
+  std::vector<DLoop> hl(n);
+  std::vector<FoldRow> rows;
+  for (int i = 0; i < n; ++i) fill_dloop(c, c->queue[i], hl[i], (int)rows.size(), rows);
+  std::string src, why;
+  double ms = 0.0;
+  const int rc = jit_compile_tilewarp_only(hl.data(), n, read_only_args(c, 0, n), c->es, c->queue[0].dims, &src,
+                                           &why, &ms);
+  if (src_len) *src_len = (int64_t)src.size();
+  if (src_out && cap > 0) {
+    const size_t k = std::min<size_t>(src.size(), (size_t)cap - 1);
+    std::memcpy(src_out, src.data(), k);
+    src_out[k] = '\0';
+  }
+  if (compile_ms) *compile_ms = ms;
+  if (rc) return fail(c, rc, "%s", why.c_str());
+  return OPS_OK;
+}
 
 int ops_compile_queued_skewed(ops_ctx c, char* src_out, int64_t cap, int64_t* src_len, double* compile_ms) {
   if (!c) return OPS_ERR_INVALID_ARG;

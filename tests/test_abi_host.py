@@ -446,6 +446,33 @@ def test_scalars_share_the_handle_space_but_not_reductions(lib):
         ops.ops_finalize(ctx)
 
 
+@pytest.mark.parametrize("name,fp32", [("edge", True), ("opensbli3d", False)])
+def test_generated_tile_per_warp_kernel_compiles(lib, name, fp32):
+    """The tile-per-warp kernel (warp-level ordering, per-warp shared-memory
+    slices) compiles for sm_103a, 2D and 3D, FP32 and FP64."""
+    from paper_1704_00693_gb300.chain import ChainRunner
+    if name == "edge":
+        from test_gpu_chain import edge_chain
+        c = edge_chain()
+    else:
+        c = W.opensbli3d(n=12, steps=1)
+    cfg = ops.ops_config_default()
+    cfg.device = ops.OPS_DEVICE_NONE
+    cfg.real = ops.OPS_REAL_F32 if fp32 else ops.OPS_REAL_F64
+    ctx = ops.ops_init(cfg)
+    r = ChainRunner(c, ctx=ctx, upload=False, mode="tilewarp")
+    r.enqueue_step()
+    try:
+        src, n, ms = ops.ops_compile_queued(ctx, want_source=True, tilewarp=True)
+    except ops.OpsError as e:
+        if e.code == ops.OPS_ERR_NO_DEVICE:
+            pytest.skip("NVRTC is not installed")
+        raise
+    assert " tww(" in src and "flush_red_warp(" in src and src.count("            case ") == len(c.loops)
+    ops.ops_queue_clear(ctx)
+    ops.ops_finalize(ctx)
+
+
 @pytest.mark.parametrize("fp32", [False, True])
 def test_generated_persistent_skewed_kernel_compiles(lib, fp32):
     """The persistent skewed kernel (every body behind one switch, bounded
