@@ -152,3 +152,21 @@ def test_many_requests_reuse_fixed_tables():
     for (k, b), (x, st) in zip(probs, res):
         assert st["converged"] == 1 and oracle.relres(k, b, x) <= TOL
 
+
+
+def test_worker_counters():
+    """ops_serve_stats accounts for every request and for the worker's time."""
+    sizes = [64, 96, 128, 160]
+    probs = problems(sizes, "counters")
+    srv = ops.ops_serve_open(TOL, ops.OPS_PREC_MIXED, hbm_budget=1 << 30)
+    try:
+        ids = [ops.ops_serve_submit(srv, k, b) for k, b in probs]
+        res = [ops.ops_serve_poll(srv, i, n) for i, n in zip(ids, sizes)]
+        c = ops.ops_serve_stats(srv)
+    finally:
+        ops.ops_serve_close(srv)
+    assert c["admitted"] == len(sizes) and c["completed"] == len(sizes)
+    assert c["rounds"] >= 1 and c["run_ms"] > 0.0
+    assert all(c[k] >= 0.0 for k in ("upload_ms", "fetch_ms", "idle_ms"))
+    for (k, b), (x, st) in zip(probs, res):
+        assert oracle.relres(k, b, x) <= TOL
