@@ -15,6 +15,7 @@
 #include <numeric>
 #include <set>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -2012,6 +2013,31 @@ int stream_after(ops_ctx dst, ops_ctx src) {
   return OPS_OK;
 }
 
+// Run f(i) for i in [lo, hi): on the calling thread for small ranges, else
+// split over up to 8 host threads (each with the device current).  The
+// contexts of a batch share no host state, and CUDA runtime calls are
+// thread-safe.
+template <class F>
+void for_contexts(int device, int lo, int hi, F f) {
+  const int n = hi - lo;
+  const int nt = n >= 16 ? std::min(8, std::max(1, (int)std::thread::hardware_concurrency())) : 1;
+  if (nt <= 1) {
+    for (int i = lo; i < hi; ++i) f(i);
+    return;
+  }
+  std::vector<std::thread> th;
+  const int per = (n + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t) {
+    const int a = lo + t * per, b = std::min(hi, a + per);
+    if (a >= b) break;
+    th.emplace_back([=, &f] {
+      cudaSetDevice(device);
+      for (int i = a; i < b; ++i) f(i);
+    });
+  }
+  for (std::thread& t : th) t.join();
+}
+
 // The batch kernel of a segment (compiled once per code, like tile_code).
 int tile_code_batch(ops_ctx c, int first, int count, const std::vector<DLoop>& hl, JitTile** out) {
   *out = nullptr;
@@ -2347,9 +2373,10 @@ std::vector<std::array<int, 5>> batch_candidates(ops_ctx c, int first, int count
 // stream twice, then the fastest kept for this signature and batch size).
 int run_batch_segment(ops_ctx* cs, int n, std::vector<FlushPrep>& F, int first, int count) {
   ops_ctx c0 = cs[0];
+  std::vector<int> drc(n, 0);
+  for_contexts(c0->cfg.device, 1, n, [&](int i) { drc[i] = segment_descriptors(cs[i], F[i], first, count); });
   for (int i = 1; i < n; ++i) {
-    int rc = segment_descriptors(cs[i], F[i], first, count);
-    if (!rc) rc = stream_after(c0, cs[i]);
+    int rc = drc[i] ? fail(c0, drc[i], "context %d of the batch: %s", i, cs[i]->err.c_str()) : stream_after(c0, cs[i]);
     if (rc) return rc;
   }
   int rc = segment_descriptors(c0, F[0], first, count);
@@ -2415,6 +2442,24 @@ bool same_descriptor(const DLoop& a, const DLoop& b) {
   return true;
 }
 
+// 0 when loop by loop ctx c's queued chain matches the first context's in
+// everything but the dats' addresses and the loops' constants, else the
+// index of the first loop that does not, plus one.
+int batch_mismatch(ops_ctx c0, const FlushPrep& F0, ops_ctx c, const FlushPrep& F) {
+  const int nloops = (int)c0->queue.size();
+  if (F.segs != F0.segs) return 1;
+  for (int l = 0; l < nloops; ++l) {
+    const QLoop &q0 = c0->queue[l], &qi = c->queue[l];
+    bool same = same_descriptor(F0.hl[l], F.hl[l]) && q0.dims == qi.dims && q0.code == qi.code &&
+                q0.args.size() == qi.args.size();
+    for (size_t k = 0; same && k < q0.args.size(); ++k)
+      same = q0.args[k].kind == qi.args[k].kind && q0.args[k].handle == qi.args[k].handle &&
+             q0.args[k].stencil == qi.args[k].stencil && q0.args[k].access == qi.args[k].access;
+    if (!same) return l + 1;
+  }
+  return 0;
+}
+
 int execute_batch(ops_ctx* cs, int n) {
   ops_ctx c0 = cs[0];
   const int nloops = (int)c0->queue.size();
@@ -2433,30 +2478,25 @@ int execute_batch(ops_ctx* cs, int n) {
   std::vector<FlushPrep> F;
   F.reserve(n);
   for (int i = 0; i < n; ++i) F.emplace_back(cs[i]);
-  for (int i = 0; i < n; ++i) {
-    int rc = flush_prepare(cs[i], F[i]);
-    if (rc) return i == 0 ? rc : fail(c0, rc, "context %d of the batch: %s", i, cs[i]->err.c_str());
-  }
-  // The chains must match loop for loop in everything but the dats'
-  // addresses: the same code then serves every instance.  Nothing has run
-  // yet when they do not, and every queue is kept.
+  int rc = flush_prepare(c0, F[0]);
+  if (rc) return rc;
+  // The other contexts' descriptors (in parallel for large batches), each
+  // checked against the first context's: the chains must match loop for
+  // loop in everything but the dats' addresses, so the same code serves
+  // every instance.  Nothing has run yet when they do not, and every queue
+  // is kept.
+  std::vector<int> prc(n, 0), mism(n, 0);
+  for_contexts(c0->cfg.device, 1, n, [&](int i) {
+    prc[i] = flush_prepare(cs[i], F[i]);
+    if (!prc[i]) mism[i] = batch_mismatch(c0, F[0], cs[i], F[i]);
+  });
   for (int i = 1; i < n; ++i) {
-    if (F[i].segs != F[0].segs)
-      return fail(c0, OPS_ERR_INVALID_ARG, "context %d cuts its chain into other segments", i);
-    for (int l = 0; l < nloops; ++l) {
-      const QLoop &q0 = c0->queue[l], &qi = cs[i]->queue[l];
-      bool same = same_descriptor(F[0].hl[l], F[i].hl[l]) && q0.dims == qi.dims && q0.code == qi.code &&
-                  q0.args.size() == qi.args.size();
-      for (size_t k = 0; same && k < q0.args.size(); ++k)
-        same = q0.args[k].kind == qi.args[k].kind && q0.args[k].handle == qi.args[k].handle &&
-               q0.args[k].stencil == qi.args[k].stencil && q0.args[k].access == qi.args[k].access;
-      if (!same)
-        return fail(c0, OPS_ERR_INVALID_ARG,
-                    "loop %d of context %d differs from the first context's in more than its dats' addresses "
-                    "and constants", l, i);
-    }
+    if (prc[i]) return fail(c0, prc[i], "context %d of the batch: %s", i, cs[i]->err.c_str());
+    if (mism[i])
+      return fail(c0, OPS_ERR_INVALID_ARG,
+                  "loop %d of context %d differs from the first context's in more than its dats' addresses "
+                  "and constants (or the chain is cut into other segments)", mism[i] - 1, i);
   }
-  int rc = OPS_OK;
   for (size_t s = 0; s < F[0].segs.size() && !rc; ++s)
     rc = run_batch_segment(cs, n, F, F[0].segs[s].first, F[0].segs[s].second);
   // the other contexts' later work follows the batch
