@@ -532,3 +532,34 @@ def test_compare_select_on_signed_zeros_and_nan():
             got, _, _ = run_gpu(c, mode, tile, interpret=interp, fp32=fp32)
             for k, (a, b) in enumerate(zip(got, ref)):
                 assert np.array_equal(a.view(ut), b.view(ut)), f"{mode} interpret={interp} fp32={fp32} dat {k}"
+
+
+@pytest.mark.parametrize("mode,tile", [("untiled", None), ("skewed", (0, 32, 0)), ("skewed", (0, 0, 0)),
+                                       ("overlapped", None), ("wavefront", (0, 0, 0)), ("tilewave", (0, 0, 0)),
+                                       ("tilewarp", (0, 0, 0)), ("auto", None)])
+def test_cloverleaf_shaped_chain_wide_rows(mode, tile):
+    """The mode matrix on 160^2, where rows are wider than the compiled
+    kernels' 128-point threshold, so every mode runs its full-width units."""
+    c = W.cloverleaf2d(n=160, steps=2)
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist, st = run_gpu(c, mode, tile)
+    assert_same(c, got, ref, hist, ref_hist, what=f"160^2 {mode} {tile}")
+
+
+@pytest.mark.parametrize("fp32,mode,tile", [(False, "wavefront", (0, 0, 0)), (True, "untiled", None),
+                                            (True, "skewed", (0, 1024, 0)), (True, "wavefront", (0, 0, 0))])
+def test_bench_size_schedules(fp32, mode, tile):
+    """The bench's CloverLeaf-shaped step at 3840^2 in the schedules it
+    times beside the headline: every point of every dat against the oracle."""
+    c = W.cloverleaf2d(n=3840, steps=1)
+    ref, ref_hist = oracle.run_chain(c, fp32=fp32)
+    got, hist, st = run_gpu(c, mode, tile, fp32=fp32)
+    assert_same(c, got, ref, hist, ref_hist, what=f"3840^2 {mode} {tile} fp32={fp32}")
+
+
+def test_overlapped_at_1024():
+    c = W.cloverleaf2d(n=1024, steps=1)
+    ref, ref_hist = oracle.run_chain(c)
+    got, hist, st = run_gpu(c, "overlapped", None)
+    assert_same(c, got, ref, hist, ref_hist, what="1024^2 overlapped")
+    assert st["redundant_points"] > 0
