@@ -868,7 +868,8 @@ def main():
     batch = None
     if rank == 0 and not args.no_batch:
         batch = {"cloverleaf2d_256": bench_batch(torch, W.cloverleaf2d(n=256, steps=1)),
-                 "small2d_256": bench_batch(torch, W.small2d(n=256, reps=10))}
+                 "small2d_256": bench_batch(torch, W.small2d(n=256, reps=10)),
+                 "opensbli3d_32": bench_batch(torch, W.opensbli3d(n=32, steps=1))}
 
     line = {"metric": "loop-chain effective GB/s", "value": value, "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
