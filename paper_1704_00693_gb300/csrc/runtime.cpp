@@ -2013,14 +2013,19 @@ int stream_after(ops_ctx dst, ops_ctx src) {
   return OPS_OK;
 }
 
-// Run f(i) for i in [lo, hi): on the calling thread for small ranges, else
-// split over up to 8 host threads (each with the device current).  The
-// contexts of a batch share no host state, and CUDA runtime calls are
-// thread-safe.
+// Run f(i) for i in [lo, hi): split over up to 8 host threads (each with
+// the device current) when there are 16 contexts or more and each brings
+// enough loops that the work outweighs starting the threads (16 x 256
+// loop descriptors at least: 64 grids of an 83-loop chain are split, 64
+// grids of an 8-loop chain are not, which measured slower split); else on
+// the calling thread.  The contexts of a batch share no host state, and
+// CUDA runtime calls are thread-safe.
 template <class F>
-void for_contexts(int device, int lo, int hi, F f) {
+void for_contexts(int device, int lo, int hi, int loops, F f) {
   const int n = hi - lo;
-  const int nt = n >= 16 ? std::min(8, std::max(1, (int)std::thread::hardware_concurrency())) : 1;
+  const int nt = n >= 16 && (int64_t)n * loops >= 4096
+                     ? std::min(8, std::max(1, (int)std::thread::hardware_concurrency()))
+                     : 1;
   if (nt <= 1) {
     for (int i = lo; i < hi; ++i) f(i);
     return;
@@ -2374,7 +2379,7 @@ std::vector<std::array<int, 5>> batch_candidates(ops_ctx c, int first, int count
 int run_batch_segment(ops_ctx* cs, int n, std::vector<FlushPrep>& F, int first, int count) {
   ops_ctx c0 = cs[0];
   std::vector<int> drc(n, 0);
-  for_contexts(c0->cfg.device, 1, n, [&](int i) { drc[i] = segment_descriptors(cs[i], F[i], first, count); });
+  for_contexts(c0->cfg.device, 1, n, count, [&](int i) { drc[i] = segment_descriptors(cs[i], F[i], first, count); });
   for (int i = 1; i < n; ++i) {
     int rc = drc[i] ? fail(c0, drc[i], "context %d of the batch: %s", i, cs[i]->err.c_str()) : stream_after(c0, cs[i]);
     if (rc) return rc;
@@ -2486,7 +2491,7 @@ int execute_batch(ops_ctx* cs, int n) {
   // every instance.  Nothing has run yet when they do not, and every queue
   // is kept.
   std::vector<int> prc(n, 0), mism(n, 0);
-  for_contexts(c0->cfg.device, 1, n, [&](int i) {
+  for_contexts(c0->cfg.device, 1, n, nloops, [&](int i) {
     prc[i] = flush_prepare(cs[i], F[i]);
     if (!prc[i]) mism[i] = batch_mismatch(c0, F[0], cs[i], F[i]);
   });
