@@ -18,7 +18,8 @@
  *     last-level cache size.
  * Loop bodies are not function pointers: they are short programs in a fixed
  * register IR (weighted stencil sums, polynomials, min/max/select,
- * reductions) that the library's CUDA kernels interpret.
+ * reductions) that the library compiles to sm_103a kernels at the first
+ * flush of each segment (NVRTC), or runs through interpreter kernels.
  *
  * Conventions for every function below:
  *   - returns OPS_OK (0) or a negative OPS_ERR_* code; on error
